@@ -1,0 +1,259 @@
+"""FP64 CPU oracle for the ghost-point multigrid solve (arXiv 1911.00994).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()``
+and the ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py``.  The
+product path (the CUDA library and its binding) never imports it.
+
+The arithmetic lives in ``gpmg_oracle.c`` (plain C, no FMA contraction); this
+module only builds it with gcc and marshals numpy arrays through ctypes.
+
+Flat vector layout of one level with N cells per side (all FP64):
+  u block: (N+2) rows j = -1..N, (N+1) columns i = 0..N     index (j+1)(N+1) + i
+  v block: (N+1) rows j = 0..N,  (N+2) columns i = -1..N    index nU + j(N+2) + i+1
+  p block: N rows, N columns                                index nU + nV + jN + i
+  last entry: xi (unknown) / mean row (equation)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gpmg_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+INACTIVE, INTERNAL, GHOST, WALL, BOXGHOST = 0, 1, 2, 3, 4
+OK, INVALID, GEOMETRY, SINGULAR, NOT_CONVERGED, DIVERGED = range(6)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into oracle/liboracle.so (gcc, -ffp-contract=off)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".%d.tmp" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+            P = ctypes.POINTER
+            L.or_create.restype = vp
+            L.or_create.argtypes = [i, d, d, d, i, d]
+            L.or_destroy.argtypes = [vp]
+            L.or_set_params.argtypes = [vp, i, i, i, i, d, i, i, ctypes.c_uint]
+            L.or_set_alpha.argtypes = [vp, d]
+            L.or_set_snap.argtypes = [vp, d]
+            L.or_last_error.restype = ctypes.c_char_p
+            L.or_last_error.argtypes = [vp]
+            for f in (L.or_n, L.or_n_int, L.or_num_ghosts):
+                f.argtypes = [vp, i]
+                f.restype = i
+            L.or_geometry.argtypes = [vp, P(d)]
+            L.or_types.argtypes = [vp, i, P(ctypes.c_int8)]
+            L.or_ghosts.argtypes = [vp, i, P(i), P(d), P(i), i]
+            L.or_boundary_point.argtypes = [vp, i, i, i, i, P(d)]
+            L.or_residual.restype = d
+            L.or_residual.argtypes = [vp, i, P(d), P(d), P(d)]
+            L.or_assemble.argtypes = [vp, i, P(i), P(i), P(d), i]
+            L.or_dense_solve.argtypes = [i, P(d), P(d)]
+            L.or_dense_matrix.argtypes = [vp, i, P(d)]
+            L.or_coarse_solve.argtypes = [vp, P(d), P(d)]
+            for f in (L.or_box_sweep, L.or_scalar_update, L.or_ghost_sweep):
+                f.argtypes = [vp, i, P(d), P(d)]
+            L.or_smooth.argtypes = [vp, i, P(d), P(d), i]
+            L.or_restrict.argtypes = [vp, i, P(d), P(d)]
+            L.or_prolong.argtypes = [vp, i, P(d), P(d)]
+            L.or_cycle.argtypes = [vp, i, P(d), P(d)]
+            L.or_solve.argtypes = [vp, P(d), P(d), d, i, P(d), P(i)]
+            _lib = L
+    return _lib
+
+
+def _p(a, ct=ctypes.c_double):
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def sizes(N: int):
+    nU = (N + 1) * (N + 2)
+    nV = (N + 2) * (N + 1)
+    nP = N * N
+    return nU, nV, nP, nU + nV + nP + 1
+
+
+def split(vec: np.ndarray, N: int):
+    """Flat oracle vector -> (u[(N+2),(N+1)], v[(N+1),(N+2)], p[N,N], xi)."""
+    nU, nV, nP, n = sizes(N)
+    u = vec[:nU].reshape(N + 2, N + 1)
+    v = vec[nU:nU + nV].reshape(N + 1, N + 2)
+    p = vec[nU + nV:nU + nV + nP].reshape(N, N)
+    return u, v, p, vec[n - 1]
+
+
+def join(u, v, p, xi, N: int) -> np.ndarray:
+    nU, nV, nP, n = sizes(N)
+    out = np.zeros(n)
+    out[:nU] = np.asarray(u).reshape(-1)
+    out[nU:nU + nV] = np.asarray(v).reshape(-1)
+    out[nU + nV:nU + nV + nP] = np.asarray(p).reshape(-1)
+    out[n - 1] = xi
+    return out
+
+
+class Oracle:
+    """One discretisation: N cells per side on [x0, x0+L] x [y0, y0+L], `levels`
+    grids (N, N/2, ...), alpha = dt / (2 Re)."""
+
+    def __init__(self, N, x0, y0, L, levels, alpha, nu1=2, nu2=1, gamma=1, lam=5, dtau=0.9,
+                 ghost_mode=0, order_mode=0, seed=12345, snap=0.3):
+        self.L = lib()
+        self.N, self.x0, self.y0, self.len, self.levels, self.alpha = N, x0, y0, L, levels, alpha
+        self.h = L / N
+        self.c = self.L.or_create(N, x0, y0, L, levels, alpha)
+        if not self.c:
+            raise ValueError("oracle: invalid sizes")
+        self.set_params(nu1, nu2, gamma, lam, dtau, ghost_mode, order_mode, seed)
+        self.snap = snap
+        self.L.or_set_snap(self.c, snap)
+
+    def set_params(self, nu1=2, nu2=1, gamma=1, lam=5, dtau=0.9, ghost_mode=0, order_mode=0, seed=12345):
+        self.params = dict(nu1=nu1, nu2=nu2, gamma=gamma, lam=lam, dtau=dtau, ghost_mode=ghost_mode,
+                           order_mode=order_mode, seed=seed)
+        self.L.or_set_params(self.c, nu1, nu2, gamma, lam, dtau, ghost_mode, order_mode, seed)
+
+    def __del__(self):
+        try:
+            if self.c:
+                self.L.or_destroy(self.c)
+                self.c = None
+        except Exception:
+            pass
+
+    def error(self):
+        return self.L.or_last_error(self.c).decode()
+
+    def n(self, lev=0):
+        return self.L.or_n(self.c, lev)
+
+    def Nl(self, lev):
+        return self.N >> lev
+
+    def geometry(self, phi_paper: np.ndarray) -> int:
+        """phi on the (2N+1)^2 half lattice, paper sign (phi > 0 inside the object)."""
+        phi = np.ascontiguousarray(phi_paper, dtype=np.float64)
+        assert phi.shape == (2 * self.N + 1, 2 * self.N + 1)
+        self._phi = phi
+        return self.L.or_geometry(self.c, _p(phi))
+
+    def types(self, lev=0) -> np.ndarray:
+        out = np.zeros(self.n(lev), dtype=np.int8)
+        self.L.or_types(self.c, lev, _p(out, ctypes.c_int8))
+        return out
+
+    def n_int(self, lev=0):
+        return self.L.or_n_int(self.c, lev)
+
+    def ghosts(self, lev=0):
+        ng = self.L.or_num_ghosts(self.c, lev)
+        iv = np.zeros((max(ng, 1), 7), dtype=np.int32)
+        dv = np.zeros((max(ng, 1), 15))
+        sv = np.zeros((max(ng, 1), 18), dtype=np.int32)
+        self.L.or_ghosts(self.c, lev, _p(iv, ctypes.c_int), _p(dv), _p(sv, ctypes.c_int), ng)
+        return dict(grid=iv[:ng, 0], i=iv[:ng, 1], j=iv[:ng, 2], sx=iv[:ng, 3], sy=iv[:ng, 4],
+                    axis=iv[:ng, 5] % 2, kind=iv[:ng, 5] // 2, nst=iv[:ng, 6], B=dv[:ng, 0:2], n=dv[:ng, 2:4], theta=dv[:ng, 4:6],
+                    w=dv[:ng, 6:15], st=sv[:ng].reshape(ng, 9, 2))
+
+    def boundary_point(self, lev, grid, i, j):
+        out = np.zeros(2)
+        st = self.L.or_boundary_point(self.c, lev, grid, i, j, _p(out))
+        return st, out
+
+    def residual(self, x, b, lev=0):
+        r = np.zeros(self.n(lev))
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        nrm = self.L.or_residual(self.c, lev, _p(x), _p(b), _p(r))
+        return r, nrm
+
+    def assemble(self, lev=0):
+        n = self.n(lev)
+        cap = 12 * n + n
+        ri = np.zeros(cap, dtype=np.int32)
+        ci = np.zeros(cap, dtype=np.int32)
+        v = np.zeros(cap)
+        nnz = self.L.or_assemble(self.c, lev, _p(ri, ctypes.c_int), _p(ci, ctypes.c_int), _p(v), cap)
+        assert nnz >= 0
+        return ri[:nnz], ci[:nnz], v[:nnz]
+
+    def dense_matrix(self, lev=0):
+        n = self.n(lev)
+        A = np.zeros((n, n))
+        self.L.or_dense_matrix(self.c, lev, _p(A))
+        return A
+
+    def dense_solve(self, b, lev=0):
+        A = self.dense_matrix(lev)
+        x = np.array(b, dtype=np.float64)
+        st = self.L.or_dense_solve(A.shape[0], _p(A), _p(x))
+        return st, x
+
+    def coarse_solve(self, b):
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x = np.zeros_like(b)
+        self.L.or_coarse_solve(self.c, _p(b), _p(x))
+        return x
+
+    def _inplace(self, fn, lev, x, b, *extra):
+        x2 = np.array(x, dtype=np.float64)
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        fn(self.c, lev, _p(x2), _p(b), *extra)
+        return x2
+
+    def box_sweep(self, x, b, lev=0):
+        return self._inplace(self.L.or_box_sweep, lev, x, b)
+
+    def scalar_update(self, x, b, lev=0):
+        return self._inplace(self.L.or_scalar_update, lev, x, b)
+
+    def ghost_sweep(self, x, b, lev=0):
+        return self._inplace(self.L.or_ghost_sweep, lev, x, b)
+
+    def smooth(self, x, b, nu=1, lev=0):
+        return self._inplace(self.L.or_smooth, lev, x, b, nu)
+
+    def restrict(self, r, lev=0):
+        out = np.zeros(self.n(lev + 1))
+        r = np.ascontiguousarray(r, dtype=np.float64)
+        self.L.or_restrict(self.c, lev, _p(r), _p(out))
+        return out
+
+    def prolong(self, eH, x, lev=0):
+        x2 = np.array(x, dtype=np.float64)
+        eH = np.ascontiguousarray(eH, dtype=np.float64)
+        self.L.or_prolong(self.c, lev, _p(eH), _p(x2))
+        return x2
+
+    def cycle(self, x, b, lev=0):
+        x2 = np.array(x, dtype=np.float64)
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        st = self.L.or_cycle(self.c, lev, _p(x2), _p(b))
+        return st, x2
+
+    def solve(self, x, b, tol, max_cycles=50):
+        x2 = np.array(x, dtype=np.float64)
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        hist = np.zeros(max_cycles + 1)
+        nc = ctypes.c_int(0)
+        st = self.L.or_solve(self.c, _p(x2), _p(b), tol, max_cycles, _p(hist), ctypes.byref(nc))
+        return st, x2, hist[:nc.value + 1]

@@ -1,0 +1,1282 @@
+/*
+ * gpmg_oracle.c -- plain, slow, FP64 CPU oracle for the ghost-point multigrid
+ * solve of one Crank-Nicolson step (Coco, arXiv 1911.00994).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests, the smoke check and the CPU-baseline
+ * leg of the benchmark may load this library.  It shares no code, header,
+ * table or helper with the CUDA path.
+ *
+ * Everything is written the direct way: every equation of the linear system
+ * is produced by one function (get_row) that lists its coefficients, and the
+ * residual, the assembled matrix, the box relaxation and the ghost relaxation
+ * all read those rows.  Nothing is fused, blocked or reordered.
+ *
+ * Paper sections followed:
+ *   Sect. 2, Eq. (spaceprobaug)  augmented problem (u, v, p, xi)
+ *   Sect. 3.2                    MAC central differences, internal points
+ *   Eq. (midpoint)               zero-mean pressure row
+ *   Sect. 3.3, Algorithm 1       boundary point B from a ghost point G
+ *   Eq. (BCu)                    biquadratic upwind ghost row
+ *   Remark 1                     which external points are ghosts
+ *   Algorithm LS                 row per grid point
+ *   Sect. 4.1                    box relaxation and ghost relaxation,
+ *                                Eq. (ghostrelax), Algorithm relax
+ *   Sect. 4.2, Eqs. (restop), (restop5)  boundary-aware restriction
+ *   Sect. 4.3                    bilinear interpolation, cycle, exact coarsest solve
+ *   Eq. (convfact)               residual infinity norm
+ *
+ * Readings where the paper is silent (numbered as in the design notes):
+ *   theta sign: theta = s (x_G - x_B)/h, so the Lagrange node k sits at theta = k.
+ *   p ghosts: p_G - 2 p_1 + p_2 = 0; u/v ghosts with theta > 1 on an axis
+ *     (B beyond the first stencil point; such ghosts only enter other ghost
+ *     stencils): x_G - 3 x_1 + 3 x_2 - x_3 = 0; both along the dominant
+ *     normal axis a (tie -> x), s = SIGN(n_a), nodes x_k = x_{G - k s e_a},
+ *     used where phi decreases strictly along the nodes, else a copy of the
+ *     axis neighbour of smallest phi.
+ *   outer walls: wall-normal velocity on the wall is a Dirichlet row; the
+ *     tangential velocity half a cell outside the wall has the Eq. (BCu) row
+ *     with theta_normal = 1/2, theta_tangential = 0: 3/8 x_G + 3/4 x_1 - 1/8 x_2.
+ *   ghosts: the external points coupled to the internal equations, closed
+ *     under the ghost stencils (the alternative marking of Remark 1), the
+ *     closure limited to points within two index steps of an internal point
+ *     of the same grid; a ghost stencil point beyond that is inactive (value 0,
+ *     the fictitious row of Algorithm LS).
+ *   a pressure cell with no internal face is not internal (its continuity row
+ *     would not contain any box unknown).
+ *   xi / mean pair: after each box sweep xi <- mean(div u - b_c) over internal
+ *     cells, then a constant shift of all internal and ghost p makes the mean
+ *     row exact.  The mean row is stored as h^2 * sum(p).
+ *   box contents: p_ij and the internal or object-ghost borders of the cell
+ *     (their own rows); wall and box-ghost borders frozen.
+ *   box colouring: cells without ghost borders by (i + 3 j) mod 5, then cells
+ *     with ghost borders by (i mod 5, j mod 5); boxes of one colour are
+ *     independent.
+ *   internal faces that belong to no internal box: point Jacobi after the box
+ *     sweep.
+ *   ghost relaxation: Jacobi over all ghost-class rows, lambda sweeps; mode 0
+ *     w += dtau r (as printed), mode 1 w += dtau r / c_G.
+ *   restriction classes: internal, and ghost-class = ghost, wall, box ghost;
+ *     mean-row residual injected.
+ *   prolongation: bilinear over the active coarse nodes around the fine
+ *     node, weights renormalised; p next to the box walls: linear
+ *     extrapolation from the two nearest coarse cells.
+ *   snap: a node within snap * h of the boundary (phi / |grad phi|) is
+ *     external (default 0.3).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_MAXLEV 16
+#define OR_MAXMARCH 64
+
+enum { T_INACTIVE = 0, T_INTERNAL = 1, T_GHOST = 2, T_WALL = 3, T_BOXGHOST = 4, T_EXT = 5 };
+enum { G_U = 0, G_V = 1, G_P = 2 };
+enum { OR_OK = 0, OR_INVALID = 1, OR_GEOMETRY = 2, OR_SINGULAR = 3, OR_NOT_CONVERGED = 4, OR_DIVERGED = 5 };
+
+/* offsets of node (0,0) of each grid, in half cells: u (0,1), v (1,0), p (1,1) */
+static const int OX2[3] = {0, 1, 1};
+static const int OY2[3] = {1, 0, 1};
+
+typedef struct {
+    int grid, i, j;
+    double xB, yB;     /* boundary point (u, v ghosts) */
+    double nx, ny;     /* unit normal at G from the bilinear interpolant */
+    int sx, sy;        /* upwind signs SIGN(n) */
+    double thx, thy;   /* Lagrange coordinates of B */
+    int axis;          /* extrapolation rows: 0 = x, 1 = y */
+    int kind;          /* 0: Eq. (BCu) row; 1: extrapolation row; 2: copy row */
+    int nst;
+    int si[9], sj[9];
+    double w[9];       /* w[0] multiplies the ghost value itself */
+} ghost_t;
+
+typedef struct {
+    int N;
+    double h;
+    int nU, nV, nP, n;
+    int8_t *tU, *tV, *tP;
+    int *gid;          /* unknown index -> ghost index, or -1 */
+    int8_t *prim;      /* 1: ghost referenced directly by an internal or box-ghost row */
+    ghost_t *gh;
+    int ngh;
+    int n_int;         /* internal pressure cells */
+    /* coarsest level: dense LU factors */
+    double *lu;
+    int *piv;
+    /* cycle work vectors */
+    double *x, *b, *r;
+} level_t;
+
+typedef struct {
+    int N, L;
+    double x0, y0, len, alpha;
+    int nu1, nu2, gamma, lam, ghost_mode, order_mode;
+    double dtau;
+    double snap;       /* nodes with phi / |grad phi| >= -snap h are external */
+    unsigned rng;
+    double *phi;       /* half lattice (2N+1)^2, paper sign */
+    level_t lv[OR_MAXLEV];
+    int geom_ok;
+    char err[256];
+} ctx_t;
+
+typedef struct {
+    int n;
+    int col[12];
+    double a[12];
+} row_t;
+
+/* ---------------------------------------------------------------- indexing */
+
+static int inU(const level_t *l, int i, int j) { return i >= 0 && i <= l->N && j >= -1 && j <= l->N; }
+static int inV(const level_t *l, int i, int j) { return i >= -1 && i <= l->N && j >= 0 && j <= l->N; }
+static int inP(const level_t *l, int i, int j) { return i >= 0 && i < l->N && j >= 0 && j < l->N; }
+static int inG(const level_t *l, int g, int i, int j)
+{
+    return g == G_U ? inU(l, i, j) : g == G_V ? inV(l, i, j) : inP(l, i, j);
+}
+static int iU(const level_t *l, int i, int j) { return (j + 1) * (l->N + 1) + i; }
+static int iV(const level_t *l, int i, int j) { return l->nU + j * (l->N + 2) + (i + 1); }
+static int iP(const level_t *l, int i, int j) { return l->nU + l->nV + j * l->N + i; }
+static int iG(const level_t *l, int g, int i, int j)
+{
+    return g == G_U ? iU(l, i, j) : g == G_V ? iV(l, i, j) : iP(l, i, j);
+}
+static int iXI(const level_t *l) { return l->n - 1; }
+
+static int8_t *tref(level_t *l, int g, int i, int j)
+{
+    if (g == G_U) return &l->tU[(j + 1) * (l->N + 1) + i];
+    if (g == G_V) return &l->tV[j * (l->N + 2) + (i + 1)];
+    return &l->tP[j * l->N + i];
+}
+static int ttype(level_t *l, int g, int i, int j)
+{
+    if (!inG(l, g, i, j)) return T_INACTIVE;
+    return *tref(l, g, i, j);
+}
+
+static void seterr(ctx_t *c, const char *m)
+{
+    if (!c->err[0]) snprintf(c->err, sizeof c->err, "%s", m);
+}
+
+/* ----------------------------------------------------------- level set */
+
+/* phi at node (i, j) of grid g on level lev, read from the half lattice */
+static int phi_node(ctx_t *c, int lev, int g, int i, int j, double *out)
+{
+    int m = 1 << lev;
+    int a = m * (2 * i + OX2[g]);
+    int b = m * (2 * j + OY2[g]);
+    int M = 2 * c->N;
+    if (a < 0 || a > M || b < 0 || b > M) return 0;
+    *out = c->phi[(size_t)b * (M + 1) + a];
+    return 1;
+}
+
+static double node_x(ctx_t *c, int lev, int g, int i) { return c->x0 + (double)(2 * i + OX2[g]) * (0.5 * c->lv[lev].h); }
+static double node_y(ctx_t *c, int lev, int g, int j) { return c->y0 + (double)(2 * j + OY2[g]) * (0.5 * c->lv[lev].h); }
+
+/* Bilinear interpolant of phi on the 2x2 cell of grid g that contains (x, y)
+ * (cell chosen by floor in each axis), its value and gradient (Sect. 3.3). */
+static int bilin(ctx_t *c, int lev, int g, double x, double y, double *val, double *gx, double *gy)
+{
+    double h = c->lv[lev].h;
+    double sx = (x - c->x0) / h - 0.5 * (double)OX2[g];
+    double sy = (y - c->y0) / h - 0.5 * (double)OY2[g];
+    double fi = floor(sx), fj = floor(sy);
+    if (!(fi > -1e9 && fi < 1e9 && fj > -1e9 && fj < 1e9)) return 0;
+    int i0 = (int)fi, j0 = (int)fj;
+    double fx = sx - fi, fy = sy - fj;
+    double p00, p10, p01, p11;
+    if (!phi_node(c, lev, g, i0, j0, &p00) || !phi_node(c, lev, g, i0 + 1, j0, &p10) ||
+        !phi_node(c, lev, g, i0, j0 + 1, &p01) || !phi_node(c, lev, g, i0 + 1, j0 + 1, &p11))
+        return 0;
+    double ex = 1.0 - fx, ey = 1.0 - fy;
+    *val = ex * ey * p00 + fx * ey * p10 + ex * fy * p01 + fx * fy * p11;
+    *gx = (ey * (p10 - p00) + fy * (p11 - p01)) / h;
+    *gy = (ex * (p01 - p00) + fx * (p11 - p10)) / h;
+    return 1;
+}
+
+static int unit_normal(ctx_t *c, int lev, int g, double x, double y, double *nx, double *ny)
+{
+    double v, gx, gy;
+    if (!bilin(c, lev, g, x, y, &v, &gx, &gy)) return 0;
+    double nrm = sqrt(gx * gx + gy * gy);
+    if (!(nrm > 0.0)) return 0;
+    *nx = gx / nrm;
+    *ny = gy / nrm;
+    return 1;
+}
+
+/* Algorithm 1: march from G against the normal by h/2 until phi <= 0, then
+ * ceil(log2(|HK| / (0.01 h))) bisection steps; B is the last midpoint.
+ * A ghost inside the fluid (phi(G) < 0, a snapped node) marches along the
+ * normal instead, until phi >= 0; the bisection is the same. */
+static int ghost_to_boundary(ctx_t *c, int lev, int g, int i, int j, double *xB, double *yB)
+{
+    double h = c->lv[lev].h;
+    double xG = node_x(c, lev, g, i), yG = node_y(c, lev, g, j);
+    double phH;
+    if (!phi_node(c, lev, g, i, j, &phH)) return 0;
+    double sg = phH > 0.0 ? 1.0 : -1.0;
+    double xH = xG, yH = yG, xK = xG, yK = yG;
+    int steps = 0;
+    while (sg * phH > 0.0) {
+        double nx, ny, gx, gy;
+        xK = xH;
+        yK = yH;
+        if (!unit_normal(c, lev, g, xH, yH, &nx, &ny)) return 0;
+        xH = xH - sg * (0.5 * h * nx);
+        yH = yH - sg * (0.5 * h * ny);
+        if (!bilin(c, lev, g, xH, yH, &phH, &gx, &gy)) return 0;
+        if (++steps > OR_MAXMARCH) return 0;
+    }
+    if (steps == 0) { /* phi(G) = 0: the ghost lies on the boundary */
+        *xB = xG;
+        *yB = yG;
+        return 1;
+    }
+    double dx = xH - xK, dy = yH - yK;
+    double dist = sqrt(dx * dx + dy * dy);
+    int nb = (int)ceil(log2(dist / (0.01 * h)));
+    double xm = xH, ym = yH;
+    for (int it = 0; it < nb; it++) {
+        double phB, gx, gy;
+        xm = 0.5 * (xH + xK);
+        ym = 0.5 * (yH + yK);
+        if (!bilin(c, lev, g, xm, ym, &phB, &gx, &gy)) return 0;
+        if (phB * phH < 0.0) {
+            xK = xm;
+            yK = ym;
+        } else {
+            xH = xm;
+            yH = ym;
+            phH = phB;
+        }
+    }
+    *xB = xm;
+    *yB = ym;
+    return 1;
+}
+
+/* Lagrange weights on nodes theta = 0, 1, 2 (Eq. BCu) */
+static void lagrange3(double t, double T[3])
+{
+    T[0] = (1.0 - t) * (2.0 - t) / 2.0;
+    T[1] = t * (2.0 - t);
+    T[2] = t * (t - 1.0) / 2.0;
+}
+
+/* Row of an external node acting as a ghost.
+ *  u, v ghosts referenced directly by an internal or box-ghost row whose
+ *  boundary point B lies within one cell of G along both axes
+ *  (theta_x, theta_y <= 1): Eq. (BCu) on the upwind nine-point stencil.
+ *  Other u, v ghosts (only other ghost stencils use them): quadratic
+ *  extrapolation along the dominant normal axis a, s = SIGN(n_a):
+ *      x_G - 3 x_{G - s e_a} + 3 x_{G - 2 s e_a} - x_{G - 3 s e_a} = 0.
+ *  p ghosts: linear extrapolation along the same axis:
+ *      p_G - 2 p_{G - s e_a} + p_{G - 2 s e_a} = 0.
+ *  An extrapolation row is used only where phi strictly decreases along its
+ *  nodes; elsewhere (a body thinner than the stencil) the ghost copies the
+ *  axis neighbour of smallest phi, x_G - x_nb = 0.  Every extrapolation or
+ *  copy row thus refers to nodes of smaller phi only. */
+static int ghost_setup(ctx_t *c, int lev, int g, int i, int j, ghost_t *G)
+{
+    double h = c->lv[lev].h;
+    double xG = node_x(c, lev, g, i), yG = node_y(c, lev, g, j);
+    double nx, ny;
+    if (!unit_normal(c, lev, g, xG, yG, &nx, &ny)) return 0;
+    memset(G, 0, sizeof *G);
+    G->grid = g;
+    G->i = i;
+    G->j = j;
+    G->nx = nx;
+    G->ny = ny;
+    G->sx = nx >= 0.0 ? 1 : -1;
+    G->sy = ny >= 0.0 ? 1 : -1;
+    G->axis = fabs(nx) >= fabs(ny) ? 0 : 1;
+    G->kind = 1;
+    if (g != G_P) {
+        double xB, yB;
+        if (!ghost_to_boundary(c, lev, g, i, j, &xB, &yB)) return 0;
+        G->xB = xB;
+        G->yB = yB;
+        G->thx = (double)G->sx * (xG - xB) / h;
+        G->thy = (double)G->sy * (yG - yB) / h;
+        if (c->lv[lev].prim[iG(&c->lv[lev], g, i, j)] && G->thx <= 1.0 && G->thy <= 1.0) G->kind = 0;
+    }
+    if (G->kind == 0) {
+        double Tx[3], Ty[3];
+        lagrange3(G->thx, Tx);
+        lagrange3(G->thy, Ty);
+        G->nst = 9;
+        for (int ky = 0; ky < 3; ky++)
+            for (int kx = 0; kx < 3; kx++) {
+                G->si[ky * 3 + kx] = i - kx * G->sx;
+                G->sj[ky * 3 + kx] = j - ky * G->sy;
+                G->w[ky * 3 + kx] = Tx[kx] * Ty[ky];
+            }
+        return 1;
+    }
+    /* extrapolation along the dominant normal axis toward the fluid, used
+     * only where phi strictly decreases along the stencil (so that no chain
+     * of extrapolation rows can loop back on itself) */
+    static const double e3[3] = {1.0, -2.0, 1.0};
+    static const double e4[4] = {1.0, -3.0, 3.0, -1.0};
+    int s = G->axis == 0 ? G->sx : G->sy;
+    int n = g == G_P ? 3 : 4;
+    double ph[4];
+    int mono = 1;
+    for (int k = 0; k < n && mono; k++) {
+        int ii = i - (G->axis == 0 ? k * s : 0), jj = j - (G->axis == 1 ? k * s : 0);
+        if (!phi_node(c, lev, g, ii, jj, &ph[k])) mono = 0;
+        else if (k > 0 && !(ph[k] < ph[k - 1])) mono = 0;
+    }
+    if (mono) {
+        G->nst = n;
+        for (int k = 0; k < n; k++) {
+            G->si[k] = i - (G->axis == 0 ? k * s : 0);
+            G->sj[k] = j - (G->axis == 1 ? k * s : 0);
+            G->w[k] = g == G_P ? e3[k] : e4[k];
+        }
+        return 1;
+    }
+    /* otherwise copy the value of the axis neighbour with the smallest phi
+     * below phi(G) (order of preference: -x, +x, -y, +y on ties) */
+    static const int di[4] = {-1, 1, 0, 0}, dj[4] = {0, 0, -1, 1};
+    double pG, best = 0.0;
+    int kb = -1;
+    if (!phi_node(c, lev, g, i, j, &pG)) return 0;
+    for (int k = 0; k < 4; k++) {
+        double q;
+        if (!phi_node(c, lev, g, i + di[k], j + dj[k], &q)) continue;
+        if (q < pG && (kb < 0 || q < best)) { best = q; kb = k; }
+    }
+    if (kb < 0) return 0;
+    G->kind = 2;
+    G->nst = 2;
+    G->si[0] = i; G->sj[0] = j; G->w[0] = 1.0;
+    G->si[1] = i + di[kb]; G->sj[1] = j + dj[kb]; G->w[1] = -1.0;
+    return 1;
+}
+
+/* ------------------------------------------------------------ geometry */
+
+static void free_level(level_t *l)
+{
+    free(l->tU); free(l->tV); free(l->tP); free(l->gid); free(l->prim); free(l->gh);
+    free(l->lu); free(l->piv); free(l->x); free(l->b); free(l->r);
+    memset(l, 0, sizeof *l);
+}
+
+/* Mark node (g,i,j) as needed by an internal or box-ghost row: an external
+ * node becomes a ghost. */
+static int mark_needed(ctx_t *c, level_t *l, int g, int i, int j, int *changed)
+{
+    if (!inG(l, g, i, j)) { seterr(c, "stencil leaves the grid"); return 0; }
+    int8_t *t = tref(l, g, i, j);
+    if (*t == T_EXT) { *t = T_GHOST; *changed = 1; }
+    else if (*t == T_INACTIVE) { seterr(c, "stencil reaches an inactive corner node"); return 0; }
+    if (*t == T_GHOST) l->prim[iG(l, g, i, j)] = 1;
+    return 1;
+}
+
+/* Is (g,i,j) within two index steps (Chebyshev) of an internal node of the
+ * same grid?  Only such nodes may join the ghost set through the stencil of
+ * another ghost; farther stencil nodes stay inactive (value 0). */
+static int near_internal(level_t *l, int g, int i, int j)
+{
+    for (int dj = -2; dj <= 2; dj++)
+        for (int di = -2; di <= 2; di++)
+            if (ttype(l, g, i + di, j + dj) == T_INTERNAL) return 1;
+    return 0;
+}
+
+/* Mark a node referenced by a ghost stencil. */
+static int mark_stencil(ctx_t *c, level_t *l, int g, int i, int j, int *changed)
+{
+    if (!inG(l, g, i, j)) { seterr(c, "stencil leaves the grid"); return 0; }
+    int8_t *t = tref(l, g, i, j);
+    if (*t == T_EXT && near_internal(l, g, i, j)) { *t = T_GHOST; *changed = 1; }
+    return 1;
+}
+
+/* Algorithm LS marks a node internal when phi < 0.  A node closer than
+ * snap * h to the boundary (first-order distance phi / |grad phi| of the
+ * bilinear interpolant of its own grid) is treated as external, so that no
+ * Eq. (BCu) row has its boundary point next to an internal node (vanishing
+ * ghost coefficient) and no internal cell sits on the boundary. */
+static int node_internal(ctx_t *c, int lev, int g, int i, int j, double ph)
+{
+    if (!(ph < 0.0)) return 0;
+    if (c->snap <= 0.0) return 1;
+    double v, gx, gy;
+    if (!bilin(c, lev, g, node_x(c, lev, g, i), node_y(c, lev, g, j), &v, &gx, &gy)) return 1;
+    double gn = sqrt(gx * gx + gy * gy);
+    return ph < -c->snap * c->lv[lev].h * gn;
+}
+
+static int classify_level(ctx_t *c, int lev)
+{
+    level_t *l = &c->lv[lev];
+    int N = l->N;
+    double ph;
+    memset(l->prim, 0, (size_t)l->n);
+    /* Algorithm LS: internal if phi < 0; walls and box ghosts by position */
+    for (int j = -1; j <= N; j++)
+        for (int i = 0; i <= N; i++) {
+            int8_t *t = tref(l, G_U, i, j);
+            if (j == -1 || j == N) *t = (i >= 1 && i <= N - 1) ? T_BOXGHOST : T_INACTIVE;
+            else if (i == 0 || i == N) *t = T_WALL;
+            else {
+                if (!phi_node(c, lev, G_U, i, j, &ph)) { seterr(c, "phi missing"); return 0; }
+                *t = node_internal(c, lev, G_U, i, j, ph) ? T_INTERNAL : T_EXT;
+            }
+        }
+    for (int j = 0; j <= N; j++)
+        for (int i = -1; i <= N; i++) {
+            int8_t *t = tref(l, G_V, i, j);
+            if (i == -1 || i == N) *t = (j >= 1 && j <= N - 1) ? T_BOXGHOST : T_INACTIVE;
+            else if (j == 0 || j == N) *t = T_WALL;
+            else {
+                if (!phi_node(c, lev, G_V, i, j, &ph)) { seterr(c, "phi missing"); return 0; }
+                *t = node_internal(c, lev, G_V, i, j, ph) ? T_INTERNAL : T_EXT;
+            }
+        }
+    for (int j = 0; j < N; j++)
+        for (int i = 0; i < N; i++) {
+            if (!phi_node(c, lev, G_P, i, j, &ph)) { seterr(c, "phi missing"); return 0; }
+            *tref(l, G_P, i, j) = node_internal(c, lev, G_P, i, j, ph) ? T_INTERNAL : T_EXT;
+        }
+    /* a pressure cell whose four faces are all non-internal has no box */
+    for (int j = 0; j < N; j++)
+        for (int i = 0; i < N; i++) {
+            int8_t *t = tref(l, G_P, i, j);
+            if (*t != T_INTERNAL) continue;
+            if (ttype(l, G_U, i, j) != T_INTERNAL && ttype(l, G_U, i + 1, j) != T_INTERNAL &&
+                ttype(l, G_V, i, j) != T_INTERNAL && ttype(l, G_V, i, j + 1) != T_INTERNAL)
+                *t = T_EXT;
+        }
+    /* external nodes referenced by internal rows and box-ghost rows */
+    int ch = 0;
+    for (int j = 0; j < N; j++)
+        for (int i = 1; i < N; i++)
+            if (ttype(l, G_U, i, j) == T_INTERNAL) {
+                if (!mark_needed(c, l, G_U, i + 1, j, &ch) || !mark_needed(c, l, G_U, i - 1, j, &ch) ||
+                    !mark_needed(c, l, G_U, i, j + 1, &ch) || !mark_needed(c, l, G_U, i, j - 1, &ch) ||
+                    !mark_needed(c, l, G_P, i, j, &ch) || !mark_needed(c, l, G_P, i - 1, j, &ch))
+                    return 0;
+            }
+    for (int j = 1; j < N; j++)
+        for (int i = 0; i < N; i++)
+            if (ttype(l, G_V, i, j) == T_INTERNAL) {
+                if (!mark_needed(c, l, G_V, i + 1, j, &ch) || !mark_needed(c, l, G_V, i - 1, j, &ch) ||
+                    !mark_needed(c, l, G_V, i, j + 1, &ch) || !mark_needed(c, l, G_V, i, j - 1, &ch) ||
+                    !mark_needed(c, l, G_P, i, j, &ch) || !mark_needed(c, l, G_P, i, j - 1, &ch))
+                    return 0;
+            }
+    for (int j = 0; j < N; j++)
+        for (int i = 0; i < N; i++)
+            if (ttype(l, G_P, i, j) == T_INTERNAL) {
+                if (!mark_needed(c, l, G_U, i, j, &ch) || !mark_needed(c, l, G_U, i + 1, j, &ch) ||
+                    !mark_needed(c, l, G_V, i, j, &ch) || !mark_needed(c, l, G_V, i, j + 1, &ch))
+                    return 0;
+            }
+    for (int i = 1; i < N; i++) {
+        if (!mark_needed(c, l, G_U, i, 0, &ch) || !mark_needed(c, l, G_U, i, 1, &ch) ||
+            !mark_needed(c, l, G_U, i, N - 1, &ch) || !mark_needed(c, l, G_U, i, N - 2, &ch))
+            return 0;
+    }
+    for (int j = 1; j < N; j++) {
+        if (!mark_needed(c, l, G_V, 0, j, &ch) || !mark_needed(c, l, G_V, 1, j, &ch) ||
+            !mark_needed(c, l, G_V, N - 1, j, &ch) || !mark_needed(c, l, G_V, N - 2, j, &ch))
+            return 0;
+    }
+    /* close the ghost set under the ghost stencils (Remark 1, coupled ghosts) */
+    for (int pass = 0;; pass++) {
+        if (pass > 64) { seterr(c, "ghost marking does not close"); return 0; }
+        ch = 0;
+        for (int g = 0; g < 3; g++) {
+            int ilo = g == G_V ? -1 : 0, ihi = g == G_P ? N - 1 : N;
+            int jlo = g == G_U ? -1 : 0, jhi = g == G_P ? N - 1 : N;
+            for (int j = jlo; j <= jhi; j++)
+                for (int i = ilo; i <= ihi; i++) {
+                    if (ttype(l, g, i, j) != T_GHOST) continue;
+                    ghost_t G;
+                    if (!ghost_setup(c, lev, g, i, j, &G)) { seterr(c, "boundary projection failed"); return 0; }
+                    for (int k = 1; k < G.nst; k++)
+                        if (!mark_stencil(c, l, g, G.si[k], G.sj[k], &ch)) return 0;
+                }
+        }
+        if (!ch) break;
+    }
+    /* everything else external is inactive; collect ghosts in (grid, j, i) order */
+    int ng = 0;
+    for (int g = 0; g < 3; g++) {
+        int ilo = g == G_V ? -1 : 0, ihi = g == G_P ? N - 1 : N;
+        int jlo = g == G_U ? -1 : 0, jhi = g == G_P ? N - 1 : N;
+        for (int j = jlo; j <= jhi; j++)
+            for (int i = ilo; i <= ihi; i++) {
+                int8_t *t = tref(l, g, i, j);
+                if (*t == T_EXT) *t = T_INACTIVE;
+                if (*t == T_GHOST) ng++;
+            }
+    }
+    l->gh = (ghost_t *)calloc(ng > 0 ? ng : 1, sizeof(ghost_t));
+    l->ngh = 0;
+    for (int k = 0; k < l->n; k++) l->gid[k] = -1;
+    for (int g = 0; g < 3; g++) {
+        int ilo = g == G_V ? -1 : 0, ihi = g == G_P ? N - 1 : N;
+        int jlo = g == G_U ? -1 : 0, jhi = g == G_P ? N - 1 : N;
+        for (int j = jlo; j <= jhi; j++)
+            for (int i = ilo; i <= ihi; i++) {
+                if (ttype(l, g, i, j) != T_GHOST) continue;
+                ghost_t *G = &l->gh[l->ngh];
+                if (!ghost_setup(c, lev, g, i, j, G)) {
+                    seterr(c, "boundary projection failed");
+                    return 0;
+                }
+                l->gid[iG(l, g, i, j)] = l->ngh;
+                l->ngh++;
+            }
+    }
+    l->n_int = 0;
+    for (int j = 0; j < N; j++)
+        for (int i = 0; i < N; i++)
+            if (ttype(l, G_P, i, j) == T_INTERNAL) l->n_int++;
+    if (l->n_int == 0) { seterr(c, "no internal pressure cell"); return 0; }
+    return 1;
+}
+
+/* ------------------------------------------------------------------ rows */
+
+static void radd(row_t *R, int col, double a)
+{
+    R->col[R->n] = col;
+    R->a[R->n] = a;
+    R->n++;
+}
+
+/* Coefficients of the equation written at node (g, i, j) (Algorithm LS). */
+static int get_row(ctx_t *c, int lev, int g, int i, int j, row_t *R)
+{
+    level_t *l = &c->lv[lev];
+    int N = l->N;
+    double h = l->h;
+    double q = 1.0 / h, a = c->alpha / (h * h), d = 1.0 + 4.0 * a;
+    int t = ttype(l, g, i, j);
+    R->n = 0;
+    switch (t) {
+    case T_INTERNAL:
+        if (g == G_U) { /* u - alpha lap u + dp/dx */
+            radd(R, iU(l, i, j), d);
+            radd(R, iU(l, i + 1, j), -a);
+            radd(R, iU(l, i - 1, j), -a);
+            radd(R, iU(l, i, j + 1), -a);
+            radd(R, iU(l, i, j - 1), -a);
+            radd(R, iP(l, i, j), q);
+            radd(R, iP(l, i - 1, j), -q);
+        } else if (g == G_V) {
+            radd(R, iV(l, i, j), d);
+            radd(R, iV(l, i + 1, j), -a);
+            radd(R, iV(l, i - 1, j), -a);
+            radd(R, iV(l, i, j + 1), -a);
+            radd(R, iV(l, i, j - 1), -a);
+            radd(R, iP(l, i, j), q);
+            radd(R, iP(l, i, j - 1), -q);
+        } else { /* div u - xi */
+            radd(R, iU(l, i + 1, j), q);
+            radd(R, iU(l, i, j), -q);
+            radd(R, iV(l, i, j + 1), q);
+            radd(R, iV(l, i, j), -q);
+            radd(R, iXI(l), -1.0);
+        }
+        break;
+    case T_GHOST: {
+        ghost_t *G = &l->gh[l->gid[iG(l, g, i, j)]];
+        for (int k = 0; k < G->nst; k++) radd(R, iG(l, g, G->si[k], G->sj[k]), G->w[k]);
+        break;
+    }
+    case T_WALL:
+        radd(R, iG(l, g, i, j), 1.0);
+        break;
+    case T_BOXGHOST:
+        if (g == G_U) {
+            int s = j == -1 ? 1 : -1;
+            radd(R, iU(l, i, j), 3.0 / 8.0);
+            radd(R, iU(l, i, j + s), 3.0 / 4.0);
+            radd(R, iU(l, i, j + 2 * s), -1.0 / 8.0);
+        } else {
+            int s = i == -1 ? 1 : -1;
+            radd(R, iV(l, i, j), 3.0 / 8.0);
+            radd(R, iV(l, i + s, j), 3.0 / 4.0);
+            radd(R, iV(l, i + 2 * s, j), -1.0 / 8.0);
+        }
+        break;
+    default: /* inactive: x = b (b = 0) */
+        radd(R, iG(l, g, i, j), 1.0);
+        break;
+    }
+    (void)N;
+    return t;
+}
+
+static double row_residual(const row_t *R, const double *x, double b)
+{
+    double s = b;
+    for (int k = 0; k < R->n; k++) s -= R->a[k] * x[R->col[k]];
+    return s;
+}
+
+/* ----------------------------------------------------------------- public */
+
+void *or_create(int N, double x0, double y0, double len, int levels, double alpha)
+{
+    if (N < 4 || levels < 1 || levels > OR_MAXLEV) return NULL;
+    if (N % (1 << (levels - 1)) != 0) return NULL;
+    ctx_t *c = (ctx_t *)calloc(1, sizeof(ctx_t));
+    c->N = N;
+    c->L = levels;
+    c->x0 = x0;
+    c->y0 = y0;
+    c->len = len;
+    c->alpha = alpha;
+    c->nu1 = 2; c->nu2 = 1; c->gamma = 1; c->lam = 5;
+    c->dtau = 0.9; c->ghost_mode = 0; c->order_mode = 0; c->rng = 12345u; c->snap = 0.3;
+    for (int k = 0; k < levels; k++) {
+        level_t *l = &c->lv[k];
+        l->N = N >> k;
+        l->h = len / (double)l->N;
+        l->nU = (l->N + 1) * (l->N + 2);
+        l->nV = (l->N + 2) * (l->N + 1);
+        l->nP = l->N * l->N;
+        l->n = l->nU + l->nV + l->nP + 1;
+        l->tU = (int8_t *)calloc(l->nU, 1);
+        l->tV = (int8_t *)calloc(l->nV, 1);
+        l->tP = (int8_t *)calloc(l->nP, 1);
+        l->gid = (int *)malloc(sizeof(int) * l->n);
+        l->prim = (int8_t *)calloc(l->n, 1);
+        l->x = (double *)calloc(l->n, sizeof(double));
+        l->b = (double *)calloc(l->n, sizeof(double));
+        l->r = (double *)calloc(l->n, sizeof(double));
+    }
+    size_t M = 2 * (size_t)N + 1;
+    c->phi = (double *)calloc(M * M, sizeof(double));
+    return c;
+}
+
+void or_destroy(void *vc)
+{
+    ctx_t *c = (ctx_t *)vc;
+    if (!c) return;
+    for (int k = 0; k < c->L; k++) free_level(&c->lv[k]);
+    free(c->phi);
+    free(c);
+}
+
+void or_set_params(void *vc, int nu1, int nu2, int gamma, int lam, double dtau, int ghost_mode, int order_mode, unsigned seed)
+{
+    ctx_t *c = (ctx_t *)vc;
+    c->nu1 = nu1; c->nu2 = nu2; c->gamma = gamma; c->lam = lam;
+    c->dtau = dtau; c->ghost_mode = ghost_mode; c->order_mode = order_mode; c->rng = seed ? seed : 1u;
+}
+
+void or_set_alpha(void *vc, double alpha) { ((ctx_t *)vc)->alpha = alpha; }
+
+void or_set_snap(void *vc, double snap) { ((ctx_t *)vc)->snap = snap; }
+
+const char *or_last_error(void *vc) { return ((ctx_t *)vc)->err; }
+
+int or_n(void *vc, int lev) { return ((ctx_t *)vc)->lv[lev].n; }
+int or_n_int(void *vc, int lev) { return ((ctx_t *)vc)->lv[lev].n_int; }
+int or_num_ghosts(void *vc, int lev) { return ((ctx_t *)vc)->lv[lev].ngh; }
+
+static int factor_coarsest(ctx_t *c);
+
+/* phi: (2N+1)^2 half lattice, row b (y) major, paper sign (phi > 0 in the object) */
+int or_geometry(void *vc, const double *phi)
+{
+    ctx_t *c = (ctx_t *)vc;
+    c->err[0] = 0;
+    c->geom_ok = 0;
+    size_t M = 2 * (size_t)c->N + 1;
+    memcpy(c->phi, phi, M * M * sizeof(double));
+    for (int k = 0; k < c->L; k++) {
+        level_t *l = &c->lv[k];
+        free(l->gh); l->gh = NULL; l->ngh = 0;
+        if (!classify_level(c, k)) return OR_GEOMETRY;
+    }
+    int st = factor_coarsest(c);
+    if (st != OR_OK) return st;
+    c->geom_ok = 1;
+    return OR_OK;
+}
+
+/* types of every unknown of level lev in the flat layout (mean slot = -1) */
+int or_types(void *vc, int lev, int8_t *out)
+{
+    level_t *l = &((ctx_t *)vc)->lv[lev];
+    memcpy(out, l->tU, l->nU);
+    memcpy(out + l->nU, l->tV, l->nV);
+    memcpy(out + l->nU + l->nV, l->tP, l->nP);
+    out[l->n - 1] = -1;
+    return l->n;
+}
+
+/* ghost records: ints [grid, i, j, sx, sy, axis + 2 kind, nst] and doubles
+ * [xB, yB, nx, ny, thx, thy, w0..w8]; stencil nodes [si0, sj0, ...] */
+int or_ghosts(void *vc, int lev, int *iout, double *dout, int *sout, int cap)
+{
+    level_t *l = &((ctx_t *)vc)->lv[lev];
+    int n = l->ngh < cap ? l->ngh : cap;
+    for (int k = 0; k < n; k++) {
+        ghost_t *G = &l->gh[k];
+        int *ip = iout + 7 * k;
+        ip[0] = G->grid; ip[1] = G->i; ip[2] = G->j; ip[3] = G->sx; ip[4] = G->sy; ip[5] = G->axis + 2 * G->kind; ip[6] = G->nst;
+        double *dp = dout + 15 * k;
+        dp[0] = G->xB; dp[1] = G->yB; dp[2] = G->nx; dp[3] = G->ny; dp[4] = G->thx; dp[5] = G->thy;
+        for (int m = 0; m < 9; m++) dp[6 + m] = m < G->nst ? G->w[m] : 0.0;
+        int *sp = sout + 18 * k;
+        for (int m = 0; m < 9; m++) {
+            sp[2 * m] = m < G->nst ? G->si[m] : 0;
+            sp[2 * m + 1] = m < G->nst ? G->sj[m] : 0;
+        }
+    }
+    return l->ngh;
+}
+
+/* Algorithm 1 on its own, for tests: B of node (g, i, j) of level lev */
+int or_boundary_point(void *vc, int lev, int g, int i, int j, double *xy)
+{
+    ctx_t *c = (ctx_t *)vc;
+    return ghost_to_boundary(c, lev, g, i, j, &xy[0], &xy[1]) ? OR_OK : OR_GEOMETRY;
+}
+
+/* full residual r = b - M x on level lev; returns ||r||_inf */
+double or_residual(void *vc, int lev, const double *x, const double *b, double *r)
+{
+    ctx_t *c = (ctx_t *)vc;
+    level_t *l = &c->lv[lev];
+    int N = l->N;
+    row_t R;
+    double mx = 0.0;
+    for (int g = 0; g < 3; g++) {
+        int ilo = g == G_V ? -1 : 0, ihi = g == G_P ? N - 1 : N;
+        int jlo = g == G_U ? -1 : 0, jhi = g == G_P ? N - 1 : N;
+        for (int j = jlo; j <= jhi; j++)
+            for (int i = ilo; i <= ihi; i++) {
+                int k = iG(l, g, i, j);
+                get_row(c, lev, g, i, j, &R);
+                double v = row_residual(&R, x, b[k]);
+                r[k] = v;
+                if (fabs(v) > mx || v != v) mx = v != v ? NAN : fabs(v);
+            }
+    }
+    /* mean row, Eq. (midpoint) scaled by h^2 */
+    double s = 0.0;
+    for (int j = 0; j < N; j++)
+        for (int i = 0; i < N; i++)
+            if (ttype(l, G_P, i, j) == T_INTERNAL) s += x[iP(l, i, j)];
+    double v = b[iXI(l)] - l->h * l->h * s;
+    r[iXI(l)] = v;
+    if (fabs(v) > mx) mx = fabs(v);
+    return mx;
+}
+
+/* assembled M_h in COO form (Eq. LS); returns nnz or -needed if cap too small */
+int or_assemble(void *vc, int lev, int *ri, int *ci, double *val, int cap)
+{
+    ctx_t *c = (ctx_t *)vc;
+    level_t *l = &c->lv[lev];
+    int N = l->N, nnz = 0;
+    row_t R;
+    for (int g = 0; g < 3; g++) {
+        int ilo = g == G_V ? -1 : 0, ihi = g == G_P ? N - 1 : N;
+        int jlo = g == G_U ? -1 : 0, jhi = g == G_P ? N - 1 : N;
+        for (int j = jlo; j <= jhi; j++)
+            for (int i = ilo; i <= ihi; i++) {
+                int k = iG(l, g, i, j);
+                get_row(c, lev, g, i, j, &R);
+                for (int m = 0; m < R.n; m++) {
+                    if (nnz < cap) { ri[nnz] = k; ci[nnz] = R.col[m]; val[nnz] = R.a[m]; }
+                    nnz++;
+                }
+            }
+    }
+    for (int j = 0; j < N; j++)
+        for (int i = 0; i < N; i++)
+            if (ttype(l, G_P, i, j) == T_INTERNAL) {
+                if (nnz < cap) { ri[nnz] = iXI(l); ci[nnz] = iP(l, i, j); val[nnz] = l->h * l->h; }
+                nnz++;
+            }
+    return nnz <= cap ? nnz : -nnz;
+}
+
+/* ------------------------------------------------------- dense LU (pivoted) */
+
+static int lu_factor(int n, double *A, int *piv)
+{
+    for (int k = 0; k < n; k++) {
+        int p = k;
+        double best = fabs(A[(size_t)k * n + k]);
+        for (int i = k + 1; i < n; i++) {
+            double v = fabs(A[(size_t)i * n + k]);
+            if (v > best) { best = v; p = i; }
+        }
+        piv[k] = p;
+        if (!(best > 0.0)) return 0;
+        if (p != k)
+            for (int jj = 0; jj < n; jj++) {
+                double t = A[(size_t)k * n + jj];
+                A[(size_t)k * n + jj] = A[(size_t)p * n + jj];
+                A[(size_t)p * n + jj] = t;
+            }
+        double dkk = A[(size_t)k * n + k];
+        for (int i = k + 1; i < n; i++) {
+            double m = A[(size_t)i * n + k] / dkk;
+            A[(size_t)i * n + k] = m;
+            if (m != 0.0)
+                for (int jj = k + 1; jj < n; jj++) A[(size_t)i * n + jj] -= m * A[(size_t)k * n + jj];
+        }
+    }
+    return 1;
+}
+
+static void lu_solve(int n, const double *A, const int *piv, double *b)
+{
+    for (int k = 0; k < n; k++) {
+        if (piv[k] != k) { double t = b[k]; b[k] = b[piv[k]]; b[piv[k]] = t; }
+    }
+    for (int i = 0; i < n; i++) {
+        double s = b[i];
+        for (int jj = 0; jj < i; jj++) s -= A[(size_t)i * n + jj] * b[jj];
+        b[i] = s;
+    }
+    for (int i = n - 1; i >= 0; i--) {
+        double s = b[i];
+        for (int jj = i + 1; jj < n; jj++) s -= A[(size_t)i * n + jj] * b[jj];
+        b[i] = s / A[(size_t)i * n + i];
+    }
+}
+
+/* dense solve of A x = b in place (A overwritten), for tests */
+int or_dense_solve(int n, double *A, double *b)
+{
+    int *piv = (int *)malloc(sizeof(int) * n);
+    int ok = lu_factor(n, A, piv);
+    if (ok) lu_solve(n, A, piv, b);
+    free(piv);
+    return ok ? OR_OK : OR_SINGULAR;
+}
+
+static int dense_matrix(ctx_t *c, int lev, double *A)
+{
+    level_t *l = &c->lv[lev];
+    int n = l->n;
+    int cap = 12 * n + l->nP + 16;
+    int *ri = (int *)malloc(sizeof(int) * cap), *ci = (int *)malloc(sizeof(int) * cap);
+    double *v = (double *)malloc(sizeof(double) * cap);
+    int nnz = or_assemble(c, lev, ri, ci, v, cap);
+    memset(A, 0, sizeof(double) * (size_t)n * n);
+    for (int k = 0; k < nnz; k++) A[(size_t)ri[k] * n + ci[k]] += v[k];
+    free(ri); free(ci); free(v);
+    return nnz > 0;
+}
+
+static int factor_coarsest(ctx_t *c)
+{
+    level_t *l = &c->lv[c->L - 1];
+    int n = l->n;
+    free(l->lu); free(l->piv);
+    l->lu = (double *)malloc(sizeof(double) * (size_t)n * n);
+    l->piv = (int *)malloc(sizeof(int) * n);
+    dense_matrix(c, c->L - 1, l->lu);
+    if (!lu_factor(n, l->lu, l->piv)) { seterr(c, "coarsest matrix is singular"); return OR_SINGULAR; }
+    return OR_OK;
+}
+
+/* dense matrix of level lev (row-major n x n), for tests */
+int or_dense_matrix(void *vc, int lev, double *A) { return dense_matrix((ctx_t *)vc, lev, A) ? OR_OK : OR_INVALID; }
+
+/* exact solve on the coarsest level: x = M^-1 b */
+int or_coarse_solve(void *vc, const double *b, double *x)
+{
+    ctx_t *c = (ctx_t *)vc;
+    level_t *l = &c->lv[c->L - 1];
+    memcpy(x, b, sizeof(double) * l->n);
+    lu_solve(l->n, l->lu, l->piv, x);
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------- smoothers */
+
+static unsigned rng_next(ctx_t *c)
+{
+    c->rng = c->rng * 1664525u + 1013904223u;
+    return c->rng >> 8;
+}
+
+/* Box relaxation of the cell (i, j) (Sect. 4.1.1): the unknowns are p_ij and
+ * the variables on the cell borders; the rows of those unknowns are solved
+ * together with everything else frozen.  A border variable takes part when it
+ * is internal (momentum row) or a ghost of the object (its ghost row); wall
+ * and box-ghost borders stay frozen. */
+static void box_relax(ctx_t *c, int lev, double *x, const double *b, int i, int j)
+{
+    level_t *l = &c->lv[lev];
+    int gg[5], ii[5], jj[5], unk[5], nu = 0;
+    const int fg[4] = {G_U, G_U, G_V, G_V};
+    const int fi[4] = {i, i + 1, i, i};
+    const int fj[4] = {j, j, j, j + 1};
+    for (int f = 0; f < 4; f++) {
+        int t = ttype(l, fg[f], fi[f], fj[f]);
+        if (t == T_INTERNAL || t == T_GHOST) {
+            gg[nu] = fg[f]; ii[nu] = fi[f]; jj[nu] = fj[f];
+            unk[nu] = iG(l, fg[f], fi[f], fj[f]);
+            nu++;
+        }
+    }
+    gg[nu] = G_P; ii[nu] = i; jj[nu] = j; unk[nu] = iP(l, i, j); nu++;
+    double A[25], rhs[5];
+    int piv[5];
+    for (int r = 0; r < nu; r++) {
+        row_t R;
+        get_row(c, lev, gg[r], ii[r], jj[r], &R);
+        rhs[r] = row_residual(&R, x, b[unk[r]]);
+        for (int cc = 0; cc < nu; cc++) {
+            double sum = 0.0;
+            for (int k = 0; k < R.n; k++)
+                if (R.col[k] == unk[cc]) sum += R.a[k];
+            A[r * nu + cc] = sum;
+        }
+    }
+    if (!lu_factor(nu, A, piv)) return;
+    lu_solve(nu, A, piv, rhs);
+    for (int r = 0; r < nu; r++) x[unk[r]] += rhs[r];
+}
+
+static int cut_cell(level_t *l, int i, int j)
+{
+    return ttype(l, G_U, i, j) == T_GHOST || ttype(l, G_U, i + 1, j) == T_GHOST ||
+           ttype(l, G_V, i, j) == T_GHOST || ttype(l, G_V, i, j + 1) == T_GHOST;
+}
+
+static void shuffle(ctx_t *c, int *v, int n)
+{
+    for (int k = n - 1; k > 0; k--) {
+        int m = (int)(rng_next(c) % (unsigned)(k + 1));
+        int t = v[k]; v[k] = v[m]; v[m] = t;
+    }
+}
+
+/* One box sweep over the internal cells: cells with no ghost border in five
+ * colours (i + 3 j) mod 5, then cells with a ghost border (their boxes reach
+ * up to four nodes through the ghost rows) in 25 colours (i mod 5, j mod 5);
+ * boxes of one colour never touch each other's unknowns.  Then a point-Jacobi
+ * update of internal faces that belong to no internal cell. */
+void or_box_sweep(void *vc, int lev, double *x, const double *b)
+{
+    ctx_t *c = (ctx_t *)vc;
+    level_t *l = &c->lv[lev];
+    int N = l->N;
+    int *cells = (int *)malloc(sizeof(int) * (size_t)N * N);
+    if (c->order_mode == 2) { /* lexicographic Gauss-Seidel (ablation) */
+        for (int j = 0; j < N; j++)
+            for (int i = 0; i < N; i++)
+                if (ttype(l, G_P, i, j) == T_INTERNAL) box_relax(c, lev, x, b, i, j);
+    } else {
+        for (int col = 0; col < 5; col++) {
+            int nc = 0;
+            for (int j = 0; j < N; j++)
+                for (int i = 0; i < N; i++)
+                    if ((i + 3 * j) % 5 == col && ttype(l, G_P, i, j) == T_INTERNAL && !cut_cell(l, i, j))
+                        cells[nc++] = j * N + i;
+            if (c->order_mode == 1) shuffle(c, cells, nc); /* random order inside a colour */
+            for (int k = 0; k < nc; k++) box_relax(c, lev, x, b, cells[k] % N, cells[k] / N);
+        }
+        for (int col = 0; col < 25; col++) {
+            int nc = 0;
+            for (int j = 0; j < N; j++)
+                for (int i = 0; i < N; i++)
+                    if ((j % 5) * 5 + (i % 5) == col && ttype(l, G_P, i, j) == T_INTERNAL && cut_cell(l, i, j))
+                        cells[nc++] = j * N + i;
+            if (c->order_mode == 1) shuffle(c, cells, nc);
+            for (int k = 0; k < nc; k++) box_relax(c, lev, x, b, cells[k] % N, cells[k] / N);
+        }
+    }
+    free(cells);
+    /* internal faces with no internal cell on either side */
+    int cnt = 0;
+    int *idx = (int *)malloc(sizeof(int) * (l->nU + l->nV));
+    double *upd = (double *)malloc(sizeof(double) * (l->nU + l->nV));
+    row_t R;
+    for (int j = 0; j < N; j++)
+        for (int i = 1; i < N; i++)
+            if (ttype(l, G_U, i, j) == T_INTERNAL && ttype(l, G_P, i - 1, j) != T_INTERNAL &&
+                ttype(l, G_P, i, j) != T_INTERNAL) {
+                get_row(c, lev, G_U, i, j, &R);
+                idx[cnt] = iU(l, i, j);
+                upd[cnt++] = row_residual(&R, x, b[iU(l, i, j)]) / R.a[0];
+            }
+    for (int j = 1; j < N; j++)
+        for (int i = 0; i < N; i++)
+            if (ttype(l, G_V, i, j) == T_INTERNAL && ttype(l, G_P, i, j - 1) != T_INTERNAL &&
+                ttype(l, G_P, i, j) != T_INTERNAL) {
+                get_row(c, lev, G_V, i, j, &R);
+                idx[cnt] = iV(l, i, j);
+                upd[cnt++] = row_residual(&R, x, b[iV(l, i, j)]) / R.a[0];
+            }
+    for (int k = 0; k < cnt; k++) x[idx[k]] += upd[k];
+    free(idx);
+    free(upd);
+}
+
+/* relaxation of the (xi, mean) pair: xi from the continuity rows, then a
+ * uniform pressure shift that satisfies the mean row exactly */
+void or_scalar_update(void *vc, int lev, double *x, const double *b)
+{
+    ctx_t *c = (ctx_t *)vc;
+    level_t *l = &c->lv[lev];
+    int N = l->N;
+    double h = l->h, s = 0.0, m = 0.0;
+    for (int j = 0; j < N; j++)
+        for (int i = 0; i < N; i++)
+            if (ttype(l, G_P, i, j) == T_INTERNAL) {
+                double div = (x[iU(l, i + 1, j)] - x[iU(l, i, j)] + x[iV(l, i, j + 1)] - x[iV(l, i, j)]) / h;
+                s += div - b[iP(l, i, j)];
+                m += x[iP(l, i, j)];
+            }
+    x[iXI(l)] = s / (double)l->n_int;
+    double shift = (b[iXI(l)] - h * h * m) / (h * h * (double)l->n_int);
+    for (int j = 0; j < N; j++)
+        for (int i = 0; i < N; i++) {
+            int t = ttype(l, G_P, i, j);
+            if (t == T_INTERNAL || t == T_GHOST) x[iP(l, i, j)] += shift;
+        }
+}
+
+static int ghost_class(int t) { return t == T_GHOST || t == T_WALL || t == T_BOXGHOST; }
+
+/* One Jacobi sweep of Eq. (ghostrelax) over every ghost, wall and box-ghost row */
+void or_ghost_sweep(void *vc, int lev, double *x, const double *b)
+{
+    ctx_t *c = (ctx_t *)vc;
+    level_t *l = &c->lv[lev];
+    int N = l->N;
+    int *idx = (int *)malloc(sizeof(int) * l->n);
+    double *upd = (double *)malloc(sizeof(double) * l->n);
+    int cnt = 0;
+    row_t R;
+    for (int g = 0; g < 3; g++) {
+        int ilo = g == G_V ? -1 : 0, ihi = g == G_P ? N - 1 : N;
+        int jlo = g == G_U ? -1 : 0, jhi = g == G_P ? N - 1 : N;
+        for (int j = jlo; j <= jhi; j++)
+            for (int i = ilo; i <= ihi; i++) {
+                if (!ghost_class(ttype(l, g, i, j))) continue;
+                int k = iG(l, g, i, j);
+                get_row(c, lev, g, i, j, &R);
+                double res = row_residual(&R, x, b[k]);
+                double cg = R.a[0]; /* the first entry is the node itself */
+                idx[cnt] = k;
+                upd[cnt++] = c->ghost_mode == 1 ? c->dtau * res / cg : c->dtau * res;
+            }
+    }
+    for (int k = 0; k < cnt; k++) x[idx[k]] += upd[k];
+    free(idx);
+    free(upd);
+}
+
+/* Algorithm relax: nu x {box sweep; (xi, mean) update; lambda ghost sweeps} */
+void or_smooth(void *vc, int lev, double *x, const double *b, int nu)
+{
+    ctx_t *c = (ctx_t *)vc;
+    for (int s = 0; s < nu; s++) {
+        or_box_sweep(c, lev, x, b);
+        or_scalar_update(c, lev, x, b);
+        for (int k = 0; k < c->lam; k++) or_ghost_sweep(c, lev, x, b);
+    }
+}
+
+/* ------------------------------------------------------------- transfers */
+
+static int same_class(int tc, int tf)
+{
+    if (tc == T_INTERNAL) return tf == T_INTERNAL;
+    return ghost_class(tf);
+}
+
+/* restriction of the fine residual r (level lev) to the rhs bH of lev+1,
+ * Eq. (restop) where every stencil point is of the coarse point's class,
+ * otherwise the plain mean over the points of that class, Eq. (restop5). */
+void or_restrict(void *vc, int lev, const double *r, double *bH)
+{
+    ctx_t *c = (ctx_t *)vc;
+    level_t *f = &c->lv[lev], *C = &c->lv[lev + 1];
+    int Nc = C->N;
+    for (int g = 0; g < 3; g++) {
+        int ilo = g == G_V ? -1 : 0, ihi = g == G_P ? Nc - 1 : Nc;
+        int jlo = g == G_U ? -1 : 0, jhi = g == G_P ? Nc - 1 : Nc;
+        for (int J = jlo; J <= jhi; J++)
+            for (int I = ilo; I <= ihi; I++) {
+                int tc = ttype(C, g, I, J);
+                int kc = iG(C, g, I, J);
+                if (tc == T_INACTIVE) { bH[kc] = 0.0; continue; }
+                int fi[6], fj[6], ns = 0;
+                double wt[6];
+                if (g == G_U) {
+                    for (int dj = 0; dj <= 1; dj++)
+                        for (int di = -1; di <= 1; di++) {
+                            fi[ns] = 2 * I + di; fj[ns] = 2 * J + dj; wt[ns] = (di == 0 ? 2.0 : 1.0) / 8.0; ns++;
+                        }
+                } else if (g == G_V) {
+                    for (int dj = -1; dj <= 1; dj++)
+                        for (int di = 0; di <= 1; di++) {
+                            fi[ns] = 2 * I + di; fj[ns] = 2 * J + dj; wt[ns] = (dj == 0 ? 2.0 : 1.0) / 8.0; ns++;
+                        }
+                } else {
+                    for (int dj = 0; dj <= 1; dj++)
+                        for (int di = 0; di <= 1; di++) {
+                            fi[ns] = 2 * I + di; fj[ns] = 2 * J + dj; wt[ns] = 0.25; ns++;
+                        }
+                }
+                int all = 1, cnt = 0;
+                double sw = 0.0, su = 0.0;
+                for (int k = 0; k < ns; k++) {
+                    int tf = ttype(f, g, fi[k], fj[k]);
+                    if (same_class(tc, tf)) {
+                        double v = r[iG(f, g, fi[k], fj[k])];
+                        sw += wt[k] * v;
+                        su += v;
+                        cnt++;
+                    } else all = 0;
+                }
+                bH[kc] = all ? sw : (cnt > 0 ? su / (double)cnt : 0.0);
+            }
+    }
+    bH[iXI(C)] = r[iXI(f)];
+}
+
+/* 1-D interpolation taps for fine index k on a coarse line with valid
+ * indices [lo, hi].  aligned != 0: fine nodes sit on coarse nodes or halfway
+ * between two; otherwise (staggered direction) fine node k sits a quarter of
+ * a coarse cell from its nearest coarse node Kc and three quarters from the
+ * next one Ko.  Where Ko does not exist, linear extrapolation from Kc and the
+ * node on its other side. */
+static int taps(int k, int aligned, int lo, int hi, int *K, double *w)
+{
+    int even = (k % 2 == 0);
+    if (aligned) {
+        if (even) { K[0] = k / 2; w[0] = 1.0; return 1; }
+        K[0] = (k - 1) / 2; w[0] = 0.5;
+        K[1] = K[0] + 1; w[1] = 0.5;
+        return 2;
+    }
+    int Kc = even ? k / 2 : (k - 1) / 2;
+    int Ko = even ? Kc - 1 : Kc + 1;
+    if (Ko < lo || Ko > hi) {
+        K[0] = Kc; w[0] = 1.25;
+        K[1] = 2 * Kc - Ko; w[1] = -0.25;
+        return 2;
+    }
+    K[0] = Kc; w[0] = 0.75;
+    K[1] = Ko; w[1] = 0.25;
+    return 2;
+}
+
+/* bilinear interpolation of the coarse correction eH (level lev+1) added to
+ * every active node of the fine iterate x (level lev), Sect. 4.3.  Inactive
+ * coarse nodes carry no value: the weights of the active ones are
+ * renormalised to sum to one. */
+void or_prolong(void *vc, int lev, const double *eH, double *x)
+{
+    ctx_t *c = (ctx_t *)vc;
+    level_t *f = &c->lv[lev], *C = &c->lv[lev + 1];
+    int N = f->N, Nc = C->N;
+    for (int g = 0; g < 3; g++) {
+        int ilo = g == G_V ? -1 : 0, ihi = g == G_P ? N - 1 : N;
+        int jlo = g == G_U ? -1 : 0, jhi = g == G_P ? N - 1 : N;
+        int Ilo = g == G_V ? -1 : 0, Ihi = g == G_P ? Nc - 1 : Nc;
+        int Jlo = g == G_U ? -1 : 0, Jhi = g == G_P ? Nc - 1 : Nc;
+        for (int j = jlo; j <= jhi; j++)
+            for (int i = ilo; i <= ihi; i++) {
+                if (ttype(f, g, i, j) == T_INACTIVE) continue;
+                int KI[2], KJ[2];
+                double wi[2], wj[2];
+                int ni = taps(i, g == G_U, Ilo, Ihi, KI, wi);
+                int nj = taps(j, g == G_V, Jlo, Jhi, KJ, wj);
+                double s = 0.0, ws = 0.0;
+                for (int a = 0; a < nj; a++)
+                    for (int bb = 0; bb < ni; bb++) {
+                        if (ttype(C, g, KI[bb], KJ[a]) == T_INACTIVE) continue;
+                        double w = wj[a] * wi[bb];
+                        s += w * eH[iG(C, g, KI[bb], KJ[a])];
+                        ws += w;
+                    }
+                if (ws > 0.0) x[iG(f, g, i, j)] += s / ws;
+            }
+    }
+    x[iXI(f)] += eH[iXI(C)];
+}
+
+/* -------------------------------------------------------------- the cycle */
+
+static void zero_inactive(ctx_t *c, int lev, double *x)
+{
+    level_t *l = &c->lv[lev];
+    for (int k = 0; k < l->nU; k++) if (l->tU[k] == T_INACTIVE) x[k] = 0.0;
+    for (int k = 0; k < l->nV; k++) if (l->tV[k] == T_INACTIVE) x[l->nU + k] = 0.0;
+    for (int k = 0; k < l->nP; k++) if (l->tP[k] == T_INACTIVE) x[l->nU + l->nV + k] = 0.0;
+}
+
+static void cycle_rec(ctx_t *c, int lev, double *x, const double *b)
+{
+    if (lev == c->L - 1) {
+        or_coarse_solve(c, b, x);
+        return;
+    }
+    level_t *l = &c->lv[lev], *C = &c->lv[lev + 1];
+    or_smooth(c, lev, x, b, c->nu1);
+    or_residual(c, lev, x, b, l->r);
+    or_restrict(c, lev, l->r, C->b);
+    memset(C->x, 0, sizeof(double) * C->n);
+    for (int k = 0; k < c->gamma; k++) cycle_rec(c, lev + 1, C->x, C->b);
+    or_prolong(c, lev, C->x, x);
+    or_smooth(c, lev, x, b, c->nu2);
+}
+
+/* one V (gamma = 1) or W (gamma = 2) cycle on level lev */
+int or_cycle(void *vc, int lev, double *x, const double *b)
+{
+    ctx_t *c = (ctx_t *)vc;
+    if (!c->geom_ok) return OR_INVALID;
+    cycle_rec(c, lev, x, b);
+    return OR_OK;
+}
+
+/* cycles from x until ||b - M x||_inf <= tol; hist[0..ncyc] residual norms */
+int or_solve(void *vc, double *x, const double *b, double tol, int max_cycles, double *hist, int *ncyc)
+{
+    ctx_t *c = (ctx_t *)vc;
+    if (!c->geom_ok) return OR_INVALID;
+    level_t *l = &c->lv[0];
+    zero_inactive(c, 0, x);
+    double r0 = or_residual(c, 0, x, b, l->r);
+    hist[0] = r0;
+    *ncyc = 0;
+    if (r0 <= tol) return OR_OK;
+    for (int k = 1; k <= max_cycles; k++) {
+        cycle_rec(c, 0, x, b);
+        double rn = or_residual(c, 0, x, b, l->r);
+        hist[k] = rn;
+        *ncyc = k;
+        if (!(rn == rn) || rn > 1e6 * r0) return OR_DIVERGED;
+        if (rn <= tol) return OR_OK;
+    }
+    return OR_NOT_CONVERGED;
+}
