@@ -1,0 +1,165 @@
+/*
+ * gpmg.h -- C ABI of libgpmg: the monolithic ghost-point multigrid solve of
+ * one Crank-Nicolson step of the incompressible Navier-Stokes equations on a
+ * staggered (MAC) grid around an object given by a level set
+ * (Coco, arXiv 1911.00994).
+ *
+ * The linear problem (Sect. 2, Eq. spaceprobaug): find (u, v, p, xi) with
+ *     u - alpha lap u + grad p = f~   in the fluid,
+ *     div u - xi = g                  in the fluid,
+ *     sum of p over internal cells = 0 (Eq. midpoint),
+ *     u = u_b on the boundary (ghost rows, Eq. BCu),
+ * alpha = dt / (2 Re), p the pressure scaled by dt.  Discretised as
+ * Algorithm LS (Sect. 3) and solved by geometric multigrid (Sect. 4).
+ *
+ * Conventions
+ *  - All array arguments are DEVICE pointers (CUDA global memory) unless the
+ *    name ends in _host.  The caller owns every buffer; the library never
+ *    allocates or frees device memory: it carves its internal arrays out of
+ *    one caller-provided workspace (gp_workspace_size / gp_create).
+ *  - Vector layout of a level with N cells per side (FP64, or FP32 where
+ *    stated): three frames of (N+2) rows x P columns, P = gp_pitch(N) (N+2
+ *    rounded up to a multiple of 32), then 32 scalars.  Node (i, j) of any
+ *    grid lives at frame offset (j+1)*P + (i+1):
+ *      u frame (offset 0):        i in [0, N],  j in [-1, N]  at (x0+i h, y0+(j+1/2) h)
+ *      v frame (offset F):        i in [-1, N], j in [0, N]   at (x0+(i+1/2) h, y0+j h)
+ *      p frame (offset 2F):       i, j in [0, N)              at cell centres
+ *      scalar 0 (offset 3F):      xi in an unknown vector, the mean row in a
+ *                                 right-hand side or residual.
+ *    F = (N+2)*P.  Frame slots outside a grid's range must hold 0.
+ *  - Level set: phi on the half-cell lattice, (2N+1) x (2N+1) FP64 values,
+ *    phi[b*(2N+1) + a] at (x0 + a h/2, y0 + b h/2).  Paper convention
+ *    (Sect. 3.1): phi > 0 inside the object, phi < 0 in the fluid; pass
+ *    phi_fluid_positive = 1 for the opposite sign.
+ *  - Every call is ordered on the context's stream.  Calls that return host
+ *    values (norms, counts, statuses) synchronise that stream.
+ *  - Errors: the return code; gp_last_error gives a message.  No call aborts,
+ *    traps or waits without bound.  On GP_NOT_CONVERGED / GP_DIVERGED the
+ *    iterate holds the last completed cycle.
+ */
+#ifndef GPMG_H
+#define GPMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gp_status {
+    GP_OK = 0,
+    GP_INVALID = 1,        /* bad argument, size or call order */
+    GP_GEOMETRY = 2,       /* level set unusable (no normal, projection failed, body too close to the walls) */
+    GP_SINGULAR = 3,       /* zero pivot in the coarsest-level inversion */
+    GP_NOT_CONVERGED = 4,  /* cycle cap reached before the tolerance */
+    GP_DIVERGED = 5,       /* NaN/Inf or residual above 1e6 x the initial one */
+    GP_CUDA = 6            /* a CUDA runtime call failed */
+} gp_status;
+
+typedef enum gp_precision { GP_FP64 = 0, GP_MIXED = 1 } gp_precision;
+
+typedef struct gp_params {
+    int N;              /* cells per side on the finest grid */
+    double x0, y0, L;   /* domain [x0, x0+L] x [y0, y0+L] */
+    int levels;         /* grids N, N/2, ..., N/2^(levels-1); the last is solved exactly */
+    double alpha;       /* dt / (2 Re) */
+    int nu1, nu2;       /* pre / post relaxations (Algorithm relax) */
+    int gamma;          /* 1: V-cycle, 2: W-cycle */
+    int lambda;         /* ghost sweeps per relaxation (Algorithm relax) */
+    double dtau;        /* fictitious time step of Eq. (ghostrelax) */
+    double snap;        /* a node within snap*h of the boundary counts as external */
+    int precision;      /* gp_precision */
+    int max_cycles;     /* cap for mg_solve */
+} gp_params;
+
+typedef struct gp_report {
+    int cycles;          /* cycles done */
+    double res0;         /* ||b - M x||_inf before the first cycle */
+    double res;          /* after the last cycle */
+    double rho;          /* geometric mean residual reduction per cycle */
+    double xi;           /* final xi */
+    double *hist_host;   /* optional host array of max_cycles + 1 norms, or NULL */
+} gp_report;
+
+typedef struct gp_ctx gp_ctx;
+
+/* Defaults: levels down to a 16 x 16 grid, V(2,1), lambda 5, dtau 0.9,
+ * snap 0.3, FP64, 100 cycles, alpha = L/N/2. */
+gp_status gp_params_default(gp_params *prm, int N, double x0, double y0, double L);
+
+/* Row pitch P and doubles per vector of a level with N cells per side. */
+int gp_pitch(int N);
+int64_t gp_vector_length(int N);
+
+/* Bytes of device workspace that gp_create needs for these parameters. */
+gp_status gp_workspace_size(const gp_params *prm, size_t *bytes);
+
+/* Create a context using `workspace` (device, >= gp_workspace_size bytes,
+ * 256-byte aligned, owned by the caller and kept alive until gp_destroy)
+ * and `stream` (a cudaStream_t, NULL for the default stream). */
+gp_status gp_create(gp_ctx **out, const gp_params *prm, void *workspace, size_t bytes, void *stream);
+gp_status gp_destroy(gp_ctx *ctx);
+const char *gp_last_error(const gp_ctx *ctx);
+
+/* Change alpha = dt / (2 Re); the coarsest-level inverse is rebuilt on the
+ * next call that needs it. */
+gp_status gp_set_alpha(gp_ctx *ctx, double alpha);
+
+/* Algorithm LS + Algorithm 1 on every level (Sect. 3.1-3.3): node types,
+ * ghost rows (Eq. BCu and extrapolation rows), cut-cell lists and the
+ * coarsest-level inverse.  phi: half lattice as described above. */
+gp_status geometry_build(gp_ctx *ctx, const double *phi, int phi_fluid_positive);
+
+/* Level information: cells per side, vector length, mesh size. */
+gp_status gp_level_info(const gp_ctx *ctx, int level, int *N, int64_t *len, double *h);
+
+/* Node types of a level copied to three device byte arrays of F bytes each
+ * (0 inactive, 1 internal, 2 ghost, 3 wall, 4 box ghost). */
+gp_status gp_types(gp_ctx *ctx, int level, uint8_t *tu, uint8_t *tv, uint8_t *tp);
+
+/* Number of object ghost rows of a level, and of all ghost-class rows
+ * (object ghosts + walls + box ghosts). */
+gp_status gp_ghost_count(gp_ctx *ctx, int level, int *n_object, int *n_rows);
+
+/* Object ghost rows of a level, in (grid, j, i) order, copied to device
+ * arrays of n_object entries: node = vector index of the ghost, kind
+ * (0 Eq. BCu, 1 extrapolation, 2 copy), nst, st[9*n] vector indices of the
+ * stencil (row-major per ghost), w[9*n], B[2*n] boundary points, th[2*n]. */
+gp_status gp_ghost_rows(gp_ctx *ctx, int level, int *node, uint8_t *kind, uint8_t *nst, int *st, double *w,
+                        double *B, double *th);
+
+/* r = b - M x on a level, Eq. (LS); returns ||r||_inf in *norm_host (may be
+ * NULL).  x, b, r: FP64 vectors of that level. */
+gp_status gp_residual(gp_ctx *ctx, int level, const double *x, const double *b, double *r, double *norm_host);
+
+/* Pieces of the relaxation (Sect. 4.1), in place on x: */
+gp_status gp_box_sweep(gp_ctx *ctx, int level, double *x, const double *b);     /* all box colours */
+gp_status gp_scalar_update(gp_ctx *ctx, int level, double *x, const double *b); /* xi and mean pressure */
+gp_status gp_ghost_sweep(gp_ctx *ctx, int level, double *x, const double *b);   /* one Eq. (ghostrelax) sweep */
+gp_status gp_smooth(gp_ctx *ctx, int level, double *x, const double *b, int nu); /* Algorithm relax */
+
+/* Restriction (Sect. 4.2, Eqs. restop, restop5) of a residual of `level`
+ * into the right-hand side of level+1. */
+gp_status gp_restrict(gp_ctx *ctx, int level, const double *r_fine, double *b_coarse);
+
+/* Prolongation (Sect. 4.3): x_fine += bilinear interpolation of e_coarse. */
+gp_status gp_prolong(gp_ctx *ctx, int level, const double *e_coarse, double *x_fine);
+
+/* Exact solve on the coarsest level: x = M^-1 b (Sect. 4.3). */
+gp_status gp_coarse_solve(gp_ctx *ctx, const double *b, double *x);
+
+/* One cycle (V or W per params) on the finest level, in place. */
+gp_status gp_cycle(gp_ctx *ctx, double *x, const double *b);
+
+/* Cycles from the iterate x until ||b - M x||_inf <= tol (absolute) or the
+ * cycle cap.  precision GP_MIXED: each outer step computes the FP64
+ * residual, runs one FP32 cycle on it from zero and adds the FP32
+ * correction to x in FP64.  rep may be NULL. */
+gp_status mg_solve(gp_ctx *ctx, double *x, const double *b, double tol, gp_report *rep);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GPMG_H */

@@ -1,0 +1,133 @@
+// Internal definitions shared by the CUDA translation units of libgpmg.
+//
+// Device layout of one multigrid level with N cells per side:
+//   frame of R = N + 2 rows and P >= N + 2 columns (P a multiple of 32);
+//   slot (row, col) = row * P + col, row = j + 1, col = i + 1 for every grid;
+//   u(i, j): i in [0, N],  j in [-1, N]   (rows j = -1 and j = N: box ghosts)
+//   v(i, j): i in [-1, N], j in [0, N]    (columns i = -1 and i = N: box ghosts)
+//   p(i, j): i, j in [0, N)
+//   vector = [u frame | v frame | p frame | 32 scalars], scalar 0 = xi
+//   (unknown) / mean row (equation).  Slots outside a grid's range are
+//   inactive and hold 0.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/gpmg.h"
+
+namespace gpmg {
+
+enum NodeType : uint8_t { T_INACTIVE = 0, T_INTERNAL = 1, T_GHOST = 2, T_WALL = 3, T_BOXGHOST = 4, T_EXT = 5 };
+enum Grid { G_U = 0, G_V = 1, G_P = 2 };
+// row kinds of the ghost list
+enum RowKind : uint8_t { K_BCU = 0, K_EXTRAP = 1, K_COPY = 2, K_WALL = 3, K_BOXGHOST = 4 };
+
+constexpr int MAX_LEVELS = 16;
+constexpr int MAX_MARCH = 64;
+constexpr int NSCAL = 32;
+constexpr int GH_ST = 9;  // stencil slots per ghost row
+
+// error bits written by kernels into the context's device status word
+enum ErrBits : unsigned {
+    E_STENCIL_OUT = 1u, E_INACTIVE_REF = 2u, E_PROJECTION = 4u, E_GHOST_CAP = 8u, E_CUT_CAP = 16u,
+    E_NO_NORMAL = 32u, E_NO_INTERNAL = 64u, E_CLOSURE = 128u, E_SINGULAR = 256u
+};
+
+__host__ __device__ inline int frame_pitch(int N) { return ((N + 2 + 31) / 32) * 32; }
+__host__ __device__ inline long long frame_size(int N) { return (long long)(N + 2) * frame_pitch(N); }
+__host__ __device__ inline long long vec_len(int N) { return 3 * frame_size(N) + NSCAL; }
+
+// Ghost-class rows of one level (object ghosts first, in (grid, j, i) order,
+// then walls and box ghosts), structure of arrays of capacity `cap`.
+struct GhostList {
+    int *count;        // device: [0] object ghosts, [1] all rows
+    int *node;         // global vector index of the row's own unknown
+    uint8_t *kind;
+    uint8_t *nst;
+    int *st;           // [GH_ST][cap] vector indices of the stencil nodes
+    double *w;         // [GH_ST][cap]
+    float *wf;         // [GH_ST][cap]
+    double *B;         // [2][cap] boundary point (Eq. BCu rows)
+    double *th;        // [2][cap] theta
+    double *upd;       // [cap] Jacobi update scratch
+    float *updf;
+    int cap;
+};
+
+// cut cells (internal cells with a ghost border) sorted by 25 colours
+struct CutList {
+    int *count;        // device [1]
+    int *off;          // device [26] colour offsets
+    int *cell;         // slot of the cell (row * P + col)
+    int *gface;        // [4][cap] ghost-list index of face W, E, S, N (or -1)
+    int cap;
+};
+
+struct Level {
+    int N;
+    int P;
+    long long F;       // frame size
+    long long VL;      // vector length
+    double h;
+    uint8_t *tU, *tV, *tP;
+    uint8_t *prim;     // [3 * F] ghost referenced by an internal row
+    uint8_t *done;     // [3 * F] ghost row computed (closure passes)
+    double *x, *b, *r; // vectors owned by the context (coarse levels; r on all)
+    float *xf, *bf, *rf;
+    GhostList gh;
+    CutList cut;
+    int *lonely;       // list of lonely internal faces (vector indices)
+    int *nlonely;      // device [1]
+    int lonely_cap;
+    int *nint;         // device [1] internal pressure cells
+    int h_nint;        // host copy
+    int h_nghost;      // host copies after geometry_build
+    int h_nrows;
+    int h_ncut;
+    int h_cutoff[26];
+    int h_nlonely;
+};
+
+struct Ctx {
+    gp_params prm;
+    cudaStream_t stream;
+    char *ws;
+    size_t ws_bytes;
+    int L;
+    Level lv[MAX_LEVELS];
+    double *phi;        // paper-sign half lattice (2N+1)^2
+    // coarsest level dense inverse
+    int nc;             // unknowns of the coarsest level (flat order)
+    double *Minv;       // nc x nc
+    float *Minvf;
+    double *aug;        // nc x 2nc work for Gauss-Jordan
+    int *cmap;          // flat index -> vector index on the coarsest level
+    double *cvec;       // 2 * nc gather/scatter buffer
+    float *cvecf;
+    int *piv;           // device pivot index
+    // reductions
+    double *part;       // block partials
+    int npart;
+    double *red;        // small result area (device)
+    unsigned long long *maxbits;
+    unsigned *err;      // device error word
+    int *flag;          // device change flag
+    double hostbuf[8];   // host staging for small device-to-host reads
+    int geom_ok;
+    int coarse_ok;
+    double alpha_factored;
+    char msg[256];
+};
+
+// ------------------------------------------------------------ indexing
+__host__ __device__ inline int slot_u(int P, int i, int j) { return (j + 1) * P + (i + 1); }
+
+__device__ inline bool in_grid(int g, int N, int i, int j)
+{
+    if (g == G_U) return i >= 0 && i <= N && j >= -1 && j <= N;
+    if (g == G_V) return i >= -1 && i <= N && j >= 0 && j <= N;
+    return i >= 0 && i < N && j >= 0 && j < N;
+}
+
+}  // namespace gpmg

@@ -1,0 +1,713 @@
+// Operator, relaxation and transfer kernels of one multigrid level
+// (Sect. 3.2 rows, Sect. 4.1 relaxation, Sect. 4.2 restriction, Sect. 4.3
+// interpolation), in FP64 and FP32.
+#include <cmath>
+#include <cstdio>
+
+#include "gpmg_internal.cuh"
+
+namespace gpmg {
+
+template <typename T> struct LevelArgs {
+    int N, P;
+    long long F;
+    T q, a, d;          // 1/h, alpha/h^2, 1 + 4 alpha/h^2
+    T h2;               // h^2
+    const uint8_t *tU, *tV, *tP;
+};
+
+template <typename T> __device__ inline const T *gw(const GhostList &gh);
+template <> __device__ inline const double *gw<double>(const GhostList &gh) { return gh.w; }
+template <> __device__ inline const float *gw<float>(const GhostList &gh) { return gh.wf; }
+template <typename T> __device__ inline T *gupd(const GhostList &gh);
+template <> __device__ inline double *gupd<double>(const GhostList &gh) { return gh.upd; }
+template <> __device__ inline float *gupd<float>(const GhostList &gh) { return gh.updf; }
+
+__device__ inline double nanmax(double a, double b) { return (a != a || b != b) ? (double)NAN : fmax(a, b); }
+
+// ---------------------------------------------------------------- residual
+
+// internal and inactive rows; ghost-class rows come from k_ghost_residual.
+// per block: [0] sum of p over internal cells, [1] max |r|
+template <typename T>
+__global__ void k_residual(LevelArgs<T> A, const T *x, const T *b, T *r, double *part)
+{
+    int col = blockIdx.x * blockDim.x + threadIdx.x;
+    int row = blockIdx.y;
+    double psum = 0.0, rmax = 0.0;
+    if (col < A.P) {
+        long long s = (long long)row * A.P + col;
+        const T *u = x, *v = x + A.F, *p = x + 2 * A.F;
+        T xi = x[3 * A.F];
+        uint8_t tu = A.tU[s], tv = A.tV[s], tp = A.tP[s];
+        if (tu == T_INTERNAL) {
+            T Au = A.d * u[s] - A.a * (u[s + 1] + u[s - 1] + u[s + A.P] + u[s - A.P]) + A.q * (p[s] - p[s - 1]);
+            T rr = b[s] - Au;
+            r[s] = rr;
+            rmax = nanmax(rmax, fabs((double)rr));
+        } else if (tu == T_INACTIVE) r[s] = 0;
+        if (tv == T_INTERNAL) {
+            long long sv = A.F + s;
+            T Av = A.d * v[s] - A.a * (v[s + 1] + v[s - 1] + v[s + A.P] + v[s - A.P]) + A.q * (p[s] - p[s - A.P]);
+            T rr = b[sv] - Av;
+            r[sv] = rr;
+            rmax = nanmax(rmax, fabs((double)rr));
+        } else if (tv == T_INACTIVE) r[A.F + s] = 0;
+        if (tp == T_INTERNAL) {
+            long long sp = 2 * A.F + s;
+            T Ac = A.q * (u[s + 1] - u[s] + v[s + A.P] - v[s]) - xi;
+            T rr = b[sp] - Ac;
+            r[sp] = rr;
+            rmax = nanmax(rmax, fabs((double)rr));
+            psum = (double)p[s];
+        } else if (tp == T_INACTIVE) r[2 * A.F + s] = 0;
+    }
+    // block reduction (fixed shape: deterministic)
+    __shared__ double ss[256], sm[256];
+    ss[threadIdx.x] = psum;
+    sm[threadIdx.x] = rmax;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            ss[threadIdx.x] += ss[threadIdx.x + o];
+            sm[threadIdx.x] = nanmax(sm[threadIdx.x], sm[threadIdx.x + o]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        long long bid = (long long)blockIdx.y * gridDim.x + blockIdx.x;
+        part[2 * bid] = ss[0];
+        part[2 * bid + 1] = sm[0];
+    }
+}
+
+template <typename T>
+__global__ void k_ghost_residual(GhostList gh, int nrows, const T *x, const T *b, T *r, unsigned long long *maxbits)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    double m = 0.0;
+    if (k < nrows) {
+        const T *w = gw<T>(gh);
+        int nst = gh.nst[k];
+        int node = gh.node[k];
+        T s = b[node];
+        for (int q = 0; q < nst; q++) s -= w[(long long)q * gh.cap + k] * x[gh.st[(long long)q * gh.cap + k]];
+        r[node] = s;
+        m = fabs((double)s);
+    }
+    // warp max then one atomic per warp (max of non-negative doubles by bits)
+    for (int o = 16; o > 0; o >>= 1) m = nanmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(maxbits, (unsigned long long)__double_as_longlong(m));
+    if ((threadIdx.x & 31) == 0 && m != m) atomicMax(maxbits, 0x7ff8000000000000ull);
+}
+
+// mean row (h^2 * sum of internal p) and the norm; one block
+template <typename T>
+__global__ void k_residual_final(const double *part, int nb, const T *b, T *r, long long imean, double h2,
+                                 unsigned long long *maxbits, double *out)
+{
+    __shared__ double ss[256], sm[256];
+    double s = 0.0, m = 0.0;
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+        s += part[2 * k];
+        m = nanmax(m, part[2 * k + 1]);
+    }
+    ss[threadIdx.x] = s;
+    sm[threadIdx.x] = m;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            ss[threadIdx.x] += ss[threadIdx.x + o];
+            sm[threadIdx.x] = nanmax(sm[threadIdx.x], sm[threadIdx.x + o]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double rm = (double)b[imean] - h2 * ss[0];
+        r[imean] = (T)rm;
+        double g = __longlong_as_double((long long)*maxbits);
+        double nrm = nanmax(nanmax(sm[0], g), fabs(rm));
+        out[0] = nrm;
+        *maxbits = 0ull;
+    }
+}
+
+// ------------------------------------------------------------ box smoother
+
+// full boxes (no ghost border): Schur complement of the pressure unknown,
+// colour (i + 3 j) mod 5; borders that are not internal stay frozen
+template <typename T>
+__global__ void k_box_full(LevelArgs<T> A, T *x, const T *b, int colour)
+{
+    int j = blockIdx.y;
+    int i0 = ((colour - 3 * j) % 5 + 5) % 5;
+    int i = i0 + 5 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (i >= A.N) return;
+    long long s = (long long)(j + 1) * A.P + (i + 1);
+    if (A.tP[s] != T_INTERNAL) return;
+    uint8_t tW = A.tU[s], tE = A.tU[s + 1], tS = A.tV[s], tN = A.tV[s + A.P];
+    if (tW == T_GHOST || tE == T_GHOST || tS == T_GHOST || tN == T_GHOST) return;
+    T *u = x, *v = x + A.F, *p = x + 2 * A.F;
+    const T *bu = b, *bv = b + A.F, *bp = b + 2 * A.F;
+    T xi = x[3 * A.F];
+    const T a = A.a, d = A.d, q = A.q;
+    bool W = tW == T_INTERNAL, E = tE == T_INTERNAL, S = tS == T_INTERNAL, Nn = tN == T_INTERNAL;
+    T rW = 0, rE = 0, rS = 0, rN = 0;
+    if (W) rW = bu[s] - (d * u[s] - a * (u[s + 1] + u[s - 1] + u[s + A.P] + u[s - A.P]) + q * (p[s] - p[s - 1]));
+    if (E) {
+        long long e = s + 1;
+        rE = bu[e] - (d * u[e] - a * (u[e + 1] + u[e - 1] + u[e + A.P] + u[e - A.P]) + q * (p[e] - p[e - 1]));
+    }
+    if (S) rS = bv[s] - (d * v[s] - a * (v[s + 1] + v[s - 1] + v[s + A.P] + v[s - A.P]) + q * (p[s] - p[s - A.P]));
+    if (Nn) {
+        long long n = s + A.P;
+        rN = bv[n] - (d * v[n] - a * (v[n + 1] + v[n - 1] + v[n + A.P] + v[n - A.P]) + q * (p[n] - p[n - A.P]));
+    }
+    T rC = bp[s] - (q * (u[s + 1] - u[s] + v[s + A.P] - v[s]) - xi);
+    // each direction contributes c0 + c1 * dp to the continuity update
+    T c0 = 0, c1 = 0;
+    if (W && E) {
+        T inv = (T)1 / (d + a);
+        c0 += q * (rE - rW) * inv;
+        c1 += 2 * q * q * inv;
+    } else if (W) {
+        c0 += -q * rW / d;
+        c1 += q * q / d;
+    } else if (E) {
+        c0 += q * rE / d;
+        c1 += q * q / d;
+    }
+    if (S && Nn) {
+        T inv = (T)1 / (d + a);
+        c0 += q * (rN - rS) * inv;
+        c1 += 2 * q * q * inv;
+    } else if (S) {
+        c0 += -q * rS / d;
+        c1 += q * q / d;
+    } else if (Nn) {
+        c0 += q * rN / d;
+        c1 += q * q / d;
+    }
+    if (c1 == (T)0) return;
+    T dp = (rC - c0) / c1;
+    // velocity corrections with dp known
+    T fW = rW - q * dp, fE = rE + q * dp, fS = rS - q * dp, fN = rN + q * dp;
+    if (W && E) {
+        T det = d * d - a * a;
+        u[s] += (d * fW + a * fE) / det;
+        u[s + 1] += (a * fW + d * fE) / det;
+    } else if (W) u[s] += fW / d;
+    else if (E) u[s + 1] += fE / d;
+    if (S && Nn) {
+        T det = d * d - a * a;
+        v[s] += (d * fS + a * fN) / det;
+        v[s + A.P] += (a * fS + d * fN) / det;
+    } else if (S) v[s] += fS / d;
+    else if (Nn) v[s + A.P] += fN / d;
+    p[s] += dp;
+}
+
+// cut boxes of one colour (i mod 5, j mod 5): p, the internal borders
+// (momentum rows) and the ghost borders (their ghost rows) solved together by
+// a pivoted LU of at most 5 x 5
+template <typename T>
+__global__ void k_box_cut(LevelArgs<T> A, T *x, const T *b, CutList cut, GhostList gh, int beg, int end)
+{
+    int k = beg + blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= end) return;
+    long long s = cut.cell[k];
+    const long long F = A.F;
+    const T *w = gw<T>(gh);
+    // face unknowns: W, E, S, N as vector indices
+    long long fidx[4] = {s, s + 1, F + s, F + s + A.P};
+    uint8_t ft[4] = {A.tU[s], A.tU[s + 1], A.tV[s], A.tV[s + A.P]};
+    long long unk[5];
+    int row_kind[5], row_f[5];
+    int n = 0;
+    for (int f = 0; f < 4; f++)
+        if (ft[f] == T_INTERNAL || ft[f] == T_GHOST) {
+            unk[n] = fidx[f];
+            row_kind[n] = ft[f];
+            row_f[n] = f;
+            n++;
+        }
+    unk[n] = 2 * F + s;
+    row_kind[n] = -1;
+    row_f[n] = -1;
+    n++;
+    T M[25], rhs[5];
+    const T a = A.a, d = A.d, q = A.q;
+    for (int r = 0; r < n; r++) {
+        for (int c = 0; c < n; c++) M[r * n + c] = 0;
+        if (row_kind[r] == T_INTERNAL) {
+            // momentum row of face f: centre d, 4 neighbours -a, pressure pair
+            long long o = unk[r];
+            bool isu = row_f[r] < 2;
+            long long loc = isu ? o : o - F;
+            const T *xx = isu ? x : x + F;
+            const T *pp = x + 2 * F;
+            long long pm = isu ? loc - 1 : loc - A.P;  // the other pressure cell
+            T Ax = d * xx[loc] - a * (xx[loc + 1] + xx[loc - 1] + xx[loc + A.P] + xx[loc - A.P]) + q * (pp[loc] - pp[pm]);
+            rhs[r] = b[o] - Ax;
+            long long nb[4] = {o + 1, o - 1, o + A.P, o - A.P};
+            for (int c = 0; c < n; c++) {
+                if (unk[c] == o) M[r * n + c] += d;
+                for (int m = 0; m < 4; m++)
+                    if (unk[c] == nb[m]) M[r * n + c] -= a;
+                if (unk[c] == 2 * F + loc) M[r * n + c] += q;
+                if (unk[c] == 2 * F + pm) M[r * n + c] -= q;
+            }
+        } else if (row_kind[r] == T_GHOST) {
+            int g = cut.gface[(long long)row_f[r] * cut.cap + k];
+            int nst = gh.nst[g];
+            T acc = b[gh.node[g]];
+            for (int m = 0; m < nst; m++) {
+                int id = gh.st[(long long)m * gh.cap + g];
+                T wm = w[(long long)m * gh.cap + g];
+                acc -= wm * x[id];
+                for (int c = 0; c < n; c++)
+                    if (unk[c] == id) M[r * n + c] += wm;
+            }
+            rhs[r] = acc;
+        } else {
+            // continuity row of the cell
+            const T *u = x, *v = x + F;
+            T xi = x[3 * F];
+            rhs[r] = b[2 * F + s] - (q * (u[s + 1] - u[s] + v[s + A.P] - v[s]) - xi);
+            for (int c = 0; c < n; c++) {
+                if (unk[c] == s + 1) M[r * n + c] += q;
+                if (unk[c] == s) M[r * n + c] -= q;
+                if (unk[c] == F + s + A.P) M[r * n + c] += q;
+                if (unk[c] == F + s) M[r * n + c] -= q;
+            }
+        }
+    }
+    // LU with partial pivoting (first largest pivot)
+    int piv[5];
+    for (int c = 0; c < n; c++) {
+        int pr = c;
+        T best = fabs(M[c * n + c]);
+        for (int r = c + 1; r < n; r++) {
+            T vv = fabs(M[r * n + c]);
+            if (vv > best) { best = vv; pr = r; }
+        }
+        piv[c] = pr;
+        if (!(best > (T)0)) return;
+        if (pr != c)
+            for (int m = 0; m < n; m++) { T t = M[c * n + m]; M[c * n + m] = M[pr * n + m]; M[pr * n + m] = t; }
+        for (int r = c + 1; r < n; r++) {
+            T f = M[r * n + c] / M[c * n + c];
+            M[r * n + c] = f;
+            for (int m = c + 1; m < n; m++) M[r * n + m] -= f * M[c * n + m];
+        }
+    }
+    for (int c = 0; c < n; c++)
+        if (piv[c] != c) { T t = rhs[c]; rhs[c] = rhs[piv[c]]; rhs[piv[c]] = t; }
+    for (int r = 0; r < n; r++)
+        for (int m = 0; m < r; m++) rhs[r] -= M[r * n + m] * rhs[m];
+    for (int r = n - 1; r >= 0; r--) {
+        for (int m = r + 1; m < n; m++) rhs[r] -= M[r * n + m] * rhs[m];
+        rhs[r] /= M[r * n + r];
+    }
+    for (int r = 0; r < n; r++) x[unk[r]] += rhs[r];
+}
+
+// internal faces with no internal cell: point Jacobi (compute, then apply)
+template <typename T>
+__global__ void k_lonely_update(LevelArgs<T> A, const T *x, const T *b, const int *list, int n, T *upd)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    long long o = list[k];
+    bool isu = o < A.F;
+    long long loc = isu ? o : o - A.F;
+    const T *xx = isu ? x : x + A.F;
+    const T *pp = x + 2 * A.F;
+    long long pm = isu ? loc - 1 : loc - A.P;
+    T Ax = A.d * xx[loc] - A.a * (xx[loc + 1] + xx[loc - 1] + xx[loc + A.P] + xx[loc - A.P]) + A.q * (pp[loc] - pp[pm]);
+    upd[k] = (b[o] - Ax) / A.d;
+}
+
+template <typename T> __global__ void k_apply_list(T *x, const int *list, const T *upd, int n)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) x[list[k]] += upd[k];
+}
+
+// ------------------------------------------------------- xi / mean pressure
+
+template <typename T>
+__global__ void k_scalar_partial(LevelArgs<T> A, const T *x, const T *b, double *part)
+{
+    int col = blockIdx.x * blockDim.x + threadIdx.x;
+    int row = blockIdx.y;
+    double s = 0.0, m = 0.0;
+    if (col < A.P) {
+        long long sl = (long long)row * A.P + col;
+        if (A.tP[sl] == T_INTERNAL) {
+            const T *u = x, *v = x + A.F;
+            T div = (u[sl + 1] - u[sl] + v[sl + A.P] - v[sl]) * A.q;
+            s = (double)(div - b[2 * A.F + sl]);
+            m = (double)x[2 * A.F + sl];
+        }
+    }
+    __shared__ double ss[256], sm[256];
+    ss[threadIdx.x] = s;
+    sm[threadIdx.x] = m;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            ss[threadIdx.x] += ss[threadIdx.x + o];
+            sm[threadIdx.x] += sm[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        long long bid = (long long)blockIdx.y * gridDim.x + blockIdx.x;
+        part[2 * bid] = ss[0];
+        part[2 * bid + 1] = sm[0];
+    }
+}
+
+// xi <- mean(div u - b_c); shift <- (b_mean - h^2 sum p) / (h^2 n_int)
+template <typename T>
+__global__ void k_scalar_final(const double *part, int nb, T *x, const T *b, long long imean, double h2, const int *nint,
+                               double *shift)
+{
+    __shared__ double ss[256], sm[256];
+    double s = 0.0, m = 0.0;
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+        s += part[2 * k];
+        m += part[2 * k + 1];
+    }
+    ss[threadIdx.x] = s;
+    sm[threadIdx.x] = m;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            ss[threadIdx.x] += ss[threadIdx.x + o];
+            sm[threadIdx.x] += sm[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double n = (double)*nint;
+        x[imean] = (T)(ss[0] / n);
+        shift[0] = ((double)b[imean] - h2 * sm[0]) / (h2 * n);
+    }
+}
+
+template <typename T> __global__ void k_pshift(LevelArgs<T> A, T *x, const double *shift)
+{
+    int col = blockIdx.x * blockDim.x + threadIdx.x;
+    int row = blockIdx.y;
+    if (col >= A.P) return;
+    long long s = (long long)row * A.P + col;
+    uint8_t t = A.tP[s];
+    if (t == T_INTERNAL || t == T_GHOST) x[2 * A.F + s] += (T)shift[0];
+}
+
+// --------------------------------------------------------- ghost relaxation
+
+// Eq. (ghostrelax), Jacobi over every ghost-class row: w += dtau (g - B w)
+template <typename T>
+__global__ void k_ghost_update(GhostList gh, int nrows, const T *x, const T *b, T dtau)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nrows) return;
+    const T *w = gw<T>(gh);
+    int nst = gh.nst[k];
+    T s = b[gh.node[k]];
+    for (int q = 0; q < nst; q++) s -= w[(long long)q * gh.cap + k] * x[gh.st[(long long)q * gh.cap + k]];
+    gupd<T>(gh)[k] = dtau * s;
+}
+
+template <typename T> __global__ void k_ghost_apply(GhostList gh, int nrows, T *x)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < nrows) x[gh.node[k]] += gupd<T>(gh)[k];
+}
+
+// ---------------------------------------------------------------- transfers
+
+__device__ inline bool same_class(uint8_t tc, uint8_t tf)
+{
+    if (tc == T_INTERNAL) return tf == T_INTERNAL;
+    return tf == T_GHOST || tf == T_WALL || tf == T_BOXGHOST;
+}
+
+__device__ inline uint8_t tget(const uint8_t *t, int g, int N, int P, int i, int j)
+{
+    if (!in_grid(g, N, i, j)) return T_INACTIVE;
+    return t[(long long)(j + 1) * P + (i + 1)];
+}
+
+// Eq. (restop) where the whole stencil is of the coarse node's class,
+// otherwise the plain mean of the fine residuals of that class (Eq. restop5)
+template <typename T>
+__global__ void k_restrict(int Nf, int Pf, long long Ff, const uint8_t *tUf, const uint8_t *tVf, const uint8_t *tPf,
+                           int Nc, int Pc, long long Fc, const uint8_t *tUc, const uint8_t *tVc, const uint8_t *tPc,
+                           const T *r, T *bH)
+{
+    int col = blockIdx.x * blockDim.x + threadIdx.x;
+    int row = blockIdx.y;
+    if (col >= Pc) return;
+    int I = col - 1, J = row - 1;
+    long long sc = (long long)row * Pc + col;
+    const uint8_t *tf[3] = {tUf, tVf, tPf};
+    const uint8_t *tc[3] = {tUc, tVc, tPc};
+    for (int g = 0; g < 3; g++) {
+        uint8_t t = tc[g][sc];
+        if (t == T_INACTIVE) {
+            bH[g * Fc + sc] = 0;
+            continue;
+        }
+        int fi[6], fj[6], ns = 0;
+        T wt[6];
+        if (g == G_U) {
+            for (int dj = 0; dj <= 1; dj++)
+                for (int di = -1; di <= 1; di++) { fi[ns] = 2 * I + di; fj[ns] = 2 * J + dj; wt[ns] = (T)(di == 0 ? 0.25 : 0.125); ns++; }
+        } else if (g == G_V) {
+            for (int dj = -1; dj <= 1; dj++)
+                for (int di = 0; di <= 1; di++) { fi[ns] = 2 * I + di; fj[ns] = 2 * J + dj; wt[ns] = (T)(dj == 0 ? 0.25 : 0.125); ns++; }
+        } else {
+            for (int dj = 0; dj <= 1; dj++)
+                for (int di = 0; di <= 1; di++) { fi[ns] = 2 * I + di; fj[ns] = 2 * J + dj; wt[ns] = (T)0.25; ns++; }
+        }
+        bool all = true;
+        int cnt = 0;
+        T sw = 0, su = 0;
+        for (int k = 0; k < ns; k++) {
+            uint8_t tff = tget(tf[g], g, Nf, Pf, fi[k], fj[k]);
+            if (same_class(t, tff)) {
+                T v = r[g * Ff + (long long)(fj[k] + 1) * Pf + (fi[k] + 1)];
+                sw += wt[k] * v;
+                su += v;
+                cnt++;
+            } else all = false;
+        }
+        bH[g * Fc + sc] = all ? sw : (cnt > 0 ? su / (T)cnt : (T)0);
+    }
+    if (row == 0 && col == 0) bH[3 * Fc] = r[3 * Ff];
+}
+
+// 1-D interpolation taps (see the oracle's description of the same rule)
+__device__ inline int taps(int k, bool aligned, int lo, int hi, int *K, double *w)
+{
+    bool even = (k % 2 == 0);
+    if (aligned) {
+        if (even) { K[0] = k / 2; w[0] = 1.0; return 1; }
+        K[0] = (k - 1) / 2; w[0] = 0.5;
+        K[1] = K[0] + 1; w[1] = 0.5;
+        return 2;
+    }
+    int Kc = even ? k / 2 : (k - 1) / 2;
+    int Ko = even ? Kc - 1 : Kc + 1;
+    if (Ko < lo || Ko > hi) {
+        K[0] = Kc; w[0] = 1.25;
+        K[1] = 2 * Kc - Ko; w[1] = -0.25;
+        return 2;
+    }
+    K[0] = Kc; w[0] = 0.75;
+    K[1] = Ko; w[1] = 0.25;
+    return 2;
+}
+
+// bilinear interpolation over the active coarse nodes (weights renormalised)
+// added to every active fine node
+template <typename T>
+__global__ void k_prolong(int Nf, int Pf, long long Ff, const uint8_t *tUf, const uint8_t *tVf, const uint8_t *tPf,
+                          int Nc, int Pc, long long Fc, const uint8_t *tUc, const uint8_t *tVc, const uint8_t *tPc,
+                          const T *eH, T *x)
+{
+    int col = blockIdx.x * blockDim.x + threadIdx.x;
+    int row = blockIdx.y;
+    if (col >= Pf) return;
+    int i = col - 1, j = row - 1;
+    long long sf = (long long)row * Pf + col;
+    const uint8_t *tf[3] = {tUf, tVf, tPf};
+    const uint8_t *tc[3] = {tUc, tVc, tPc};
+    for (int g = 0; g < 3; g++) {
+        if (!in_grid(g, Nf, i, j) || tf[g][sf] == T_INACTIVE) continue;
+        int Ilo = g == G_V ? -1 : 0, Ihi = g == G_P ? Nc - 1 : Nc;
+        int Jlo = g == G_U ? -1 : 0, Jhi = g == G_P ? Nc - 1 : Nc;
+        int KI[2], KJ[2];
+        double wi[2], wj[2];
+        int ni = taps(i, g == G_U, Ilo, Ihi, KI, wi);
+        int nj = taps(j, g == G_V, Jlo, Jhi, KJ, wj);
+        double s = 0.0, ws = 0.0;
+        for (int a = 0; a < nj; a++)
+            for (int bb = 0; bb < ni; bb++) {
+                if (tget(tc[g], g, Nc, Pc, KI[bb], KJ[a]) == T_INACTIVE) continue;
+                double w = wj[a] * wi[bb];
+                s += w * (double)eH[g * Fc + (long long)(KJ[a] + 1) * Pc + (KI[bb] + 1)];
+                ws += w;
+            }
+        if (ws > 0.0) x[g * Ff + sf] += (T)(s / ws);
+    }
+    if (row == 0 && col == 0) x[3 * Ff] += eH[3 * Fc];
+}
+
+template <typename T> __global__ void k_zero(T *x, long long n)
+{
+    long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k < n) x[k] = 0;
+}
+
+// x = 0 on inactive nodes of a level
+template <typename T> __global__ void k_zero_inactive(LevelArgs<T> A, T *x)
+{
+    int col = blockIdx.x * blockDim.x + threadIdx.x;
+    int row = blockIdx.y;
+    if (col >= A.P) return;
+    long long s = (long long)row * A.P + col;
+    if (A.tU[s] == T_INACTIVE) x[s] = 0;
+    if (A.tV[s] == T_INACTIVE) x[A.F + s] = 0;
+    if (A.tP[s] == T_INACTIVE) x[2 * A.F + s] = 0;
+}
+
+__global__ void k_to_float(const double *a, float *b, long long n)
+{
+    long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k < n) b[k] = (float)a[k];
+}
+
+__global__ void k_add_float(double *x, const float *e, long long n)
+{
+    long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k < n) x[k] += (double)e[k];
+}
+
+// ----------------------------------------------------------- host wrappers
+
+template <typename T> LevelArgs<T> level_args(const Ctx *c, int lev)
+{
+    const Level &l = c->lv[lev];
+    LevelArgs<T> A;
+    A.N = l.N;
+    A.P = l.P;
+    A.F = l.F;
+    double h = c->prm.L / (double)l.N;
+    A.q = (T)(1.0 / h);
+    A.a = (T)(c->prm.alpha / (h * h));
+    A.d = (T)(1.0 + 4.0 * (c->prm.alpha / (h * h)));
+    A.h2 = (T)(h * h);
+    A.tU = l.tU;
+    A.tV = l.tV;
+    A.tP = l.tP;
+    return A;
+}
+
+static inline dim3 frame_grid(const Level &l) { return dim3((l.P + 255) / 256, l.N + 2); }
+
+template <typename T> void residual(Ctx *c, int lev, const T *x, const T *b, T *r)
+{
+    const Level &l = c->lv[lev];
+    cudaStream_t st = c->stream;
+    dim3 g = frame_grid(l);
+    int nb = g.x * g.y;
+    k_residual<T><<<g, 256, 0, st>>>(level_args<T>(c, lev), x, b, r, c->part);
+    if (l.h_nrows > 0) k_ghost_residual<T><<<(l.h_nrows + 255) / 256, 256, 0, st>>>(l.gh, l.h_nrows, x, b, r, c->maxbits);
+    double h = c->prm.L / (double)l.N;
+    k_residual_final<T><<<1, 256, 0, st>>>(c->part, nb, b, r, 3 * l.F, h * h, c->maxbits, c->red);
+}
+
+template <typename T> void box_sweep(Ctx *c, int lev, T *x, const T *b)
+{
+    const Level &l = c->lv[lev];
+    cudaStream_t st = c->stream;
+    LevelArgs<T> A = level_args<T>(c, lev);
+    int per_row = (l.N + 4) / 5;
+    dim3 g((per_row + 127) / 128, l.N);
+    for (int colour = 0; colour < 5; colour++) k_box_full<T><<<g, 128, 0, st>>>(A, x, b, colour);
+    for (int colour = 0; colour < 25; colour++) {
+        int beg = l.h_cutoff[colour], end = l.h_cutoff[colour + 1];
+        if (end > beg) k_box_cut<T><<<(end - beg + 127) / 128, 128, 0, st>>>(A, x, b, l.cut, l.gh, beg, end);
+    }
+    if (l.h_nlonely > 0) {
+        T *upd = (T *)c->part;
+        k_lonely_update<T><<<(l.h_nlonely + 127) / 128, 128, 0, st>>>(A, x, b, l.lonely, l.h_nlonely, upd);
+        k_apply_list<T><<<(l.h_nlonely + 127) / 128, 128, 0, st>>>(x, l.lonely, upd, l.h_nlonely);
+    }
+}
+
+template <typename T> void scalar_update(Ctx *c, int lev, T *x, const T *b)
+{
+    const Level &l = c->lv[lev];
+    cudaStream_t st = c->stream;
+    LevelArgs<T> A = level_args<T>(c, lev);
+    dim3 g = frame_grid(l);
+    int nb = g.x * g.y;
+    k_scalar_partial<T><<<g, 256, 0, st>>>(A, x, b, c->part);
+    double h = c->prm.L / (double)l.N;
+    k_scalar_final<T><<<1, 256, 0, st>>>(c->part, nb, x, b, 3 * l.F, h * h, l.nint, c->red + 1);
+    k_pshift<T><<<g, 256, 0, st>>>(A, x, c->red + 1);
+}
+
+template <typename T> void ghost_sweep(Ctx *c, int lev, T *x, const T *b)
+{
+    const Level &l = c->lv[lev];
+    if (l.h_nrows <= 0) return;
+    cudaStream_t st = c->stream;
+    int nb = (l.h_nrows + 255) / 256;
+    k_ghost_update<T><<<nb, 256, 0, st>>>(l.gh, l.h_nrows, x, b, (T)c->prm.dtau);
+    k_ghost_apply<T><<<nb, 256, 0, st>>>(l.gh, l.h_nrows, x);
+}
+
+template <typename T> void smooth(Ctx *c, int lev, T *x, const T *b, int nu)
+{
+    for (int s = 0; s < nu; s++) {
+        box_sweep<T>(c, lev, x, b);
+        scalar_update<T>(c, lev, x, b);
+        for (int k = 0; k < c->prm.lambda; k++) ghost_sweep<T>(c, lev, x, b);
+    }
+}
+
+template <typename T> void restrict_level(Ctx *c, int lev, const T *r, T *bH)
+{
+    const Level &f = c->lv[lev], &C = c->lv[lev + 1];
+    dim3 g((C.P + 255) / 256, C.N + 2);
+    k_restrict<T><<<g, 256, 0, c->stream>>>(f.N, f.P, f.F, f.tU, f.tV, f.tP, C.N, C.P, C.F, C.tU, C.tV, C.tP, r, bH);
+}
+
+template <typename T> void prolong_level(Ctx *c, int lev, const T *eH, T *x)
+{
+    const Level &f = c->lv[lev], &C = c->lv[lev + 1];
+    dim3 g((f.P + 255) / 256, f.N + 2);
+    k_prolong<T><<<g, 256, 0, c->stream>>>(f.N, f.P, f.F, f.tU, f.tV, f.tP, C.N, C.P, C.F, C.tU, C.tV, C.tP, eH, x);
+}
+
+template <typename T> void zero_vec(Ctx *c, T *x, long long n)
+{
+    k_zero<T><<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(x, n);
+}
+
+template <typename T> void zero_inactive(Ctx *c, int lev, T *x)
+{
+    k_zero_inactive<T><<<frame_grid(c->lv[lev]), 256, 0, c->stream>>>(level_args<T>(c, lev), x);
+}
+
+void to_float(Ctx *c, const double *a, float *b, long long n)
+{
+    k_to_float<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(a, b, n);
+}
+
+void add_float(Ctx *c, double *x, const float *e, long long n)
+{
+    k_add_float<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(x, e, n);
+}
+
+#define INST(T)                                                                 \
+    template void residual<T>(Ctx *, int, const T *, const T *, T *);           \
+    template void box_sweep<T>(Ctx *, int, T *, const T *);                     \
+    template void scalar_update<T>(Ctx *, int, T *, const T *);                 \
+    template void ghost_sweep<T>(Ctx *, int, T *, const T *);                   \
+    template void smooth<T>(Ctx *, int, T *, const T *, int);                   \
+    template void restrict_level<T>(Ctx *, int, const T *, T *);                \
+    template void prolong_level<T>(Ctx *, int, const T *, T *);                 \
+    template void zero_vec<T>(Ctx *, T *, long long);                           \
+    template void zero_inactive<T>(Ctx *, int, T *);
+INST(double)
+INST(float)
+
+}  // namespace gpmg

@@ -1,0 +1,534 @@
+// Context, workspace layout, cycle driver and the C ABI (include/gpmg.h).
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "gpmg_internal.cuh"
+
+namespace gpmg {
+
+int build_geometry_levels(Ctx *c, const double *phi_in, int phi_fluid_positive);
+int build_coarse_inverse(Ctx *c);
+void coarse_maps_host(int N, int P, long long F, int *cmap, int *inv, long long vl);
+template <typename T> void residual(Ctx *c, int lev, const T *x, const T *b, T *r);
+template <typename T> void box_sweep(Ctx *c, int lev, T *x, const T *b);
+template <typename T> void scalar_update(Ctx *c, int lev, T *x, const T *b);
+template <typename T> void ghost_sweep(Ctx *c, int lev, T *x, const T *b);
+template <typename T> void smooth(Ctx *c, int lev, T *x, const T *b, int nu);
+template <typename T> void restrict_level(Ctx *c, int lev, const T *r, T *bH);
+template <typename T> void prolong_level(Ctx *c, int lev, const T *eH, T *x);
+template <typename T> void zero_vec(Ctx *c, T *x, long long n);
+template <typename T> void zero_inactive(Ctx *c, int lev, T *x);
+template <typename T> void coarse_solve(Ctx *c, const T *b, T *x);
+void to_float(Ctx *c, const double *a, float *b, long long n);
+void add_float(Ctx *c, double *x, const float *e, long long n);
+
+// ------------------------------------------------------------- workspace
+
+struct Carver {
+    char *base;
+    size_t off;
+    template <typename T> T *take(size_t count)
+    {
+        off = (off + 255) & ~(size_t)255;
+        T *p = base ? (T *)(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+static int ghost_cap(int N) { return 48 * (N + 2) + 8 * N + 1024; }
+static int cut_cap(int N) { return 16 * (N + 2) + 256; }
+static int lonely_cap(int N) { return 4 * (N + 2) + 64; }
+
+static int validate(const gp_params *p, char *msg, size_t nmsg)
+{
+    if (!p || p->N < 4 || p->levels < 1 || p->levels > MAX_LEVELS) {
+        snprintf(msg, nmsg, "invalid N or levels");
+        return 0;
+    }
+    if (p->N % (1 << (p->levels - 1)) != 0 || (p->N >> (p->levels - 1)) < 4) {
+        snprintf(msg, nmsg, "N must be divisible by 2^(levels-1) with a coarsest grid of at least 4 cells");
+        return 0;
+    }
+    if ((p->N >> (p->levels - 1)) > 64) {
+        snprintf(msg, nmsg, "coarsest grid larger than 64 cells per side (dense inverse too large)");
+        return 0;
+    }
+    if (!(p->L > 0.0) || !(p->alpha >= 0.0) || p->nu1 < 0 || p->nu2 < 0 || p->gamma < 1 || p->gamma > 2 ||
+        p->lambda < 0 || p->max_cycles < 1 || (p->precision != GP_FP64 && p->precision != GP_MIXED)) {
+        snprintf(msg, nmsg, "invalid solver parameters");
+        return 0;
+    }
+    if ((long long)(2 * p->N + 1) * (2 * p->N + 1) > (1ll << 40) || vec_len(p->N) * 3 > (1ll << 31)) {
+        snprintf(msg, nmsg, "grid too large for 32-bit vector indices");
+        return 0;
+    }
+    return 1;
+}
+
+// assigns every device array of the context (c may have base == null to size)
+static size_t carve(Ctx *c, char *base)
+{
+    Carver cv{base, 0};
+    const gp_params &p = c->prm;
+    int L = p.levels;
+    long long maxpart = 0;
+    for (int k = 0; k < L; k++) {
+        Level &l = c->lv[k];
+        l.N = p.N >> k;
+        l.P = frame_pitch(l.N);
+        l.F = frame_size(l.N);
+        l.VL = vec_len(l.N);
+        l.h = p.L / (double)l.N;
+        l.tU = cv.take<uint8_t>(l.F);
+        l.tV = cv.take<uint8_t>(l.F);
+        l.tP = cv.take<uint8_t>(l.F);
+        l.prim = cv.take<uint8_t>(3 * l.F);
+        l.done = cv.take<uint8_t>(3 * l.F);
+        l.r = cv.take<double>(l.VL);
+        if (k > 0) {
+            l.x = cv.take<double>(l.VL);
+            l.b = cv.take<double>(l.VL);
+        } else {
+            l.x = l.b = nullptr;
+        }
+        if (p.precision == GP_MIXED) {
+            l.xf = cv.take<float>(l.VL);
+            l.bf = cv.take<float>(l.VL);
+            l.rf = cv.take<float>(l.VL);
+        } else {
+            l.xf = l.bf = l.rf = nullptr;
+        }
+        int gc = ghost_cap(l.N);
+        GhostList &g = l.gh;
+        g.cap = gc;
+        g.count = cv.take<int>(2);
+        g.node = cv.take<int>(gc);
+        g.kind = cv.take<uint8_t>(gc);
+        g.nst = cv.take<uint8_t>(gc);
+        g.st = cv.take<int>((size_t)GH_ST * gc);
+        g.w = cv.take<double>((size_t)GH_ST * gc);
+        g.wf = cv.take<float>((size_t)GH_ST * gc);
+        g.B = cv.take<double>(2 * (size_t)gc);
+        g.th = cv.take<double>(2 * (size_t)gc);
+        g.upd = cv.take<double>(gc);
+        g.updf = cv.take<float>(gc);
+        int cc = cut_cap(l.N);
+        l.cut.cap = cc;
+        l.cut.count = cv.take<int>(1);
+        l.cut.off = cv.take<int>(26);
+        l.cut.cell = cv.take<int>(cc);
+        l.cut.gface = cv.take<int>(4 * (size_t)cc);
+        l.lonely_cap = lonely_cap(l.N);
+        l.lonely = cv.take<int>(l.lonely_cap);
+        l.nlonely = cv.take<int>(1);
+        l.nint = cv.take<int>(1);
+        long long nb = (long long)((l.P + 255) / 256) * (l.N + 2);
+        long long need = 2 * nb + 3 * (l.N + 2) + 64 + 2 * l.lonely_cap;
+        if (need > maxpart) maxpart = need;
+    }
+    c->phi = cv.take<double>((size_t)(2 * p.N + 1) * (2 * p.N + 1));
+    c->npart = (int)maxpart;
+    c->part = cv.take<double>(maxpart);
+    c->red = cv.take<double>(32);
+    c->maxbits = cv.take<unsigned long long>(4);
+    c->err = cv.take<unsigned>(4);
+    c->flag = cv.take<int>(4);
+    const Level &lc = c->lv[L - 1];
+    int nc = 2 * (lc.N + 1) * (lc.N + 2) + lc.N * lc.N + 1;
+    c->nc = nc;
+    c->Minv = cv.take<double>((size_t)nc * nc);
+    c->Minvf = cv.take<float>((size_t)nc * nc);
+    c->aug = cv.take<double>((size_t)nc * 2 * nc);
+    c->cmap = cv.take<int>((size_t)nc + lc.VL);
+    c->cvec = cv.take<double>(2 * (size_t)nc + 8);
+    c->cvecf = cv.take<float>(2 * (size_t)nc + 8);
+    return cv.off + 256;
+}
+
+// ------------------------------------------------------------------ cycle
+
+template <typename T> struct Vecs {
+    static T *x(Ctx *c, int l);
+    static T *b(Ctx *c, int l);
+    static T *r(Ctx *c, int l);
+};
+template <> double *Vecs<double>::x(Ctx *c, int l) { return c->lv[l].x; }
+template <> double *Vecs<double>::b(Ctx *c, int l) { return c->lv[l].b; }
+template <> double *Vecs<double>::r(Ctx *c, int l) { return c->lv[l].r; }
+template <> float *Vecs<float>::x(Ctx *c, int l) { return c->lv[l].xf; }
+template <> float *Vecs<float>::b(Ctx *c, int l) { return c->lv[l].bf; }
+template <> float *Vecs<float>::r(Ctx *c, int l) { return c->lv[l].rf; }
+
+template <typename T> void cycle_rec(Ctx *c, int lev, T *x, const T *b)
+{
+    if (lev == c->L - 1) {
+        coarse_solve<T>(c, b, x);
+        return;
+    }
+    smooth<T>(c, lev, x, b, c->prm.nu1);
+    T *r = Vecs<T>::r(c, lev);
+    residual<T>(c, lev, x, b, r);
+    T *xH = Vecs<T>::x(c, lev + 1), *bH = Vecs<T>::b(c, lev + 1);
+    restrict_level<T>(c, lev, r, bH);
+    zero_vec<T>(c, xH, c->lv[lev + 1].VL);
+    for (int k = 0; k < c->prm.gamma; k++) cycle_rec<T>(c, lev + 1, xH, bH);
+    prolong_level<T>(c, lev, xH, x);
+    smooth<T>(c, lev, x, b, c->prm.nu2);
+}
+
+}  // namespace gpmg
+
+using namespace gpmg;
+
+struct gp_ctx {
+    Ctx c;
+};
+
+static gp_status fail(gp_ctx *ctx, gp_status s, const char *m)
+{
+    if (ctx) snprintf(ctx->c.msg, sizeof ctx->c.msg, "%s", m);
+    return s;
+}
+
+static gp_status check_cuda(gp_ctx *ctx, const char *where)
+{
+    cudaError_t e = cudaPeekAtLastError();
+    if (e == cudaSuccess) return GP_OK;
+    cudaGetLastError();
+    snprintf(ctx->c.msg, sizeof ctx->c.msg, "%s: %s", where, cudaGetErrorString(e));
+    return GP_CUDA;
+}
+
+static gp_status ensure_coarse(gp_ctx *ctx)
+{
+    Ctx *c = &ctx->c;
+    if (!c->geom_ok) return fail(ctx, GP_INVALID, "geometry_build has not succeeded");
+    if (c->coarse_ok && c->alpha_factored == c->prm.alpha) return GP_OK;
+    return (gp_status)build_coarse_inverse(c);
+}
+
+static bool level_ok(gp_ctx *ctx, int level) { return ctx && level >= 0 && level < ctx->c.L; }
+
+extern "C" {
+
+gp_status gp_params_default(gp_params *prm, int N, double x0, double y0, double L)
+{
+    if (!prm || N < 4 || !(L > 0.0)) return GP_INVALID;
+    memset(prm, 0, sizeof *prm);
+    prm->N = N;
+    prm->x0 = x0;
+    prm->y0 = y0;
+    prm->L = L;
+    int lev = 1;
+    while ((N >> lev) >= 16 && (N >> (lev - 1)) > 16 && (N % (1 << lev)) == 0) lev++;
+    prm->levels = lev;
+    prm->alpha = L / N / 2.0;
+    prm->nu1 = 2;
+    prm->nu2 = 1;
+    prm->gamma = 1;
+    prm->lambda = 5;
+    prm->dtau = 0.9;
+    prm->snap = 0.3;
+    prm->precision = GP_FP64;
+    prm->max_cycles = 100;
+    return GP_OK;
+}
+
+int gp_pitch(int N) { return frame_pitch(N); }
+int64_t gp_vector_length(int N) { return vec_len(N); }
+
+gp_status gp_workspace_size(const gp_params *prm, size_t *bytes)
+{
+    char msg[256];
+    if (!bytes || !validate(prm, msg, sizeof msg)) return GP_INVALID;
+    Ctx *c = new (std::nothrow) Ctx();
+    if (!c) return GP_INVALID;
+    c->prm = *prm;
+    c->L = prm->levels;
+    *bytes = carve(c, nullptr);
+    delete c;
+    return GP_OK;
+}
+
+gp_status gp_create(gp_ctx **out, const gp_params *prm, void *workspace, size_t bytes, void *stream)
+{
+    if (!out) return GP_INVALID;
+    *out = nullptr;
+    gp_ctx *ctx = new (std::nothrow) gp_ctx();
+    if (!ctx) return GP_INVALID;
+    Ctx *c = &ctx->c;
+    if (!validate(prm, c->msg, sizeof c->msg)) {
+        delete ctx;
+        return GP_INVALID;
+    }
+    c->prm = *prm;
+    c->L = prm->levels;
+    size_t need = carve(c, nullptr);
+    if (!workspace || bytes < need || ((uintptr_t)workspace & 255)) {
+        delete ctx;
+        return GP_INVALID;
+    }
+    c->ws = (char *)workspace;
+    c->ws_bytes = bytes;
+    c->stream = (cudaStream_t)stream;
+    carve(c, c->ws);
+    // coarsest-level index maps (host -> device)
+    const Level &lc = c->lv[c->L - 1];
+    std::vector<int> maps((size_t)c->nc + lc.VL);
+    coarse_maps_host(lc.N, lc.P, lc.F, maps.data(), maps.data() + c->nc, lc.VL);
+    cudaError_t e = cudaMemcpyAsync(c->cmap, maps.data(), maps.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->maxbits, 0, 4 * sizeof(unsigned long long), c->stream);
+    for (int k = 0; k < c->L && e == cudaSuccess; k++) {
+        Level &l = c->lv[k];
+        e = cudaMemsetAsync(l.r, 0, l.VL * sizeof(double), c->stream);
+        if (e == cudaSuccess && l.x) e = cudaMemsetAsync(l.x, 0, l.VL * sizeof(double), c->stream);
+        if (e == cudaSuccess && l.b) e = cudaMemsetAsync(l.b, 0, l.VL * sizeof(double), c->stream);
+        if (e == cudaSuccess && l.xf) {
+            cudaMemsetAsync(l.xf, 0, l.VL * sizeof(float), c->stream);
+            cudaMemsetAsync(l.bf, 0, l.VL * sizeof(float), c->stream);
+            e = cudaMemsetAsync(l.rf, 0, l.VL * sizeof(float), c->stream);
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        delete ctx;
+        return GP_CUDA;
+    }
+    *out = ctx;
+    return GP_OK;
+}
+
+gp_status gp_destroy(gp_ctx *ctx)
+{
+    if (!ctx) return GP_INVALID;
+    cudaStreamSynchronize(ctx->c.stream);
+    delete ctx;
+    return GP_OK;
+}
+
+const char *gp_last_error(const gp_ctx *ctx) { return ctx ? ctx->c.msg : "null context"; }
+
+gp_status gp_set_alpha(gp_ctx *ctx, double alpha)
+{
+    if (!ctx || !(alpha >= 0.0)) return GP_INVALID;
+    ctx->c.prm.alpha = alpha;
+    return GP_OK;
+}
+
+gp_status geometry_build(gp_ctx *ctx, const double *phi, int phi_fluid_positive)
+{
+    if (!ctx || !phi) return GP_INVALID;
+    Ctx *c = &ctx->c;
+    c->geom_ok = 0;
+    c->coarse_ok = 0;
+    c->msg[0] = 0;
+    int s = build_geometry_levels(c, phi, phi_fluid_positive);
+    if (s != GP_OK) return (gp_status)s;
+    gp_status cs = check_cuda(ctx, "geometry_build");
+    if (cs != GP_OK) return cs;
+    c->geom_ok = 1;
+    s = build_coarse_inverse(c);
+    if (s != GP_OK) {
+        c->geom_ok = 0;
+        return (gp_status)s;
+    }
+    return check_cuda(ctx, "coarse inverse");
+}
+
+gp_status gp_level_info(const gp_ctx *ctx, int level, int *N, int64_t *len, double *h)
+{
+    if (!ctx || level < 0 || level >= ctx->c.L) return GP_INVALID;
+    const Level &l = ctx->c.lv[level];
+    if (N) *N = l.N;
+    if (len) *len = l.VL;
+    if (h) *h = l.h;
+    return GP_OK;
+}
+
+gp_status gp_types(gp_ctx *ctx, int level, uint8_t *tu, uint8_t *tv, uint8_t *tp)
+{
+    if (!level_ok(ctx, level) || !ctx->c.geom_ok) return GP_INVALID;
+    Ctx *c = &ctx->c;
+    const Level &l = c->lv[level];
+    cudaMemcpyAsync(tu, l.tU, l.F, cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(tv, l.tV, l.F, cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(tp, l.tP, l.F, cudaMemcpyDeviceToDevice, c->stream);
+    return check_cuda(ctx, "gp_types");
+}
+
+gp_status gp_ghost_count(gp_ctx *ctx, int level, int *n_object, int *n_rows)
+{
+    if (!level_ok(ctx, level) || !ctx->c.geom_ok) return GP_INVALID;
+    if (n_object) *n_object = ctx->c.lv[level].h_nghost;
+    if (n_rows) *n_rows = ctx->c.lv[level].h_nrows;
+    return GP_OK;
+}
+
+gp_status gp_ghost_rows(gp_ctx *ctx, int level, int *node, uint8_t *kind, uint8_t *nst, int *st, double *w, double *B,
+                        double *th)
+{
+    if (!level_ok(ctx, level) || !ctx->c.geom_ok) return GP_INVALID;
+    Ctx *c = &ctx->c;
+    const Level &l = c->lv[level];
+    int n = l.h_nghost;
+    if (n == 0) return GP_OK;
+    cudaStream_t s = c->stream;
+    if (node) cudaMemcpyAsync(node, l.gh.node, n * sizeof(int), cudaMemcpyDeviceToDevice, s);
+    if (kind) cudaMemcpyAsync(kind, l.gh.kind, n, cudaMemcpyDeviceToDevice, s);
+    if (nst) cudaMemcpyAsync(nst, l.gh.nst, n, cudaMemcpyDeviceToDevice, s);
+    // stencils and weights: [m][cap] -> row-major [k][m]
+    for (int m = 0; m < GH_ST; m++) {
+        if (st) cudaMemcpy2DAsync(st + m, GH_ST * sizeof(int), l.gh.st + (size_t)m * l.gh.cap, sizeof(int), sizeof(int), n,
+                                  cudaMemcpyDeviceToDevice, s);
+        if (w) cudaMemcpy2DAsync(w + m, GH_ST * sizeof(double), l.gh.w + (size_t)m * l.gh.cap, sizeof(double),
+                                 sizeof(double), n, cudaMemcpyDeviceToDevice, s);
+    }
+    for (int m = 0; m < 2; m++) {
+        if (B) cudaMemcpy2DAsync(B + m, 2 * sizeof(double), l.gh.B + (size_t)m * l.gh.cap, sizeof(double), sizeof(double), n,
+                                 cudaMemcpyDeviceToDevice, s);
+        if (th) cudaMemcpy2DAsync(th + m, 2 * sizeof(double), l.gh.th + (size_t)m * l.gh.cap, sizeof(double),
+                                  sizeof(double), n, cudaMemcpyDeviceToDevice, s);
+    }
+    return check_cuda(ctx, "gp_ghost_rows");
+}
+
+gp_status gp_residual(gp_ctx *ctx, int level, const double *x, const double *b, double *r, double *norm_host)
+{
+    if (!level_ok(ctx, level) || !ctx->c.geom_ok || !x || !b || !r) return GP_INVALID;
+    Ctx *c = &ctx->c;
+    residual<double>(c, level, x, b, r);
+    if (norm_host) {
+        cudaMemcpyAsync(norm_host, c->red, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess) return check_cuda(ctx, "gp_residual");
+    }
+    return check_cuda(ctx, "gp_residual");
+}
+
+gp_status gp_box_sweep(gp_ctx *ctx, int level, double *x, const double *b)
+{
+    if (!level_ok(ctx, level) || !ctx->c.geom_ok || !x || !b) return GP_INVALID;
+    box_sweep<double>(&ctx->c, level, x, b);
+    return check_cuda(ctx, "gp_box_sweep");
+}
+
+gp_status gp_scalar_update(gp_ctx *ctx, int level, double *x, const double *b)
+{
+    if (!level_ok(ctx, level) || !ctx->c.geom_ok || !x || !b) return GP_INVALID;
+    scalar_update<double>(&ctx->c, level, x, b);
+    return check_cuda(ctx, "gp_scalar_update");
+}
+
+gp_status gp_ghost_sweep(gp_ctx *ctx, int level, double *x, const double *b)
+{
+    if (!level_ok(ctx, level) || !ctx->c.geom_ok || !x || !b) return GP_INVALID;
+    ghost_sweep<double>(&ctx->c, level, x, b);
+    return check_cuda(ctx, "gp_ghost_sweep");
+}
+
+gp_status gp_smooth(gp_ctx *ctx, int level, double *x, const double *b, int nu)
+{
+    if (!level_ok(ctx, level) || !ctx->c.geom_ok || !x || !b || nu < 0) return GP_INVALID;
+    smooth<double>(&ctx->c, level, x, b, nu);
+    return check_cuda(ctx, "gp_smooth");
+}
+
+gp_status gp_restrict(gp_ctx *ctx, int level, const double *r_fine, double *b_coarse)
+{
+    if (!ctx || level < 0 || level + 1 >= ctx->c.L || !ctx->c.geom_ok || !r_fine || !b_coarse) return GP_INVALID;
+    restrict_level<double>(&ctx->c, level, r_fine, b_coarse);
+    return check_cuda(ctx, "gp_restrict");
+}
+
+gp_status gp_prolong(gp_ctx *ctx, int level, const double *e_coarse, double *x_fine)
+{
+    if (!ctx || level < 0 || level + 1 >= ctx->c.L || !ctx->c.geom_ok || !e_coarse || !x_fine) return GP_INVALID;
+    prolong_level<double>(&ctx->c, level, e_coarse, x_fine);
+    return check_cuda(ctx, "gp_prolong");
+}
+
+gp_status gp_coarse_solve(gp_ctx *ctx, const double *b, double *x)
+{
+    if (!ctx || !b || !x) return GP_INVALID;
+    gp_status s = ensure_coarse(ctx);
+    if (s != GP_OK) return s;
+    coarse_solve<double>(&ctx->c, b, x);
+    return check_cuda(ctx, "gp_coarse_solve");
+}
+
+gp_status gp_cycle(gp_ctx *ctx, double *x, const double *b)
+{
+    if (!ctx || !x || !b) return GP_INVALID;
+    gp_status s = ensure_coarse(ctx);
+    if (s != GP_OK) return s;
+    cycle_rec<double>(&ctx->c, 0, x, b);
+    return check_cuda(ctx, "gp_cycle");
+}
+
+gp_status mg_solve(gp_ctx *ctx, double *x, const double *b, double tol, gp_report *rep)
+{
+    if (!ctx || !x || !b || !(tol >= 0.0)) return GP_INVALID;
+    gp_status s = ensure_coarse(ctx);
+    if (s != GP_OK) return s;
+    Ctx *c = &ctx->c;
+    Level &l0 = c->lv[0];
+    bool mixed = c->prm.precision == GP_MIXED;
+    zero_inactive<double>(c, 0, x);
+    residual<double>(c, 0, x, b, l0.r);
+    double nrm = 0.0;
+    cudaMemcpyAsync(&nrm, c->red, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return check_cuda(ctx, "mg_solve");
+    double r0 = nrm;
+    if (rep) {
+        rep->res0 = r0;
+        rep->cycles = 0;
+        if (rep->hist_host) rep->hist_host[0] = r0;
+    }
+    gp_status st = GP_NOT_CONVERGED;
+    int k = 0;
+    if (!(r0 == r0)) st = GP_DIVERGED;
+    else if (r0 <= tol) st = GP_OK;
+    else
+        for (k = 1; k <= c->prm.max_cycles; k++) {
+            if (mixed) {
+                to_float(c, l0.r, l0.bf, l0.VL);
+                zero_vec<float>(c, l0.xf, l0.VL);
+                cycle_rec<float>(c, 0, l0.xf, l0.bf);
+                add_float(c, x, l0.xf, l0.VL);
+            } else {
+                cycle_rec<double>(c, 0, x, b);
+            }
+            residual<double>(c, 0, x, b, l0.r);
+            cudaMemcpyAsync(&nrm, c->red, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+            if (cudaStreamSynchronize(c->stream) != cudaSuccess) return check_cuda(ctx, "mg_solve");
+            if (rep && rep->hist_host) rep->hist_host[k] = nrm;
+            if (!(nrm == nrm) || nrm > 1e6 * r0) {
+                st = GP_DIVERGED;
+                break;
+            }
+            if (nrm <= tol) {
+                st = GP_OK;
+                break;
+            }
+        }
+    if (k > c->prm.max_cycles) k = c->prm.max_cycles;
+    if (rep) {
+        rep->cycles = k;
+        rep->res = nrm;
+        rep->rho = (k > 0 && r0 > 0 && nrm > 0) ? pow(nrm / r0, 1.0 / k) : 0.0;
+        double xi = 0.0;
+        cudaMemcpyAsync(&xi, x + 3 * l0.F, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+        cudaStreamSynchronize(c->stream);
+        rep->xi = xi;
+    }
+    if (st == GP_NOT_CONVERGED) snprintf(c->msg, sizeof c->msg, "not converged: %.3e after %d cycles", nrm, k);
+    if (st == GP_DIVERGED) snprintf(c->msg, sizeof c->msg, "diverged: %.3e (initial %.3e)", nrm, r0);
+    gp_status cs = check_cuda(ctx, "mg_solve");
+    return cs != GP_OK ? cs : st;
+}
+
+}  // extern "C"

@@ -1,0 +1,39 @@
+"""The C ABI library builds, loads without a GPU and exports every entry point
+declared in include/gpmg.h; the binding declares the same set.  No compute
+call is made here."""
+import ctypes
+import os
+import re
+
+from paper_1911_00994_gb300 import build, gpmg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "gpmg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^[A-Za-z_][\w \*]*?\b([a-z_][a-z0-9_]*)\s*\(", src, flags=re.M)
+    return sorted(set(n for n in names if n not in ("if", "while")))
+
+
+def test_library_exports_every_declared_symbol():
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    names = declared_functions()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_covers_the_header():
+    bound = {n for n, _, _ in gpmg.SIGNATURES}
+    assert bound == set(declared_functions())
+
+
+def test_layout_helpers():
+    assert gpmg.pitch(30) == 32 and gpmg.pitch(31) == 64
+    assert gpmg.vec_len(16) == 3 * 18 * 32 + 32
+    m = gpmg.flat_to_vec(8)
+    assert len(m) == 2 * 9 * 10 + 64 + 1
+    assert len(set(m.tolist())) == len(m)
