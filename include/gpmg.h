@@ -158,6 +158,18 @@ gp_status gp_cycle(gp_ctx *ctx, double *x, const double *b);
  * correction to x in FP64.  rep may be NULL. */
 gp_status mg_solve(gp_ctx *ctx, double *x, const double *b, double tol, gp_report *rep);
 
+/* Instrumentation (no counterpart in the paper; used by the benchmark).
+ * gp_launch_count: kernels this context has launched so far.
+ * gp_timer_start: record CUDA events on the context stream around every
+ * launch of one kernel family on one level (kernel: 0 residual, 1 full-box
+ * colour sweep, 2 cut-box colour sweep, 3 ghost sweep, 4 xi/mean partial
+ * sums, 5 restriction, 6 prolongation, 7 coarsest GEMV); gp_timer_stop
+ * synchronises and returns the number of timed launches and their summed
+ * device time in milliseconds. */
+int64_t gp_launch_count(const gp_ctx *ctx);
+gp_status gp_timer_start(gp_ctx *ctx, int kernel, int level);
+gp_status gp_timer_stop(gp_ctx *ctx, int64_t *launches, double *total_ms);
+
 #ifdef __cplusplus
 }
 #endif

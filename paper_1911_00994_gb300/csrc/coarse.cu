@@ -231,8 +231,11 @@ template <typename T> void coarse_solve(Ctx *c, const T *b, T *x)
     T *cv = cvec_ptr<T>(c);
     k_zero_n<T><<<(unsigned)((l.VL + 255) / 256), 256, 0, st>>>(x, l.VL);
     k_gather<T><<<(n + 255) / 256, 256, 0, st>>>(b, c->cmap, cv, n);
+    tmr_begin(c, KT_COARSE, c->L - 1);
     k_gemv<T><<<(n + 7) / 8, 256, 0, st>>>(minv_ptr<T>(c), cv, cv + n, n);
+    tmr_end(c, KT_COARSE, c->L - 1);
     k_scatter<T><<<(n + 255) / 256, 256, 0, st>>>(cv + n, c->cmap, x, n);
+    c->launches += 4;
 }
 
 template void coarse_solve<double>(Ctx *, const double *, double *);

@@ -114,11 +114,25 @@ struct Ctx {
     unsigned *err;      // device error word
     int *flag;          // device change flag
     double hostbuf[8];   // host staging for small device-to-host reads
+    // instrumentation: kernels launched, and an optional event timer around
+    // the launches of one kernel family on one level
+    long long launches;
+    int tmr_kernel, tmr_level, tmr_n, tmr_ready;
+    cudaEvent_t tmr_ev[2 * 512];
+    double tmr_ms;
+    long long tmr_launches;
     int geom_ok;
     int coarse_ok;
     double alpha_factored;
     char msg[256];
 };
+
+// kernel families for the event timer (gp_timer_start)
+enum TimedKernel { KT_RESIDUAL = 0, KT_BOX_FULL = 1, KT_BOX_CUT = 2, KT_GHOST = 3, KT_SCALAR = 4, KT_RESTRICT = 5,
+                   KT_PROLONG = 6, KT_COARSE = 7 };
+
+void tmr_begin(Ctx *c, int kernel, int lev);
+void tmr_end(Ctx *c, int kernel, int lev);
 
 // ------------------------------------------------------------ indexing
 __host__ __device__ inline int slot_u(int P, int i, int j) { return (j + 1) * P + (i + 1); }

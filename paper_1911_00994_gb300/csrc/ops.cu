@@ -578,6 +578,34 @@ __global__ void k_add_float(double *x, const float *e, long long n)
     if (k < n) x[k] += (double)e[k];
 }
 
+// ------------------------------------------------------------- event timer
+
+void tmr_flush(Ctx *c)
+{
+    if (c->tmr_n == 0) return;
+    cudaEventSynchronize(c->tmr_ev[2 * c->tmr_n - 1]);
+    for (int k = 0; k < c->tmr_n; k++) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->tmr_ev[2 * k], c->tmr_ev[2 * k + 1]) == cudaSuccess) c->tmr_ms += ms;
+    }
+    c->tmr_launches += c->tmr_n;
+    c->tmr_n = 0;
+}
+
+void tmr_begin(Ctx *c, int kernel, int lev)
+{
+    if (c->tmr_kernel != kernel || c->tmr_level != lev) return;
+    if (c->tmr_n == 512) tmr_flush(c);
+    cudaEventRecord(c->tmr_ev[2 * c->tmr_n], c->stream);
+}
+
+void tmr_end(Ctx *c, int kernel, int lev)
+{
+    if (c->tmr_kernel != kernel || c->tmr_level != lev) return;
+    cudaEventRecord(c->tmr_ev[2 * c->tmr_n + 1], c->stream);
+    c->tmr_n++;
+}
+
 // ----------------------------------------------------------- host wrappers
 
 template <typename T> LevelArgs<T> level_args(const Ctx *c, int lev)
@@ -606,10 +634,13 @@ template <typename T> void residual(Ctx *c, int lev, const T *x, const T *b, T *
     cudaStream_t st = c->stream;
     dim3 g = frame_grid(l);
     int nb = g.x * g.y;
+    tmr_begin(c, KT_RESIDUAL, lev);
     k_residual<T><<<g, 256, 0, st>>>(level_args<T>(c, lev), x, b, r, c->part);
+    tmr_end(c, KT_RESIDUAL, lev);
     if (l.h_nrows > 0) k_ghost_residual<T><<<(l.h_nrows + 255) / 256, 256, 0, st>>>(l.gh, l.h_nrows, x, b, r, c->maxbits);
     double h = c->prm.L / (double)l.N;
     k_residual_final<T><<<1, 256, 0, st>>>(c->part, nb, b, r, 3 * l.F, h * h, c->maxbits, c->red);
+    c->launches += 2 + (l.h_nrows > 0);
 }
 
 template <typename T> void box_sweep(Ctx *c, int lev, T *x, const T *b)
@@ -619,15 +650,26 @@ template <typename T> void box_sweep(Ctx *c, int lev, T *x, const T *b)
     LevelArgs<T> A = level_args<T>(c, lev);
     int per_row = (l.N + 4) / 5;
     dim3 g((per_row + 127) / 128, l.N);
-    for (int colour = 0; colour < 5; colour++) k_box_full<T><<<g, 128, 0, st>>>(A, x, b, colour);
+    for (int colour = 0; colour < 5; colour++) {
+        tmr_begin(c, KT_BOX_FULL, lev);
+        k_box_full<T><<<g, 128, 0, st>>>(A, x, b, colour);
+        tmr_end(c, KT_BOX_FULL, lev);
+        c->launches++;
+    }
     for (int colour = 0; colour < 25; colour++) {
         int beg = l.h_cutoff[colour], end = l.h_cutoff[colour + 1];
-        if (end > beg) k_box_cut<T><<<(end - beg + 127) / 128, 128, 0, st>>>(A, x, b, l.cut, l.gh, beg, end);
+        if (end > beg) {
+            tmr_begin(c, KT_BOX_CUT, lev);
+            k_box_cut<T><<<(end - beg + 127) / 128, 128, 0, st>>>(A, x, b, l.cut, l.gh, beg, end);
+            tmr_end(c, KT_BOX_CUT, lev);
+            c->launches++;
+        }
     }
     if (l.h_nlonely > 0) {
         T *upd = (T *)c->part;
         k_lonely_update<T><<<(l.h_nlonely + 127) / 128, 128, 0, st>>>(A, x, b, l.lonely, l.h_nlonely, upd);
         k_apply_list<T><<<(l.h_nlonely + 127) / 128, 128, 0, st>>>(x, l.lonely, upd, l.h_nlonely);
+        c->launches += 2;
     }
 }
 
@@ -638,10 +680,13 @@ template <typename T> void scalar_update(Ctx *c, int lev, T *x, const T *b)
     LevelArgs<T> A = level_args<T>(c, lev);
     dim3 g = frame_grid(l);
     int nb = g.x * g.y;
+    tmr_begin(c, KT_SCALAR, lev);
     k_scalar_partial<T><<<g, 256, 0, st>>>(A, x, b, c->part);
+    tmr_end(c, KT_SCALAR, lev);
     double h = c->prm.L / (double)l.N;
     k_scalar_final<T><<<1, 256, 0, st>>>(c->part, nb, x, b, 3 * l.F, h * h, l.nint, c->red + 1);
     k_pshift<T><<<g, 256, 0, st>>>(A, x, c->red + 1);
+    c->launches += 3;
 }
 
 template <typename T> void ghost_sweep(Ctx *c, int lev, T *x, const T *b)
@@ -650,8 +695,11 @@ template <typename T> void ghost_sweep(Ctx *c, int lev, T *x, const T *b)
     if (l.h_nrows <= 0) return;
     cudaStream_t st = c->stream;
     int nb = (l.h_nrows + 255) / 256;
+    tmr_begin(c, KT_GHOST, lev);
     k_ghost_update<T><<<nb, 256, 0, st>>>(l.gh, l.h_nrows, x, b, (T)c->prm.dtau);
+    tmr_end(c, KT_GHOST, lev);
     k_ghost_apply<T><<<nb, 256, 0, st>>>(l.gh, l.h_nrows, x);
+    c->launches += 2;
 }
 
 template <typename T> void smooth(Ctx *c, int lev, T *x, const T *b, int nu)
@@ -667,34 +715,44 @@ template <typename T> void restrict_level(Ctx *c, int lev, const T *r, T *bH)
 {
     const Level &f = c->lv[lev], &C = c->lv[lev + 1];
     dim3 g((C.P + 255) / 256, C.N + 2);
+    tmr_begin(c, KT_RESTRICT, lev);
     k_restrict<T><<<g, 256, 0, c->stream>>>(f.N, f.P, f.F, f.tU, f.tV, f.tP, C.N, C.P, C.F, C.tU, C.tV, C.tP, r, bH);
+    tmr_end(c, KT_RESTRICT, lev);
+    c->launches++;
 }
 
 template <typename T> void prolong_level(Ctx *c, int lev, const T *eH, T *x)
 {
     const Level &f = c->lv[lev], &C = c->lv[lev + 1];
     dim3 g((f.P + 255) / 256, f.N + 2);
+    tmr_begin(c, KT_PROLONG, lev);
     k_prolong<T><<<g, 256, 0, c->stream>>>(f.N, f.P, f.F, f.tU, f.tV, f.tP, C.N, C.P, C.F, C.tU, C.tV, C.tP, eH, x);
+    tmr_end(c, KT_PROLONG, lev);
+    c->launches++;
 }
 
 template <typename T> void zero_vec(Ctx *c, T *x, long long n)
 {
     k_zero<T><<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(x, n);
+    c->launches++;
 }
 
 template <typename T> void zero_inactive(Ctx *c, int lev, T *x)
 {
     k_zero_inactive<T><<<frame_grid(c->lv[lev]), 256, 0, c->stream>>>(level_args<T>(c, lev), x);
+    c->launches++;
 }
 
 void to_float(Ctx *c, const double *a, float *b, long long n)
 {
     k_to_float<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(a, b, n);
+    c->launches++;
 }
 
 void add_float(Ctx *c, double *x, const float *e, long long n)
 {
     k_add_float<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(x, e, n);
+    c->launches++;
 }
 
 #define INST(T)                                                                 \

@@ -24,6 +24,7 @@ template <typename T> void zero_vec(Ctx *c, T *x, long long n);
 template <typename T> void zero_inactive(Ctx *c, int lev, T *x);
 template <typename T> void coarse_solve(Ctx *c, const T *b, T *x);
 void to_float(Ctx *c, const double *a, float *b, long long n);
+void tmr_flush(Ctx *c);
 void add_float(Ctx *c, double *x, const float *e, long long n);
 
 // ------------------------------------------------------------- workspace
@@ -275,6 +276,7 @@ gp_status gp_create(gp_ctx **out, const gp_params *prm, void *workspace, size_t 
     }
     c->ws = (char *)workspace;
     c->ws_bytes = bytes;
+    c->tmr_kernel = -1;
     c->stream = (cudaStream_t)stream;
     carve(c, c->ws);
     // coarsest-level index maps (host -> device)
@@ -307,8 +309,40 @@ gp_status gp_destroy(gp_ctx *ctx)
 {
     if (!ctx) return GP_INVALID;
     cudaStreamSynchronize(ctx->c.stream);
+    if (ctx->c.tmr_ready)
+        for (int k = 0; k < 2 * 512; k++) cudaEventDestroy(ctx->c.tmr_ev[k]);
     delete ctx;
     return GP_OK;
+}
+
+int64_t gp_launch_count(const gp_ctx *ctx) { return ctx ? ctx->c.launches : -1; }
+
+gp_status gp_timer_start(gp_ctx *ctx, int kernel, int level)
+{
+    if (!ctx || kernel < 0 || kernel > KT_COARSE || level < 0 || level >= ctx->c.L) return GP_INVALID;
+    Ctx *c = &ctx->c;
+    if (!c->tmr_ready) {
+        for (int k = 0; k < 2 * 512; k++)
+            if (cudaEventCreate(&c->tmr_ev[k]) != cudaSuccess) return check_cuda(ctx, "gp_timer_start");
+        c->tmr_ready = 1;
+    }
+    tmr_flush(c);
+    c->tmr_kernel = kernel;
+    c->tmr_level = level;
+    c->tmr_ms = 0.0;
+    c->tmr_launches = 0;
+    return GP_OK;
+}
+
+gp_status gp_timer_stop(gp_ctx *ctx, int64_t *launches, double *total_ms)
+{
+    if (!ctx) return GP_INVALID;
+    Ctx *c = &ctx->c;
+    tmr_flush(c);
+    if (launches) *launches = c->tmr_launches;
+    if (total_ms) *total_ms = c->tmr_ms;
+    c->tmr_kernel = -1;
+    return check_cuda(ctx, "gp_timer_stop");
 }
 
 const char *gp_last_error(const gp_ctx *ctx) { return ctx ? ctx->c.msg : "null context"; }

@@ -68,7 +68,12 @@ SIGNATURES = [
     ("gp_coarse_solve", _I, [_VP, _VP, _VP]),
     ("gp_cycle", _I, [_VP, _VP, _VP]),
     ("mg_solve", _I, [_VP, _VP, _VP, _D, _P(gp_report)]),
+    ("gp_launch_count", ctypes.c_int64, [_VP]),
+    ("gp_timer_start", _I, [_VP, _I, _I]),
+    ("gp_timer_stop", _I, [_VP, _P(ctypes.c_int64), _P(_D)]),
 ]
+KERNELS = {"residual": 0, "box_full": 1, "box_cut": 2, "ghost": 3, "scalar": 4, "restrict": 5, "prolong": 6,
+           "coarse": 7}
 
 
 def lib():
@@ -264,6 +269,17 @@ class Solver:
 
     def cycle(self, x, b):
         self._check(self.L.gp_cycle(self.ctx, _ptr(x), _ptr(b)), "gp_cycle")
+
+    def launch_count(self):
+        return int(self.L.gp_launch_count(self.ctx))
+
+    def timer_start(self, kernel, level=0):
+        self._check(self.L.gp_timer_start(self.ctx, KERNELS[kernel], level), "gp_timer_start")
+
+    def timer_stop(self):
+        n, ms = ctypes.c_int64(0), ctypes.c_double(0.0)
+        self._check(self.L.gp_timer_stop(self.ctx, ctypes.byref(n), ctypes.byref(ms)), "gp_timer_stop")
+        return int(n.value), float(ms.value)
 
     def solve(self, x, b, tol, hist=True):
         rep = gp_report()
