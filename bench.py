@@ -1,0 +1,381 @@
+#!/usr/bin/env python
+"""Benchmark of the ghost-point multigrid solve of one Crank-Nicolson step.
+
+Workload (lid-driven cavity around a steady flower): [0,1]^2 with N x N
+cells (default 4096), flower r < 0.2 + 0.05 sin(5 theta) centred at
+(0.5, 0.5), Re = 1000, dt = h (alpha = dt / (2 Re)), no-slip on the flower
+and the walls, lid u = 1 at y = 1.  One step = the linear system of the first
+Crank-Nicolson step from rest solved from a zero start to ||r||_inf <= 1e-10
+by V(2,1) cycles.  The headline runs FP32 cycles inside FP64 residual
+correction; the plain FP64 solve of the same system is timed in the same run.
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle on the
+same system instead (one V-cycle per step).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-1e-10 residual per CN step & MG cycles/s at 4096²; HBM GB/s % peak"
+TOL = 1e-10
+
+
+def workload(N):
+    return {"workload": "lid-driven cavity %dx%d on [0,1]^2, steady flower r=0.2+0.05sin(5t) at (0.5,0.5), "
+                        "Re=1000, dt=h; first CN step from rest, V(2,1) to ||r||_inf<=1e-10 from zero" % (N, N),
+            "N": N, "Re": 1000.0, "dt": "h", "tol": TOL}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def ncu_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current kernel source."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            d = json.load(f)
+        src = open(os.path.join(ROOT, "paper_1911_00994_gb300", "csrc", "ops.cu"), "rb").read()
+        e = d.get(kernel)
+        if e and e.get("ops_cu_sha1") == hashlib.sha1(src).hexdigest():
+            return e
+    except Exception:
+        pass
+    return None
+
+
+def build_case(N, precision, device, levels=None):
+    import torch
+    from paper_1911_00994_gb300 import gpmg
+    from paper_1911_00994_gb300 import workloads as W
+    h = 1.0 / N
+    alpha = h / (2.0 * 1000.0)
+    s = gpmg.Solver(N, 0.0, 0.0, 1.0, levels=levels, alpha=alpha, precision=precision, device=device,
+                    max_cycles=200)
+    phi = torch.from_numpy(W.phi_half_lattice(W.flower(0.2, 0.05, 5, 0.5, 0.5), N, 0.0, 0.0, 1.0)).to(device)
+    st = s.geometry(phi, 0)
+    if st:
+        raise RuntimeError("geometry_build: " + s.error())
+    b = s.new_vec()
+    P = gpmg.pitch(N)
+    # lid: box-ghost rows of u above the top wall carry u = 1
+    b[(N + 1) * P + 2:(N + 1) * P + N + 1] = 1.0
+    return s, b
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    from paper_1911_00994_gb300 import gpmg
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    N = args.N
+    gpmg.lib()
+
+    def barrier():
+        if dist:
+            import torch.distributed as tdist
+            tdist.barrier()
+        torch.cuda.synchronize(dev)
+
+    # ---- mixed precision (headline)
+    s, b = build_case(N, gpmg.GP_MIXED, dev)
+    x = s.new_vec()
+    stream = s.stream
+    for _ in range(args.warmup):
+        x.zero_()
+        st, rep, _ = s.solve(x, b, TOL, hist=False)
+        if st:
+            raise RuntimeError("warm-up solve failed: %s" % s.error())
+    tp = s.types_flat(0)
+    nU, nV = (N + 1) * (N + 2), (N + 2) * (N + 1)
+    n_int = int((tp[nU + nV:-1] == 1).sum())
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    s.timer_start("box_full", 0)
+    barrier()
+    l0 = s.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    cycles = 0
+    rhos = []
+    for _ in range(args.steps):
+        x.zero_()
+        st, rep, _ = s.solve(x, b, TOL, hist=False)
+        if st:
+            raise RuntimeError("solve failed: %s" % s.error())
+        cycles += rep.cycles
+        rhos.append(rep.rho)
+    e1.record(stream)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    launches = s.launch_count() - l0
+    nbox, box_ms = s.timer_stop()
+    clocks = sampler.stop()
+    # max over ranks
+    t = torch.tensor([ms, float(cycles)], dtype=torch.float64, device=dev)
+    if dist:
+        import torch.distributed as tdist
+        tmax = t.clone()
+        tdist.all_reduce(tmax[:1], op=tdist.ReduceOp.MAX)
+        tdist.all_reduce(t[1:], op=tdist.ReduceOp.SUM)
+        ms_all, cycles_all = float(tmax[0]), float(t[1])
+    else:
+        ms_all, cycles_all = ms, float(cycles)
+    value = cycles_all / (ms_all / 1e3)
+
+    # ---- end to end through the public API with host buffers
+    x_host = torch.zeros(s.vec_len(), dtype=torch.float64).pin_memory()
+    b_host = b.cpu().pin_memory()
+    out_host = torch.empty_like(x_host).pin_memory()
+    barrier()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_e2e0 = time.perf_counter()
+    f0.record(stream)
+    ecycles = 0
+    with torch.cuda.stream(stream):
+        for _ in range(args.steps):
+            b.copy_(b_host, non_blocking=True)
+            x.copy_(x_host, non_blocking=True)
+            st, rep, _ = s.solve(x, b, TOL, hist=False)
+            ecycles += rep.cycles
+            out_host.copy_(x, non_blocking=True)
+    f1.record(stream)
+    barrier()
+    e2e_ms = f0.elapsed_time(f1)
+    e2e = {"value": ecycles / (e2e_ms / 1e3), "unit": "V-cycles/s",
+           "h2d_bytes_per_step": 2 * 8 * s.vec_len(), "d2h_bytes_per_step": 8 * s.vec_len(),
+           "ms_per_step": e2e_ms / args.steps, "host_wall_s": time.perf_counter() - t_e2e0}
+
+    levels = s.levels
+    # ---- plain FP64 solve of the same system
+    del s
+    torch.cuda.empty_cache()
+    s64, b64 = build_case(N, gpmg.GP_FP64, dev)
+    x64 = s64.new_vec()
+    for _ in range(max(1, args.warmup // 2)):
+        x64.zero_()
+        s64.solve(x64, b64, TOL, hist=False)
+    barrier()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(s64.stream)
+    c64 = 0
+    n64 = max(1, min(args.steps, 3))
+    for _ in range(n64):
+        x64.zero_()
+        st, rep64, _ = s64.solve(x64, b64, TOL, hist=False)
+        if st:
+            raise RuntimeError("fp64 solve failed: %s" % s64.error())
+        c64 += rep64.cycles
+    g1.record(s64.stream)
+    barrier()
+    ms64 = g0.elapsed_time(g1)
+
+    if rank != 0:
+        if dist:
+            import torch.distributed as tdist
+            tdist.destroy_process_group()
+        return None
+
+    hbm, src = peaks()
+    # algorithmic bytes of one colour launch of the FP32 full-box sweep: the
+    # 5-colour sweep reads x and b (3 fields each) and writes x once per
+    # internal cell (9 words) plus 3 type bytes; one launch is a fifth of that
+    bytes_per_launch = n_int * (9 * 4 + 3) / 5.0
+    avg_ms = box_ms / max(1, nbox)
+    achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
+    tr = ncu_traffic("k_box_full<float>")
+    line = {
+        "metric": METRIC, "value": value, "unit": "V-cycles/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": dict(workload(N), precision="fp32 cycles in fp64 residual correction", levels=levels,
+                       l2="inputs larger than L2 (each vector %.0f MB)" % (8 * gpmg.vec_len(N) / 1e6),
+                       parallelism="replicas" if world > 1 else "single GPU"),
+        "time_to_tol_ms": ms_all / args.steps, "cycles_per_step": cycles / args.steps,
+        "rho_mean": float(np.mean(rhos)),
+        "fp64": {"time_to_tol_ms": ms64 / n64, "cycles_per_step": c64 / n64, "cycles_per_s": c64 / (ms64 / 1e3),
+                 "steps": n64},
+        "roofline": {"kernel": "k_box_full<float> (one colour of the finest-level box sweep)", "bound": "hbm",
+                     "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "peak_source": src, "avg_launch_ms": avg_ms, "launches": nbox,
+                     "algorithmic_bytes_per_launch": bytes_per_launch,
+                     "traffic": tr["bytes_per_launch"] if tr else None},
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if not args.no_cpu and world == 1:
+        line["cpu_baseline"] = cpu_baseline(N)
+    print(json.dumps(line), flush=True)
+    return line
+
+
+def cpu_baseline(N):
+    """The oracle, as it stands, timed on the host: one V-cycle of the same
+    system (geometry built outside the timed region)."""
+    import numpy as np
+
+    import oracle as O
+    from paper_1911_00994_gb300 import workloads as W
+    h = 1.0 / N
+    lev = 1
+    while (N >> lev) >= 16:
+        lev += 1
+    o = O.Oracle(N, 0.0, 0.0, 1.0, lev, h / 2000.0)
+    st = o.geometry(W.phi_half_lattice(W.flower(0.2, 0.05, 5, 0.5, 0.5), N, 0.0, 0.0, 1.0))
+    if st:
+        return {"value": None, "error": o.error()}
+    b = np.zeros(o.n())
+    g, i, j, X, Y = W.flat_coords(N, 0.0, 0.0, 1.0)
+    t = o.types()
+    b[(g == 0) & (j == N) & (t == W.BOXGHOST)] = 1.0
+    x = np.zeros_like(b)
+    t0 = time.perf_counter()
+    st, x = o.cycle(x, b)
+    dt = time.perf_counter() - t0
+    return {"value": 1.0 / dt, "unit": "V-cycles/s", "cores": 1, "kind": "oracle",
+            "sample": "one V(2,1) cycle of the %dx%d system from zero (FP64, single thread; geometry excluded)" % (N, N),
+            "seconds": dt}
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle on the same system, one V-cycle per step."""
+    import numpy as np
+
+    import oracle as O
+    from paper_1911_00994_gb300 import workloads as W
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    N = args.N
+    h = 1.0 / N
+    lev = 1
+    while (N >> lev) >= 16:
+        lev += 1
+    o = O.Oracle(N, 0.0, 0.0, 1.0, lev, h / 2000.0)
+    st = o.geometry(W.phi_half_lattice(W.flower(0.2, 0.05, 5, 0.5, 0.5), N, 0.0, 0.0, 1.0))
+    if st:
+        print(json.dumps({"impl": "reference", "unavailable": "oracle geometry failed: " + o.error()}))
+        return None
+    b = np.zeros(o.n())
+    g, i, j, X, Y = W.flat_coords(N, 0.0, 0.0, 1.0)
+    t = o.types()
+    b[(g == 0) & (j == N) & (t == W.BOXGHOST)] = 1.0
+    x = np.zeros_like(b)
+    for _ in range(args.warmup):
+        st, x = o.cycle(x, b)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        st, x = o.cycle(x, b)
+    dt = time.perf_counter() - t0
+    value = args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "V-cycles/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload(N),
+            "cpu_baseline": {"value": value, "unit": "V-cycles/s", "cores": 1, "kind": "oracle",
+                             "sample": "one V(2,1) cycle per step of the %dx%d system (FP64, single thread)" % (N, N)},
+            "e2e": {"value": value, "unit": "V-cycles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return line
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--warmup", type=int, default=None)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--N", type=int, default=4096)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        args.steps = 2 if args.steps is None else args.steps
+        args.warmup = 1 if args.warmup is None else args.warmup
+        run_reference(args)
+    else:
+        args.steps = 10 if args.steps is None else args.steps
+        args.warmup = 3 if args.warmup is None else args.warmup
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()
