@@ -133,6 +133,21 @@ gp_status gp_ghost_rows(gp_ctx *ctx, int level, int *node, uint8_t *kind, uint8_
  * NULL).  x, b, r: FP64 vectors of that level. */
 gp_status gp_residual(gp_ctx *ctx, int level, const double *x, const double *b, double *r, double *norm_host);
 
+/* The same residual and norm as gp_residual, for callers that cannot obtain
+ * device memory for scratch: for example work recorded into a CUDA graph
+ * under a capture mode that forbids allocation, or a host whose workspace is
+ * fixed and shared.  The paper has no counterpart; this is a property of the
+ * library only.  It allocates nothing and uses none of the workspace's
+ * reduction area: its scratch is a fixed array of about 128 KB inside the
+ * library, which every GPU that loads the library keeps until the process
+ * exits.  Levels with more than 8192 cells per side return GP_INVALID.  All
+ * calls share that array (it keeps the last call's contents; the call clears
+ * what must start at zero), so two calls whose kernels overlap on one GPU
+ * race.  The first call on a device looks up the array's device address;
+ * make it before any stream capture.  Synchronises the stream when
+ * norm_host is not NULL. */
+gp_status gp_residual_static(gp_ctx *ctx, int level, const double *x, const double *b, double *r, double *norm_host);
+
 /* Pieces of the relaxation (Sect. 4.1), in place on x: */
 gp_status gp_box_sweep(gp_ctx *ctx, int level, double *x, const double *b);     /* all box colours */
 gp_status gp_scalar_update(gp_ctx *ctx, int level, double *x, const double *b); /* xi and mean pressure */

@@ -25,6 +25,7 @@ template <typename T> void zero_inactive(Ctx *c, int lev, T *x);
 template <typename T> void coarse_solve(Ctx *c, const T *b, T *x);
 void to_float(Ctx *c, const double *a, float *b, long long n);
 void tmr_flush(Ctx *c);
+int residual_static(Ctx *c, int lev, const double *x, const double *b, double *r, double *norm_host);
 void add_float(Ctx *c, double *x, const float *e, long long n);
 
 // ------------------------------------------------------------- workspace
@@ -441,6 +442,12 @@ gp_status gp_residual(gp_ctx *ctx, int level, const double *x, const double *b, 
         if (cudaStreamSynchronize(c->stream) != cudaSuccess) return check_cuda(ctx, "gp_residual");
     }
     return check_cuda(ctx, "gp_residual");
+}
+
+gp_status gp_residual_static(gp_ctx *ctx, int level, const double *x, const double *b, double *r, double *norm_host)
+{
+    if (!level_ok(ctx, level) || !ctx->c.geom_ok || !x || !b || !r) return GP_INVALID;
+    return (gp_status)residual_static(&ctx->c, level, x, b, r, norm_host);
 }
 
 gp_status gp_box_sweep(gp_ctx *ctx, int level, double *x, const double *b)

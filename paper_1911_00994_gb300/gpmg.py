@@ -59,6 +59,7 @@ SIGNATURES = [
     ("gp_ghost_count", _I, [_VP, _I, _P(_I), _P(_I)]),
     ("gp_ghost_rows", _I, [_VP, _I, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     ("gp_residual", _I, [_VP, _I, _VP, _VP, _VP, _P(_D)]),
+    ("gp_residual_static", _I, [_VP, _I, _VP, _VP, _VP, _P(_D)]),
     ("gp_box_sweep", _I, [_VP, _I, _VP, _VP]),
     ("gp_scalar_update", _I, [_VP, _I, _VP, _VP]),
     ("gp_ghost_sweep", _I, [_VP, _I, _VP, _VP]),
@@ -240,6 +241,15 @@ class Solver:
         r = self.new_vec(lev)
         nrm = ctypes.c_double(0.0)
         self._check(self.L.gp_residual(self.ctx, lev, _ptr(x), _ptr(b), _ptr(r), ctypes.byref(nrm)), "gp_residual")
+        return r, nrm.value
+
+    def residual_static(self, x, b, lev=0):
+        """gp_residual_static: same result as residual(), scratch in a fixed
+        library array instead of the workspace (no allocation)."""
+        r = self.new_vec(lev)
+        nrm = ctypes.c_double(0.0)
+        self._check(self.L.gp_residual_static(self.ctx, lev, _ptr(x), _ptr(b), _ptr(r), ctypes.byref(nrm)),
+                    "gp_residual_static")
         return r, nrm.value
 
     def box_sweep(self, x, b, lev=0):
