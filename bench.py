@@ -112,14 +112,14 @@ def ncu_traffic(kernel):
     return None
 
 
-def build_case(N, precision, device, levels=None):
+def build_case(N, precision, device, stream, levels=None):
     import torch
     from paper_1911_00994_gb300 import gpmg
     from paper_1911_00994_gb300 import workloads as W
     h = 1.0 / N
     alpha = h / (2.0 * 1000.0)
     s = gpmg.Solver(N, 0.0, 0.0, 1.0, levels=levels, alpha=alpha, precision=precision, device=device,
-                    max_cycles=200)
+                    max_cycles=200, stream=stream)
     phi = torch.from_numpy(W.phi_half_lattice(W.flower(0.2, 0.05, 5, 0.5, 0.5), N, 0.0, 0.0, 1.0)).to(device)
     st = s.geometry(phi, 0)
     if st:
@@ -154,10 +154,12 @@ def run_ours(args):
             tdist.barrier()
         torch.cuda.synchronize(dev)
 
-    # ---- mixed precision (headline)
-    s, b = build_case(N, gpmg.GP_MIXED, dev)
+    # ---- mixed precision (headline); the solver runs on its own stream so that
+    # each multigrid iteration is replayed as a captured CUDA graph
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    s, b = build_case(N, gpmg.GP_MIXED, dev, stream)
     x = s.new_vec()
-    stream = s.stream
     for _ in range(args.warmup):
         x.zero_()
         st, rep, _ = s.solve(x, b, TOL, hist=False)
@@ -169,10 +171,10 @@ def run_ours(args):
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
-    s.timer_start("box_full", 0)
     barrier()
     l0 = s.launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
     e0.record(stream)
     cycles = 0
     rhos = []
@@ -185,10 +187,18 @@ def run_ours(args):
         rhos.append(rep.rho)
     e1.record(stream)
     barrier()
+    torch.cuda.nvtx.range_pop()
     ms = e0.elapsed_time(e1)
     launches = s.launch_count() - l0
-    nbox, box_ms = s.timer_stop()
     clocks = sampler.stop()
+    # the dominant kernel, timed with CUDA events around each of its launches
+    # over a second pass of the same steps (the event timer replaces graph
+    # replay with direct launches; the kernels are the same)
+    s.timer_start("box_full", 0)
+    for _ in range(args.steps):
+        x.zero_()
+        s.solve(x, b, TOL, hist=False)
+    nbox, box_ms = s.timer_stop()
     # max over ranks
     t = torch.tensor([ms, float(cycles)], dtype=torch.float64, device=dev)
     if dist:
@@ -210,13 +220,12 @@ def run_ours(args):
     t_e2e0 = time.perf_counter()
     f0.record(stream)
     ecycles = 0
-    with torch.cuda.stream(stream):
-        for _ in range(args.steps):
-            b.copy_(b_host, non_blocking=True)
-            x.copy_(x_host, non_blocking=True)
-            st, rep, _ = s.solve(x, b, TOL, hist=False)
-            ecycles += rep.cycles
-            out_host.copy_(x, non_blocking=True)
+    for _ in range(args.steps):
+        b.copy_(b_host, non_blocking=True)
+        x.copy_(x_host, non_blocking=True)
+        st, rep, _ = s.solve(x, b, TOL, hist=False)
+        ecycles += rep.cycles
+        out_host.copy_(x, non_blocking=True)
     f1.record(stream)
     barrier()
     e2e_ms = f0.elapsed_time(f1)
@@ -228,7 +237,7 @@ def run_ours(args):
     # ---- plain FP64 solve of the same system
     del s
     torch.cuda.empty_cache()
-    s64, b64 = build_case(N, gpmg.GP_FP64, dev)
+    s64, b64 = build_case(N, gpmg.GP_FP64, dev, stream)
     x64 = s64.new_vec()
     for _ in range(max(1, args.warmup // 2)):
         x64.zero_()
@@ -276,6 +285,7 @@ def run_ours(args):
         "roofline": {"kernel": "k_box_full<float> (one colour of the finest-level box sweep)", "bound": "hbm",
                      "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "peak_source": src, "avg_launch_ms": avg_ms, "launches": nbox,
+                     "timing": "CUDA events on the solver stream around every launch, second pass of the timed steps",
                      "algorithmic_bytes_per_launch": bytes_per_launch,
                      "traffic": tr["bytes_per_launch"] if tr else None},
         "e2e": e2e,

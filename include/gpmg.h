@@ -71,6 +71,9 @@ typedef struct gp_params {
     double snap;        /* a node within snap*h of the boundary counts as external */
     int precision;      /* gp_precision */
     int max_cycles;     /* cap for mg_solve */
+    int cn_buffers;     /* nonzero: carve the four finest-level vectors cn_step needs */
+    int graphs;         /* nonzero: mg_solve replays each cycle as a captured CUDA graph
+                           (needs a stream other than the legacy default stream) */
 } gp_params;
 
 typedef struct gp_report {
@@ -82,10 +85,29 @@ typedef struct gp_report {
     double *hist_host;   /* optional host array of max_cycles + 1 norms, or NULL */
 } gp_report;
 
+/* Rigid-body velocity of the object: u_b(B) = (U - omega (B_y - cy),
+ * V + omega (B_x - cx)) at a boundary point B. */
+typedef struct gp_body {
+    double U, V, omega, cx, cy;
+} gp_body;
+
+/* Tangential velocities of the four box walls (the wall-normal velocities
+ * are 0): u on y = y0, u on y = y0 + L, v on x = x0, v on x = x0 + L. */
+typedef struct gp_walls {
+    double u_bottom, u_top, v_left, v_right;
+} gp_walls;
+
+typedef struct gp_cn_report {
+    int picard;          /* Picard iterations (Eq. NSitconv); 0 when extrapolated */
+    int cycles;          /* multigrid cycles over all solves of the step */
+    double res;          /* final ||b - M x||_inf of the last solve */
+    double mom_res;      /* Eq. (iterativeNS) residual of the last Picard iterate */
+} gp_cn_report;
+
 typedef struct gp_ctx gp_ctx;
 
 /* Defaults: levels down to a 16 x 16 grid, V(2,1), lambda 5, dtau 0.9,
- * snap 0.3, FP64, 100 cycles, alpha = L/N/2. */
+ * snap 0.3, FP64, 100 cycles, alpha = L/N/2, cn_buffers 1, graphs 1. */
 gp_status gp_params_default(gp_params *prm, int N, double x0, double y0, double L);
 
 /* Row pitch P and doubles per vector of a level with N cells per side. */
@@ -172,6 +194,37 @@ gp_status gp_cycle(gp_ctx *ctx, double *x, const double *b);
  * residual, runs one FP32 cycle on it from zero and adds the FP32
  * correction to x in FP64.  rep may be NULL. */
 gp_status mg_solve(gp_ctx *ctx, double *x, const double *b, double tol, gp_report *rep);
+
+/* One Crank-Nicolson step (Sect. 2) on the finest level, in place.
+ *  x:      state (u, v with ghost values, p scaled by dt, xi) at t^n, FP64
+ *          vector of the finest level; on return the state at t^(n+1) (and
+ *          the multigrid warm start is the old state).
+ *  N1, N2: convective terms u.grad u of steps n-1 and n-2 (same layout);
+ *          rotated on return (N2 <- N1, N1 <- N^n).  Unused for n < 2.
+ *  step:   n.  n < 2: mid-point Picard iteration (Eq. NSitconv) until
+ *          Eq. (iterativeNS) holds with eps, at most kmax solves; n >= 2:
+ *          extrapolation N^n + N^(n-1)/2 - N^(n-2)/2 (Eq. extrUdU).
+ *  f:      forcing at t^(n+1/2) on the u, v frames (NULL for none).
+ *  bc:     boundary values on the ghost, wall and box-ghost rows of the
+ *          finest vector layout (Eq. BCu rows: velocity at B, see
+ *          gp_ghost_rows); NULL: rigid-body velocity `body` on the object
+ *          and `walls` on the box.
+ *  dt, Re: alpha = dt / (2 Re) is set on the context (the coarsest inverse
+ *          is rebuilt when alpha changes).
+ *  Each linear solve runs mg_solve to `tol`.  The right-hand side is
+ *  u^n + alpha lap u^n + dt f - dt N^(n+1/2) on internal momentum rows
+ *  (Eqs. NSCN1, spaceprob), 0 on continuity, extrapolation and mean rows.
+ *  Needs cn_buffers.  rep may be NULL. */
+gp_status cn_step(gp_ctx *ctx, double *x, double *N1, double *N2, int step, const double *f, const double *bc,
+                  double dt, double Re, const gp_body *body, const gp_walls *walls, double tol, double eps, int kmax,
+                  gp_cn_report *rep);
+
+/* Pieces of cn_step for tests: the convective term of x on internal u, v
+ * nodes (0 elsewhere on the u, v frames), and the right-hand side for a
+ * given N^(n+1/2). */
+gp_status gp_convective(gp_ctx *ctx, const double *x, double *out);
+gp_status gp_cn_rhs(gp_ctx *ctx, const double *xn, const double *Nh, const double *f, double dt, const double *bc,
+                    const gp_body *body, const gp_walls *walls, double *b);
 
 /* Instrumentation (no counterpart in the paper; used by the benchmark).
  * gp_launch_count: kernels this context has launched so far.

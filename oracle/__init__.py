@@ -77,6 +77,10 @@ def lib():
             L.or_prolong.argtypes = [vp, i, P(d), P(d)]
             L.or_cycle.argtypes = [vp, i, P(d), P(d)]
             L.or_solve.argtypes = [vp, P(d), P(d), d, i, P(d), P(i)]
+            L.or_convective.argtypes = [vp, P(d), P(d)]
+            L.or_cn_rhs.argtypes = [vp, P(d), P(d), vp, d, vp, P(d), P(d), P(d)]
+            L.or_momentum_residual.argtypes = [vp, P(d), P(d), P(d), P(d)]
+            L.or_cn_step.argtypes = [vp, P(d), P(d), P(d), i, vp, vp, d, P(d), P(d), d, d, i, P(d)]
             _lib = L
     return _lib
 
@@ -257,3 +261,39 @@ class Oracle:
         nc = ctypes.c_int(0)
         st = self.L.or_solve(self.c, _p(x2), _p(b), tol, max_cycles, _p(hist), ctypes.byref(nc))
         return st, x2, hist[:nc.value + 1]
+
+    # ------------------------------------------------- Crank-Nicolson step
+    def convective(self, x):
+        out = np.zeros(self.n())
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        self.L.or_convective(self.c, _p(x), _p(out))
+        return out
+
+    @staticmethod
+    def _opt(a):
+        return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+    def cn_rhs(self, xn, Nh, dt, f=None, bc=None, body=(0, 0, 0, 0, 0), walls=(0, 0, 0, 0)):
+        b = np.zeros(self.n())
+        xn = np.ascontiguousarray(xn, dtype=np.float64)
+        Nh = np.ascontiguousarray(Nh, dtype=np.float64)
+        f, bc = self._opt(f), self._opt(bc)
+        bd = np.array(body, dtype=np.float64)
+        wl = np.array(walls, dtype=np.float64)
+        self.L.or_cn_rhs(self.c, _p(xn), _p(Nh), None if f is None else f.ctypes.data, dt,
+                         None if bc is None else bc.ctypes.data, _p(bd), _p(wl), _p(b))
+        return b
+
+    def cn_step(self, x, N1, N2, step, dt, f=None, bc=None, body=(0, 0, 0, 0, 0), walls=(0, 0, 0, 0), tol=1e-10,
+                eps=1e-6, kmax=10):
+        x2 = np.array(x, dtype=np.float64)
+        N1 = np.array(N1, dtype=np.float64)
+        N2 = np.array(N2, dtype=np.float64)
+        f, bc = self._opt(f), self._opt(bc)
+        bd = np.array(body, dtype=np.float64)
+        wl = np.array(walls, dtype=np.float64)
+        info = np.zeros(3)
+        st = self.L.or_cn_step(self.c, _p(x2), _p(N1), _p(N2), step, None if f is None else f.ctypes.data,
+                               None if bc is None else bc.ctypes.data, dt, _p(bd), _p(wl), tol, eps, kmax, _p(info))
+        return st, x2, N1, N2, info
+

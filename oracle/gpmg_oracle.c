@@ -1280,3 +1280,180 @@ int or_solve(void *vc, double *x, const double *b, double tol, int max_cycles, d
     }
     return OR_NOT_CONVERGED;
 }
+
+/* ------------------------------------------------------ Crank-Nicolson step */
+
+/* Convective term N = u . grad u at every internal u and v node of level 0
+ * (Sect. 2; central differences, the cross velocity averaged over the four
+ * nearest nodes of the other grid).  out is a flat vector, zero elsewhere. */
+void or_convective(void *vc, const double *x, double *out)
+{
+    ctx_t *c = (ctx_t *)vc;
+    level_t *l = &c->lv[0];
+    int N = l->N;
+    double h = l->h;
+    memset(out, 0, sizeof(double) * l->n);
+    for (int j = 0; j < N; j++)
+        for (int i = 1; i < N; i++) {
+            if (ttype(l, G_U, i, j) != T_INTERNAL) continue;
+            double u = x[iU(l, i, j)];
+            double vb = 0.25 * (x[iV(l, i - 1, j)] + x[iV(l, i, j)] + x[iV(l, i - 1, j + 1)] + x[iV(l, i, j + 1)]);
+            double dudx = (x[iU(l, i + 1, j)] - x[iU(l, i - 1, j)]) / (2.0 * h);
+            double dudy = (x[iU(l, i, j + 1)] - x[iU(l, i, j - 1)]) / (2.0 * h);
+            out[iU(l, i, j)] = u * dudx + vb * dudy;
+        }
+    for (int j = 1; j < N; j++)
+        for (int i = 0; i < N; i++) {
+            if (ttype(l, G_V, i, j) != T_INTERNAL) continue;
+            double v = x[iV(l, i, j)];
+            double ub = 0.25 * (x[iU(l, i, j - 1)] + x[iU(l, i + 1, j - 1)] + x[iU(l, i, j)] + x[iU(l, i + 1, j)]);
+            double dvdx = (x[iV(l, i + 1, j)] - x[iV(l, i - 1, j)]) / (2.0 * h);
+            double dvdy = (x[iV(l, i, j + 1)] - x[iV(l, i, j - 1)]) / (2.0 * h);
+            out[iV(l, i, j)] = ub * dvdx + v * dvdy;
+        }
+}
+
+/* Right-hand side of the CN system (Eq. NSCN1 with the convective term moved
+ * to the right, Eq. spaceprob): at internal u, v nodes
+ *     b = u^n + alpha lap u^n + dt f - dt Nh,
+ * continuity rows 0, ghost rows (Eq. BCu) the rigid-body velocity at B,
+ * wall and box-ghost rows the wall velocities, extrapolation rows and the
+ * mean row 0.  Boundary values: from the flat vector bc at the ghost-class
+ * rows when bc is given; otherwise body = {U, V, omega, cx, cy}:
+ * u_b(B) = (U - omega (B_y - cy), V + omega (B_x - cx)) and walls = {u on
+ * y = y0, u on y = y0 + L, v on x = x0, v on x = x0 + L} (tangential
+ * velocities; normal velocities 0).
+ * f: flat vector with the forcing at internal u, v nodes (NULL for none). */
+void or_cn_rhs(void *vc, const double *xn, const double *Nh, const double *f, double dt, const double *bc,
+               const double *body, const double *walls, double *b)
+{
+    ctx_t *c = (ctx_t *)vc;
+    level_t *l = &c->lv[0];
+    int N = l->N;
+    double h = l->h, a = c->alpha / (h * h);
+    memset(b, 0, sizeof(double) * l->n);
+    for (int j = 0; j < N; j++)
+        for (int i = 1; i < N; i++) {
+            if (ttype(l, G_U, i, j) != T_INTERNAL) continue;
+            int k = iU(l, i, j);
+            double lap = xn[iU(l, i + 1, j)] + xn[iU(l, i - 1, j)] + xn[iU(l, i, j + 1)] + xn[iU(l, i, j - 1)] - 4.0 * xn[k];
+            b[k] = xn[k] + a * lap + dt * (f ? f[k] : 0.0) - dt * Nh[k];
+        }
+    for (int j = 1; j < N; j++)
+        for (int i = 0; i < N; i++) {
+            if (ttype(l, G_V, i, j) != T_INTERNAL) continue;
+            int k = iV(l, i, j);
+            double lap = xn[iV(l, i + 1, j)] + xn[iV(l, i - 1, j)] + xn[iV(l, i, j + 1)] + xn[iV(l, i, j - 1)] - 4.0 * xn[k];
+            b[k] = xn[k] + a * lap + dt * (f ? f[k] : 0.0) - dt * Nh[k];
+        }
+    for (int k = 0; k < l->ngh; k++) {
+        ghost_t *G = &l->gh[k];
+        if (G->kind != 0) continue;
+        int kk = iG(l, G->grid, G->i, G->j);
+        double ub = body[0] - body[2] * (G->yB - body[4]);
+        double vb = body[1] + body[2] * (G->xB - body[3]);
+        b[kk] = bc ? bc[kk] : (G->grid == G_U ? ub : vb);
+    }
+    for (int i = 1; i < N; i++) {
+        b[iU(l, i, -1)] = bc ? bc[iU(l, i, -1)] : walls[0];
+        b[iU(l, i, N)] = bc ? bc[iU(l, i, N)] : walls[1];
+    }
+    for (int j = 1; j < N; j++) {
+        b[iV(l, -1, j)] = bc ? bc[iV(l, -1, j)] : walls[2];
+        b[iV(l, N, j)] = bc ? bc[iV(l, N, j)] : walls[3];
+    }
+    if (bc) { /* wall-normal velocities on the walls */
+        for (int j = 0; j < N; j++) {
+            b[iU(l, 0, j)] = bc[iU(l, 0, j)];
+            b[iU(l, N, j)] = bc[iU(l, N, j)];
+        }
+        for (int i = 0; i < N; i++) {
+            b[iV(l, i, 0)] = bc[iV(l, i, 0)];
+            b[iV(l, i, N)] = bc[iV(l, i, N)];
+        }
+    }
+}
+
+/* max |b - M x| over internal momentum rows (Eq. iterativeNS) and max |b| there */
+void or_momentum_residual(void *vc, const double *x, const double *b, double *res, double *bmax)
+{
+    ctx_t *c = (ctx_t *)vc;
+    level_t *l = &c->lv[0];
+    int N = l->N;
+    row_t R;
+    double m = 0.0, mb = 0.0;
+    for (int g = 0; g < 2; g++) {
+        int ilo = g == G_V ? -1 : 0, jlo = g == G_U ? -1 : 0;
+        for (int j = jlo; j <= N; j++)
+            for (int i = ilo; i <= N; i++) {
+                if (ttype(l, g, i, j) != T_INTERNAL) continue;
+                int k = iG(l, g, i, j);
+                get_row(c, 0, g, i, j, &R);
+                double v = fabs(row_residual(&R, x, b[k]));
+                if (v > m) m = v;
+                if (fabs(b[k]) > mb) mb = fabs(b[k]);
+            }
+    }
+    *res = m;
+    *bmax = mb;
+}
+
+/* One CN step (Sect. 2) from the state x (u^n, v^n, p, xi on level 0) with the
+ * convective history N1 = N^{n-1}, N2 = N^{n-2} (flat vectors).  step is n.
+ * n < 2: mid-point Picard iteration (Eq. NSitconv) until Eq. (iterativeNS)
+ * holds with eps (at most kmax iterations); n >= 2: extrapolation
+ * (Eq. extrUdU).  Each linear solve runs the multigrid to tol from the
+ * previous iterate.  On return x holds the new state, N1/N2 are rotated.
+ * info = {picard iterations, total cycles, last residual}. */
+int or_cn_step(void *vc, double *x, double *N1, double *N2, int step, const double *f, const double *bc, double dt,
+               const double *body, const double *walls, double tol, double eps, int kmax, double *info)
+{
+    ctx_t *c = (ctx_t *)vc;
+    level_t *l = &c->lv[0];
+    int n = l->n, st = OR_OK, cycles = 0, it = 0;
+    double *Nn = (double *)malloc(sizeof(double) * n), *Nh = (double *)malloc(sizeof(double) * n);
+    double *Nk = (double *)malloc(sizeof(double) * n), *b = (double *)malloc(sizeof(double) * n);
+    double *xn = (double *)malloc(sizeof(double) * n), *hist = (double *)malloc(sizeof(double) * 1024);
+    memcpy(xn, x, sizeof(double) * n);
+    or_convective(c, xn, Nn);
+    double res = 0.0;
+    if (step >= 2) {
+        for (int k = 0; k < n; k++) Nh[k] = Nn[k] + 0.5 * N1[k] - 0.5 * N2[k];
+        or_cn_rhs(c, xn, Nh, f, dt, bc, body, walls, b);
+        int nc = 0;
+        st = or_solve(c, x, b, tol, 1000, hist, &nc);
+        cycles += nc;
+        res = hist[nc];
+    } else {
+        /* ||f~|| of Eq. (iterativeNS): f~ = u^n + alpha lap u^n + dt f */
+        double fmax, dummy;
+        memset(Nk, 0, sizeof(double) * n);
+        or_cn_rhs(c, xn, Nk, f, dt, bc, body, walls, b);
+        or_momentum_residual(c, xn, b, &dummy, &fmax);
+        memcpy(Nh, Nn, sizeof(double) * n); /* u^{n+1,0} = u^n */
+        for (it = 1; it <= kmax; it++) {
+            or_cn_rhs(c, xn, Nh, f, dt, bc, body, walls, b);
+            int nc = 0;
+            st = or_solve(c, x, b, tol, 1000, hist, &nc);
+            cycles += nc;
+            res = hist[nc];
+            if (st != OR_OK) break;
+            or_convective(c, x, Nk);
+            for (int k = 0; k < n; k++) Nh[k] = 0.5 * (Nn[k] + Nk[k]);
+            or_cn_rhs(c, xn, Nh, f, dt, bc, body, walls, b);
+            double rm, bm;
+            or_momentum_residual(c, x, b, &rm, &bm);
+            double lim = eps * (fmax > 1.0 ? fmax : 1.0);
+            if (rm < lim) break;
+        }
+        if (it > kmax) it = kmax;
+    }
+    memcpy(N2, N1, sizeof(double) * n);
+    memcpy(N1, Nn, sizeof(double) * n);
+    info[0] = it;
+    info[1] = cycles;
+    info[2] = res;
+    free(Nn); free(Nh); free(Nk); free(b); free(xn); free(hist);
+    return st;
+}
+

@@ -97,6 +97,7 @@ struct Ctx {
     int L;
     Level lv[MAX_LEVELS];
     double *phi;        // paper-sign half lattice (2N+1)^2
+    double *cn_xn, *cn_Nn, *cn_Nh, *cn_b;  // cn_step scratch (finest level)
     // coarsest level dense inverse
     int nc;             // unknowns of the coarsest level (flat order)
     double *Minv;       // nc x nc
@@ -121,6 +122,13 @@ struct Ctx {
     cudaEvent_t tmr_ev[2 * 512];
     double tmr_ms;
     long long tmr_launches;
+    // captured mg_solve iterations: [0] FP64 cycle + residual, [1] FP32 cycle
+    // inside FP64 residual correction; keyed by the iterate and rhs pointers
+    cudaGraphExec_t gexec[2];
+    const void *gx[2], *gb[2];
+    int gvalid[2];
+    long long glaunches[2];
+    int graphs_off;
     int geom_ok;
     int coarse_ok;
     double alpha_factored;

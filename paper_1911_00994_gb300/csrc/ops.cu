@@ -8,6 +8,10 @@
 
 namespace gpmg {
 
+// levels solved by the one-block smoother, and ghost lists swept by one block
+constexpr int SMALL_N = 64;
+constexpr int GHOST_BLOCK_ROWS = 16384;
+
 template <typename T> struct LevelArgs {
     int N, P;
     long long F;
@@ -32,11 +36,9 @@ __device__ inline double nanmax(double a, double b) { return (a != a || b != b) 
 template <typename T>
 __global__ void k_residual(LevelArgs<T> A, const T *x, const T *b, T *r, double *part)
 {
-    int col = blockIdx.x * blockDim.x + threadIdx.x;
-    int row = blockIdx.y;
     double psum = 0.0, rmax = 0.0;
-    if (col < A.P) {
-        long long s = (long long)row * A.P + col;
+    const long long nslot = (long long)(A.N + 2) * A.P;
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < nslot; s += (long long)gridDim.x * blockDim.x) {
         const T *u = x, *v = x + A.F, *p = x + 2 * A.F;
         T xi = x[3 * A.F];
         uint8_t tu = A.tU[s], tv = A.tV[s], tp = A.tP[s];
@@ -59,7 +61,7 @@ __global__ void k_residual(LevelArgs<T> A, const T *x, const T *b, T *r, double 
             T rr = b[sp] - Ac;
             r[sp] = rr;
             rmax = nanmax(rmax, fabs((double)rr));
-            psum = (double)p[s];
+            psum += (double)p[s];
         } else if (tp == T_INACTIVE) r[2 * A.F + s] = 0;
     }
     // block reduction (fixed shape: deterministic)
@@ -75,9 +77,8 @@ __global__ void k_residual(LevelArgs<T> A, const T *x, const T *b, T *r, double 
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        long long bid = (long long)blockIdx.y * gridDim.x + blockIdx.x;
-        part[2 * bid] = ss[0];
-        part[2 * bid + 1] = sm[0];
+        part[2 * blockIdx.x] = ss[0];
+        part[2 * blockIdx.x + 1] = sm[0];
     }
 }
 
@@ -137,12 +138,8 @@ __global__ void k_residual_final(const double *part, int nb, const T *b, T *r, l
 // full boxes (no ghost border): Schur complement of the pressure unknown,
 // colour (i + 3 j) mod 5; borders that are not internal stay frozen
 template <typename T>
-__global__ void k_box_full(LevelArgs<T> A, T *x, const T *b, int colour)
+__device__ __forceinline__ void box_full_one(const LevelArgs<T> &A, T *x, const T *b, int i, int j)
 {
-    int j = blockIdx.y;
-    int i0 = ((colour - 3 * j) % 5 + 5) % 5;
-    int i = i0 + 5 * (blockIdx.x * blockDim.x + threadIdx.x);
-    if (i >= A.N) return;
     long long s = (long long)(j + 1) * A.P + (i + 1);
     if (A.tP[s] != T_INTERNAL) return;
     uint8_t tW = A.tU[s], tE = A.tU[s + 1], tS = A.tV[s], tN = A.tV[s + A.P];
@@ -207,109 +204,159 @@ __global__ void k_box_full(LevelArgs<T> A, T *x, const T *b, int colour)
     p[s] += dp;
 }
 
-// cut boxes of one colour (i mod 5, j mod 5): p, the internal borders
-// (momentum rows) and the ghost borders (their ghost rows) solved together by
-// a pivoted LU of at most 5 x 5
 template <typename T>
-__global__ void k_box_cut(LevelArgs<T> A, T *x, const T *b, CutList cut, GhostList gh, int beg, int end)
+__global__ void k_box_full(LevelArgs<T> A, T *x, const T *b, int colour)
 {
-    int k = beg + blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= end) return;
+    int j = blockIdx.y;
+    int i0 = ((colour - 3 * j) % 5 + 5) % 5;
+    int i = i0 + 5 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (i >= A.N) return;
+    box_full_one<T>(A, x, b, i, j);
+}
+
+// row of border f of a cut box: momentum row (internal border) or its ghost
+// row (object-ghost border); identity when the border takes no part
+template <typename T, int f>
+__device__ __forceinline__ void cut_row(const LevelArgs<T> &A, const T *x, const T *b, const CutList &cut,
+                                        const GhostList &gh, const T *w, int k, const long long (&unk)[5],
+                                        const bool (&act)[5], const uint8_t (&ft)[4], T (&M)[5][5], T (&r)[5])
+{
+    const long long F = A.F;
+    const long long P = A.P;
+    if (!act[f]) {
+        M[f][f] = 1;
+        return;
+    }
+    if (ft[f] == T_INTERNAL) {
+        // momentum row of border f: centre d, four neighbours -a, pressure pair
+        long long o = unk[f];
+        constexpr bool isu = f < 2;
+        long long loc = isu ? o : o - F;
+        const T *xx = isu ? x : x + F;
+        const T *pp = x + 2 * F;
+        long long pm = isu ? loc - 1 : loc - P;
+        T Ax = A.d * xx[loc] - A.a * (xx[loc + 1] + xx[loc - 1] + xx[loc + P] + xx[loc - P]) + A.q * (pp[loc] - pp[pm]);
+        r[f] = b[o] - Ax;
+        M[f][f] += A.d;
+        // the opposite border of the same direction is a neighbour at +-1 (u) or +-P (v)
+        constexpr int opp = f ^ 1;
+        if (act[opp]) M[f][opp] -= A.a;
+        // pressure: p(cell) enters W and S rows with +1/h, E and N rows with -1/h
+        M[f][4] += (f == 0 || f == 2) ? A.q : -A.q;
+    } else {
+        int g = cut.gface[(long long)f * cut.cap + k];
+        int nst = gh.nst[g];
+        T acc = b[gh.node[g]];
+        for (int m = 0; m < nst; m++) {
+            int id = gh.st[(long long)m * gh.cap + g];
+            T wm = w[(long long)m * gh.cap + g];
+            acc -= wm * x[id];
+            if (act[0] && unk[0] == id) M[f][0] += wm;
+            if (act[1] && unk[1] == id) M[f][1] += wm;
+            if (act[2] && unk[2] == id) M[f][2] += wm;
+            if (act[3] && unk[3] == id) M[f][3] += wm;
+        }
+        r[f] = acc;
+    }
+}
+
+// One cut box (an internal cell with a ghost border): p, the internal borders
+// (momentum rows) and the object-ghost borders (their ghost rows) solved
+// together by a pivoted LU.  The system is always 5 x 5: a border that takes
+// no part gets an identity row and a zero column, which leaves the pivots and
+// the result of the smaller system unchanged; fixed sizes keep it in registers.
+template <typename T>
+__device__ __forceinline__ void box_cut_one(const LevelArgs<T> &A, T *x, const T *b, const CutList &cut,
+                                            const GhostList &gh, int k)
+{
     long long s = cut.cell[k];
     const long long F = A.F;
+    const long long P = A.P;
     const T *w = gw<T>(gh);
-    // face unknowns: W, E, S, N as vector indices
-    long long fidx[4] = {s, s + 1, F + s, F + s + A.P};
-    uint8_t ft[4] = {A.tU[s], A.tU[s + 1], A.tV[s], A.tV[s + A.P]};
-    long long unk[5];
-    int row_kind[5], row_f[5];
-    int n = 0;
-    for (int f = 0; f < 4; f++)
-        if (ft[f] == T_INTERNAL || ft[f] == T_GHOST) {
-            unk[n] = fidx[f];
-            row_kind[n] = ft[f];
-            row_f[n] = f;
-            n++;
-        }
-    unk[n] = 2 * F + s;
-    row_kind[n] = -1;
-    row_f[n] = -1;
-    n++;
-    T M[25], rhs[5];
-    const T a = A.a, d = A.d, q = A.q;
-    for (int r = 0; r < n; r++) {
-        for (int c = 0; c < n; c++) M[r * n + c] = 0;
-        if (row_kind[r] == T_INTERNAL) {
-            // momentum row of face f: centre d, 4 neighbours -a, pressure pair
-            long long o = unk[r];
-            bool isu = row_f[r] < 2;
-            long long loc = isu ? o : o - F;
-            const T *xx = isu ? x : x + F;
-            const T *pp = x + 2 * F;
-            long long pm = isu ? loc - 1 : loc - A.P;  // the other pressure cell
-            T Ax = d * xx[loc] - a * (xx[loc + 1] + xx[loc - 1] + xx[loc + A.P] + xx[loc - A.P]) + q * (pp[loc] - pp[pm]);
-            rhs[r] = b[o] - Ax;
-            long long nb[4] = {o + 1, o - 1, o + A.P, o - A.P};
-            for (int c = 0; c < n; c++) {
-                if (unk[c] == o) M[r * n + c] += d;
-                for (int m = 0; m < 4; m++)
-                    if (unk[c] == nb[m]) M[r * n + c] -= a;
-                if (unk[c] == 2 * F + loc) M[r * n + c] += q;
-                if (unk[c] == 2 * F + pm) M[r * n + c] -= q;
-            }
-        } else if (row_kind[r] == T_GHOST) {
-            int g = cut.gface[(long long)row_f[r] * cut.cap + k];
-            int nst = gh.nst[g];
-            T acc = b[gh.node[g]];
-            for (int m = 0; m < nst; m++) {
-                int id = gh.st[(long long)m * gh.cap + g];
-                T wm = w[(long long)m * gh.cap + g];
-                acc -= wm * x[id];
-                for (int c = 0; c < n; c++)
-                    if (unk[c] == id) M[r * n + c] += wm;
-            }
-            rhs[r] = acc;
-        } else {
-            // continuity row of the cell
-            const T *u = x, *v = x + F;
-            T xi = x[3 * F];
-            rhs[r] = b[2 * F + s] - (q * (u[s + 1] - u[s] + v[s + A.P] - v[s]) - xi);
-            for (int c = 0; c < n; c++) {
-                if (unk[c] == s + 1) M[r * n + c] += q;
-                if (unk[c] == s) M[r * n + c] -= q;
-                if (unk[c] == F + s + A.P) M[r * n + c] += q;
-                if (unk[c] == F + s) M[r * n + c] -= q;
-            }
-        }
+    long long unk[5] = {s, s + 1, F + s, F + s + P, 2 * F + s};
+    uint8_t ft[4] = {A.tU[s], A.tU[s + 1], A.tV[s], A.tV[s + P]};
+    bool act[5];
+#pragma unroll
+    for (int f = 0; f < 4; f++) act[f] = ft[f] == T_INTERNAL || ft[f] == T_GHOST;
+    act[4] = true;
+    T M[5][5], r[5];
+    const T q = A.q;
+#pragma unroll
+    for (int rr = 0; rr < 5; rr++) {
+#pragma unroll
+        for (int c = 0; c < 5; c++) M[rr][c] = 0;
+        r[rr] = 0;
     }
-    // LU with partial pivoting (first largest pivot)
-    int piv[5];
-    for (int c = 0; c < n; c++) {
+    cut_row<T, 0>(A, x, b, cut, gh, w, k, unk, act, ft, M, r);
+    cut_row<T, 1>(A, x, b, cut, gh, w, k, unk, act, ft, M, r);
+    cut_row<T, 2>(A, x, b, cut, gh, w, k, unk, act, ft, M, r);
+    cut_row<T, 3>(A, x, b, cut, gh, w, k, unk, act, ft, M, r);
+    {
+        // continuity row of the cell
+        const T *u = x, *v = x + F;
+        T xi = x[3 * F];
+        r[4] = b[2 * F + s] - (q * (u[s + 1] - u[s] + v[s + P] - v[s]) - xi);
+        if (act[0]) M[4][0] -= q;
+        if (act[1]) M[4][1] += q;
+        if (act[2]) M[4][2] -= q;
+        if (act[3]) M[4][3] += q;
+    }
+    // LU with partial pivoting (first largest pivot), applied to the rhs
+    bool ok = true;
+#pragma unroll
+    for (int c = 0; c < 5; c++) {
         int pr = c;
-        T best = fabs(M[c * n + c]);
-        for (int r = c + 1; r < n; r++) {
-            T vv = fabs(M[r * n + c]);
-            if (vv > best) { best = vv; pr = r; }
+        T best = fabs(M[c][c]);
+#pragma unroll
+        for (int rr = c + 1; rr < 5; rr++) {
+            T vv = fabs(M[rr][c]);
+            if (vv > best) { best = vv; pr = rr; }
         }
-        piv[c] = pr;
-        if (!(best > (T)0)) return;
-        if (pr != c)
-            for (int m = 0; m < n; m++) { T t = M[c * n + m]; M[c * n + m] = M[pr * n + m]; M[pr * n + m] = t; }
-        for (int r = c + 1; r < n; r++) {
-            T f = M[r * n + c] / M[c * n + c];
-            M[r * n + c] = f;
-            for (int m = c + 1; m < n; m++) M[r * n + m] -= f * M[c * n + m];
+        ok = ok && best > (T)0;
+        // row swap by selection (keeps the system in registers)
+#pragma unroll
+        for (int rr = c + 1; rr < 5; rr++) {
+            const bool sw = rr == pr;
+#pragma unroll
+            for (int m = 0; m < 5; m++) {
+                T lo = M[c][m], hi = M[rr][m];
+                M[c][m] = sw ? hi : lo;
+                M[rr][m] = sw ? lo : hi;
+            }
+            T lo = r[c], hi = r[rr];
+            r[c] = sw ? hi : lo;
+            r[rr] = sw ? lo : hi;
+        }
+#pragma unroll
+        for (int rr = c + 1; rr < 5; rr++) {
+            T f = M[rr][c] / M[c][c];
+#pragma unroll
+            for (int m = c + 1; m < 5; m++) M[rr][m] -= f * M[c][m];
+            r[rr] -= f * r[c];
         }
     }
-    for (int c = 0; c < n; c++)
-        if (piv[c] != c) { T t = rhs[c]; rhs[c] = rhs[piv[c]]; rhs[piv[c]] = t; }
-    for (int r = 0; r < n; r++)
-        for (int m = 0; m < r; m++) rhs[r] -= M[r * n + m] * rhs[m];
-    for (int r = n - 1; r >= 0; r--) {
-        for (int m = r + 1; m < n; m++) rhs[r] -= M[r * n + m] * rhs[m];
-        rhs[r] /= M[r * n + r];
+#pragma unroll
+    for (int rr = 4; rr >= 0; rr--) {
+#pragma unroll
+        for (int m = rr + 1; m < 5; m++) r[rr] -= M[rr][m] * r[m];
+        r[rr] /= M[rr][rr];
     }
-    for (int r = 0; r < n; r++) x[unk[r]] += rhs[r];
+    if (!ok) return;
+#pragma unroll
+    for (int f = 0; f < 5; f++)
+        if (act[f]) x[unk[f]] += r[f];
+}
+
+// all 25 colours (i mod 5, j mod 5) of the cut boxes in one block: the
+// barrier between colours orders them; boxes of one colour are independent
+template <typename T>
+__global__ void __launch_bounds__(256) k_box_cut(LevelArgs<T> A, T *x, const T *b, CutList cut, GhostList gh)
+{
+    for (int colour = 0; colour < 25; colour++) {
+        int beg = cut.off[colour], end = cut.off[colour + 1];
+        for (int k = beg + threadIdx.x; k < end; k += blockDim.x) box_cut_one<T>(A, x, b, cut, gh, k);
+        __syncthreads();
+    }
 }
 
 // internal faces with no internal cell: point Jacobi (compute, then apply)
@@ -339,16 +386,15 @@ template <typename T> __global__ void k_apply_list(T *x, const int *list, const 
 template <typename T>
 __global__ void k_scalar_partial(LevelArgs<T> A, const T *x, const T *b, double *part)
 {
-    int col = blockIdx.x * blockDim.x + threadIdx.x;
-    int row = blockIdx.y;
     double s = 0.0, m = 0.0;
-    if (col < A.P) {
-        long long sl = (long long)row * A.P + col;
+    const long long nslot = (long long)(A.N + 2) * A.P;
+    for (long long sl = blockIdx.x * (long long)blockDim.x + threadIdx.x; sl < nslot;
+         sl += (long long)gridDim.x * blockDim.x) {
         if (A.tP[sl] == T_INTERNAL) {
             const T *u = x, *v = x + A.F;
             T div = (u[sl + 1] - u[sl] + v[sl + A.P] - v[sl]) * A.q;
-            s = (double)(div - b[2 * A.F + sl]);
-            m = (double)x[2 * A.F + sl];
+            s += (double)(div - b[2 * A.F + sl]);
+            m += (double)x[2 * A.F + sl];
         }
     }
     __shared__ double ss[256], sm[256];
@@ -363,9 +409,8 @@ __global__ void k_scalar_partial(LevelArgs<T> A, const T *x, const T *b, double 
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        long long bid = (long long)blockIdx.y * gridDim.x + blockIdx.x;
-        part[2 * bid] = ss[0];
-        part[2 * bid + 1] = sm[0];
+        part[2 * blockIdx.x] = ss[0];
+        part[2 * blockIdx.x + 1] = sm[0];
     }
 }
 
@@ -492,24 +537,24 @@ __global__ void k_restrict(int Nf, int Pf, long long Ff, const uint8_t *tUf, con
 }
 
 // 1-D interpolation taps (see the oracle's description of the same rule)
-__device__ inline int taps(int k, bool aligned, int lo, int hi, int *K, double *w)
+template <typename T> __device__ inline int taps(int k, bool aligned, int lo, int hi, int *K, T *w)
 {
     bool even = (k % 2 == 0);
     if (aligned) {
-        if (even) { K[0] = k / 2; w[0] = 1.0; return 1; }
-        K[0] = (k - 1) / 2; w[0] = 0.5;
-        K[1] = K[0] + 1; w[1] = 0.5;
+        if (even) { K[0] = k / 2; w[0] = (T)1; return 1; }
+        K[0] = (k - 1) / 2; w[0] = (T)0.5;
+        K[1] = K[0] + 1; w[1] = (T)0.5;
         return 2;
     }
     int Kc = even ? k / 2 : (k - 1) / 2;
     int Ko = even ? Kc - 1 : Kc + 1;
     if (Ko < lo || Ko > hi) {
-        K[0] = Kc; w[0] = 1.25;
-        K[1] = 2 * Kc - Ko; w[1] = -0.25;
+        K[0] = Kc; w[0] = (T)1.25;
+        K[1] = 2 * Kc - Ko; w[1] = (T)-0.25;
         return 2;
     }
-    K[0] = Kc; w[0] = 0.75;
-    K[1] = Ko; w[1] = 0.25;
+    K[0] = Kc; w[0] = (T)0.75;
+    K[1] = Ko; w[1] = (T)0.25;
     return 2;
 }
 
@@ -532,18 +577,18 @@ __global__ void k_prolong(int Nf, int Pf, long long Ff, const uint8_t *tUf, cons
         int Ilo = g == G_V ? -1 : 0, Ihi = g == G_P ? Nc - 1 : Nc;
         int Jlo = g == G_U ? -1 : 0, Jhi = g == G_P ? Nc - 1 : Nc;
         int KI[2], KJ[2];
-        double wi[2], wj[2];
-        int ni = taps(i, g == G_U, Ilo, Ihi, KI, wi);
-        int nj = taps(j, g == G_V, Jlo, Jhi, KJ, wj);
-        double s = 0.0, ws = 0.0;
+        T wi[2], wj[2];
+        int ni = taps<T>(i, g == G_U, Ilo, Ihi, KI, wi);
+        int nj = taps<T>(j, g == G_V, Jlo, Jhi, KJ, wj);
+        T s = 0, ws = 0;
         for (int a = 0; a < nj; a++)
             for (int bb = 0; bb < ni; bb++) {
                 if (tget(tc[g], g, Nc, Pc, KI[bb], KJ[a]) == T_INACTIVE) continue;
-                double w = wj[a] * wi[bb];
-                s += w * (double)eH[g * Fc + (long long)(KJ[a] + 1) * Pc + (KI[bb] + 1)];
+                T w = wj[a] * wi[bb];
+                s += w * eH[g * Fc + (long long)(KJ[a] + 1) * Pc + (KI[bb] + 1)];
                 ws += w;
             }
-        if (ws > 0.0) x[g * Ff + sf] += (T)(s / ws);
+        if (ws > (T)0) x[g * Ff + sf] += ws == (T)1 ? s : s / ws;
     }
     if (row == 0 && col == 0) x[3 * Ff] += eH[3 * Fc];
 }
@@ -576,6 +621,112 @@ __global__ void k_add_float(double *x, const float *e, long long n)
 {
     long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (k < n) x[k] += (double)e[k];
+}
+
+// ---------------------------------------------- one-block kernels, small levels
+
+// lambda Eq. (ghostrelax) Jacobi sweeps in one block (levels with few rows)
+template <typename T>
+__device__ __forceinline__ void ghost_sweeps_block(GhostList &gh, int nrows, T *x, const T *b, T dtau, int lambda)
+{
+    const T *w = gw<T>(gh);
+    T *upd = gupd<T>(gh);
+    for (int it = 0; it < lambda; it++) {
+        for (int k = threadIdx.x; k < nrows; k += blockDim.x) {
+            int nst = gh.nst[k];
+            T s = b[gh.node[k]];
+            for (int q = 0; q < nst; q++) s -= w[(long long)q * gh.cap + k] * x[gh.st[(long long)q * gh.cap + k]];
+            upd[k] = dtau * s;
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < nrows; k += blockDim.x) x[gh.node[k]] += upd[k];
+        __syncthreads();
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_ghost_block(GhostList gh, int nrows, T *x, const T *b, T dtau, int lambda)
+{
+    ghost_sweeps_block<T>(gh, nrows, x, b, dtau, lambda);
+}
+
+// nu relaxations (Algorithm relax) of a small level in one block: full boxes
+// by 5 colours, cut boxes by 25 colours, lonely faces, xi and the mean
+// pressure, lambda ghost sweeps; the same steps in the same order as the
+// multi-kernel path, with block barriers in place of kernel boundaries
+template <typename T>
+__global__ void __launch_bounds__(512) k_smooth_small(LevelArgs<T> A, T *x, const T *b, CutList cut, GhostList gh,
+                                                         int nrows, const int *lonely, int nlonely, const int *nint,
+                                                         double h2, T dtau, int lambda, int nu)
+{
+    __shared__ double ss[1024], sm[1024];
+    __shared__ double shift;
+    const int N = A.N;
+    const int per_row = (N + 4) / 5;
+    T *upd = gupd<T>(gh);
+    for (int sweep = 0; sweep < nu; sweep++) {
+        for (int colour = 0; colour < 5; colour++) {
+            for (int idx = threadIdx.x; idx < N * per_row; idx += blockDim.x) {
+                int j = idx / per_row, t = idx - j * per_row;
+                int i = ((colour - 3 * j) % 5 + 5) % 5 + 5 * t;
+                if (i < N) box_full_one<T>(A, x, b, i, j);
+            }
+            __syncthreads();
+        }
+        for (int colour = 0; colour < 25; colour++) {
+            int beg = cut.off[colour], end = cut.off[colour + 1];
+            for (int k = beg + threadIdx.x; k < end; k += blockDim.x) box_cut_one<T>(A, x, b, cut, gh, k);
+            __syncthreads();
+        }
+        if (nlonely > 0) {
+            for (int k = threadIdx.x; k < nlonely; k += blockDim.x) {
+                long long o = lonely[k];
+                bool isu = o < A.F;
+                long long loc = isu ? o : o - A.F;
+                const T *xx = isu ? x : x + A.F;
+                const T *pp = x + 2 * A.F;
+                long long pm = isu ? loc - 1 : loc - A.P;
+                T Ax = A.d * xx[loc] - A.a * (xx[loc + 1] + xx[loc - 1] + xx[loc + A.P] + xx[loc - A.P]) +
+                       A.q * (pp[loc] - pp[pm]);
+                upd[k] = (b[o] - Ax) / A.d;
+            }
+            __syncthreads();
+            for (int k = threadIdx.x; k < nlonely; k += blockDim.x) x[lonely[k]] += upd[k];
+            __syncthreads();
+        }
+        // xi and the mean pressure
+        double sa = 0.0, ma = 0.0;
+        const long long nslot = (long long)(N + 2) * A.P;
+        for (long long sl = threadIdx.x; sl < nslot; sl += blockDim.x)
+            if (A.tP[sl] == T_INTERNAL) {
+                T div = (x[sl + 1] - x[sl] + x[A.F + sl + A.P] - x[A.F + sl]) * A.q;
+                sa += (double)(div - b[2 * A.F + sl]);
+                ma += (double)x[2 * A.F + sl];
+            }
+        ss[threadIdx.x] = sa;
+        sm[threadIdx.x] = ma;
+        __syncthreads();
+        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+            if (threadIdx.x < o) {
+                ss[threadIdx.x] += ss[threadIdx.x + o];
+                sm[threadIdx.x] += sm[threadIdx.x + o];
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            double n = (double)*nint;
+            x[3 * A.F] = (T)(ss[0] / n);
+            shift = ((double)b[3 * A.F] - h2 * sm[0]) / (h2 * n);
+        }
+        __syncthreads();
+        T sh = (T)shift;
+        for (long long sl = threadIdx.x; sl < nslot; sl += blockDim.x) {
+            uint8_t t = A.tP[sl];
+            if (t == T_INTERNAL || t == T_GHOST) x[2 * A.F + sl] += sh;
+        }
+        __syncthreads();
+        ghost_sweeps_block<T>(gh, nrows, x, b, dtau, lambda);
+    }
 }
 
 // ------------------------------------------------------------- event timer
@@ -628,14 +779,20 @@ template <typename T> LevelArgs<T> level_args(const Ctx *c, int lev)
 
 static inline dim3 frame_grid(const Level &l) { return dim3((l.P + 255) / 256, l.N + 2); }
 
+// blocks of the reduction kernels: enough to fill the GPU, at most 1024
+static inline int red_blocks(const Level &l)
+{
+    long long n = (l.F + 255) / 256;
+    return (int)(n < 1024 ? n : 1024);
+}
+
 template <typename T> void residual(Ctx *c, int lev, const T *x, const T *b, T *r)
 {
     const Level &l = c->lv[lev];
     cudaStream_t st = c->stream;
-    dim3 g = frame_grid(l);
-    int nb = g.x * g.y;
+    int nb = red_blocks(l);
     tmr_begin(c, KT_RESIDUAL, lev);
-    k_residual<T><<<g, 256, 0, st>>>(level_args<T>(c, lev), x, b, r, c->part);
+    k_residual<T><<<nb, 256, 0, st>>>(level_args<T>(c, lev), x, b, r, c->part);
     tmr_end(c, KT_RESIDUAL, lev);
     if (l.h_nrows > 0) k_ghost_residual<T><<<(l.h_nrows + 255) / 256, 256, 0, st>>>(l.gh, l.h_nrows, x, b, r, c->maxbits);
     double h = c->prm.L / (double)l.N;
@@ -656,14 +813,12 @@ template <typename T> void box_sweep(Ctx *c, int lev, T *x, const T *b)
         tmr_end(c, KT_BOX_FULL, lev);
         c->launches++;
     }
-    for (int colour = 0; colour < 25; colour++) {
-        int beg = l.h_cutoff[colour], end = l.h_cutoff[colour + 1];
-        if (end > beg) {
-            tmr_begin(c, KT_BOX_CUT, lev);
-            k_box_cut<T><<<(end - beg + 127) / 128, 128, 0, st>>>(A, x, b, l.cut, l.gh, beg, end);
-            tmr_end(c, KT_BOX_CUT, lev);
-            c->launches++;
-        }
+    if (l.h_ncut > 0) {
+        int nt = l.h_ncut >= 25 * 128 ? 256 : 128;
+        tmr_begin(c, KT_BOX_CUT, lev);
+        k_box_cut<T><<<1, nt, 0, st>>>(A, x, b, l.cut, l.gh);
+        tmr_end(c, KT_BOX_CUT, lev);
+        c->launches++;
     }
     if (l.h_nlonely > 0) {
         T *upd = (T *)c->part;
@@ -679,9 +834,9 @@ template <typename T> void scalar_update(Ctx *c, int lev, T *x, const T *b)
     cudaStream_t st = c->stream;
     LevelArgs<T> A = level_args<T>(c, lev);
     dim3 g = frame_grid(l);
-    int nb = g.x * g.y;
+    int nb = red_blocks(l);
     tmr_begin(c, KT_SCALAR, lev);
-    k_scalar_partial<T><<<g, 256, 0, st>>>(A, x, b, c->part);
+    k_scalar_partial<T><<<nb, 256, 0, st>>>(A, x, b, c->part);
     tmr_end(c, KT_SCALAR, lev);
     double h = c->prm.L / (double)l.N;
     k_scalar_final<T><<<1, 256, 0, st>>>(c->part, nb, x, b, 3 * l.F, h * h, l.nint, c->red + 1);
@@ -704,10 +859,26 @@ template <typename T> void ghost_sweep(Ctx *c, int lev, T *x, const T *b)
 
 template <typename T> void smooth(Ctx *c, int lev, T *x, const T *b, int nu)
 {
+    const Level &l = c->lv[lev];
+    if (nu <= 0) return;
+    if (l.N <= SMALL_N && l.h_nlonely <= l.gh.cap) {
+        double h = c->prm.L / (double)l.N;
+        k_smooth_small<T><<<1, 512, 0, c->stream>>>(level_args<T>(c, lev), x, b, l.cut, l.gh, l.h_nrows, l.lonely,
+                                                      l.h_nlonely, l.nint, h * h, (T)c->prm.dtau, c->prm.lambda, nu);
+        c->launches++;
+        return;
+    }
     for (int s = 0; s < nu; s++) {
         box_sweep<T>(c, lev, x, b);
         scalar_update<T>(c, lev, x, b);
-        for (int k = 0; k < c->prm.lambda; k++) ghost_sweep<T>(c, lev, x, b);
+        if (l.h_nrows > 0 && l.h_nrows <= GHOST_BLOCK_ROWS && c->prm.lambda > 0) {
+            tmr_begin(c, KT_GHOST, lev);
+            k_ghost_block<T><<<1, 1024, 0, c->stream>>>(l.gh, l.h_nrows, x, b, (T)c->prm.dtau, c->prm.lambda);
+            tmr_end(c, KT_GHOST, lev);
+            c->launches++;
+        } else {
+            for (int k = 0; k < c->prm.lambda; k++) ghost_sweep<T>(c, lev, x, b);
+        }
     }
 }
 

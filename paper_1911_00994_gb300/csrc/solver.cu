@@ -26,6 +26,12 @@ template <typename T> void coarse_solve(Ctx *c, const T *b, T *x);
 void to_float(Ctx *c, const double *a, float *b, long long n);
 void tmr_flush(Ctx *c);
 int residual_static(Ctx *c, int lev, const double *x, const double *b, double *r, double *norm_host);
+void cn_convective(Ctx *c, const double *x, const double *Nn, double *out, int mode);
+void cn_rhs(Ctx *c, const double *xn, const double *Nh, const double *f, double dt, const double *bc, const gp_body &body,
+            const gp_walls &walls, double *b);
+int cn_momentum_residual(Ctx *c, const double *x, const double *b, double *res, double *bmax);
+void cn_extrapolate(Ctx *c, const double *Nn, const double *N1, const double *N2, double *Nh);
+void cn_copy(Ctx *c, const double *a, double *b, long long n);
 void add_float(Ctx *c, double *x, const float *e, long long n);
 
 // ------------------------------------------------------------- workspace
@@ -134,6 +140,14 @@ static size_t carve(Ctx *c, char *base)
         if (need > maxpart) maxpart = need;
     }
     c->phi = cv.take<double>((size_t)(2 * p.N + 1) * (2 * p.N + 1));
+    if (p.cn_buffers) {
+        c->cn_xn = cv.take<double>(c->lv[0].VL);
+        c->cn_Nn = cv.take<double>(c->lv[0].VL);
+        c->cn_Nh = cv.take<double>(c->lv[0].VL);
+        c->cn_b = cv.take<double>(c->lv[0].VL);
+    } else {
+        c->cn_xn = c->cn_Nn = c->cn_Nh = c->cn_b = nullptr;
+    }
     c->npart = (int)maxpart;
     c->part = cv.take<double>(maxpart);
     c->red = cv.take<double>(32);
@@ -183,6 +197,74 @@ template <typename T> void cycle_rec(Ctx *c, int lev, T *x, const T *b)
     smooth<T>(c, lev, x, b, c->prm.nu2);
 }
 
+// one mg_solve iteration: the cycle and the finest FP64 residual (which = 0),
+// or FP32 cycle on the FP64 residual and the FP64 update (which = 1)
+static void solve_iteration(Ctx *c, int which, double *x, const double *b)
+{
+    Level &l0 = c->lv[0];
+    if (which == 1) {
+        to_float(c, l0.r, l0.bf, l0.VL);
+        zero_vec<float>(c, l0.xf, l0.VL);
+        cycle_rec<float>(c, 0, l0.xf, l0.bf);
+        add_float(c, x, l0.xf, l0.VL);
+    } else {
+        cycle_rec<double>(c, 0, x, b);
+    }
+    residual<double>(c, 0, x, b, l0.r);
+}
+
+void graphs_reset(Ctx *c)
+{
+    for (int w = 0; w < 2; w++)
+        if (c->gvalid[w]) {
+            cudaGraphExecDestroy(c->gexec[w]);
+            c->gvalid[w] = 0;
+        }
+}
+
+// replay (capturing first if needed) one iteration as a CUDA graph; false
+// when graphs are unavailable here (then the caller launches directly)
+static bool run_graph(Ctx *c, int which, double *x, const double *b)
+{
+    if (!c->prm.graphs || c->graphs_off || c->stream == nullptr || c->tmr_kernel >= 0) return false;
+    if (!c->gvalid[which] || c->gx[which] != x || c->gb[which] != b) {
+        if (c->gvalid[which]) {
+            cudaGraphExecDestroy(c->gexec[which]);
+            c->gvalid[which] = 0;
+        }
+        long long l0 = c->launches;
+        if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            c->graphs_off = 1;
+            return false;
+        }
+        solve_iteration(c, which, x, b);
+        long long per = c->launches - l0;  // kernels of one iteration
+        c->launches = l0;
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&c->gexec[which], g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            c->graphs_off = 1;
+            return false;
+        }
+        c->glaunches[which] = per;
+        c->gx[which] = x;
+        c->gb[which] = b;
+        c->gvalid[which] = 1;
+    }
+    if (cudaGraphLaunch(c->gexec[which], c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        graphs_reset(c);
+        c->graphs_off = 1;
+        return false;
+    }
+    c->launches += c->glaunches[which];
+    return true;
+}
+
 }  // namespace gpmg
 
 using namespace gpmg;
@@ -211,6 +293,7 @@ static gp_status ensure_coarse(gp_ctx *ctx)
     Ctx *c = &ctx->c;
     if (!c->geom_ok) return fail(ctx, GP_INVALID, "geometry_build has not succeeded");
     if (c->coarse_ok && c->alpha_factored == c->prm.alpha) return GP_OK;
+    graphs_reset(c);  // the captured launches carry alpha in their arguments
     return (gp_status)build_coarse_inverse(c);
 }
 
@@ -238,6 +321,8 @@ gp_status gp_params_default(gp_params *prm, int N, double x0, double y0, double 
     prm->snap = 0.3;
     prm->precision = GP_FP64;
     prm->max_cycles = 100;
+    prm->cn_buffers = 1;
+    prm->graphs = 1;
     return GP_OK;
 }
 
@@ -312,6 +397,7 @@ gp_status gp_destroy(gp_ctx *ctx)
     cudaStreamSynchronize(ctx->c.stream);
     if (ctx->c.tmr_ready)
         for (int k = 0; k < 2 * 512; k++) cudaEventDestroy(ctx->c.tmr_ev[k]);
+    graphs_reset(&ctx->c);
     delete ctx;
     return GP_OK;
 }
@@ -362,6 +448,7 @@ gp_status geometry_build(gp_ctx *ctx, const double *phi, int phi_fluid_positive)
     c->geom_ok = 0;
     c->coarse_ok = 0;
     c->msg[0] = 0;
+    graphs_reset(c);
     int s = build_geometry_levels(c, phi, phi_fluid_positive);
     if (s != GP_OK) return (gp_status)s;
     gp_status cs = check_cuda(ctx, "geometry_build");
@@ -535,15 +622,8 @@ gp_status mg_solve(gp_ctx *ctx, double *x, const double *b, double tol, gp_repor
     else if (r0 <= tol) st = GP_OK;
     else
         for (k = 1; k <= c->prm.max_cycles; k++) {
-            if (mixed) {
-                to_float(c, l0.r, l0.bf, l0.VL);
-                zero_vec<float>(c, l0.xf, l0.VL);
-                cycle_rec<float>(c, 0, l0.xf, l0.bf);
-                add_float(c, x, l0.xf, l0.VL);
-            } else {
-                cycle_rec<double>(c, 0, x, b);
-            }
-            residual<double>(c, 0, x, b, l0.r);
+            int which = mixed ? 1 : 0;
+            if (!run_graph(c, which, x, b)) solve_iteration(c, which, x, b);
             cudaMemcpyAsync(&nrm, c->red, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
             if (cudaStreamSynchronize(c->stream) != cudaSuccess) return check_cuda(ctx, "mg_solve");
             if (rep && rep->hist_host) rep->hist_host[k] = nrm;
@@ -569,6 +649,81 @@ gp_status mg_solve(gp_ctx *ctx, double *x, const double *b, double tol, gp_repor
     if (st == GP_NOT_CONVERGED) snprintf(c->msg, sizeof c->msg, "not converged: %.3e after %d cycles", nrm, k);
     if (st == GP_DIVERGED) snprintf(c->msg, sizeof c->msg, "diverged: %.3e (initial %.3e)", nrm, r0);
     gp_status cs = check_cuda(ctx, "mg_solve");
+    return cs != GP_OK ? cs : st;
+}
+
+gp_status gp_convective(gp_ctx *ctx, const double *x, double *out)
+{
+    if (!ctx || !ctx->c.geom_ok || !x || !out) return GP_INVALID;
+    cn_convective(&ctx->c, x, nullptr, out, 0);
+    return check_cuda(ctx, "gp_convective");
+}
+
+gp_status gp_cn_rhs(gp_ctx *ctx, const double *xn, const double *Nh, const double *f, double dt, const double *bc,
+                    const gp_body *body, const gp_walls *walls, double *b)
+{
+    if (!ctx || !ctx->c.geom_ok || !xn || !Nh || !b) return GP_INVALID;
+    gp_body bd = body ? *body : gp_body{0, 0, 0, 0, 0};
+    gp_walls wl = walls ? *walls : gp_walls{0, 0, 0, 0};
+    cn_rhs(&ctx->c, xn, Nh, f, dt, bc, bd, wl, b);
+    return check_cuda(ctx, "gp_cn_rhs");
+}
+
+gp_status cn_step(gp_ctx *ctx, double *x, double *N1, double *N2, int step, const double *f, const double *bc,
+                  double dt, double Re, const gp_body *body, const gp_walls *walls, double tol, double eps, int kmax,
+                  gp_cn_report *rep)
+{
+    if (!ctx || !x || !N1 || !N2 || step < 0 || !(dt > 0.0) || !(Re > 0.0) || !(tol >= 0.0) || kmax < 1)
+        return GP_INVALID;
+    Ctx *c = &ctx->c;
+    if (!c->cn_xn) return fail(ctx, GP_INVALID, "cn_step needs cn_buffers in gp_params");
+    if (!c->geom_ok) return fail(ctx, GP_INVALID, "geometry_build has not succeeded");
+    c->prm.alpha = dt / (2.0 * Re);
+    gp_body bd = body ? *body : gp_body{0, 0, 0, 0, 0};
+    gp_walls wl = walls ? *walls : gp_walls{0, 0, 0, 0};
+    const Level &l0 = c->lv[0];
+    long long VL = l0.VL;
+    cn_copy(c, x, c->cn_xn, VL);
+    cn_convective(c, c->cn_xn, nullptr, c->cn_Nn, 0);
+    gp_report r;
+    memset(&r, 0, sizeof r);
+    int cycles = 0, picard = 0;
+    double mom = 0.0;
+    gp_status st = GP_OK;
+    if (step >= 2) {
+        cn_extrapolate(c, c->cn_Nn, N1, N2, c->cn_Nh);
+        cn_rhs(c, c->cn_xn, c->cn_Nh, f, dt, bc, bd, wl, c->cn_b);
+        st = mg_solve(ctx, x, c->cn_b, tol, &r);
+        cycles = r.cycles;
+    } else {
+        // ||f~|| with f~ = u^n + alpha lap u^n + dt f (Eq. iterativeNS)
+        double dummy = 0.0, fmax = 0.0;
+        cudaMemsetAsync(c->cn_Nh, 0, VL * sizeof(double), c->stream);
+        cn_rhs(c, c->cn_xn, c->cn_Nh, f, dt, bc, bd, wl, c->cn_b);
+        if (cn_momentum_residual(c, c->cn_xn, c->cn_b, &dummy, &fmax) != GP_OK) return check_cuda(ctx, "cn_step");
+        cn_copy(c, c->cn_Nn, c->cn_Nh, VL);  // u^(n+1,0) = u^n
+        for (picard = 1; picard <= kmax; picard++) {
+            cn_rhs(c, c->cn_xn, c->cn_Nh, f, dt, bc, bd, wl, c->cn_b);
+            st = mg_solve(ctx, x, c->cn_b, tol, &r);
+            cycles += r.cycles;
+            if (st != GP_OK) break;
+            cn_convective(c, x, c->cn_Nn, c->cn_Nh, 1);
+            cn_rhs(c, c->cn_xn, c->cn_Nh, f, dt, bc, bd, wl, c->cn_b);
+            double bm = 0.0;
+            if (cn_momentum_residual(c, x, c->cn_b, &mom, &bm) != GP_OK) return check_cuda(ctx, "cn_step");
+            if (mom < eps * (fmax > 1.0 ? fmax : 1.0)) break;
+        }
+        if (picard > kmax) picard = kmax;
+    }
+    cn_copy(c, N1, N2, VL);
+    cn_copy(c, c->cn_Nn, N1, VL);
+    if (rep) {
+        rep->picard = step >= 2 ? 0 : picard;
+        rep->cycles = cycles;
+        rep->res = r.res;
+        rep->mom_res = mom;
+    }
+    gp_status cs = check_cuda(ctx, "cn_step");
     return cs != GP_OK ? cs : st;
 }
 

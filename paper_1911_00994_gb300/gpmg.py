@@ -25,12 +25,28 @@ class gp_params(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int), ("x0", ctypes.c_double), ("y0", ctypes.c_double), ("L", ctypes.c_double),
                 ("levels", ctypes.c_int), ("alpha", ctypes.c_double), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
                 ("gamma", ctypes.c_int), ("lam", ctypes.c_int), ("dtau", ctypes.c_double), ("snap", ctypes.c_double),
-                ("precision", ctypes.c_int), ("max_cycles", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("max_cycles", ctypes.c_int), ("cn_buffers", ctypes.c_int),
+                ("graphs", ctypes.c_int)]
 
 
 class gp_report(ctypes.Structure):
     _fields_ = [("cycles", ctypes.c_int), ("res0", ctypes.c_double), ("res", ctypes.c_double),
                 ("rho", ctypes.c_double), ("xi", ctypes.c_double), ("hist_host", ctypes.POINTER(ctypes.c_double))]
+
+
+class gp_body(ctypes.Structure):
+    _fields_ = [("U", ctypes.c_double), ("V", ctypes.c_double), ("omega", ctypes.c_double), ("cx", ctypes.c_double),
+                ("cy", ctypes.c_double)]
+
+
+class gp_walls(ctypes.Structure):
+    _fields_ = [("u_bottom", ctypes.c_double), ("u_top", ctypes.c_double), ("v_left", ctypes.c_double),
+                ("v_right", ctypes.c_double)]
+
+
+class gp_cn_report(ctypes.Structure):
+    _fields_ = [("picard", ctypes.c_int), ("cycles", ctypes.c_int), ("res", ctypes.c_double),
+                ("mom_res", ctypes.c_double)]
 
 
 class GpmgError(RuntimeError):
@@ -69,6 +85,10 @@ SIGNATURES = [
     ("gp_coarse_solve", _I, [_VP, _VP, _VP]),
     ("gp_cycle", _I, [_VP, _VP, _VP]),
     ("mg_solve", _I, [_VP, _VP, _VP, _D, _P(gp_report)]),
+    ("cn_step", _I, [_VP, _VP, _VP, _VP, _I, _VP, _VP, _D, _D, _P(gp_body), _P(gp_walls), _D, _D, _I,
+                     _P(gp_cn_report)]),
+    ("gp_convective", _I, [_VP, _VP, _VP]),
+    ("gp_cn_rhs", _I, [_VP, _VP, _VP, _VP, _D, _VP, _P(gp_body), _P(gp_walls), _VP]),
     ("gp_launch_count", ctypes.c_int64, [_VP]),
     ("gp_timer_start", _I, [_VP, _I, _I]),
     ("gp_timer_stop", _I, [_VP, _P(ctypes.c_int64), _P(_D)]),
@@ -125,7 +145,8 @@ class Solver:
     tensor on the device) and the device stream."""
 
     def __init__(self, N, x0, y0, L, levels=None, alpha=None, nu1=2, nu2=1, gamma=1, lam=5, dtau=0.9,
-                 snap=0.3, precision=GP_FP64, max_cycles=100, device="cuda", stream=None):
+                 snap=0.3, precision=GP_FP64, max_cycles=100, device="cuda", stream=None, cn_buffers=True,
+                 graphs=True):
         import torch
         self.torch = torch
         self.L = lib()
@@ -139,6 +160,8 @@ class Solver:
             p.alpha = alpha
         p.nu1, p.nu2, p.gamma, p.lam, p.dtau, p.snap = nu1, nu2, gamma, lam, dtau, snap
         p.precision, p.max_cycles = precision, max_cycles
+        p.cn_buffers = 1 if cn_buffers else 0
+        p.graphs = 1 if graphs else 0
         self.prm = p
         nb = ctypes.c_size_t(0)
         st = self.L.gp_workspace_size(ctypes.byref(p), ctypes.byref(nb))
@@ -279,6 +302,32 @@ class Solver:
 
     def cycle(self, x, b):
         self._check(self.L.gp_cycle(self.ctx, _ptr(x), _ptr(b)), "gp_cycle")
+
+    # ------------------------------------------------ Crank-Nicolson step
+    @staticmethod
+    def _opt(t):
+        return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+    def convective(self, x):
+        out = self.new_vec()
+        self._check(self.L.gp_convective(self.ctx, _ptr(x), _ptr(out)), "gp_convective")
+        return out
+
+    def cn_rhs(self, xn, Nh, dt, f=None, bc=None, body=(0, 0, 0, 0, 0), walls=(0, 0, 0, 0)):
+        b = self.new_vec()
+        bd, wl = gp_body(*body), gp_walls(*walls)
+        self._check(self.L.gp_cn_rhs(self.ctx, _ptr(xn), _ptr(Nh), self._opt(f), dt, self._opt(bc),
+                                     ctypes.byref(bd), ctypes.byref(wl), _ptr(b)), "gp_cn_rhs")
+        return b
+
+    def cn_step(self, x, N1, N2, step, dt, Re, f=None, bc=None, body=(0, 0, 0, 0, 0), walls=(0, 0, 0, 0),
+                tol=1e-10, eps=1e-6, kmax=10):
+        """One Crank-Nicolson step in place on x (and the history N1, N2)."""
+        bd, wl = gp_body(*body), gp_walls(*walls)
+        rep = gp_cn_report()
+        st = self.L.cn_step(self.ctx, _ptr(x), _ptr(N1), _ptr(N2), step, self._opt(f), self._opt(bc), dt, Re,
+                            ctypes.byref(bd), ctypes.byref(wl), tol, eps, kmax, ctypes.byref(rep))
+        return st, rep
 
     def launch_count(self):
         return int(self.L.gp_launch_count(self.ctx))

@@ -167,3 +167,35 @@ def test_solution_matches_oracle_config_params(case, N, Re):
     assert st == 0, s.error()
     assert rel(s.to_flat(xg), x_o) <= 1e-9
     assert abs(len(h_g) - len(h_o)) <= 1
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_graph_replay_matches_direct_launches(precision):
+    # mg_solve replays each iteration as a captured CUDA graph on a side
+    # stream; the iterate must be bitwise the one of direct launches
+    import torch
+    from paper_1911_00994_gb300 import gpmg
+    shape, x0, L = CASES["flower5"]
+    N = 128
+    lev = levels_for(N)
+    h = L / N
+    o, phi, st = make_oracle("flower5", N, alpha=h / 2000.0, levels=lev)
+    ex = W.taylor_green()
+    b, xe, t, gh = manufactured(o, ex)
+    out = []
+    for graphs in (False, True):
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            s = gpmg.Solver(N, x0, x0, L, levels=lev, alpha=h / 2000.0, precision=precision, graphs=graphs,
+                            stream=stream)
+            assert s.geometry(phi) == 0, s.error()
+            x = s.new_vec()
+            bd = s.to_device(b)
+            st, rep, hist = s.solve(x, bd, 1e-10)
+            assert st == 0, s.error()
+            x.zero_()
+            st, rep2, hist2 = s.solve(x, bd, 1e-10)  # second solve replays the captured graph
+            stream.synchronize()
+            out.append((s.to_flat(x), hist2))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
