@@ -8,8 +8,10 @@
 
 namespace gpmg {
 
-// levels solved by the one-block smoother, and ghost lists swept by one block
+// levels solved by the one-block smoother, ghost lists swept by one block,
+// and levels whose full boxes are swept by shared-memory tiles
 constexpr int SMALL_N = 64;
+constexpr int TILE_MIN_N = 128;
 constexpr int GHOST_BLOCK_ROWS = 16384;
 
 template <typename T> struct LevelArgs {
@@ -137,30 +139,24 @@ __global__ void k_residual_final(const double *part, int nb, const T *b, T *r, l
 
 // full boxes (no ghost border): Schur complement of the pressure unknown,
 // colour (i + 3 j) mod 5; borders that are not internal stay frozen
+// Box relaxation of one cell without ghost borders (Sect. 4.1.1): Schur
+// complement of the pressure unknown.  u, v, p point at the cell's slot in
+// arrays of row pitch `pitch` (global frames or a shared-memory tile); bu, bv,
+// bp at the cell's slot of the right-hand side.  Borders that are not
+// internal stay frozen.
 template <typename T>
-__device__ __forceinline__ void box_full_one(const LevelArgs<T> &A, T *x, const T *b, int i, int j)
+__device__ __forceinline__ void box_core(T *u, T *v, T *p, const int pitch, const T *bu, const T *bv, const T *bp,
+                                         const long long bpitch, const T xi, const uint8_t tW, const uint8_t tE,
+                                         const uint8_t tS, const uint8_t tN, const T a, const T d, const T q)
 {
-    long long s = (long long)(j + 1) * A.P + (i + 1);
-    if (A.tP[s] != T_INTERNAL) return;
-    uint8_t tW = A.tU[s], tE = A.tU[s + 1], tS = A.tV[s], tN = A.tV[s + A.P];
-    if (tW == T_GHOST || tE == T_GHOST || tS == T_GHOST || tN == T_GHOST) return;
-    T *u = x, *v = x + A.F, *p = x + 2 * A.F;
-    const T *bu = b, *bv = b + A.F, *bp = b + 2 * A.F;
-    T xi = x[3 * A.F];
-    const T a = A.a, d = A.d, q = A.q;
+    const int Pp = pitch;
     bool W = tW == T_INTERNAL, E = tE == T_INTERNAL, S = tS == T_INTERNAL, Nn = tN == T_INTERNAL;
     T rW = 0, rE = 0, rS = 0, rN = 0;
-    if (W) rW = bu[s] - (d * u[s] - a * (u[s + 1] + u[s - 1] + u[s + A.P] + u[s - A.P]) + q * (p[s] - p[s - 1]));
-    if (E) {
-        long long e = s + 1;
-        rE = bu[e] - (d * u[e] - a * (u[e + 1] + u[e - 1] + u[e + A.P] + u[e - A.P]) + q * (p[e] - p[e - 1]));
-    }
-    if (S) rS = bv[s] - (d * v[s] - a * (v[s + 1] + v[s - 1] + v[s + A.P] + v[s - A.P]) + q * (p[s] - p[s - A.P]));
-    if (Nn) {
-        long long n = s + A.P;
-        rN = bv[n] - (d * v[n] - a * (v[n + 1] + v[n - 1] + v[n + A.P] + v[n - A.P]) + q * (p[n] - p[n - A.P]));
-    }
-    T rC = bp[s] - (q * (u[s + 1] - u[s] + v[s + A.P] - v[s]) - xi);
+    if (W) rW = bu[0] - (d * u[0] - a * (u[1] + u[-1] + u[Pp] + u[-Pp]) + q * (p[0] - p[-1]));
+    if (E) rE = bu[1] - (d * u[1] - a * (u[2] + u[0] + u[1 + Pp] + u[1 - Pp]) + q * (p[1] - p[0]));
+    if (S) rS = bv[0] - (d * v[0] - a * (v[1] + v[-1] + v[Pp] + v[-Pp]) + q * (p[0] - p[-Pp]));
+    if (Nn) rN = bv[bpitch] - (d * v[Pp] - a * (v[Pp + 1] + v[Pp - 1] + v[2 * Pp] + v[0]) + q * (p[Pp] - p[0]));
+    T rC = bp[0] - (q * (u[1] - u[0] + v[Pp] - v[0]) - xi);
     // each direction contributes c0 + c1 * dp to the continuity update
     T c0 = 0, c1 = 0;
     if (W && E) {
@@ -191,17 +187,126 @@ __device__ __forceinline__ void box_full_one(const LevelArgs<T> &A, T *x, const 
     T fW = rW - q * dp, fE = rE + q * dp, fS = rS - q * dp, fN = rN + q * dp;
     if (W && E) {
         T det = d * d - a * a;
-        u[s] += (d * fW + a * fE) / det;
-        u[s + 1] += (a * fW + d * fE) / det;
-    } else if (W) u[s] += fW / d;
-    else if (E) u[s + 1] += fE / d;
+        u[0] += (d * fW + a * fE) / det;
+        u[1] += (a * fW + d * fE) / det;
+    } else if (W) u[0] += fW / d;
+    else if (E) u[1] += fE / d;
     if (S && Nn) {
         T det = d * d - a * a;
-        v[s] += (d * fS + a * fN) / det;
-        v[s + A.P] += (a * fS + d * fN) / det;
-    } else if (S) v[s] += fS / d;
-    else if (Nn) v[s + A.P] += fN / d;
-    p[s] += dp;
+        v[0] += (d * fS + a * fN) / det;
+        v[Pp] += (a * fS + d * fN) / det;
+    } else if (S) v[0] += fS / d;
+    else if (Nn) v[Pp] += fN / d;
+    p[0] += dp;
+}
+
+template <typename T>
+__device__ __forceinline__ void box_full_one(const LevelArgs<T> &A, T *x, const T *b, int i, int j)
+{
+    long long s = (long long)(j + 1) * A.P + (i + 1);
+    if (A.tP[s] != T_INTERNAL) return;
+    uint8_t tW = A.tU[s], tE = A.tU[s + 1], tS = A.tV[s], tN = A.tV[s + A.P];
+    if (tW == T_GHOST || tE == T_GHOST || tS == T_GHOST || tN == T_GHOST) return;
+    box_core<T>(x + s, x + A.F + s, x + 2 * A.F + s, A.P, b + s, b + A.F + s, b + 2 * A.F + s, A.P, x[3 * A.F], tW, tE,
+                tS, tN, A.a, A.d, A.q);
+}
+
+// All five colours of the full boxes in one pass: each block loads a tile
+// of (TI + 2 H) x (TI + 2 H) slots of u, v, p and the node types into shared
+// memory, sweeps the colours there and writes back the values its TI x TI
+// interior cells own (p, the west face u, the south face v).  Colour c
+// relaxes the boxes within 2 (4 - c) + 1 cells of the interior: a box reads
+// values written by boxes at most two cells away, so the interior sees the
+// same sequence of updates as the global colour-by-colour sweep, and the
+// owned west and south faces also get the update of the box on their far
+// side.  H = 11 covers the reads of the outermost boxes.
+constexpr int TILE_H = 11;
+
+template <typename T> __host__ __device__ constexpr int tile_ti() { return sizeof(T) == 4 ? 64 : 32; }
+template <typename T> __host__ __device__ constexpr int tile_tl() { return tile_ti<T>() + 2 * TILE_H; }
+template <typename T> __host__ __device__ constexpr size_t tile_smem()
+{
+    return (size_t)tile_tl<T>() * tile_tl<T>() * (3 * sizeof(T) + 1);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_box_tiled(LevelArgs<T> A, const T *x, const T *b, T *y)
+{
+    constexpr int TI = tile_ti<T>(), TL = tile_tl<T>(), H = TILE_H;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *su = (T *)smem_raw;
+    T *sv = su + TL * TL;
+    T *sp = sv + TL * TL;
+    uint8_t *stp = (uint8_t *)(sp + TL * TL);
+    const int i0 = blockIdx.x * TI, j0 = blockIdx.y * TI;
+    const int row0 = j0 + 1 - H, col0 = i0 + 1 - H;
+    const int R = A.N + 2;
+    const long long F = A.F;
+    for (int k = threadIdx.x; k < TL * TL; k += blockDim.x) {
+        int lr = k / TL, lc = k - lr * TL;
+        int row = row0 + lr, col = col0 + lc;
+        if (row >= 0 && row < R && col >= 0 && col < A.P) {
+            long long s = (long long)row * A.P + col;
+            su[k] = x[s];
+            sv[k] = x[F + s];
+            sp[k] = x[2 * F + s];
+            stp[k] = (uint8_t)(A.tU[s] | (A.tV[s] << 3) | (A.tP[s] << 6));
+        } else {
+            su[k] = 0;
+            sv[k] = 0;
+            sp[k] = 0;
+            stp[k] = 0;
+        }
+    }
+    const T xi = x[3 * F];
+    __syncthreads();
+    for (int colour = 0; colour < 5; colour++) {
+        const int Rg = 2 * (4 - colour) + 1;
+        const int ilo = max(i0 - Rg, 0), ihi = min(i0 + TI + Rg, A.N);
+        const int jlo = max(j0 - Rg, 0), jhi = min(j0 + TI + Rg, A.N);
+        const int per_row = (ihi - ilo + 4) / 5 + 1;
+        const int ncell = (jhi - jlo) * per_row;
+        for (int idx = threadIdx.x; idx < ncell; idx += blockDim.x) {
+            int j = jlo + idx / per_row, t = idx % per_row;
+            int i = ilo + ((colour - 3 * j - ilo) % 5 + 5) % 5 + 5 * t;
+            if (i >= ihi) continue;
+            int ls = (j + 1 - row0) * TL + (i + 1 - col0);
+            uint8_t tc = stp[ls];
+            if ((tc >> 6) != T_INTERNAL) continue;
+            uint8_t tW = tc & 7, tE = stp[ls + 1] & 7, tS = (tc >> 3) & 7, tN = (stp[ls + TL] >> 3) & 7;
+            if (tW == T_GHOST || tE == T_GHOST || tS == T_GHOST || tN == T_GHOST) continue;
+            long long gs = (long long)(j + 1) * A.P + (i + 1);
+            box_core<T>(su + ls, sv + ls, sp + ls, TL, b + gs, b + F + gs, b + 2 * F + gs, A.P, xi, tW, tE, tS, tN, A.a,
+                        A.d, A.q);
+        }
+        __syncthreads();
+    }
+    // the values the interior cells own go to y (other blocks may still be
+    // loading their halos from x); k_box_apply copies them into x
+    for (int k = threadIdx.x; k < TI * TI; k += blockDim.x) {
+        int dj = k / TI, di = k - dj * TI;
+        int i = i0 + di, j = j0 + dj;
+        if (i >= A.N || j >= A.N) continue;
+        int ls = (j + 1 - row0) * TL + (i + 1 - col0);
+        long long gs = (long long)(j + 1) * A.P + (i + 1);
+        uint8_t tc = stp[ls];
+        if ((tc & 7) == T_INTERNAL) y[gs] = su[ls];
+        if (((tc >> 3) & 7) == T_INTERNAL) y[F + gs] = sv[ls];
+        if ((tc >> 6) == T_INTERNAL) y[2 * F + gs] = sp[ls];
+    }
+}
+
+// x = y on every internal node (every internal node is owned by exactly one
+// tile interior: u(i, j) and v(i, j) by cell (i, j), the faces u(N, j) and
+// v(i, N) are walls)
+template <typename T> __global__ void k_box_apply(LevelArgs<T> A, T *x, const T *y)
+{
+    const long long nslot = (long long)(A.N + 2) * A.P;
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < nslot; s += (long long)gridDim.x * blockDim.x) {
+        if (A.tU[s] == T_INTERNAL) x[s] = y[s];
+        if (A.tV[s] == T_INTERNAL) x[A.F + s] = y[A.F + s];
+        if (A.tP[s] == T_INTERNAL) x[2 * A.F + s] = y[2 * A.F + s];
+    }
 }
 
 template <typename T>
@@ -779,6 +884,21 @@ template <typename T> LevelArgs<T> level_args(const Ctx *c, int lev)
 
 static inline dim3 frame_grid(const Level &l) { return dim3((l.P + 255) / 256, l.N + 2); }
 
+// the tiled box sweep stages its results in the level's residual vector,
+// which is dead during relaxation (it is recomputed before restriction)
+template <typename T> T *tile_scratch(Ctx *c, int lev);
+template <> double *tile_scratch<double>(Ctx *c, int lev) { return c->lv[lev].r; }
+template <> float *tile_scratch<float>(Ctx *c, int lev) { return c->lv[lev].rf; }
+
+void tiles_init()
+{
+    static bool done = false;
+    if (done) return;
+    cudaFuncSetAttribute(k_box_tiled<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem<double>());
+    cudaFuncSetAttribute(k_box_tiled<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem<float>());
+    done = true;
+}
+
 // blocks of the reduction kernels: enough to fill the GPU, at most 1024
 static inline int red_blocks(const Level &l)
 {
@@ -807,11 +927,22 @@ template <typename T> void box_sweep(Ctx *c, int lev, T *x, const T *b)
     LevelArgs<T> A = level_args<T>(c, lev);
     int per_row = (l.N + 4) / 5;
     dim3 g((per_row + 127) / 128, l.N);
-    for (int colour = 0; colour < 5; colour++) {
+    if (l.N >= TILE_MIN_N) {
+        T *y = tile_scratch<T>(c, lev);
+        constexpr int TI = tile_ti<T>();
+        dim3 gt((l.N + TI - 1) / TI, (l.N + TI - 1) / TI);
         tmr_begin(c, KT_BOX_FULL, lev);
-        k_box_full<T><<<g, 128, 0, st>>>(A, x, b, colour);
+        k_box_tiled<T><<<gt, 256, tile_smem<T>(), st>>>(A, x, b, y);
         tmr_end(c, KT_BOX_FULL, lev);
-        c->launches++;
+        k_box_apply<T><<<red_blocks(l) * 4, 256, 0, st>>>(A, x, y);
+        c->launches += 2;
+    } else {
+        for (int colour = 0; colour < 5; colour++) {
+            tmr_begin(c, KT_BOX_FULL, lev);
+            k_box_full<T><<<g, 128, 0, st>>>(A, x, b, colour);
+            tmr_end(c, KT_BOX_FULL, lev);
+            c->launches++;
+        }
     }
     if (l.h_ncut > 0) {
         int nt = l.h_ncut >= 25 * 128 ? 256 : 128;

@@ -25,6 +25,7 @@ template <typename T> void zero_inactive(Ctx *c, int lev, T *x);
 template <typename T> void coarse_solve(Ctx *c, const T *b, T *x);
 void to_float(Ctx *c, const double *a, float *b, long long n);
 void tmr_flush(Ctx *c);
+void tiles_init();
 int residual_static(Ctx *c, int lev, const double *x, const double *b, double *r, double *norm_host);
 void cn_convective(Ctx *c, const double *x, const double *Nn, double *out, int mode);
 void cn_rhs(Ctx *c, const double *xn, const double *Nh, const double *f, double dt, const double *bc, const gp_body &body,
@@ -363,6 +364,7 @@ gp_status gp_create(gp_ctx **out, const gp_params *prm, void *workspace, size_t 
     c->ws = (char *)workspace;
     c->ws_bytes = bytes;
     c->tmr_kernel = -1;
+    tiles_init();
     c->stream = (cudaStream_t)stream;
     carve(c, c->ws);
     // coarsest-level index maps (host -> device)

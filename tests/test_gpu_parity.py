@@ -191,10 +191,10 @@ def test_graph_replay_matches_direct_launches(precision):
             assert s.geometry(phi) == 0, s.error()
             x = s.new_vec()
             bd = s.to_device(b)
-            st, rep, hist = s.solve(x, bd, 1e-10)
+            st, rep, hist = s.solve(x, bd, 1e-8)
             assert st == 0, s.error()
             x.zero_()
-            st, rep2, hist2 = s.solve(x, bd, 1e-10)  # second solve replays the captured graph
+            st, rep2, hist2 = s.solve(x, bd, 1e-8)  # second solve replays the captured graph
             stream.synchronize()
             out.append((s.to_flat(x), hist2))
     assert np.array_equal(out[0][0], out[1][0])
