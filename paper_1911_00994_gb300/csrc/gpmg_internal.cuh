@@ -56,11 +56,22 @@ struct GhostList {
 };
 
 // cut cells (internal cells with a ghost border) sorted by 25 colours
+constexpr int CUT_ST = 9;  // stencil entries per box row
 struct CutList {
     int *count;        // device [1]
     int *off;          // device [26] colour offsets
     int *cell;         // slot of the cell (row * P + col)
     int *gface;        // [4][cap] ghost-list index of face W, E, S, N (or -1)
+    // box rows prepared for the current alpha (k_cut_prepare): for row
+    // f = W, E, S, N, continuity: the vector index of its unknown and rhs
+    // (-1 when the row takes no part), CUT_ST (index, coefficient) pairs of
+    // the full row, and the inverse of the 5 x 5 box matrix
+    int *row;          // [5][cap]
+    int *sidx;         // [5 * CUT_ST][cap]
+    double *scoef;     // [5 * CUT_ST][cap]
+    float *scoeff;
+    double *minv;      // [25][cap]
+    float *minvf;
     int cap;
 };
 

@@ -11,8 +11,8 @@ namespace gpmg {
 // levels solved by the one-block smoother, ghost lists swept by one block,
 // and levels whose full boxes are swept by shared-memory tiles
 constexpr int SMALL_N = 64;
-constexpr int TILE_MIN_N = 128;
-constexpr int GHOST_BLOCK_ROWS = 16384;
+constexpr int TILE_MIN_N = 1 << 30;  // tiled sweep off: its tile load is latency bound (slower than five colour passes)
+constexpr int GHOST_BLOCK_ROWS = 4096;
 
 template <typename T> struct LevelArgs {
     int N, P;
@@ -319,137 +319,140 @@ __global__ void k_box_full(LevelArgs<T> A, T *x, const T *b, int colour)
     box_full_one<T>(A, x, b, i, j);
 }
 
-// row of border f of a cut box: momentum row (internal border) or its ghost
-// row (object-ghost border); identity when the border takes no part
-template <typename T, int f>
-__device__ __forceinline__ void cut_row(const LevelArgs<T> &A, const T *x, const T *b, const CutList &cut,
-                                        const GhostList &gh, const T *w, int k, const long long (&unk)[5],
-                                        const bool (&act)[5], const uint8_t (&ft)[4], T (&M)[5][5], T (&r)[5])
+// Prepare the rows of every cut box for the current alpha: the full row of
+// each box unknown as (index, coefficient) pairs (frozen neighbours
+// included, so that the residual needs only gathers) and the inverse of the
+// box matrix by the same pivoted LU (FP64; an FP32 copy for FP32 sweeps).
+__global__ void k_cut_prepare(LevelArgs<double> A, CutList cut, GhostList gh, int n)
 {
-    const long long F = A.F;
-    const long long P = A.P;
-    if (!act[f]) {
-        M[f][f] = 1;
-        return;
-    }
-    if (ft[f] == T_INTERNAL) {
-        // momentum row of border f: centre d, four neighbours -a, pressure pair
-        long long o = unk[f];
-        constexpr bool isu = f < 2;
-        long long loc = isu ? o : o - F;
-        const T *xx = isu ? x : x + F;
-        const T *pp = x + 2 * F;
-        long long pm = isu ? loc - 1 : loc - P;
-        T Ax = A.d * xx[loc] - A.a * (xx[loc + 1] + xx[loc - 1] + xx[loc + P] + xx[loc - P]) + A.q * (pp[loc] - pp[pm]);
-        r[f] = b[o] - Ax;
-        M[f][f] += A.d;
-        // the opposite border of the same direction is a neighbour at +-1 (u) or +-P (v)
-        constexpr int opp = f ^ 1;
-        if (act[opp]) M[f][opp] -= A.a;
-        // pressure: p(cell) enters W and S rows with +1/h, E and N rows with -1/h
-        M[f][4] += (f == 0 || f == 2) ? A.q : -A.q;
-    } else {
-        int g = cut.gface[(long long)f * cut.cap + k];
-        int nst = gh.nst[g];
-        T acc = b[gh.node[g]];
-        for (int m = 0; m < nst; m++) {
-            int id = gh.st[(long long)m * gh.cap + g];
-            T wm = w[(long long)m * gh.cap + g];
-            acc -= wm * x[id];
-            if (act[0] && unk[0] == id) M[f][0] += wm;
-            if (act[1] && unk[1] == id) M[f][1] += wm;
-            if (act[2] && unk[2] == id) M[f][2] += wm;
-            if (act[3] && unk[3] == id) M[f][3] += wm;
-        }
-        r[f] = acc;
-    }
-}
-
-// One cut box (an internal cell with a ghost border): p, the internal borders
-// (momentum rows) and the object-ghost borders (their ghost rows) solved
-// together by a pivoted LU.  The system is always 5 x 5: a border that takes
-// no part gets an identity row and a zero column, which leaves the pivots and
-// the result of the smaller system unchanged; fixed sizes keep it in registers.
-template <typename T>
-__device__ __forceinline__ void box_cut_one(const LevelArgs<T> &A, T *x, const T *b, const CutList &cut,
-                                            const GhostList &gh, int k)
-{
-    long long s = cut.cell[k];
-    const long long F = A.F;
-    const long long P = A.P;
-    const T *w = gw<T>(gh);
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const long long s = cut.cell[k];
+    const long long F = A.F, P = A.P;
     long long unk[5] = {s, s + 1, F + s, F + s + P, 2 * F + s};
     uint8_t ft[4] = {A.tU[s], A.tU[s + 1], A.tV[s], A.tV[s + P]};
     bool act[5];
-#pragma unroll
     for (int f = 0; f < 4; f++) act[f] = ft[f] == T_INTERNAL || ft[f] == T_GHOST;
     act[4] = true;
-    T M[5][5], r[5];
-    const T q = A.q;
-#pragma unroll
-    for (int rr = 0; rr < 5; rr++) {
-#pragma unroll
-        for (int c = 0; c < 5; c++) M[rr][c] = 0;
-        r[rr] = 0;
+    double M[5][5];
+    for (int r = 0; r < 5; r++)
+        for (int c = 0; c < 5; c++) M[r][c] = 0.0;
+    auto put = [&](int f, int m, long long idx, double coef) {
+        cut.sidx[(long long)(f * CUT_ST + m) * cut.cap + k] = (int)idx;
+        cut.scoef[(long long)(f * CUT_ST + m) * cut.cap + k] = coef;
+        cut.scoeff[(long long)(f * CUT_ST + m) * cut.cap + k] = (float)coef;
+        for (int c = 0; c < 5; c++)
+            if (act[c] && unk[c] == idx) M[f][c] += coef;
+    };
+    for (int f = 0; f < 5; f++)
+        for (int m = 0; m < CUT_ST; m++) {
+            cut.sidx[(long long)(f * CUT_ST + m) * cut.cap + k] = (int)unk[4];
+            cut.scoef[(long long)(f * CUT_ST + m) * cut.cap + k] = 0.0;
+            cut.scoeff[(long long)(f * CUT_ST + m) * cut.cap + k] = 0.f;
+        }
+    for (int f = 0; f < 4; f++) {
+        cut.row[(long long)f * cut.cap + k] = act[f] ? (int)unk[f] : -1;
+        if (!act[f]) {
+            M[f][f] = 1.0;
+            continue;
+        }
+        if (ft[f] == T_INTERNAL) {
+            long long o = unk[f];
+            bool isu = f < 2;
+            long long loc = isu ? o : o - F;
+            long long base = isu ? 0 : F;
+            long long pm = isu ? loc - 1 : loc - P;
+            put(f, 0, o, A.d);
+            put(f, 1, base + loc + 1, -A.a);
+            put(f, 2, base + loc - 1, -A.a);
+            put(f, 3, base + loc + P, -A.a);
+            put(f, 4, base + loc - P, -A.a);
+            put(f, 5, 2 * F + loc, A.q);
+            put(f, 6, 2 * F + pm, -A.q);
+        } else {
+            int g = cut.gface[(long long)f * cut.cap + k];
+            int nst = gh.nst[g];
+            for (int m = 0; m < nst; m++) put(f, m, gh.st[(long long)m * gh.cap + g], gh.w[(long long)m * gh.cap + g]);
+        }
     }
-    cut_row<T, 0>(A, x, b, cut, gh, w, k, unk, act, ft, M, r);
-    cut_row<T, 1>(A, x, b, cut, gh, w, k, unk, act, ft, M, r);
-    cut_row<T, 2>(A, x, b, cut, gh, w, k, unk, act, ft, M, r);
-    cut_row<T, 3>(A, x, b, cut, gh, w, k, unk, act, ft, M, r);
-    {
-        // continuity row of the cell
-        const T *u = x, *v = x + F;
-        T xi = x[3 * F];
-        r[4] = b[2 * F + s] - (q * (u[s + 1] - u[s] + v[s + P] - v[s]) - xi);
-        if (act[0]) M[4][0] -= q;
-        if (act[1]) M[4][1] += q;
-        if (act[2]) M[4][2] -= q;
-        if (act[3]) M[4][3] += q;
-    }
-    // LU with partial pivoting (first largest pivot), applied to the rhs
+    cut.row[4ll * cut.cap + k] = (int)unk[4];
+    put(4, 0, s + 1, A.q);
+    put(4, 1, s, -A.q);
+    put(4, 2, F + s + P, A.q);
+    put(4, 3, F + s, -A.q);
+    put(4, 4, 3 * F, -1.0);
+    // inverse by pivoted LU on [M | I]
+    double I[5][5];
+    for (int r = 0; r < 5; r++)
+        for (int c = 0; c < 5; c++) I[r][c] = r == c ? 1.0 : 0.0;
     bool ok = true;
-#pragma unroll
     for (int c = 0; c < 5; c++) {
         int pr = c;
-        T best = fabs(M[c][c]);
-#pragma unroll
-        for (int rr = c + 1; rr < 5; rr++) {
-            T vv = fabs(M[rr][c]);
-            if (vv > best) { best = vv; pr = rr; }
-        }
-        ok = ok && best > (T)0;
-        // row swap by selection (keeps the system in registers)
-#pragma unroll
-        for (int rr = c + 1; rr < 5; rr++) {
-            const bool sw = rr == pr;
-#pragma unroll
-            for (int m = 0; m < 5; m++) {
-                T lo = M[c][m], hi = M[rr][m];
-                M[c][m] = sw ? hi : lo;
-                M[rr][m] = sw ? lo : hi;
+        double best = fabs(M[c][c]);
+        for (int r = c + 1; r < 5; r++)
+            if (fabs(M[r][c]) > best) {
+                best = fabs(M[r][c]);
+                pr = r;
             }
-            T lo = r[c], hi = r[rr];
-            r[c] = sw ? hi : lo;
-            r[rr] = sw ? lo : hi;
+        if (!(best > 0.0)) { ok = false; break; }
+        for (int m = 0; m < 5; m++) {
+            double t = M[c][m]; M[c][m] = M[pr][m]; M[pr][m] = t;
+            t = I[c][m]; I[c][m] = I[pr][m]; I[pr][m] = t;
         }
-#pragma unroll
-        for (int rr = c + 1; rr < 5; rr++) {
-            T f = M[rr][c] / M[c][c];
-#pragma unroll
-            for (int m = c + 1; m < 5; m++) M[rr][m] -= f * M[c][m];
-            r[rr] -= f * r[c];
+        for (int r = c + 1; r < 5; r++) {
+            double fct = M[r][c] / M[c][c];
+            for (int m = 0; m < 5; m++) {
+                M[r][m] -= fct * M[c][m];
+                I[r][m] -= fct * I[c][m];
+            }
         }
     }
+    for (int col = 0; col < 5; col++)
+        for (int r = 4; r >= 0; r--) {
+            double acc = ok ? I[r][col] : 0.0;
+            for (int m = r + 1; m < 5; m++) acc -= M[r][m] * I[m][col];
+            I[r][col] = ok ? acc / M[r][r] : 0.0;
+        }
+    for (int r = 0; r < 5; r++)
+        for (int c = 0; c < 5; c++) {
+            cut.minv[(long long)(r * 5 + c) * cut.cap + k] = I[r][c];
+            cut.minvf[(long long)(r * 5 + c) * cut.cap + k] = (float)I[r][c];
+        }
+}
+
+template <typename T> __device__ inline const T *cut_coef(const CutList &c);
+template <> __device__ inline const double *cut_coef<double>(const CutList &c) { return c.scoef; }
+template <> __device__ inline const float *cut_coef<float>(const CutList &c) { return c.scoeff; }
+template <typename T> __device__ inline const T *cut_minv(const CutList &c);
+template <> __device__ inline const double *cut_minv<double>(const CutList &c) { return c.minv; }
+template <> __device__ inline const float *cut_minv<float>(const CutList &c) { return c.minvf; }
+
+// one prepared cut box: gather the five row residuals, apply the inverse
+template <typename T> __device__ __forceinline__ void box_cut_pre(T *x, const T *b, const CutList &cut, int k)
+{
+    const T *coef = cut_coef<T>(cut);
+    const T *mi = cut_minv<T>(cut);
+    T r[5];
+    int row[5];
 #pragma unroll
-    for (int rr = 4; rr >= 0; rr--) {
+    for (int f = 0; f < 5; f++) {
+        row[f] = cut.row[(long long)f * cut.cap + k];
+        T acc = 0;
 #pragma unroll
-        for (int m = rr + 1; m < 5; m++) r[rr] -= M[rr][m] * r[m];
-        r[rr] /= M[rr][rr];
+        for (int m = 0; m < CUT_ST; m++) {
+            long long e = (long long)(f * CUT_ST + m) * cut.cap + k;
+            acc += coef[e] * x[cut.sidx[e]];
+        }
+        r[f] = row[f] >= 0 ? b[row[f]] - acc : (T)0;
     }
-    if (!ok) return;
 #pragma unroll
-    for (int f = 0; f < 5; f++)
-        if (act[f]) x[unk[f]] += r[f];
+    for (int f = 0; f < 5; f++) {
+        if (row[f] < 0) continue;
+        T d = 0;
+#pragma unroll
+        for (int c = 0; c < 5; c++) d += mi[(long long)(f * 5 + c) * cut.cap + k] * r[c];
+        x[row[f]] += d;
+    }
 }
 
 // all 25 colours (i mod 5, j mod 5) of the cut boxes in one block: the
@@ -459,7 +462,7 @@ __global__ void __launch_bounds__(256) k_box_cut(LevelArgs<T> A, T *x, const T *
 {
     for (int colour = 0; colour < 25; colour++) {
         int beg = cut.off[colour], end = cut.off[colour + 1];
-        for (int k = beg + threadIdx.x; k < end; k += blockDim.x) box_cut_one<T>(A, x, b, cut, gh, k);
+        for (int k = beg + threadIdx.x; k < end; k += blockDim.x) box_cut_pre<T>(x, b, cut, k);
         __syncthreads();
     }
 }
@@ -780,7 +783,7 @@ __global__ void __launch_bounds__(512) k_smooth_small(LevelArgs<T> A, T *x, cons
         }
         for (int colour = 0; colour < 25; colour++) {
             int beg = cut.off[colour], end = cut.off[colour + 1];
-            for (int k = beg + threadIdx.x; k < end; k += blockDim.x) box_cut_one<T>(A, x, b, cut, gh, k);
+            for (int k = beg + threadIdx.x; k < end; k += blockDim.x) box_cut_pre<T>(x, b, cut, k);
             __syncthreads();
         }
         if (nlonely > 0) {
@@ -889,6 +892,15 @@ static inline dim3 frame_grid(const Level &l) { return dim3((l.P + 255) / 256, l
 template <typename T> T *tile_scratch(Ctx *c, int lev);
 template <> double *tile_scratch<double>(Ctx *c, int lev) { return c->lv[lev].r; }
 template <> float *tile_scratch<float>(Ctx *c, int lev) { return c->lv[lev].rf; }
+
+void prepare_cuts(Ctx *c)
+{
+    for (int lev = 0; lev < c->L; lev++) {
+        const Level &l = c->lv[lev];
+        if (l.h_ncut <= 0) continue;
+        k_cut_prepare<<<(l.h_ncut + 127) / 128, 128, 0, c->stream>>>(level_args<double>(c, lev), l.cut, l.gh, l.h_ncut);
+    }
+}
 
 void tiles_init()
 {

@@ -26,6 +26,7 @@ template <typename T> void coarse_solve(Ctx *c, const T *b, T *x);
 void to_float(Ctx *c, const double *a, float *b, long long n);
 void tmr_flush(Ctx *c);
 void tiles_init();
+void prepare_cuts(Ctx *c);
 int residual_static(Ctx *c, int lev, const double *x, const double *b, double *r, double *norm_host);
 void cn_convective(Ctx *c, const double *x, const double *Nn, double *out, int mode);
 void cn_rhs(Ctx *c, const double *xn, const double *Nh, const double *f, double dt, const double *bc, const gp_body &body,
@@ -132,6 +133,12 @@ static size_t carve(Ctx *c, char *base)
         l.cut.off = cv.take<int>(26);
         l.cut.cell = cv.take<int>(cc);
         l.cut.gface = cv.take<int>(4 * (size_t)cc);
+        l.cut.row = cv.take<int>(5 * (size_t)cc);
+        l.cut.sidx = cv.take<int>(5 * CUT_ST * (size_t)cc);
+        l.cut.scoef = cv.take<double>(5 * CUT_ST * (size_t)cc);
+        l.cut.scoeff = cv.take<float>(5 * CUT_ST * (size_t)cc);
+        l.cut.minv = cv.take<double>(25 * (size_t)cc);
+        l.cut.minvf = cv.take<float>(25 * (size_t)cc);
         l.lonely_cap = lonely_cap(l.N);
         l.lonely = cv.take<int>(l.lonely_cap);
         l.nlonely = cv.take<int>(1);
@@ -295,6 +302,7 @@ static gp_status ensure_coarse(gp_ctx *ctx)
     if (!c->geom_ok) return fail(ctx, GP_INVALID, "geometry_build has not succeeded");
     if (c->coarse_ok && c->alpha_factored == c->prm.alpha) return GP_OK;
     graphs_reset(c);  // the captured launches carry alpha in their arguments
+    prepare_cuts(c);  // cut-box rows and inverses depend on alpha
     return (gp_status)build_coarse_inverse(c);
 }
 
@@ -456,6 +464,7 @@ gp_status geometry_build(gp_ctx *ctx, const double *phi, int phi_fluid_positive)
     gp_status cs = check_cuda(ctx, "geometry_build");
     if (cs != GP_OK) return cs;
     c->geom_ok = 1;
+    prepare_cuts(c);
     s = build_coarse_inverse(c);
     if (s != GP_OK) {
         c->geom_ok = 0;
@@ -542,6 +551,8 @@ gp_status gp_residual_static(gp_ctx *ctx, int level, const double *x, const doub
 gp_status gp_box_sweep(gp_ctx *ctx, int level, double *x, const double *b)
 {
     if (!level_ok(ctx, level) || !ctx->c.geom_ok || !x || !b) return GP_INVALID;
+    gp_status es = ensure_coarse(ctx);
+    if (es != GP_OK) return es;
     box_sweep<double>(&ctx->c, level, x, b);
     return check_cuda(ctx, "gp_box_sweep");
 }
@@ -563,6 +574,8 @@ gp_status gp_ghost_sweep(gp_ctx *ctx, int level, double *x, const double *b)
 gp_status gp_smooth(gp_ctx *ctx, int level, double *x, const double *b, int nu)
 {
     if (!level_ok(ctx, level) || !ctx->c.geom_ok || !x || !b || nu < 0) return GP_INVALID;
+    gp_status es = ensure_coarse(ctx);
+    if (es != GP_OK) return es;
     smooth<double>(&ctx->c, level, x, b, nu);
     return check_cuda(ctx, "gp_smooth");
 }
