@@ -112,14 +112,14 @@ def ncu_traffic(kernel):
     return None
 
 
-def build_case(N, precision, device, stream, levels=None):
+def build_case(N, precision, device, stream, levels=None, krylov=False):
     import torch
     from paper_1911_00994_gb300 import gpmg
     from paper_1911_00994_gb300 import workloads as W
     h = 1.0 / N
     alpha = h / (2.0 * 1000.0)
     s = gpmg.Solver(N, 0.0, 0.0, 1.0, levels=levels, alpha=alpha, precision=precision, device=device,
-                    max_cycles=200, stream=stream)
+                    max_cycles=200, stream=stream, krylov=krylov)
     phi = torch.from_numpy(W.phi_half_lattice(W.flower(0.2, 0.05, 5, 0.5, 0.5), N, 0.0, 0.0, 1.0)).to(device)
     st = s.geometry(phi, 0)
     if st:
@@ -234,8 +234,31 @@ def run_ours(args):
            "ms_per_step": e2e_ms / args.steps, "host_wall_s": time.perf_counter() - t_e2e0}
 
     levels = s.levels
-    # ---- plain FP64 solve of the same system
     del s
+    torch.cuda.empty_cache()
+    # ---- BiCGSTAB preconditioned by one mixed-precision cycle, same system
+    sk, bk = build_case(N, gpmg.GP_MIXED, dev, stream, krylov=True)
+    xk = sk.new_vec()
+    for _ in range(max(1, args.warmup // 2)):
+        xk.zero_()
+        sk.solve(xk, bk, TOL, hist=False)
+    barrier()
+    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k0.record(stream)
+    kc, kit = 0, 0
+    nk = max(1, min(args.steps, 5))
+    for _ in range(nk):
+        xk.zero_()
+        st, repk, _ = sk.solve(xk, bk, TOL, hist=False)
+        if st:
+            raise RuntimeError("krylov solve failed: %s" % sk.error())
+        kc += repk.cycles
+        kit += repk.iterations
+    k1.record(stream)
+    barrier()
+    msk = k0.elapsed_time(k1)
+    del sk
+    # ---- plain FP64 solve of the same system
     torch.cuda.empty_cache()
     s64, b64 = build_case(N, gpmg.GP_FP64, dev, stream)
     x64 = s64.new_vec()
@@ -282,6 +305,8 @@ def run_ours(args):
         "rho_mean": float(np.mean(rhos)),
         "fp64": {"time_to_tol_ms": ms64 / n64, "cycles_per_step": c64 / n64, "cycles_per_s": c64 / (ms64 / 1e3),
                  "steps": n64},
+        "bicgstab_mixed": {"time_to_tol_ms": msk / nk, "iterations_per_step": kit / nk, "cycles_per_step": kc / nk,
+                           "cycles_per_s": kc / (msk / 1e3), "steps": nk},
         "roofline": {"kernel": "k_box_full<float> (one colour of the finest-level full-box sweep)", "bound": "hbm",
                      "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "peak_source": src, "avg_launch_ms": avg_ms, "launches": nbox,

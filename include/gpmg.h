@@ -74,15 +74,21 @@ typedef struct gp_params {
     int cn_buffers;     /* nonzero: carve the four finest-level vectors cn_step needs */
     int graphs;         /* nonzero: mg_solve replays each cycle as a captured CUDA graph
                            (needs a stream other than the legacy default stream) */
+    int band;           /* moving bodies (Sect. 3.4): external nodes of the finest grid within
+                           `band` index steps of the fluid are ghosts too (extrapolation rows),
+                           so that the previous step has values where the fluid advances */
+    int krylov;         /* 0: plain cycles; 1: BiCGSTAB preconditioned on the right by one
+                           cycle (two cycles per iteration), same stopping test */
 } gp_params;
 
 typedef struct gp_report {
-    int cycles;          /* cycles done */
+    int cycles;          /* multigrid cycles done */
+    int iterations;      /* outer iterations (= cycles for plain cycles; BiCGSTAB: 2 cycles each) */
     double res0;         /* ||b - M x||_inf before the first cycle */
     double res;          /* after the last cycle */
     double rho;          /* geometric mean residual reduction per cycle */
     double xi;           /* final xi */
-    double *hist_host;   /* optional host array of max_cycles + 1 norms, or NULL */
+    double *hist_host;   /* optional host array of max_cycles + 1 norms (one per iteration), or NULL */
 } gp_report;
 
 /* Rigid-body velocity of the object: u_b(B) = (U - omega (B_y - cy),
@@ -132,6 +138,35 @@ gp_status gp_set_alpha(gp_ctx *ctx, double alpha);
  * ghost rows (Eq. BCu and extrapolation rows), cut-cell lists and the
  * coarsest-level inverse.  phi: half lattice as described above. */
 gp_status geometry_build(gp_ctx *ctx, const double *phi, int phi_fluid_positive);
+
+/* Shapes of the test bodies (Sect. 5, Eq. domains) moving rigidly: at time t
+ * the body centre is c(t) = (xc + R cos(2 pi t / T + phase), yc + R sin(...))
+ * (R = orbit_r; a fixed body when R = 0) and the body is turned by omega t
+ * about c(t).  In body coordinates q:
+ *   GP_CIRCLE:  phi = a - |q|
+ *   GP_ELLIPSE: phi = 1 - sqrt(q_x^2 / a^2 + q_y^2 / b^2)
+ *   GP_FLOWER:  phi = a + b sin(k atan2(q_y, q_x)) - |q|
+ * (paper sign: positive inside the body). */
+typedef enum gp_shape_kind { GP_CIRCLE = 0, GP_ELLIPSE = 1, GP_FLOWER = 2 } gp_shape_kind;
+
+typedef struct gp_shape {
+    int kind;
+    double a, b;
+    int k;
+    double xc, yc;
+    double orbit_r, orbit_period, orbit_phase;
+    double omega;
+} gp_shape;
+
+/* geometry_build for a shape at time t: the level set is evaluated on the
+ * half-cell lattice on the device (Sect. 3.1), then as geometry_build.  The
+ * rigid-body velocity at t (dc/dt and omega about c(t)) is returned in
+ * body_out when it is not NULL. */
+gp_status geometry_build_shape(gp_ctx *ctx, const gp_shape *shape, double t, gp_body *body_out);
+
+/* The level-set lattice the geometry was built from, (2N+1)^2 FP64 values in
+ * the paper sign, copied to phi_out (device). */
+gp_status gp_level_set(gp_ctx *ctx, double *phi_out);
 
 /* Level information: cells per side, vector length, mesh size. */
 gp_status gp_level_info(const gp_ctx *ctx, int level, int *N, int64_t *len, double *h);
@@ -189,10 +224,12 @@ gp_status gp_coarse_solve(gp_ctx *ctx, const double *b, double *x);
 /* One cycle (V or W per params) on the finest level, in place. */
 gp_status gp_cycle(gp_ctx *ctx, double *x, const double *b);
 
-/* Cycles from the iterate x until ||b - M x||_inf <= tol (absolute) or the
- * cycle cap.  precision GP_MIXED: each outer step computes the FP64
- * residual, runs one FP32 cycle on it from zero and adds the FP32
- * correction to x in FP64.  rep may be NULL. */
+/* Iterations from the iterate x until ||b - M x||_inf <= tol (absolute) or
+ * max_cycles iterations.  Plain cycles (krylov = 0): each iteration is one
+ * cycle; precision GP_MIXED computes the FP64 residual, runs one FP32 cycle
+ * on it from zero and adds the FP32 correction to x in FP64.  krylov = 1:
+ * BiCGSTAB with one cycle from zero as right preconditioner (FP64 cycle, or
+ * FP32 cycle on the FP64 vector in GP_MIXED).  rep may be NULL. */
 gp_status mg_solve(gp_ctx *ctx, double *x, const double *b, double tol, gp_report *rep);
 
 /* One Crank-Nicolson step (Sect. 2) on the finest level, in place.

@@ -55,6 +55,7 @@ def lib():
             L.or_set_params.argtypes = [vp, i, i, i, i, d, i, i, ctypes.c_uint]
             L.or_set_alpha.argtypes = [vp, d]
             L.or_set_snap.argtypes = [vp, d]
+            L.or_set_band.argtypes = [vp, i]
             L.or_last_error.restype = ctypes.c_char_p
             L.or_last_error.argtypes = [vp]
             for f in (L.or_n, L.or_n_int, L.or_num_ghosts):
@@ -78,6 +79,7 @@ def lib():
             L.or_cycle.argtypes = [vp, i, P(d), P(d)]
             L.or_solve.argtypes = [vp, P(d), P(d), d, i, P(d), P(i)]
             L.or_convective.argtypes = [vp, P(d), P(d)]
+            L.or_solve_krylov.argtypes = [vp, P(d), P(d), d, i, P(d), P(i)]
             L.or_cn_rhs.argtypes = [vp, P(d), P(d), vp, d, vp, P(d), P(d), P(d)]
             L.or_momentum_residual.argtypes = [vp, P(d), P(d), P(d), P(d)]
             L.or_cn_step.argtypes = [vp, P(d), P(d), P(d), i, vp, vp, d, P(d), P(d), d, d, i, P(d)]
@@ -120,7 +122,7 @@ class Oracle:
     grids (N, N/2, ...), alpha = dt / (2 Re)."""
 
     def __init__(self, N, x0, y0, L, levels, alpha, nu1=2, nu2=1, gamma=1, lam=5, dtau=0.9,
-                 ghost_mode=0, order_mode=0, seed=12345, snap=0.3):
+                 ghost_mode=0, order_mode=0, seed=12345, snap=0.3, band=0):
         self.L = lib()
         self.N, self.x0, self.y0, self.len, self.levels, self.alpha = N, x0, y0, L, levels, alpha
         self.h = L / N
@@ -130,6 +132,8 @@ class Oracle:
         self.set_params(nu1, nu2, gamma, lam, dtau, ghost_mode, order_mode, seed)
         self.snap = snap
         self.L.or_set_snap(self.c, snap)
+        self.band = band
+        self.L.or_set_band(self.c, band)
 
     def set_params(self, nu1=2, nu2=1, gamma=1, lam=5, dtau=0.9, ghost_mode=0, order_mode=0, seed=12345):
         self.params = dict(nu1=nu1, nu2=nu2, gamma=gamma, lam=lam, dtau=dtau, ghost_mode=ghost_mode,
@@ -260,6 +264,15 @@ class Oracle:
         hist = np.zeros(max_cycles + 1)
         nc = ctypes.c_int(0)
         st = self.L.or_solve(self.c, _p(x2), _p(b), tol, max_cycles, _p(hist), ctypes.byref(nc))
+        return st, x2, hist[:nc.value + 1]
+
+    def solve_krylov(self, x, b, tol, maxit=100):
+        """BiCGSTAB preconditioned by one cycle; hist = true residual norms."""
+        x2 = np.array(x, dtype=np.float64)
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        hist = np.zeros(maxit + 1)
+        nc = ctypes.c_int(0)
+        st = self.L.or_solve_krylov(self.c, _p(x2), _p(b), tol, maxit, _p(hist), ctypes.byref(nc))
         return st, x2, hist[:nc.value + 1]
 
     # ------------------------------------------------- Crank-Nicolson step

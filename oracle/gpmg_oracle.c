@@ -116,6 +116,7 @@ typedef struct {
     int nu1, nu2, gamma, lam, ghost_mode, order_mode;
     double dtau;
     double snap;       /* nodes with phi / |grad phi| >= -snap h are external */
+    int band;          /* extra ghost layers around the fluid (moving bodies) */
     unsigned rng;
     double *phi;       /* half lattice (2N+1)^2, paper sign */
     level_t lv[OR_MAXLEV];
@@ -390,10 +391,10 @@ static int mark_needed(ctx_t *c, level_t *l, int g, int i, int j, int *changed)
 /* Is (g,i,j) within two index steps (Chebyshev) of an internal node of the
  * same grid?  Only such nodes may join the ghost set through the stencil of
  * another ghost; farther stencil nodes stay inactive (value 0). */
-static int near_internal(level_t *l, int g, int i, int j)
+static int near_internal(level_t *l, int g, int i, int j, int rad)
 {
-    for (int dj = -2; dj <= 2; dj++)
-        for (int di = -2; di <= 2; di++)
+    for (int dj = -rad; dj <= rad; dj++)
+        for (int di = -rad; di <= rad; di++)
             if (ttype(l, g, i + di, j + dj) == T_INTERNAL) return 1;
     return 0;
 }
@@ -403,7 +404,8 @@ static int mark_stencil(ctx_t *c, level_t *l, int g, int i, int j, int *changed)
 {
     if (!inG(l, g, i, j)) { seterr(c, "stencil leaves the grid"); return 0; }
     int8_t *t = tref(l, g, i, j);
-    if (*t == T_EXT && near_internal(l, g, i, j)) { *t = T_GHOST; *changed = 1; }
+    int rad = (c->band > 2 && l == &c->lv[0]) ? c->band : 2;
+    if (*t == T_EXT && near_internal(l, g, i, j, rad)) { *t = T_GHOST; *changed = 1; }
     return 1;
 }
 
@@ -498,6 +500,25 @@ static int classify_level(ctx_t *c, int lev)
             !mark_needed(c, l, G_V, N - 1, j, &ch) || !mark_needed(c, l, G_V, N - 2, j, &ch))
             return 0;
     }
+    /* moving bodies (Sect. 3.4): on the finest grid every external node
+     * within `band` index steps of an internal node of its grid is a ghost
+     * too, so that values from the previous step exist where the fluid
+     * advances; the closure radius grows to `band` there */
+    if (c->band > 0 && lev == 0)
+        for (int g = 0; g < 3; g++) {
+            int ilo = g == G_V ? -1 : 0, ihi = g == G_P ? N - 1 : N;
+            int jlo = g == G_U ? -1 : 0, jhi = g == G_P ? N - 1 : N;
+            for (int j = jlo; j <= jhi; j++)
+                for (int i = ilo; i <= ihi; i++) {
+                    int8_t *t = tref(l, g, i, j);
+                    if (*t != T_EXT) continue;
+                    int near = 0;
+                    for (int dj = -c->band; dj <= c->band && !near; dj++)
+                        for (int di = -c->band; di <= c->band && !near; di++)
+                            if (ttype(l, g, i + di, j + dj) == T_INTERNAL) near = 1;
+                    if (near) *t = T_GHOST;
+                }
+        }
     /* close the ghost set under the ghost stencils (Remark 1, coupled ghosts) */
     for (int pass = 0;; pass++) {
         if (pass > 64) { seterr(c, "ghost marking does not close"); return 0; }
@@ -690,6 +711,7 @@ void or_set_params(void *vc, int nu1, int nu2, int gamma, int lam, double dtau, 
 void or_set_alpha(void *vc, double alpha) { ((ctx_t *)vc)->alpha = alpha; }
 
 void or_set_snap(void *vc, double snap) { ((ctx_t *)vc)->snap = snap; }
+void or_set_band(void *vc, int band) { ((ctx_t *)vc)->band = band; }
 
 const char *or_last_error(void *vc) { return ((ctx_t *)vc)->err; }
 
@@ -1454,6 +1476,73 @@ int or_cn_step(void *vc, double *x, double *N1, double *N2, int step, const doub
     info[1] = cycles;
     info[2] = res;
     free(Nn); free(Nh); free(Nk); free(b); free(xn); free(hist);
+    return st;
+}
+
+/* ------------------------------------------------- Krylov acceleration */
+
+static double dotv(const double *a, const double *b, int n)
+{
+    double s = 0.0;
+    for (int k = 0; k < n; k++) s += a[k] * b[k];
+    return s;
+}
+
+/* y = M x on the finest level (the residual of x against b = 0, negated) */
+static void apply_M(ctx_t *c, const double *x, double *y, double *zero)
+{
+    level_t *l = &c->lv[0];
+    or_residual(c, 0, x, zero, y);
+    for (int k = 0; k < l->n; k++) y[k] = -y[k];
+}
+
+/* BiCGSTAB on M x = b, preconditioned on the right by one multigrid cycle
+ * from zero (the same cycle as or_solve).  Stops when ||b - M x||_inf <= tol
+ * (the true residual, computed every iteration); hist[k] is that norm after
+ * iteration k. */
+int or_solve_krylov(void *vc, double *x, const double *b, double tol, int maxit, double *hist, int *nit)
+{
+    ctx_t *c = (ctx_t *)vc;
+    if (!c->geom_ok) return OR_INVALID;
+    level_t *l = &c->lv[0];
+    int n = l->n;
+    double *r = calloc(n, sizeof(double)), *rh = calloc(n, sizeof(double)), *p = calloc(n, sizeof(double));
+    double *v = calloc(n, sizeof(double)), *s = calloc(n, sizeof(double)), *t = calloc(n, sizeof(double));
+    double *y = calloc(n, sizeof(double)), *z = calloc(n, sizeof(double)), *zero = calloc(n, sizeof(double));
+    double *tr = calloc(n, sizeof(double));
+    zero_inactive(c, 0, x);
+    double r0 = or_residual(c, 0, x, b, r);
+    memcpy(rh, r, sizeof(double) * n);
+    hist[0] = r0;
+    *nit = 0;
+    int st = OR_NOT_CONVERGED;
+    if (r0 <= tol) st = OR_OK;
+    double rho = 1.0, alpha = 1.0, omega = 1.0;
+    for (int it = 1; st == OR_NOT_CONVERGED && it <= maxit; it++) {
+        double rn = dotv(rh, r, n);
+        double beta = (rn / rho) * (alpha / omega);
+        rho = rn;
+        for (int k = 0; k < n; k++) p[k] = r[k] + beta * (p[k] - omega * v[k]);
+        memset(y, 0, sizeof(double) * n);
+        cycle_rec(c, 0, y, p);
+        apply_M(c, y, v, zero);
+        alpha = rho / dotv(rh, v, n);
+        for (int k = 0; k < n; k++) s[k] = r[k] - alpha * v[k];
+        memset(z, 0, sizeof(double) * n);
+        cycle_rec(c, 0, z, s);
+        apply_M(c, z, t, zero);
+        omega = dotv(t, s, n) / dotv(t, t, n);
+        for (int k = 0; k < n; k++) {
+            x[k] += alpha * y[k] + omega * z[k];
+            r[k] = s[k] - omega * t[k];
+        }
+        double rt = or_residual(c, 0, x, b, tr);
+        hist[it] = rt;
+        *nit = it;
+        if (!(rt == rt) || rt > 1e6 * r0) st = OR_DIVERGED;
+        else if (rt <= tol) st = OR_OK;
+    }
+    free(r); free(rh); free(p); free(v); free(s); free(t); free(y); free(z); free(zero); free(tr);
     return st;
 }
 

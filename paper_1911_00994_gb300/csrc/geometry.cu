@@ -26,6 +26,7 @@ struct Geo {
     int P;
     long long F;
     double x0, y0, h, snap;
+    int band;           // extra ghost layers (finest level only)
     uint8_t *t[3];      // node types per grid (frame layout)
     uint8_t *prim;      // [3F]
     uint8_t *done;      // [3F]
@@ -241,6 +242,28 @@ __device__ bool node_internal(const Geo &G, int g, int i, int j, double ph)
 
 // ------------------------------------------------------------------ kernels
 
+// level set of a rigidly moving test body on the half-cell lattice (paper
+// sign), see gp_shape in gpmg.h
+__global__ void k_shape_phi(double *phi, int Nf, double x0, double y0, double L, gp_shape sh, double cx, double cy,
+                            double ang)
+{
+    long long n = (long long)(2 * Nf + 1) * (2 * Nf + 1);
+    long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int a = (int)(k % (2 * Nf + 1)), bq = (int)(k / (2 * Nf + 1));
+    double hh = 0.5 * (L / Nf);
+    double x = x0 + a * hh, y = y0 + bq * hh;
+    double dx = x - cx, dy = y - cy;
+    double c = cos(ang), s = sin(ang);
+    double qx = c * dx + s * dy, qy = -s * dx + c * dy;  // rotate by -ang
+    double r = sqrt(qx * qx + qy * qy);
+    double v;
+    if (sh.kind == GP_CIRCLE) v = sh.a - r;
+    else if (sh.kind == GP_ELLIPSE) v = 1.0 - sqrt(qx * qx / (sh.a * sh.a) + qy * qy / (sh.b * sh.b));
+    else v = sh.a + sh.b * sin(sh.k * atan2(qy, qx)) - r;
+    phi[k] = v;
+}
+
 __global__ void k_phi_sign(const double *in, double *out, long long n, double s)
 {
     long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -340,12 +363,25 @@ __global__ void k_mark_primary(Geo G)
     }
 }
 
-__device__ inline bool near_internal(const Geo &G, int g, int i, int j)
+__device__ inline bool near_internal(const Geo &G, int g, int i, int j, int rad)
 {
-    for (int dj = -2; dj <= 2; dj++)
-        for (int di = -2; di <= 2; di++)
+    for (int dj = -rad; dj <= rad; dj++)
+        for (int di = -rad; di <= rad; di++)
             if (ttype(G, g, i + di, j + dj) == T_INTERNAL) return true;
     return false;
+}
+
+// moving bodies (Sect. 3.4): external nodes of the finest grid within `band`
+// index steps of an internal node of their grid are ghosts too
+__global__ void k_mark_band(Geo G)
+{
+    int col = blockIdx.x * blockDim.x + threadIdx.x;
+    int row = blockIdx.y;
+    if (col >= G.P) return;
+    int i = col - 1, j = row - 1;
+    long long s = (long long)row * G.P + col;
+    for (int g = 0; g < 3; g++)
+        if (G.t[g][s] == T_EXT && near_internal(G, g, i, j, G.band)) G.t[g][s] = T_GHOST;
 }
 
 // one closure pass: the stencil of every ghost not processed yet marks its
@@ -372,7 +408,7 @@ __global__ void k_closure(Geo G)
                 continue;
             }
             long long s2 = (long long)(jj + 1) * G.P + (ii + 1);
-            if (G.t[g][s2] == T_EXT && near_internal(G, g, ii, jj)) {
+            if (G.t[g][s2] == T_EXT && near_internal(G, g, ii, jj, G.band > 2 ? G.band : 2)) {
                 G.t[g][s2] = T_GHOST;
                 atomicExch(G.flag, 1);
             }
@@ -619,6 +655,7 @@ static Geo make_geo(Ctx *c, int lev)
     G.y0 = c->prm.y0;
     G.h = c->prm.L / (double)l.N;
     G.snap = c->prm.snap;
+    G.band = lev == 0 ? c->prm.band : 0;
     G.t[0] = l.tU; G.t[1] = l.tV; G.t[2] = l.tP;
     G.prim = l.prim;
     G.done = l.done;
@@ -635,12 +672,22 @@ static int cuda_fail(Ctx *c, cudaError_t e, const char *where)
 }
 
 // returns a gp_status
+void shape_phi(Ctx *c, const gp_shape &sh, double cx, double cy, double ang)
+{
+    int Nf = c->prm.N;
+    long long nphi = (long long)(2 * Nf + 1) * (2 * Nf + 1);
+    k_shape_phi<<<(unsigned)((nphi + 255) / 256), 256, 0, c->stream>>>(c->phi, Nf, c->prm.x0, c->prm.y0, c->prm.L, sh, cx,
+                                                                       cy, ang);
+}
+
+// phi_in == nullptr: the context's lattice is already filled (paper sign)
 int build_geometry_levels(Ctx *c, const double *phi_in, int phi_fluid_positive)
 {
     cudaStream_t st = c->stream;
     int Nf = c->prm.N;
     long long nphi = (long long)(2 * Nf + 1) * (2 * Nf + 1);
-    k_phi_sign<<<(unsigned)((nphi + 255) / 256), 256, 0, st>>>(phi_in, c->phi, nphi, phi_fluid_positive ? -1.0 : 1.0);
+    if (phi_in)
+        k_phi_sign<<<(unsigned)((nphi + 255) / 256), 256, 0, st>>>(phi_in, c->phi, nphi, phi_fluid_positive ? -1.0 : 1.0);
     if (cuda_fail(c, cudaMemsetAsync(c->err, 0, sizeof(unsigned), st), "memset")) return GP_CUDA;
     int *hflag = (int *)c->hostbuf;
     for (int lev = 0; lev < c->L; lev++) {
@@ -650,6 +697,7 @@ int build_geometry_levels(Ctx *c, const double *phi_in, int phi_fluid_positive)
         k_classify<<<grd, blk, 0, st>>>(G);
         k_pcell_reclass<<<grd, blk, 0, st>>>(G);
         k_mark_primary<<<grd, blk, 0, st>>>(G);
+        if (G.band > 0) k_mark_band<<<grd, blk, 0, st>>>(G);
         int pass = 0;
         for (;; pass++) {
             if (pass > 64) {

@@ -134,12 +134,18 @@ struct Ctx {
     double tmr_ms;
     long long tmr_launches;
     // captured mg_solve iterations: [0] FP64 cycle + residual, [1] FP32 cycle
-    // inside FP64 residual correction; keyed by the iterate and rhs pointers
-    cudaGraphExec_t gexec[2];
-    const void *gx[2], *gb[2];
-    int gvalid[2];
-    long long glaunches[2];
+    // inside FP64 residual correction, [2] / [3] BiCGSTAB iteration with an
+    // FP64 / FP32 cycle; keyed by the iterate and rhs pointers
+    cudaGraphExec_t gexec[4];
+    const void *gx[4], *gb[4];
+    int gvalid[4];
+    long long glaunches[4];
     int graphs_off;
+    // BiCGSTAB vectors (finest level): r, rh, p, -v, s, -t, y, z, 0, true residual
+    double *kv[10];
+    double *ks;          // device scalars rho, alpha, omega, beta
+    double *kpart;       // dot-product partials
+    int kpart_n;
     int geom_ok;
     int coarse_ok;
     double alpha_factored;

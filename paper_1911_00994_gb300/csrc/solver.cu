@@ -11,6 +11,7 @@
 namespace gpmg {
 
 int build_geometry_levels(Ctx *c, const double *phi_in, int phi_fluid_positive);
+void shape_phi(Ctx *c, const gp_shape &sh, double cx, double cy, double ang);
 int build_coarse_inverse(Ctx *c);
 void coarse_maps_host(int N, int P, long long F, int *cmap, int *inv, long long vl);
 template <typename T> void residual(Ctx *c, int lev, const T *x, const T *b, T *r);
@@ -27,6 +28,8 @@ void to_float(Ctx *c, const double *a, float *b, long long n);
 void tmr_flush(Ctx *c);
 void tiles_init();
 void prepare_cuts(Ctx *c);
+void krylov_init(Ctx *c, double *x, const double *b);
+void krylov_iteration(Ctx *c, double *x, const double *b);
 int residual_static(Ctx *c, int lev, const double *x, const double *b, double *r, double *norm_host);
 void cn_convective(Ctx *c, const double *x, const double *Nn, double *out, int mode);
 void cn_rhs(Ctx *c, const double *xn, const double *Nh, const double *f, double dt, const double *bc, const gp_body &body,
@@ -162,6 +165,9 @@ static size_t carve(Ctx *c, char *base)
     c->maxbits = cv.take<unsigned long long>(4);
     c->err = cv.take<unsigned>(4);
     c->flag = cv.take<int>(4);
+    for (int k = 0; k < 10; k++) c->kv[k] = p.krylov ? cv.take<double>(c->lv[0].VL) : nullptr;
+    c->ks = cv.take<double>(8);
+    c->kpart = cv.take<double>(2 * 1024);
     const Level &lc = c->lv[L - 1];
     int nc = 2 * (lc.N + 1) * (lc.N + 2) + lc.N * lc.N + 1;
     c->nc = nc;
@@ -210,6 +216,10 @@ template <typename T> void cycle_rec(Ctx *c, int lev, T *x, const T *b)
 static void solve_iteration(Ctx *c, int which, double *x, const double *b)
 {
     Level &l0 = c->lv[0];
+    if (which >= 2) {
+        krylov_iteration(c, x, b);
+        return;
+    }
     if (which == 1) {
         to_float(c, l0.r, l0.bf, l0.VL);
         zero_vec<float>(c, l0.xf, l0.VL);
@@ -223,7 +233,7 @@ static void solve_iteration(Ctx *c, int which, double *x, const double *b)
 
 void graphs_reset(Ctx *c)
 {
-    for (int w = 0; w < 2; w++)
+    for (int w = 0; w < 4; w++)
         if (c->gvalid[w]) {
             cudaGraphExecDestroy(c->gexec[w]);
             c->gvalid[w] = 0;
@@ -235,6 +245,11 @@ void graphs_reset(Ctx *c)
 static bool run_graph(Ctx *c, int which, double *x, const double *b)
 {
     if (!c->prm.graphs || c->graphs_off || c->stream == nullptr || c->tmr_kernel >= 0) return false;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(c->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return false;  // the caller is capturing: launch directly into its capture
+    }
     if (!c->gvalid[which] || c->gx[which] != x || c->gb[which] != b) {
         if (c->gvalid[which]) {
             cudaGraphExecDestroy(c->gexec[which]);
@@ -392,6 +407,8 @@ gp_status gp_create(gp_ctx **out, const gp_params *prm, void *workspace, size_t 
             e = cudaMemsetAsync(l.rf, 0, l.VL * sizeof(float), c->stream);
         }
     }
+    for (int k = 0; k < 10 && e == cudaSuccess; k++)
+        if (c->kv[k]) e = cudaMemsetAsync(c->kv[k], 0, c->lv[0].VL * sizeof(double), c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         delete ctx;
@@ -451,9 +468,35 @@ gp_status gp_set_alpha(gp_ctx *ctx, double alpha)
     return GP_OK;
 }
 
+static gp_status geometry_finish(gp_ctx *ctx, const double *phi, int phi_fluid_positive);
+
 gp_status geometry_build(gp_ctx *ctx, const double *phi, int phi_fluid_positive)
 {
     if (!ctx || !phi) return GP_INVALID;
+    return geometry_finish(ctx, phi, phi_fluid_positive);
+}
+
+gp_status geometry_build_shape(gp_ctx *ctx, const gp_shape *shape, double t, gp_body *body_out)
+{
+    if (!ctx || !shape || shape->kind < GP_CIRCLE || shape->kind > GP_FLOWER) return GP_INVALID;
+    if (shape->orbit_r != 0.0 && !(shape->orbit_period > 0.0)) return GP_INVALID;
+    const double two_pi = 6.283185307179586;
+    double w = shape->orbit_r != 0.0 ? two_pi / shape->orbit_period : 0.0;
+    double ph = w * t + shape->orbit_phase;
+    double cx = shape->xc + shape->orbit_r * cos(ph), cy = shape->yc + shape->orbit_r * sin(ph);
+    shape_phi(&ctx->c, *shape, cx, cy, shape->omega * t);
+    if (body_out) {
+        body_out->U = -shape->orbit_r * w * sin(ph);
+        body_out->V = shape->orbit_r * w * cos(ph);
+        body_out->omega = shape->omega;
+        body_out->cx = cx;
+        body_out->cy = cy;
+    }
+    return geometry_finish(ctx, nullptr, 0);
+}
+
+static gp_status geometry_finish(gp_ctx *ctx, const double *phi, int phi_fluid_positive)
+{
     Ctx *c = &ctx->c;
     c->geom_ok = 0;
     c->coarse_ok = 0;
@@ -471,6 +514,15 @@ gp_status geometry_build(gp_ctx *ctx, const double *phi, int phi_fluid_positive)
         return (gp_status)s;
     }
     return check_cuda(ctx, "coarse inverse");
+}
+
+gp_status gp_level_set(gp_ctx *ctx, double *phi_out)
+{
+    if (!ctx || !phi_out) return GP_INVALID;
+    Ctx *c = &ctx->c;
+    size_t n = (size_t)(2 * c->prm.N + 1) * (2 * c->prm.N + 1);
+    cudaMemcpyAsync(phi_out, c->phi, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+    return check_cuda(ctx, "gp_level_set");
 }
 
 gp_status gp_level_info(const gp_ctx *ctx, int level, int *N, int64_t *len, double *h)
@@ -620,7 +672,9 @@ gp_status mg_solve(gp_ctx *ctx, double *x, const double *b, double tol, gp_repor
     Ctx *c = &ctx->c;
     Level &l0 = c->lv[0];
     bool mixed = c->prm.precision == GP_MIXED;
+    bool kry = c->prm.krylov != 0;
     zero_inactive<double>(c, 0, x);
+    if (kry) krylov_init(c, x, b);
     residual<double>(c, 0, x, b, l0.r);
     double nrm = 0.0;
     cudaMemcpyAsync(&nrm, c->red, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
@@ -629,6 +683,7 @@ gp_status mg_solve(gp_ctx *ctx, double *x, const double *b, double tol, gp_repor
     if (rep) {
         rep->res0 = r0;
         rep->cycles = 0;
+        rep->iterations = 0;
         if (rep->hist_host) rep->hist_host[0] = r0;
     }
     gp_status st = GP_NOT_CONVERGED;
@@ -637,7 +692,7 @@ gp_status mg_solve(gp_ctx *ctx, double *x, const double *b, double tol, gp_repor
     else if (r0 <= tol) st = GP_OK;
     else
         for (k = 1; k <= c->prm.max_cycles; k++) {
-            int which = mixed ? 1 : 0;
+            int which = (kry ? 2 : 0) + (mixed ? 1 : 0);
             if (!run_graph(c, which, x, b)) solve_iteration(c, which, x, b);
             cudaMemcpyAsync(&nrm, c->red, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
             if (cudaStreamSynchronize(c->stream) != cudaSuccess) return check_cuda(ctx, "mg_solve");
@@ -653,7 +708,8 @@ gp_status mg_solve(gp_ctx *ctx, double *x, const double *b, double tol, gp_repor
         }
     if (k > c->prm.max_cycles) k = c->prm.max_cycles;
     if (rep) {
-        rep->cycles = k;
+        rep->iterations = k;
+        rep->cycles = kry ? 2 * k : k;
         rep->res = nrm;
         rep->rho = (k > 0 && r0 > 0 && nrm > 0) ? pow(nrm / r0, 1.0 / k) : 0.0;
         double xi = 0.0;

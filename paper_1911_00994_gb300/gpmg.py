@@ -26,11 +26,12 @@ class gp_params(ctypes.Structure):
                 ("levels", ctypes.c_int), ("alpha", ctypes.c_double), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
                 ("gamma", ctypes.c_int), ("lam", ctypes.c_int), ("dtau", ctypes.c_double), ("snap", ctypes.c_double),
                 ("precision", ctypes.c_int), ("max_cycles", ctypes.c_int), ("cn_buffers", ctypes.c_int),
-                ("graphs", ctypes.c_int)]
+                ("graphs", ctypes.c_int), ("band", ctypes.c_int), ("krylov", ctypes.c_int)]
 
 
 class gp_report(ctypes.Structure):
-    _fields_ = [("cycles", ctypes.c_int), ("res0", ctypes.c_double), ("res", ctypes.c_double),
+    _fields_ = [("cycles", ctypes.c_int), ("iterations", ctypes.c_int), ("res0", ctypes.c_double),
+                ("res", ctypes.c_double),
                 ("rho", ctypes.c_double), ("xi", ctypes.c_double), ("hist_host", ctypes.POINTER(ctypes.c_double))]
 
 
@@ -42,6 +43,15 @@ class gp_body(ctypes.Structure):
 class gp_walls(ctypes.Structure):
     _fields_ = [("u_bottom", ctypes.c_double), ("u_top", ctypes.c_double), ("v_left", ctypes.c_double),
                 ("v_right", ctypes.c_double)]
+
+
+class gp_shape(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("a", ctypes.c_double), ("b", ctypes.c_double), ("k", ctypes.c_int),
+                ("xc", ctypes.c_double), ("yc", ctypes.c_double), ("orbit_r", ctypes.c_double),
+                ("orbit_period", ctypes.c_double), ("orbit_phase", ctypes.c_double), ("omega", ctypes.c_double)]
+
+
+GP_CIRCLE, GP_ELLIPSE, GP_FLOWER = 0, 1, 2
 
 
 class gp_cn_report(ctypes.Structure):
@@ -70,6 +80,8 @@ SIGNATURES = [
     ("gp_last_error", ctypes.c_char_p, [_VP]),
     ("gp_set_alpha", _I, [_VP, _D]),
     ("geometry_build", _I, [_VP, _VP, _I]),
+    ("geometry_build_shape", _I, [_VP, _P(gp_shape), _D, _P(gp_body)]),
+    ("gp_level_set", _I, [_VP, _VP]),
     ("gp_level_info", _I, [_VP, _I, _P(_I), _P(ctypes.c_int64), _P(_D)]),
     ("gp_types", _I, [_VP, _I, _VP, _VP, _VP]),
     ("gp_ghost_count", _I, [_VP, _I, _P(_I), _P(_I)]),
@@ -146,7 +158,7 @@ class Solver:
 
     def __init__(self, N, x0, y0, L, levels=None, alpha=None, nu1=2, nu2=1, gamma=1, lam=5, dtau=0.9,
                  snap=0.3, precision=GP_FP64, max_cycles=100, device="cuda", stream=None, cn_buffers=True,
-                 graphs=True):
+                 graphs=True, band=0, krylov=False):
         import torch
         self.torch = torch
         self.L = lib()
@@ -162,6 +174,8 @@ class Solver:
         p.precision, p.max_cycles = precision, max_cycles
         p.cn_buffers = 1 if cn_buffers else 0
         p.graphs = 1 if graphs else 0
+        p.band = int(band)
+        p.krylov = 1 if krylov else 0
         self.prm = p
         nb = ctypes.c_size_t(0)
         st = self.L.gp_workspace_size(ctypes.byref(p), ctypes.byref(nb))
@@ -226,6 +240,22 @@ class Solver:
         t = self.torch.as_tensor(phi, dtype=self.torch.float64, device=self.device).contiguous()
         self._phi = t
         return self.L.geometry_build(self.ctx, _ptr(t), int(phi_fluid_positive))
+
+    def geometry_shape(self, kind, a, b=0.0, k=0, xc=0.0, yc=0.0, orbit_r=0.0, orbit_period=1.0, orbit_phase=0.0,
+                       omega=0.0, t=0.0):
+        """geometry_build_shape: level set of a moving test body at time t,
+        evaluated on the device; returns (status, body velocity tuple)."""
+        sh = gp_shape(kind, a, b, k, xc, yc, orbit_r, orbit_period, orbit_phase, omega)
+        bd = gp_body()
+        st = self.L.geometry_build_shape(self.ctx, ctypes.byref(sh), t, ctypes.byref(bd))
+        return st, (bd.U, bd.V, bd.omega, bd.cx, bd.cy)
+
+    def level_set(self):
+        """gp_level_set: the context's level-set lattice (paper sign)."""
+        n = 2 * self.N + 1
+        out = self.torch.empty(n * n, dtype=self.torch.float64, device=self.device)
+        self._check(self.L.gp_level_set(self.ctx, _ptr(out)), "gp_level_set")
+        return out.view(n, n)
 
     def error(self):
         return self.L.gp_last_error(self.ctx).decode()
@@ -347,5 +377,5 @@ class Solver:
             h = (ctypes.c_double * (self.prm.max_cycles + 1))()
             rep.hist_host = ctypes.cast(h, ctypes.POINTER(ctypes.c_double))
         st = self.L.mg_solve(self.ctx, _ptr(x), _ptr(b), tol, ctypes.byref(rep))
-        hist_arr = np.array(h[:rep.cycles + 1]) if hist else None
+        hist_arr = np.array(h[:rep.iterations + 1]) if hist else None
         return st, rep, hist_arr

@@ -280,3 +280,15 @@ def test_coarse_solve_matches_library_solve():
     b = rng.standard_normal(o.n(lev))
     x = o.coarse_solve(b)
     assert np.abs(x - np.linalg.solve(A, b)).max() < 1e-9 * np.abs(x).max()
+
+
+def test_krylov_equals_direct_solve():
+    # BiCGSTAB preconditioned by one cycle reaches the dense solution of the
+    # assembled system (config 1)
+    o, phi, st = make_oracle("circle", 32)
+    ex = W.taylor_green()
+    b, xe, t, gh = manufactured(o, ex)
+    st, xd = o.dense_solve(b)
+    st, xk, hist = o.solve_krylov(np.zeros_like(b), b, 1e-12, 60)
+    assert st == 0
+    assert np.abs(xk - xd).max() / np.abs(xd).max() <= 1e-10
