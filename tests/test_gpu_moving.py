@@ -40,10 +40,14 @@ def test_shape_level_set_matches_closed_form(kind, a, b, k):
 
 def test_moving_circle_cn_steps_match_oracle():
     from paper_1911_00994_gb300 import gpmg
+    # Sects. 3.4 and 5.1 bound the step by dt <= min(h, h / max |u|); the body moves at
+    # 0.4 pi (about 1.26), and at this resolution the impulsively started
+    # boundary layer makes the mid-point Picard iteration of Eq. (NSitconv)
+    # diverge already at dt = 0.6 h, so the step is 0.3 h (0.38 h of motion)
     N, x0, L, Re = 64, -1.0, 2.0, 100.0
     h = L / N
-    dt = h
-    band = 3  # the body moves about 1.26 h per step
+    dt = 0.3 * h
+    band = 3
     lev = levels_for(N)
     o = O.Oracle(N, x0, x0, L, lev, dt / (2 * Re), band=band)
     s = gpmg.Solver(N, x0, x0, L, levels=lev, alpha=dt / (2 * Re), band=band)
