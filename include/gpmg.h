@@ -79,6 +79,10 @@ typedef struct gp_params {
                            so that the previous step has values where the fluid advances */
     int krylov;         /* 0: plain cycles; 1: BiCGSTAB preconditioned on the right by one
                            cycle (two cycles per iteration), same stopping test */
+    int tile_min;       /* levels with at least this many cells per side sweep their full
+                           boxes in one pass of shared-memory tiles (same iterate as the five
+                           colour passes); 0: 512 for the FP32 cycles of the mixed mode and
+                           never for FP64; negative: never */
 } gp_params;
 
 typedef struct gp_report {

@@ -1,8 +1,11 @@
 // Operator, relaxation and transfer kernels of one multigrid level
 // (Sect. 3.2 rows, Sect. 4.1 relaxation, Sect. 4.2 restriction, Sect. 4.3
 // interpolation), in FP64 and FP32.
+#include <cuda.h>
+
 #include <cmath>
 #include <cstdio>
+#include <mutex>
 
 #include "gpmg_internal.cuh"
 
@@ -11,8 +14,18 @@ namespace gpmg {
 // levels solved by the one-block smoother, ghost lists swept by one block,
 // and levels whose full boxes are swept by shared-memory tiles
 constexpr int SMALL_N = 64;
-constexpr int TILE_MIN_N = 1 << 30;  // tiled sweep off: its tile load is latency bound (slower than five colour passes)
+constexpr int TILE_MIN_N = 512;  // default finest size swept by TMA tiles (gp_params.tile_min overrides)
 constexpr int GHOST_BLOCK_ROWS = 4096;
+constexpr int CUT_SPLIT = 64;  // cut boxes per colour above which each colour gets its own multi-block launch
+
+// constants of the box solves of one level (Sect. 4.1.1), reciprocals
+// precomputed so that a box needs no division
+template <typename T> struct BoxK {
+    T a, d, q;          // alpha/h^2, 1 + 4 alpha/h^2, 1/h
+    T qida, qid;        // q/(d + a), q/d
+    T id, idet;         // 1/d, 1/(d^2 - a^2)
+    T ic1[9];           // 1/c1 for (faces in x) * 3 + (faces in y), c1 the pressure pivot of the Schur complement
+};
 
 template <typename T> struct LevelArgs {
     int N, P;
@@ -20,6 +33,7 @@ template <typename T> struct LevelArgs {
     T q, a, d;          // 1/h, alpha/h^2, 1 + 4 alpha/h^2
     T h2;               // h^2
     const uint8_t *tU, *tV, *tP;
+    BoxK<T> K;
 };
 
 template <typename T> __device__ inline const T *gw(const GhostList &gh);
@@ -147,9 +161,10 @@ __global__ void k_residual_final(const double *part, int nb, const T *b, T *r, l
 template <typename T>
 __device__ __forceinline__ void box_core(T *u, T *v, T *p, const int pitch, const T *bu, const T *bv, const T *bp,
                                          const long long bpitch, const T xi, const uint8_t tW, const uint8_t tE,
-                                         const uint8_t tS, const uint8_t tN, const T a, const T d, const T q)
+                                         const uint8_t tS, const uint8_t tN, const BoxK<T> &K)
 {
     const int Pp = pitch;
+    const T a = K.a, d = K.d, q = K.q;
     bool W = tW == T_INTERNAL, E = tE == T_INTERNAL, S = tS == T_INTERNAL, Nn = tN == T_INTERNAL;
     T rW = 0, rE = 0, rS = 0, rN = 0;
     if (W) rW = bu[0] - (d * u[0] - a * (u[1] + u[-1] + u[Pp] + u[-Pp]) + q * (p[0] - p[-1]));
@@ -157,46 +172,52 @@ __device__ __forceinline__ void box_core(T *u, T *v, T *p, const int pitch, cons
     if (S) rS = bv[0] - (d * v[0] - a * (v[1] + v[-1] + v[Pp] + v[-Pp]) + q * (p[0] - p[-Pp]));
     if (Nn) rN = bv[bpitch] - (d * v[Pp] - a * (v[Pp + 1] + v[Pp - 1] + v[2 * Pp] + v[0]) + q * (p[Pp] - p[0]));
     T rC = bp[0] - (q * (u[1] - u[0] + v[Pp] - v[0]) - xi);
-    // each direction contributes c0 + c1 * dp to the continuity update
-    T c0 = 0, c1 = 0;
+    // eliminating the velocities leaves c1 dp = rC - c0 for the pressure;
+    // each direction contributes to c0, and c1 depends only on which faces
+    // take part
+    T c0 = 0;
+    int nx = 0, ny = 0;
     if (W && E) {
-        T inv = (T)1 / (d + a);
-        c0 += q * (rE - rW) * inv;
-        c1 += 2 * q * q * inv;
+        c0 += K.qida * (rE - rW);
+        nx = 2;
     } else if (W) {
-        c0 += -q * rW / d;
-        c1 += q * q / d;
+        c0 -= K.qid * rW;
+        nx = 1;
     } else if (E) {
-        c0 += q * rE / d;
-        c1 += q * q / d;
+        c0 += K.qid * rE;
+        nx = 1;
     }
     if (S && Nn) {
-        T inv = (T)1 / (d + a);
-        c0 += q * (rN - rS) * inv;
-        c1 += 2 * q * q * inv;
+        c0 += K.qida * (rN - rS);
+        ny = 2;
     } else if (S) {
-        c0 += -q * rS / d;
-        c1 += q * q / d;
+        c0 -= K.qid * rS;
+        ny = 1;
     } else if (Nn) {
-        c0 += q * rN / d;
-        c1 += q * q / d;
+        c0 += K.qid * rN;
+        ny = 1;
     }
-    if (c1 == (T)0) return;
-    T dp = (rC - c0) / c1;
+    if (nx + ny == 0) return;
+    // select the pivot reciprocal with constant indices (a dynamic index
+    // would copy the table to local memory)
+    const int kc = nx * 3 + ny;
+    T ic = K.ic1[1];
+#pragma unroll
+    for (int k = 2; k < 9; k++)
+        if (kc == k) ic = K.ic1[k];
+    T dp = (rC - c0) * ic;
     // velocity corrections with dp known
     T fW = rW - q * dp, fE = rE + q * dp, fS = rS - q * dp, fN = rN + q * dp;
     if (W && E) {
-        T det = d * d - a * a;
-        u[0] += (d * fW + a * fE) / det;
-        u[1] += (a * fW + d * fE) / det;
-    } else if (W) u[0] += fW / d;
-    else if (E) u[1] += fE / d;
+        u[0] += (d * fW + a * fE) * K.idet;
+        u[1] += (a * fW + d * fE) * K.idet;
+    } else if (W) u[0] += fW * K.id;
+    else if (E) u[1] += fE * K.id;
     if (S && Nn) {
-        T det = d * d - a * a;
-        v[0] += (d * fS + a * fN) / det;
-        v[Pp] += (a * fS + d * fN) / det;
-    } else if (S) v[0] += fS / d;
-    else if (Nn) v[Pp] += fN / d;
+        v[0] += (d * fS + a * fN) * K.idet;
+        v[Pp] += (a * fS + d * fN) * K.idet;
+    } else if (S) v[0] += fS * K.id;
+    else if (Nn) v[Pp] += fN * K.id;
     p[0] += dp;
 }
 
@@ -208,105 +229,167 @@ __device__ __forceinline__ void box_full_one(const LevelArgs<T> &A, T *x, const 
     uint8_t tW = A.tU[s], tE = A.tU[s + 1], tS = A.tV[s], tN = A.tV[s + A.P];
     if (tW == T_GHOST || tE == T_GHOST || tS == T_GHOST || tN == T_GHOST) return;
     box_core<T>(x + s, x + A.F + s, x + 2 * A.F + s, A.P, b + s, b + A.F + s, b + 2 * A.F + s, A.P, x[3 * A.F], tW, tE,
-                tS, tN, A.a, A.d, A.q);
+                tS, tN, A.K);
 }
 
-// All five colours of the full boxes in one pass: each block loads a tile
-// of (TI + 2 H) x (TI + 2 H) slots of u, v, p and the node types into shared
-// memory, sweeps the colours there and writes back the values its TI x TI
-// interior cells own (p, the west face u, the south face v).  Colour c
-// relaxes the boxes within 2 (4 - c) + 1 cells of the interior: a box reads
-// values written by boxes at most two cells away, so the interior sees the
-// same sequence of updates as the global colour-by-colour sweep, and the
-// owned west and south faces also get the update of the box on their far
-// side.  H = 11 covers the reads of the outermost boxes.
-constexpr int TILE_H = 11;
+// All five colours of the full boxes in one pass over the level.  Each
+// block owns TW x TH frame slots (all three frames).  One TMA copy brings the
+// u, v, p frames of a (TH + 20) x LW window around them into shared memory
+// (10 slots above and below, 16 left, at least 10 right) and another the
+// three node-type frames.  Colour c relaxes the boxes within 2 (4 - c) + 1
+// cells below and 2 (4 - c) cells above the owned cells: a box reads only
+// values written by boxes at most two cells away, so the owned slots see the
+// same sequence of updates as the global colour-by-colour sweep (the extra
+// cell below gives the owned west and south faces the update of the box on
+// their far side).  The block then writes every owned slot, changed or not,
+// to the other vector y, so y is a complete copy of the swept x and no block
+// reads what another writes.
+template <typename T> struct TileGeom;
+template <> struct TileGeom<float> {
+    static constexpr int TW = 64, LW = 96;
+};
+template <> struct TileGeom<double> {
+    static constexpr int TW = 32, LW = 64;
+};
+constexpr int TT_H = 32;             // owned rows
+constexpr int TT_RLO = 10;           // rows loaded above (and below) the owned ones
+constexpr int TT_LH = TT_H + 2 * TT_RLO;
+constexpr int TT_CLO = 16;           // columns loaded left of the owned ones (TMA x offsets: multiples of 16 bytes)
+constexpr unsigned long long TT_WAIT_NS = 2000000000ull;  // bound on the wait for the tile copies
+constexpr int TT_THREADS = 384;
 
-template <typename T> __host__ __device__ constexpr int tile_ti() { return sizeof(T) == 4 ? 64 : 32; }
-template <typename T> __host__ __device__ constexpr int tile_tl() { return tile_ti<T>() + 2 * TILE_H; }
-template <typename T> __host__ __device__ constexpr size_t tile_smem()
+template <typename T> __host__ __device__ constexpr size_t tt_smem()
 {
-    return (size_t)tile_tl<T>() * tile_tl<T>() * (3 * sizeof(T) + 1);
+    return (size_t)3 * TT_LH * TileGeom<T>::LW * (sizeof(T) + 1) + 16;
 }
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned phase)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+// wait for phase 0 of the barrier for at most `ns` nanoseconds
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned long long ns)
+{
+    unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, 0))
+        if (global_ns() - t0 > ns) return false;
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];"
+        :
+        : "r"(smem_u32(dst)), "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+template <typename T> struct Vec16;
+template <> struct Vec16<float> {
+    using type = float4;
+};
+template <> struct Vec16<double> {
+    using type = double2;
+};
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_box_tiled(LevelArgs<T> A, const T *x, const T *b, T *y)
+__global__ void __launch_bounds__(TT_THREADS) k_box_tma(const __grid_constant__ CUtensorMap mx,
+                                                 const __grid_constant__ CUtensorMap mt, LevelArgs<T> A, const T *x,
+                                                 const T *b, T *y, unsigned *err)
 {
-    constexpr int TI = tile_ti<T>(), TL = tile_tl<T>(), H = TILE_H;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int TW = TileGeom<T>::TW, LW = TileGeom<T>::LW, LH = TT_LH, FR = LH * LW;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     T *su = (T *)smem_raw;
-    T *sv = su + TL * TL;
-    T *sp = sv + TL * TL;
-    uint8_t *stp = (uint8_t *)(sp + TL * TL);
-    const int i0 = blockIdx.x * TI, j0 = blockIdx.y * TI;
-    const int row0 = j0 + 1 - H, col0 = i0 + 1 - H;
-    const int R = A.N + 2;
-    const long long F = A.F;
-    for (int k = threadIdx.x; k < TL * TL; k += blockDim.x) {
-        int lr = k / TL, lc = k - lr * TL;
-        int row = row0 + lr, col = col0 + lc;
-        if (row >= 0 && row < R && col >= 0 && col < A.P) {
-            long long s = (long long)row * A.P + col;
-            su[k] = x[s];
-            sv[k] = x[F + s];
-            sp[k] = x[2 * F + s];
-            stp[k] = (uint8_t)(A.tU[s] | (A.tV[s] << 3) | (A.tP[s] << 6));
-        } else {
-            su[k] = 0;
-            sv[k] = 0;
-            sp[k] = 0;
-            stp[k] = 0;
-        }
+    T *sv = su + FR;
+    T *sp = sv + FR;
+    uint8_t *tu = (uint8_t *)(sp + FR);
+    uint8_t *tv = tu + FR;
+    uint8_t *tp = tv + FR;
+    uint64_t *bar = (uint64_t *)(tp + FR);
+    const int c0 = blockIdx.x * TW, r0 = blockIdx.y * TT_H;
+    const int col0 = c0 - TT_CLO, row0 = r0 - TT_RLO;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    const T xi = x[3 * F];
     __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned bytes = (unsigned)(3 * FR * (sizeof(T) + 1));
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                     : "memory");
+        tma_load_3d(su, &mx, col0, row0, 0, bar);
+        tma_load_3d(tu, &mt, col0, row0, 0, bar);
+    }
+    bool ok = __syncthreads_and(mbar_wait_bounded(bar, TT_WAIT_NS));
+    if (!ok) {
+        // copies still in flight get a second bounded wait before the block
+        // leaves; the NaN in the scalar block makes the solve report failure
+        mbar_wait_bounded(bar, TT_WAIT_NS / 2);
+        if (threadIdx.x == 0) {
+            atomicOr(err + 2, 1u);
+            y[3 * A.F] = (T)NAN;
+        }
+        return;
+    }
+    const T xi = x[3 * A.F];
     for (int colour = 0; colour < 5; colour++) {
-        const int Rg = 2 * (4 - colour) + 1;
-        const int ilo = max(i0 - Rg, 0), ihi = min(i0 + TI + Rg, A.N);
-        const int jlo = max(j0 - Rg, 0), jhi = min(j0 + TI + Rg, A.N);
-        const int per_row = (ihi - ilo + 4) / 5 + 1;
-        const int ncell = (jhi - jlo) * per_row;
-        for (int idx = threadIdx.x; idx < ncell; idx += blockDim.x) {
-            int j = jlo + idx / per_row, t = idx % per_row;
-            int i = ilo + ((colour - 3 * j - ilo) % 5 + 5) % 5 + 5 * t;
-            if (i >= ihi) continue;
-            int ls = (j + 1 - row0) * TL + (i + 1 - col0);
-            uint8_t tc = stp[ls];
-            if ((tc >> 6) != T_INTERNAL) continue;
-            uint8_t tW = tc & 7, tE = stp[ls + 1] & 7, tS = (tc >> 3) & 7, tN = (stp[ls + TL] >> 3) & 7;
-            if (tW == T_GHOST || tE == T_GHOST || tS == T_GHOST || tN == T_GHOST) continue;
-            long long gs = (long long)(j + 1) * A.P + (i + 1);
-            box_core<T>(su + ls, sv + ls, sp + ls, TL, b + gs, b + F + gs, b + 2 * F + gs, A.P, xi, tW, tE, tS, tN, A.a,
-                        A.d, A.q);
+        const int hi = 2 * (4 - colour), lo = hi + 1;
+        const int ilo = max(c0 - 1 - lo, 0), ihi = min(c0 - 1 + TW + hi, A.N);
+        const int jlo = max(r0 - 1 - lo, 0), jhi = min(r0 - 1 + TT_H + hi, A.N);
+        // groups of 16 threads walk the rows; a group's threads take every
+        // fifth cell of the row (consecutive rows of one warp hit different
+        // shared-memory banks)
+        const int g16 = threadIdx.x >> 4, l16 = threadIdx.x & 15, ng = blockDim.x >> 4;
+        for (int j = jlo + g16; j < jhi; j += ng) {
+            const int i0 = ilo + ((colour - 3 * j - ilo) % 5 + 5) % 5;
+            const int lrow = (j + 1 - row0) * LW + 1 - col0;
+            const long long grow = (long long)(j + 1) * A.P + 1;
+            for (int i = i0 + 5 * l16; i < ihi; i += 80) {
+                const int ls = lrow + i;
+                if (tp[ls] != T_INTERNAL) continue;
+                const uint8_t tW = tu[ls], tE = tu[ls + 1], tS = tv[ls], tN = tv[ls + LW];
+                if (tW == T_GHOST || tE == T_GHOST || tS == T_GHOST || tN == T_GHOST) continue;
+                const long long gs = grow + i;
+                box_core<T>(su + ls, sv + ls, sp + ls, LW, b + gs, b + A.F + gs, b + 2 * A.F + gs, A.P, xi, tW, tE, tS,
+                            tN, A.K);
+            }
         }
         __syncthreads();
     }
-    // the values the interior cells own go to y (other blocks may still be
-    // loading their halos from x); k_box_apply copies them into x
-    for (int k = threadIdx.x; k < TI * TI; k += blockDim.x) {
-        int dj = k / TI, di = k - dj * TI;
-        int i = i0 + di, j = j0 + dj;
-        if (i >= A.N || j >= A.N) continue;
-        int ls = (j + 1 - row0) * TL + (i + 1 - col0);
-        long long gs = (long long)(j + 1) * A.P + (i + 1);
-        uint8_t tc = stp[ls];
-        if ((tc & 7) == T_INTERNAL) y[gs] = su[ls];
-        if (((tc >> 3) & 7) == T_INTERNAL) y[F + gs] = sv[ls];
-        if ((tc >> 6) == T_INTERNAL) y[2 * F + gs] = sp[ls];
+    // owned slots of the three frames, 16 bytes at a time (P and TW are
+    // multiples of 32 elements, so every row segment is whole vectors)
+    using V = typename Vec16<T>::type;
+    constexpr int VW = 16 / sizeof(T);
+    const int rows = min(TT_H, A.N + 2 - r0), vpr = min(TW, A.P - c0) / VW;
+    const int per_frame = rows * vpr;
+    for (int k = threadIdx.x; k < 3 * per_frame; k += blockDim.x) {
+        const int f = k / per_frame, rem = k - f * per_frame;
+        const int rr = rem / vpr, vv = rem - rr * vpr;
+        const V *src = (const V *)(su + f * FR + (rr + TT_RLO) * LW + TT_CLO) + vv;
+        V *dst = (V *)(y + f * A.F + (long long)(r0 + rr) * A.P + c0) + vv;
+        *dst = *src;
     }
-}
-
-// x = y on every internal node (every internal node is owned by exactly one
-// tile interior: u(i, j) and v(i, j) by cell (i, j), the faces u(N, j) and
-// v(i, N) are walls)
-template <typename T> __global__ void k_box_apply(LevelArgs<T> A, T *x, const T *y)
-{
-    const long long nslot = (long long)(A.N + 2) * A.P;
-    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < nslot; s += (long long)gridDim.x * blockDim.x) {
-        if (A.tU[s] == T_INTERNAL) x[s] = y[s];
-        if (A.tV[s] == T_INTERNAL) x[A.F + s] = y[A.F + s];
-        if (A.tP[s] == T_INTERNAL) x[2 * A.F + s] = y[2 * A.F + s];
-    }
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x < NSCAL) y[3 * A.F + threadIdx.x] = x[3 * A.F + threadIdx.x];
 }
 
 template <typename T>
@@ -455,14 +538,65 @@ template <typename T> __device__ __forceinline__ void box_cut_pre(T *x, const T 
     }
 }
 
-// all 25 colours (i mod 5, j mod 5) of the cut boxes in one block: the
-// barrier between colours orders them; boxes of one colour are independent
-template <typename T>
-__global__ void __launch_bounds__(256) k_box_cut(LevelArgs<T> A, T *x, const T *b, CutList cut, GhostList gh)
+// one prepared cut box relaxed by a whole warp: lane e (and e + 32) loads
+// entry e of the 5 x CUT_ST row entries and gathers its x, so the gathers of
+// a box are in flight together; lanes 0..4 then accumulate one row each in
+// the order box_cut_pre uses (same rounding) and apply the inverse.  k must
+// be the same on every lane of the warp.
+template <typename T> __device__ __forceinline__ void box_cut_warp(T *x, const T *b, const CutList &cut, int k, int lane)
 {
+    constexpr int NE = 5 * CUT_ST;
+    const T *coef = cut_coef<T>(cut);
+    const T *mi = cut_minv<T>(cut);
+    T c0 = 0, x0 = 0, c1 = 0, x1 = 0;
+    {
+        const long long e = (long long)lane * cut.cap + k;
+        c0 = coef[e];
+        x0 = x[cut.sidx[e]];
+    }
+    if (lane < NE - 32) {
+        const long long e = (long long)(lane + 32) * cut.cap + k;
+        c1 = coef[e];
+        x1 = x[cut.sidx[e]];
+    }
+    const int f = lane < 5 ? lane : 0;
+    const int row = cut.row[(long long)f * cut.cap + k];
+    const T bf = row >= 0 ? b[row] : (T)0;
+    T acc = 0;
+#pragma unroll
+    for (int m = 0; m < CUT_ST; m++) {
+        const int e = f * CUT_ST + m;
+        const T ca = __shfl_sync(0xffffffffu, c0, e & 31), xa = __shfl_sync(0xffffffffu, x0, e & 31);
+        const T cb = __shfl_sync(0xffffffffu, c1, e & 31), xb = __shfl_sync(0xffffffffu, x1, e & 31);
+        acc += (e < 32 ? ca : cb) * (e < 32 ? xa : xb);
+    }
+    const T r = row >= 0 ? bf - acc : (T)0;
+    T d = 0;
+#pragma unroll
+    for (int cc = 0; cc < 5; cc++) {
+        const T rc = __shfl_sync(0xffffffffu, r, cc);
+        d += mi[(long long)(f * 5 + cc) * cut.cap + k] * rc;
+    }
+    if (lane < 5 && row >= 0) x[row] += d;
+}
+
+// one colour of the cut boxes, a warp per box, over as many blocks as needed
+template <typename T> __global__ void __launch_bounds__(256) k_box_cut_colour(T *x, const T *b, CutList cut, int beg, int end)
+{
+    const int k = beg + (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+    if (k < end) box_cut_warp<T>(x, b, cut, k, threadIdx.x & 31);
+}
+
+// all 25 colours (i mod 5, j mod 5) of the cut boxes in one block of 32
+// warps: the barrier between colours orders them; boxes of one colour are
+// independent
+template <typename T>
+__global__ void __launch_bounds__(1024) k_box_cut(LevelArgs<T> A, T *x, const T *b, CutList cut, GhostList gh)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int colour = 0; colour < 25; colour++) {
         int beg = cut.off[colour], end = cut.off[colour + 1];
-        for (int k = beg + threadIdx.x; k < end; k += blockDim.x) box_cut_pre<T>(x, b, cut, k);
+        for (int k = beg + warp; k < end; k += nw) box_cut_warp<T>(x, b, cut, k, lane);
         __syncthreads();
     }
 }
@@ -667,11 +801,11 @@ template <typename T> __device__ inline int taps(int k, bool aligned, int lo, in
 }
 
 // bilinear interpolation over the active coarse nodes (weights renormalised)
-// added to every active fine node
+// added to every active fine node; y = x + P eH on every slot (y may be x)
 template <typename T>
 __global__ void k_prolong(int Nf, int Pf, long long Ff, const uint8_t *tUf, const uint8_t *tVf, const uint8_t *tPf,
                           int Nc, int Pc, long long Fc, const uint8_t *tUc, const uint8_t *tVc, const uint8_t *tPc,
-                          const T *eH, T *x)
+                          const T *eH, const T *x, T *y)
 {
     int col = blockIdx.x * blockDim.x + threadIdx.x;
     int row = blockIdx.y;
@@ -680,8 +814,14 @@ __global__ void k_prolong(int Nf, int Pf, long long Ff, const uint8_t *tUf, cons
     long long sf = (long long)row * Pf + col;
     const uint8_t *tf[3] = {tUf, tVf, tPf};
     const uint8_t *tc[3] = {tUc, tVc, tPc};
+    if (row == 0 && col < NSCAL) y[3 * Ff + col] = col == 0 ? x[3 * Ff] + eH[3 * Fc] : x[3 * Ff + col];
+#pragma unroll
     for (int g = 0; g < 3; g++) {
-        if (!in_grid(g, Nf, i, j) || tf[g][sf] == T_INACTIVE) continue;
+        const long long k = g * Ff + sf;
+        if (!in_grid(g, Nf, i, j) || tf[g][sf] == T_INACTIVE) {
+            if (y != x) y[k] = x[k];
+            continue;
+        }
         int Ilo = g == G_V ? -1 : 0, Ihi = g == G_P ? Nc - 1 : Nc;
         int Jlo = g == G_U ? -1 : 0, Jhi = g == G_P ? Nc - 1 : Nc;
         int KI[2], KJ[2];
@@ -696,9 +836,15 @@ __global__ void k_prolong(int Nf, int Pf, long long Ff, const uint8_t *tUf, cons
                 s += w * eH[g * Fc + (long long)(KJ[a] + 1) * Pc + (KI[bb] + 1)];
                 ws += w;
             }
-        if (ws > (T)0) x[g * Ff + sf] += ws == (T)1 ? s : s / ws;
+        if (ws > (T)0) y[k] = x[k] + (ws == (T)1 ? s : s / ws);
+        else if (y != x) y[k] = x[k];
     }
-    if (row == 0 && col == 0) x[3 * Ff] += eH[3 * Fc];
+}
+
+template <typename T> __global__ void k_copy_t(const T *a, T *b, long long n)
+{
+    long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k < n) b[k] = a[k];
 }
 
 template <typename T> __global__ void k_zero(T *x, long long n)
@@ -882,16 +1028,76 @@ template <typename T> LevelArgs<T> level_args(const Ctx *c, int lev)
     A.tU = l.tU;
     A.tV = l.tV;
     A.tP = l.tP;
+    const double q = 1.0 / h, a = c->prm.alpha / (h * h), d = 1.0 + 4.0 * a;
+    A.K.a = (T)a;
+    A.K.d = (T)d;
+    A.K.q = (T)q;
+    A.K.qida = (T)(q / (d + a));
+    A.K.qid = (T)(q / d);
+    A.K.id = (T)(1.0 / d);
+    A.K.idet = (T)(1.0 / (d * d - a * a));
+    const double cx[3] = {0.0, q * q / d, 2.0 * q * q / (d + a)};
+    for (int nx = 0; nx < 3; nx++)
+        for (int ny = 0; ny < 3; ny++) A.K.ic1[nx * 3 + ny] = nx + ny == 0 ? (T)0 : (T)(1.0 / (cx[nx] + cx[ny]));
     return A;
 }
 
 static inline dim3 frame_grid(const Level &l) { return dim3((l.P + 255) / 256, l.N + 2); }
 
-// the tiled box sweep stages its results in the level's residual vector,
-// which is dead during relaxation (it is recomputed before restriction)
+// the other vector of the tiled sweep: the level's residual vector, which is
+// dead during relaxation (it is recomputed before restriction)
 template <typename T> T *tile_scratch(Ctx *c, int lev);
 template <> double *tile_scratch<double>(Ctx *c, int lev) { return c->lv[lev].r; }
 template <> float *tile_scratch<float>(Ctx *c, int lev) { return c->lv[lev].rf; }
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// the driver's tensor-map encoder, looked up once through the runtime
+static EncodeTiledFn encode_fn()
+{
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// 3-D tensor map over the three frames of a level (x: column, y: frame row,
+// z: frame), box = the tile window of k_box_tma
+static bool encode_frames(CUtensorMap *m, const void *base, CUtensorMapDataType dt, int esize, const Level &l,
+                          long long frame_stride_bytes, int LW)
+{
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)l.P, (cuuint64_t)(l.N + 2), 3};
+    cuuint64_t strides[2] = {(cuuint64_t)l.P * esize, (cuuint64_t)frame_stride_bytes};
+    cuuint32_t box[3] = {(cuuint32_t)LW, (cuuint32_t)TT_LH, 3};
+    cuuint32_t es[3] = {1, 1, 1};
+    return fn(m, dt, 3, const_cast<void *>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
+// does this level sweep its full boxes with k_box_tma (T's other vector must exist)
+template <typename T> static bool tiled(Ctx *c, int lev)
+{
+    const Level &l = c->lv[lev];
+    // default: FP32 levels from TILE_MIN_N; FP64 boxes are bound by the FP64
+    // units, where the halo boxes a tile recomputes cost more than the four
+    // extra passes over memory they save
+    int tmin = c->prm.tile_min != 0 ? c->prm.tile_min : sizeof(T) == 4 ? TILE_MIN_N : -1;
+    if (tmin < 0 || l.N < tmin || !tile_scratch<T>(c, lev) || !encode_fn()) return false;
+    return l.tV - l.tU == l.tP - l.tV;  // the type frames are equally spaced (one 3-D map)
+}
 
 void prepare_cuts(Ctx *c)
 {
@@ -906,9 +1112,15 @@ void tiles_init()
 {
     static bool done = false;
     if (done) return;
-    cudaFuncSetAttribute(k_box_tiled<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem<double>());
-    cudaFuncSetAttribute(k_box_tiled<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem<float>());
+    cudaFuncSetAttribute(k_box_tma<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tt_smem<double>());
+    cudaFuncSetAttribute(k_box_tma<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tt_smem<float>());
     done = true;
+}
+
+template <typename T> static void copy_vec(Ctx *c, const T *a, T *b, long long n)
+{
+    k_copy_t<T><<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(a, b, n);
+    c->launches++;
 }
 
 // blocks of the reduction kernels: enough to fill the GPU, at most 1024
@@ -932,34 +1144,56 @@ template <typename T> void residual(Ctx *c, int lev, const T *x, const T *b, T *
     c->launches += 2 + (l.h_nrows > 0);
 }
 
-template <typename T> void box_sweep(Ctx *c, int lev, T *x, const T *b)
+// full boxes from `in` into `out`: with out != in the level is tiled and out
+// becomes a complete copy of the swept vector; with out == in the five colour
+// passes run in place.  Then the cut boxes and lonely faces, in place on out.
+template <typename T> static void box_pass(Ctx *c, int lev, const T *in, T *out, const T *b)
 {
     const Level &l = c->lv[lev];
     cudaStream_t st = c->stream;
     LevelArgs<T> A = level_args<T>(c, lev);
-    int per_row = (l.N + 4) / 5;
-    dim3 g((per_row + 127) / 128, l.N);
-    if (l.N >= TILE_MIN_N) {
-        T *y = tile_scratch<T>(c, lev);
-        constexpr int TI = tile_ti<T>();
-        dim3 gt((l.N + TI - 1) / TI, (l.N + TI - 1) / TI);
-        tmr_begin(c, KT_BOX_FULL, lev);
-        k_box_tiled<T><<<gt, 256, tile_smem<T>(), st>>>(A, x, b, y);
-        tmr_end(c, KT_BOX_FULL, lev);
-        k_box_apply<T><<<red_blocks(l) * 4, 256, 0, st>>>(A, x, y);
-        c->launches += 2;
-    } else {
+    bool done = false;
+    if (out != in) {
+        constexpr int TW = TileGeom<T>::TW, LW = TileGeom<T>::LW;
+        const CUtensorMapDataType dt = sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+        CUtensorMap mx, mt;
+        if (encode_frames(&mx, in, dt, (int)sizeof(T), l, l.F * (long long)sizeof(T), LW) &&
+            encode_frames(&mt, l.tU, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, l, (long long)(l.tV - l.tU), LW)) {
+            dim3 gt((l.P + TW - 1) / TW, (l.N + 2 + TT_H - 1) / TT_H);
+            tmr_begin(c, KT_BOX_FULL, lev);
+            k_box_tma<T><<<gt, TT_THREADS, tt_smem<T>(), st>>>(mx, mt, A, in, b, out, c->err);
+            tmr_end(c, KT_BOX_FULL, lev);
+            c->launches++;
+            done = true;
+        } else {
+            copy_vec<T>(c, in, out, l.VL);
+        }
+    }
+    if (!done) {
+        int per_row = (l.N + 4) / 5;
+        dim3 g((per_row + 127) / 128, l.N);
         for (int colour = 0; colour < 5; colour++) {
             tmr_begin(c, KT_BOX_FULL, lev);
-            k_box_full<T><<<g, 128, 0, st>>>(A, x, b, colour);
+            k_box_full<T><<<g, 128, 0, st>>>(A, out, b, colour);
             tmr_end(c, KT_BOX_FULL, lev);
             c->launches++;
         }
     }
-    if (l.h_ncut > 0) {
-        int nt = l.h_ncut >= 25 * 128 ? 256 : 128;
+    T *x = out;
+    int most = 0;  // largest colour of cut boxes
+    for (int colour = 0; colour < 25; colour++) most = max(most, l.h_cutoff[colour + 1] - l.h_cutoff[colour]);
+    if (most > CUT_SPLIT) {
         tmr_begin(c, KT_BOX_CUT, lev);
-        k_box_cut<T><<<1, nt, 0, st>>>(A, x, b, l.cut, l.gh);
+        for (int colour = 0; colour < 25; colour++) {
+            int beg = l.h_cutoff[colour], end = l.h_cutoff[colour + 1];
+            if (end <= beg) continue;
+            k_box_cut_colour<T><<<(end - beg + 7) / 8, 256, 0, st>>>(x, b, l.cut, beg, end);
+            c->launches++;
+        }
+        tmr_end(c, KT_BOX_CUT, lev);
+    } else if (l.h_ncut > 0) {
+        tmr_begin(c, KT_BOX_CUT, lev);
+        k_box_cut<T><<<1, 1024, 0, st>>>(A, x, b, l.cut, l.gh);
         tmr_end(c, KT_BOX_CUT, lev);
         c->launches++;
     }
@@ -968,6 +1202,19 @@ template <typename T> void box_sweep(Ctx *c, int lev, T *x, const T *b)
         k_lonely_update<T><<<(l.h_nlonely + 127) / 128, 128, 0, st>>>(A, x, b, l.lonely, l.h_nlonely, upd);
         k_apply_list<T><<<(l.h_nlonely + 127) / 128, 128, 0, st>>>(x, l.lonely, upd, l.h_nlonely);
         c->launches += 2;
+    }
+}
+
+// one box sweep in place on x (a tiled level sweeps into its other vector and
+// copies back)
+template <typename T> void box_sweep(Ctx *c, int lev, T *x, const T *b)
+{
+    if (tiled<T>(c, lev)) {
+        T *t = tile_scratch<T>(c, lev);
+        box_pass<T>(c, lev, x, t, b);
+        copy_vec<T>(c, t, x, c->lv[lev].VL);
+    } else {
+        box_pass<T>(c, lev, x, x, b);
     }
 }
 
@@ -1000,9 +1247,18 @@ template <typename T> void ghost_sweep(Ctx *c, int lev, T *x, const T *b)
     c->launches += 2;
 }
 
-template <typename T> void smooth(Ctx *c, int lev, T *x, const T *b, int nu)
+// nu relaxations (Algorithm relax) of the iterate held in `in` (x or the
+// level's other vector); the result ends in x.  Tiled levels alternate
+// between the two vectors, so an even count from x, or an odd count from the
+// other vector, needs no copy.
+template <typename T> void smooth_from(Ctx *c, int lev, T *x, T *in, const T *b, int nu)
 {
     const Level &l = c->lv[lev];
+    const bool tl = tiled<T>(c, lev);
+    if (in != x && (nu <= 0 || !tl || (l.N <= SMALL_N && l.h_nlonely <= l.gh.cap))) {
+        copy_vec<T>(c, in, x, l.VL);
+        in = x;
+    }
     if (nu <= 0) return;
     if (l.N <= SMALL_N && l.h_nlonely <= l.gh.cap) {
         double h = c->prm.L / (double)l.N;
@@ -1011,18 +1267,34 @@ template <typename T> void smooth(Ctx *c, int lev, T *x, const T *b, int nu)
         c->launches++;
         return;
     }
+    T *t = tl ? tile_scratch<T>(c, lev) : x;
+    T *cur = in;
     for (int s = 0; s < nu; s++) {
-        box_sweep<T>(c, lev, x, b);
-        scalar_update<T>(c, lev, x, b);
+        T *out = tl ? (cur == x ? t : x) : cur;
+        box_pass<T>(c, lev, cur, out, b);
+        cur = out;
+        scalar_update<T>(c, lev, cur, b);
         if (l.h_nrows > 0 && l.h_nrows <= GHOST_BLOCK_ROWS && c->prm.lambda > 0) {
             tmr_begin(c, KT_GHOST, lev);
-            k_ghost_block<T><<<1, 1024, 0, c->stream>>>(l.gh, l.h_nrows, x, b, (T)c->prm.dtau, c->prm.lambda);
+            k_ghost_block<T><<<1, 1024, 0, c->stream>>>(l.gh, l.h_nrows, cur, b, (T)c->prm.dtau, c->prm.lambda);
             tmr_end(c, KT_GHOST, lev);
             c->launches++;
         } else {
-            for (int k = 0; k < c->prm.lambda; k++) ghost_sweep<T>(c, lev, x, b);
+            for (int k = 0; k < c->prm.lambda; k++) ghost_sweep<T>(c, lev, cur, b);
         }
     }
+    if (cur != x) copy_vec<T>(c, cur, x, l.VL);
+}
+
+template <typename T> void smooth(Ctx *c, int lev, T *x, const T *b, int nu) { smooth_from<T>(c, lev, x, x, b, nu); }
+
+// where the cycle should put x + P e before `nu` post-relaxations so that the
+// tiled sweeps end in x without a copy
+template <typename T> T *post_buffer(Ctx *c, int lev, T *x, int nu)
+{
+    const Level &l = c->lv[lev];
+    if (nu % 2 == 0 || !tiled<T>(c, lev) || (l.N <= SMALL_N && l.h_nlonely <= l.gh.cap)) return x;
+    return tile_scratch<T>(c, lev);
 }
 
 template <typename T> void restrict_level(Ctx *c, int lev, const T *r, T *bH)
@@ -1035,15 +1307,17 @@ template <typename T> void restrict_level(Ctx *c, int lev, const T *r, T *bH)
     c->launches++;
 }
 
-template <typename T> void prolong_level(Ctx *c, int lev, const T *eH, T *x)
+template <typename T> void prolong_to(Ctx *c, int lev, const T *eH, const T *x, T *y)
 {
     const Level &f = c->lv[lev], &C = c->lv[lev + 1];
     dim3 g((f.P + 255) / 256, f.N + 2);
     tmr_begin(c, KT_PROLONG, lev);
-    k_prolong<T><<<g, 256, 0, c->stream>>>(f.N, f.P, f.F, f.tU, f.tV, f.tP, C.N, C.P, C.F, C.tU, C.tV, C.tP, eH, x);
+    k_prolong<T><<<g, 256, 0, c->stream>>>(f.N, f.P, f.F, f.tU, f.tV, f.tP, C.N, C.P, C.F, C.tU, C.tV, C.tP, eH, x, y);
     tmr_end(c, KT_PROLONG, lev);
     c->launches++;
 }
+
+template <typename T> void prolong_level(Ctx *c, int lev, const T *eH, T *x) { prolong_to<T>(c, lev, eH, x, x); }
 
 template <typename T> void zero_vec(Ctx *c, T *x, long long n)
 {
@@ -1075,6 +1349,9 @@ void add_float(Ctx *c, double *x, const float *e, long long n)
     template void scalar_update<T>(Ctx *, int, T *, const T *);                 \
     template void ghost_sweep<T>(Ctx *, int, T *, const T *);                   \
     template void smooth<T>(Ctx *, int, T *, const T *, int);                   \
+    template void smooth_from<T>(Ctx *, int, T *, T *, const T *, int);         \
+    template T *post_buffer<T>(Ctx *, int, T *, int);                           \
+    template void prolong_to<T>(Ctx *, int, const T *, const T *, T *);         \
     template void restrict_level<T>(Ctx *, int, const T *, T *);                \
     template void prolong_level<T>(Ctx *, int, const T *, T *);                 \
     template void zero_vec<T>(Ctx *, T *, long long);                           \

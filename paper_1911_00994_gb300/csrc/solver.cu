@@ -21,6 +21,9 @@ template <typename T> void ghost_sweep(Ctx *c, int lev, T *x, const T *b);
 template <typename T> void smooth(Ctx *c, int lev, T *x, const T *b, int nu);
 template <typename T> void restrict_level(Ctx *c, int lev, const T *r, T *bH);
 template <typename T> void prolong_level(Ctx *c, int lev, const T *eH, T *x);
+template <typename T> void prolong_to(Ctx *c, int lev, const T *eH, const T *x, T *y);
+template <typename T> void smooth_from(Ctx *c, int lev, T *x, T *in, const T *b, int nu);
+template <typename T> T *post_buffer(Ctx *c, int lev, T *x, int nu);
 template <typename T> void zero_vec(Ctx *c, T *x, long long n);
 template <typename T> void zero_inactive(Ctx *c, int lev, T *x);
 template <typename T> void coarse_solve(Ctx *c, const T *b, T *x);
@@ -207,8 +210,9 @@ template <typename T> void cycle_rec(Ctx *c, int lev, T *x, const T *b)
     restrict_level<T>(c, lev, r, bH);
     zero_vec<T>(c, xH, c->lv[lev + 1].VL);
     for (int k = 0; k < c->prm.gamma; k++) cycle_rec<T>(c, lev + 1, xH, bH);
-    prolong_level<T>(c, lev, xH, x);
-    smooth<T>(c, lev, x, b, c->prm.nu2);
+    T *y = post_buffer<T>(c, lev, x, c->prm.nu2);
+    prolong_to<T>(c, lev, xH, x, y);
+    smooth_from<T>(c, lev, x, y, b, c->prm.nu2);
 }
 
 // one mg_solve iteration: the cycle and the finest FP64 residual (which = 0),

@@ -1,0 +1,90 @@
+"""The one-pass tiled sweep of the full boxes (Sect. 4.1.1, five colours in
+shared-memory tiles, the result written to the level's other vector) against
+the oracle's colour-by-colour sweep.  `tile_min` forces the tiled path on
+small levels; N = 96 and N = 200 leave ragged tiles at the right and top
+edges (frame pitch 128 and 224, 98 and 202 frame rows)."""
+import numpy as np
+import pytest
+
+from paper_1911_00994_gb300 import workloads as W
+from tests._cases import CASES, levels_for, make_oracle, manufactured
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / max(1e-300, np.abs(b).max())
+
+
+def pair(case, N, alpha, **kw):
+    from paper_1911_00994_gb300 import gpmg
+    shape, x0, L = CASES[case]
+    lev = levels_for(N)
+    o, phi, st = make_oracle(case, N, alpha=alpha, levels=lev)
+    assert st == 0, o.error()
+    s = gpmg.Solver(N, x0, x0, L, levels=lev, alpha=alpha, **kw)
+    assert s.geometry(phi, 0) == 0, s.error()
+    return o, s
+
+
+@pytest.mark.parametrize("case,N", [("flower5", 256), ("circle_off", 96), ("ellipse", 200), ("nobody", 128)])
+def test_tiled_sweep_pieces_match(case, N):
+    shape, x0, L = CASES[case]
+    o, s = pair(case, N, alpha=(L / N) / 2.0, tile_min=65)
+    for lev in range(o.levels):
+        Nl = N >> lev
+        if Nl < 65:
+            break
+        t = o.types(lev)
+        x = W.random_flat(Nl, t, 500 + lev)
+        b = W.random_flat(Nl, t, 600 + lev) * 10
+        bd = s.to_device(b, lev)
+        want = o.box_sweep(x, b, lev)
+        xg = s.to_device(x, lev)
+        s.box_sweep(xg, bd, lev)
+        assert rel(s.to_flat(xg, lev), want) < 1e-12, lev
+        for nu in (1, 2, 3):
+            want = o.smooth(x, b, nu, lev)
+            xg = s.to_device(x, lev)
+            s.smooth(xg, bd, nu, lev)
+            assert rel(s.to_flat(xg, lev), want) < 1e-11, (lev, nu)
+
+
+@pytest.mark.parametrize("case,N,ah2", [("flower5", 256, 2.0), ("circle_off", 200, None)])
+def test_tiled_cycle_history_matches(case, N, ah2):
+    shape, x0, L = CASES[case]
+    h = L / N
+    alpha = h / 2.0 if ah2 is None else ah2 * h * h
+    o, s = pair(case, N, alpha=alpha, tile_min=65)
+    ex = W.taylor_green()
+    b, xe, t, gh = manufactured(o, ex)
+    x = np.zeros_like(b)
+    xg, bd = s.to_device(x), s.to_device(b)
+    for k in range(4):
+        st, x = o.cycle(x, b)
+        s.cycle(xg, bd)
+        assert rel(s.to_flat(xg), x) < 1e-9, k
+
+
+@pytest.mark.parametrize("case,N", [("flower5", 256), ("ellipse", 200)])
+def test_tiled_mixed_solve_matches_oracle(case, N):
+    # FP32 tiles inside FP64 residual correction: the converged solution is
+    # the oracle's FP64 solution to the tolerance
+    shape, x0, L = CASES[case]
+    h = L / N
+    alpha = h / 2000.0 if case == "flower5" else h / 200.0
+    o, s = pair(case, N, alpha=alpha, tile_min=65, precision=1)
+    ex = W.taylor_green()
+    b, xe, t, gh = manufactured(o, ex)
+    st_o, x_o, h_o = o.solve(np.zeros_like(b), b, 1e-10, 200)
+    assert st_o == 0
+    xg = s.new_vec()
+    st, rep, h_g = s.solve(xg, s.to_device(b), 1e-10)
+    assert st == 0, s.error()
+    assert rel(s.to_flat(xg), x_o) <= 1e-8
+    # the same solve with the five colour passes takes as many cycles
+    o2, s2 = pair(case, N, alpha=alpha, tile_min=-1, precision=1)
+    xg2 = s2.new_vec()
+    st2, rep2, h_g2 = s2.solve(xg2, s2.to_device(b), 1e-10)
+    assert st2 == 0
+    assert abs(len(h_g) - len(h_g2)) <= 1
