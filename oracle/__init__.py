@@ -78,6 +78,15 @@ def lib():
             L.or_prolong.argtypes = [vp, i, P(d), P(d)]
             L.or_cycle.argtypes = [vp, i, P(d), P(d)]
             L.or_solve.argtypes = [vp, P(d), P(d), d, i, P(d), P(i)]
+            L.or_residual_t.restype = d
+            L.or_residual_t.argtypes = [vp, i, P(d), P(d), P(d)]
+            for f in (L.or_box_sweep_t, L.or_scalar_update_t, L.or_ghost_sweep_t):
+                f.argtypes = [vp, i, P(d), P(d)]
+            L.or_smooth_t.argtypes = [vp, i, P(d), P(d), i]
+            L.or_restrict_t.argtypes = [vp, i, P(d), P(d)]
+            L.or_prolong_t.argtypes = [vp, i, P(d), P(d)]
+            L.or_cycle_t.argtypes = [vp, i, P(d), P(d)]
+            L.or_solve_t.argtypes = [vp, P(d), P(d), d, i, P(d), P(i)]
             L.or_convective.argtypes = [vp, P(d), P(d)]
             L.or_solve_krylov.argtypes = [vp, P(d), P(d), d, i, P(d), P(i)]
             L.or_cn_rhs.argtypes = [vp, P(d), P(d), vp, d, vp, P(d), P(d), P(d)]
@@ -257,6 +266,56 @@ class Oracle:
         b = np.ascontiguousarray(b, dtype=np.float64)
         st = self.L.or_cycle(self.c, lev, _p(x2), _p(b))
         return st, x2
+
+    # ---- adjoint (transposed system M^T lam = c, transposed cycle)
+
+    def residual_t(self, lam, cc, lev=0):
+        """r = c - M^T lam and ||r||_inf."""
+        r = np.zeros(self.n(lev))
+        lam = np.ascontiguousarray(lam, dtype=np.float64)
+        cc = np.ascontiguousarray(cc, dtype=np.float64)
+        nrm = self.L.or_residual_t(self.c, lev, _p(lam), _p(cc), _p(r))
+        return r, nrm
+
+    def box_sweep_t(self, lam, cc, lev=0):
+        return self._inplace(self.L.or_box_sweep_t, lev, lam, cc)
+
+    def scalar_update_t(self, lam, cc, lev=0):
+        return self._inplace(self.L.or_scalar_update_t, lev, lam, cc)
+
+    def ghost_sweep_t(self, lam, cc, lev=0):
+        return self._inplace(self.L.or_ghost_sweep_t, lev, lam, cc)
+
+    def smooth_t(self, lam, cc, nu=1, lev=0):
+        return self._inplace(self.L.or_smooth_t, lev, lam, cc, nu)
+
+    def restrict_t(self, yH, lam, lev=0):
+        """lam + R^T yH (R the restriction from level lev to lev + 1)."""
+        out = np.array(lam, dtype=np.float64)
+        yH = np.ascontiguousarray(yH, dtype=np.float64)
+        self.L.or_restrict_t(self.c, lev, _p(yH), _p(out))
+        return out
+
+    def prolong_t(self, r, lev=0):
+        """P^T r (P the interpolation from level lev + 1 to lev)."""
+        out = np.zeros(self.n(lev + 1))
+        r = np.ascontiguousarray(r, dtype=np.float64)
+        self.L.or_prolong_t(self.c, lev, _p(r), _p(out))
+        return out
+
+    def cycle_t(self, lam, cc, lev=0):
+        lam2 = np.array(lam, dtype=np.float64)
+        cc = np.ascontiguousarray(cc, dtype=np.float64)
+        st = self.L.or_cycle_t(self.c, lev, _p(lam2), _p(cc))
+        return st, lam2
+
+    def solve_t(self, lam, cc, tol, max_cycles=50):
+        lam2 = np.array(lam, dtype=np.float64)
+        cc = np.ascontiguousarray(cc, dtype=np.float64)
+        hist = np.zeros(max_cycles + 1)
+        nc = ctypes.c_int(0)
+        st = self.L.or_solve_t(self.c, _p(lam2), _p(cc), tol, max_cycles, _p(hist), ctypes.byref(nc))
+        return st, lam2, hist[:nc.value + 1]
 
     def solve(self, x, b, tol, max_cycles=50):
         x2 = np.array(x, dtype=np.float64)

@@ -108,6 +108,12 @@ typedef struct {
     int *piv;
     /* cycle work vectors */
     double *x, *b, *r;
+    /* adjoint: the columns of M (compressed by column) and, on the coarsest
+     * level, the LU factors of M^T */
+    int *cptr, *crow;
+    double *cval;
+    double *lut;
+    int *pivt;
 } level_t;
 
 typedef struct {
@@ -121,6 +127,8 @@ typedef struct {
     double *phi;       /* half lattice (2N+1)^2, paper sign */
     level_t lv[OR_MAXLEV];
     int geom_ok;
+    int adj_ok;        /* columns and transposed factors built for adj_alpha */
+    double adj_alpha;
     char err[256];
 } ctx_t;
 
@@ -373,6 +381,7 @@ static void free_level(level_t *l)
 {
     free(l->tU); free(l->tV); free(l->tP); free(l->gid); free(l->prim); free(l->gh);
     free(l->lu); free(l->piv); free(l->x); free(l->b); free(l->r);
+    free(l->cptr); free(l->crow); free(l->cval); free(l->lut); free(l->pivt);
     memset(l, 0, sizeof *l);
 }
 
@@ -727,6 +736,7 @@ int or_geometry(void *vc, const double *phi)
     ctx_t *c = (ctx_t *)vc;
     c->err[0] = 0;
     c->geom_ok = 0;
+    c->adj_ok = 0;
     size_t M = 2 * (size_t)c->N + 1;
     memcpy(c->phi, phi, M * M * sizeof(double));
     for (int k = 0; k < c->L; k++) {
@@ -1546,3 +1556,385 @@ int or_solve_krylov(void *vc, double *x, const double *b, double tol, int maxit,
     return st;
 }
 
+
+/* ------------------------------------------------------------- adjoint
+ *
+ * The adjoint of one linear solve is the transposed system M^T lam = c.  Its
+ * multigrid cycle is the transpose of the cycle above.  One relaxation stage
+ * of the cycle changes x by Q (b - M x) for a fixed matrix Q (a box solve, the
+ * lonely-face Jacobi step, the (xi, mean) update, a ghost Jacobi sweep, the
+ * coarse-grid correction P B_H R), so a cycle from x = 0 is a linear map B
+ * of b.  Writing I - B M as the product of the stages' (I - Q M) and
+ * transposing gives B^T = the cycle for M^T whose stages run in reverse
+ * order, each with Q^T: boxes with the transposed box matrix, colours in
+ * reverse order, post-relaxations before pre-relaxations, P^T as restriction
+ * and R^T as interpolation, and the coarsest solve with M^T.  The tests check
+ * <B b, c> = <b, C c> for this cycle C.  Inactive rows of M (x = b, Alg. LS)
+ * are referenced by ghost stencils, so the adjoint unknown at an inactive
+ * node is c minus those ghost contributions; no stage of the cycle touches
+ * it, and it appears in no other equation of M^T, so the solve sets it
+ * exactly after each cycle. */
+
+/* columns of M on level lev (from the assembled rows and the mean row) */
+static void build_columns(ctx_t *c, int lev)
+{
+    level_t *l = &c->lv[lev];
+    int n = l->n, cap = 12 * n + l->nP + 16;
+    int *ri = (int *)malloc(sizeof(int) * cap), *ci = (int *)malloc(sizeof(int) * cap);
+    double *v = (double *)malloc(sizeof(double) * cap);
+    int nnz = or_assemble(c, lev, ri, ci, v, cap);
+    free(l->cptr); free(l->crow); free(l->cval);
+    l->cptr = (int *)calloc(n + 1, sizeof(int));
+    l->crow = (int *)malloc(sizeof(int) * (nnz > 0 ? nnz : 1));
+    l->cval = (double *)malloc(sizeof(double) * (nnz > 0 ? nnz : 1));
+    for (int k = 0; k < nnz; k++) l->cptr[ci[k] + 1]++;
+    for (int k = 0; k < n; k++) l->cptr[k + 1] += l->cptr[k];
+    int *fill = (int *)malloc(sizeof(int) * n);
+    memcpy(fill, l->cptr, sizeof(int) * n);
+    for (int k = 0; k < nnz; k++) {
+        int at = fill[ci[k]]++;
+        l->crow[at] = ri[k];
+        l->cval[at] = v[k];
+    }
+    free(fill); free(ri); free(ci); free(v);
+}
+
+static int adjoint_prepare(ctx_t *c)
+{
+    if (!c->geom_ok) return OR_INVALID;
+    if (c->adj_ok && c->adj_alpha == c->alpha) return OR_OK;
+    for (int k = 0; k < c->L; k++) build_columns(c, k);
+    level_t *l = &c->lv[c->L - 1];
+    int n = l->n;
+    double *A = (double *)malloc(sizeof(double) * (size_t)n * n);
+    dense_matrix(c, c->L - 1, A);
+    free(l->lut); free(l->pivt);
+    l->lut = (double *)malloc(sizeof(double) * (size_t)n * n);
+    l->pivt = (int *)malloc(sizeof(int) * n);
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++) l->lut[(size_t)i * n + j] = A[(size_t)j * n + i];
+    free(A);
+    if (!lu_factor(n, l->lut, l->pivt)) { seterr(c, "transposed coarsest matrix is singular"); return OR_SINGULAR; }
+    c->adj_alpha = c->alpha;
+    c->adj_ok = 1;
+    return OR_OK;
+}
+
+/* (c - M^T lam) at unknown k */
+static double col_residual(const level_t *l, int k, const double *lam, const double *cc)
+{
+    double s = cc[k];
+    for (int e = l->cptr[k]; e < l->cptr[k + 1]; e++) s -= l->cval[e] * lam[l->crow[e]];
+    return s;
+}
+
+/* r = c - M^T lam on level lev; returns ||r||_inf */
+double or_residual_t(void *vc, int lev, const double *lam, const double *cc, double *r)
+{
+    ctx_t *c = (ctx_t *)vc;
+    if (adjoint_prepare(c) != OR_OK) return NAN;
+    level_t *l = &c->lv[lev];
+    double mx = 0.0;
+    for (int k = 0; k < l->n; k++) {
+        double v = col_residual(l, k, lam, cc);
+        r[k] = v;
+        if (fabs(v) > mx || v != v) mx = v != v ? NAN : fabs(v);
+    }
+    return mx;
+}
+
+/* the box of cell (i, j) relaxed on M^T: same unknowns as box_relax, the
+ * transposed box matrix, residuals of the transposed rows */
+static void box_relax_t(ctx_t *c, int lev, double *lam, const double *cc, int i, int j)
+{
+    level_t *l = &c->lv[lev];
+    int gg[5], ii[5], jj[5], unk[5], nu = 0;
+    const int fg[4] = {G_U, G_U, G_V, G_V};
+    const int fi[4] = {i, i + 1, i, i};
+    const int fj[4] = {j, j, j, j + 1};
+    for (int f = 0; f < 4; f++) {
+        int t = ttype(l, fg[f], fi[f], fj[f]);
+        if (t == T_INTERNAL || t == T_GHOST) {
+            gg[nu] = fg[f]; ii[nu] = fi[f]; jj[nu] = fj[f];
+            unk[nu] = iG(l, fg[f], fi[f], fj[f]);
+            nu++;
+        }
+    }
+    gg[nu] = G_P; ii[nu] = i; jj[nu] = j; unk[nu] = iP(l, i, j); nu++;
+    double A[25], At[25], rhs[5];
+    int piv[5];
+    for (int r = 0; r < nu; r++) {
+        row_t R;
+        get_row(c, lev, gg[r], ii[r], jj[r], &R);
+        for (int q = 0; q < nu; q++) {
+            double sum = 0.0;
+            for (int k = 0; k < R.n; k++)
+                if (R.col[k] == unk[q]) sum += R.a[k];
+            A[r * nu + q] = sum;
+        }
+    }
+    for (int r = 0; r < nu; r++) {
+        rhs[r] = col_residual(l, unk[r], lam, cc);
+        for (int q = 0; q < nu; q++) At[r * nu + q] = A[q * nu + r];
+    }
+    if (!lu_factor(nu, At, piv)) return;
+    lu_solve(nu, At, piv, rhs);
+    for (int r = 0; r < nu; r++) lam[unk[r]] += rhs[r];
+}
+
+/* the transposed box sweep: the lonely faces, then the cut cells in colours
+ * 24..0, then the other cells in colours 4..0 (colour-by-colour ordering) */
+void or_box_sweep_t(void *vc, int lev, double *lam, const double *cc)
+{
+    ctx_t *c = (ctx_t *)vc;
+    if (adjoint_prepare(c) != OR_OK) return;
+    level_t *l = &c->lv[lev];
+    int N = l->N;
+    /* lonely internal faces: point Jacobi with the diagonal d */
+    int cnt = 0;
+    int *idx = (int *)malloc(sizeof(int) * (l->nU + l->nV));
+    double *upd = (double *)malloc(sizeof(double) * (l->nU + l->nV));
+    row_t R;
+    for (int j = 0; j < N; j++)
+        for (int i = 1; i < N; i++)
+            if (ttype(l, G_U, i, j) == T_INTERNAL && ttype(l, G_P, i - 1, j) != T_INTERNAL &&
+                ttype(l, G_P, i, j) != T_INTERNAL) {
+                get_row(c, lev, G_U, i, j, &R);
+                idx[cnt] = iU(l, i, j);
+                upd[cnt++] = col_residual(l, iU(l, i, j), lam, cc) / R.a[0];
+            }
+    for (int j = 1; j < N; j++)
+        for (int i = 0; i < N; i++)
+            if (ttype(l, G_V, i, j) == T_INTERNAL && ttype(l, G_P, i, j - 1) != T_INTERNAL &&
+                ttype(l, G_P, i, j) != T_INTERNAL) {
+                get_row(c, lev, G_V, i, j, &R);
+                idx[cnt] = iV(l, i, j);
+                upd[cnt++] = col_residual(l, iV(l, i, j), lam, cc) / R.a[0];
+            }
+    for (int k = 0; k < cnt; k++) lam[idx[k]] += upd[k];
+    free(idx);
+    free(upd);
+    for (int col = 24; col >= 0; col--)
+        for (int j = 0; j < N; j++)
+            for (int i = 0; i < N; i++)
+                if ((j % 5) * 5 + (i % 5) == col && ttype(l, G_P, i, j) == T_INTERNAL && cut_cell(l, i, j))
+                    box_relax_t(c, lev, lam, cc, i, j);
+    for (int col = 4; col >= 0; col--)
+        for (int j = 0; j < N; j++)
+            for (int i = 0; i < N; i++)
+                if ((i + 3 * j) % 5 == col && ttype(l, G_P, i, j) == T_INTERNAL && !cut_cell(l, i, j))
+                    box_relax_t(c, lev, lam, cc, i, j);
+}
+
+/* transpose of the (xi, mean) update: the update adds -1/n_int times the
+ * mean of the continuity residuals to xi and 1/(h^2 n_int) times the mean-row
+ * residual to every internal and ghost p, so its transpose adds -1/n_int times
+ * the xi residual of M^T to the unknown of every internal continuity row and
+ * 1/(h^2 n_int) times the sum of the p residuals of M^T to the mean-row
+ * unknown (both residuals taken before either change) */
+void or_scalar_update_t(void *vc, int lev, double *lam, const double *cc)
+{
+    ctx_t *c = (ctx_t *)vc;
+    if (adjoint_prepare(c) != OR_OK) return;
+    level_t *l = &c->lv[lev];
+    int N = l->N;
+    double h = l->h;
+    double rxi = col_residual(l, iXI(l), lam, cc);
+    double sp = 0.0;
+    for (int j = 0; j < N; j++)
+        for (int i = 0; i < N; i++) {
+            int t = ttype(l, G_P, i, j);
+            if (t == T_INTERNAL || t == T_GHOST) sp += col_residual(l, iP(l, i, j), lam, cc);
+        }
+    double n = (double)l->n_int;
+    for (int j = 0; j < N; j++)
+        for (int i = 0; i < N; i++)
+            if (ttype(l, G_P, i, j) == T_INTERNAL) lam[iP(l, i, j)] += -rxi / n;
+    lam[iXI(l)] += sp / (h * h * n);
+}
+
+/* transpose of one ghost Jacobi sweep: the same diagonal step on the rows of
+ * M^T at every ghost, wall and box-ghost node */
+void or_ghost_sweep_t(void *vc, int lev, double *lam, const double *cc)
+{
+    ctx_t *c = (ctx_t *)vc;
+    if (adjoint_prepare(c) != OR_OK) return;
+    level_t *l = &c->lv[lev];
+    int N = l->N;
+    int *idx = (int *)malloc(sizeof(int) * l->n);
+    double *upd = (double *)malloc(sizeof(double) * l->n);
+    int cnt = 0;
+    row_t R;
+    for (int g = 0; g < 3; g++) {
+        int ilo = g == G_V ? -1 : 0, ihi = g == G_P ? N - 1 : N;
+        int jlo = g == G_U ? -1 : 0, jhi = g == G_P ? N - 1 : N;
+        for (int j = jlo; j <= jhi; j++)
+            for (int i = ilo; i <= ihi; i++) {
+                if (!ghost_class(ttype(l, g, i, j))) continue;
+                int k = iG(l, g, i, j);
+                get_row(c, lev, g, i, j, &R);
+                double res = col_residual(l, k, lam, cc);
+                idx[cnt] = k;
+                upd[cnt++] = c->ghost_mode == 1 ? c->dtau * res / R.a[0] : c->dtau * res;
+            }
+    }
+    for (int k = 0; k < cnt; k++) lam[idx[k]] += upd[k];
+    free(idx);
+    free(upd);
+}
+
+/* transposed relaxation: nu x {lambda transposed ghost sweeps; transposed
+ * (xi, mean) update; transposed box sweep} */
+void or_smooth_t(void *vc, int lev, double *lam, const double *cc, int nu)
+{
+    ctx_t *c = (ctx_t *)vc;
+    for (int s = 0; s < nu; s++) {
+        for (int k = 0; k < c->lam; k++) or_ghost_sweep_t(c, lev, lam, cc);
+        or_scalar_update_t(c, lev, lam, cc);
+        or_box_sweep_t(c, lev, lam, cc);
+    }
+}
+
+/* R^T: lam (level lev) += R^T yH (yH on level lev+1), R the restriction of
+ * or_restrict */
+void or_restrict_t(void *vc, int lev, const double *yH, double *lam)
+{
+    ctx_t *c = (ctx_t *)vc;
+    level_t *f = &c->lv[lev], *C = &c->lv[lev + 1];
+    int Nc = C->N;
+    for (int g = 0; g < 3; g++) {
+        int ilo = g == G_V ? -1 : 0, ihi = g == G_P ? Nc - 1 : Nc;
+        int jlo = g == G_U ? -1 : 0, jhi = g == G_P ? Nc - 1 : Nc;
+        for (int J = jlo; J <= jhi; J++)
+            for (int I = ilo; I <= ihi; I++) {
+                int tc = ttype(C, g, I, J);
+                if (tc == T_INACTIVE) continue;
+                double y = yH[iG(C, g, I, J)];
+                int fi[6], fj[6], ns = 0;
+                double wt[6];
+                if (g == G_U) {
+                    for (int dj = 0; dj <= 1; dj++)
+                        for (int di = -1; di <= 1; di++) {
+                            fi[ns] = 2 * I + di; fj[ns] = 2 * J + dj; wt[ns] = (di == 0 ? 2.0 : 1.0) / 8.0; ns++;
+                        }
+                } else if (g == G_V) {
+                    for (int dj = -1; dj <= 1; dj++)
+                        for (int di = 0; di <= 1; di++) {
+                            fi[ns] = 2 * I + di; fj[ns] = 2 * J + dj; wt[ns] = (dj == 0 ? 2.0 : 1.0) / 8.0; ns++;
+                        }
+                } else {
+                    for (int dj = 0; dj <= 1; dj++)
+                        for (int di = 0; di <= 1; di++) {
+                            fi[ns] = 2 * I + di; fj[ns] = 2 * J + dj; wt[ns] = 0.25; ns++;
+                        }
+                }
+                int all = 1, cnt = 0;
+                for (int k = 0; k < ns; k++) {
+                    if (same_class(tc, ttype(f, g, fi[k], fj[k]))) cnt++;
+                    else all = 0;
+                }
+                for (int k = 0; k < ns; k++) {
+                    if (!same_class(tc, ttype(f, g, fi[k], fj[k]))) continue;
+                    lam[iG(f, g, fi[k], fj[k])] += all ? wt[k] * y : y / (double)cnt;
+                }
+            }
+    }
+    lam[iXI(f)] += yH[iXI(C)];
+}
+
+/* P^T: cH (level lev+1) = P^T r (r on level lev), P the interpolation of
+ * or_prolong */
+void or_prolong_t(void *vc, int lev, const double *r, double *cH)
+{
+    ctx_t *c = (ctx_t *)vc;
+    level_t *f = &c->lv[lev], *C = &c->lv[lev + 1];
+    int N = f->N, Nc = C->N;
+    memset(cH, 0, sizeof(double) * C->n);
+    for (int g = 0; g < 3; g++) {
+        int ilo = g == G_V ? -1 : 0, ihi = g == G_P ? N - 1 : N;
+        int jlo = g == G_U ? -1 : 0, jhi = g == G_P ? N - 1 : N;
+        int Ilo = g == G_V ? -1 : 0, Ihi = g == G_P ? Nc - 1 : Nc;
+        int Jlo = g == G_U ? -1 : 0, Jhi = g == G_P ? Nc - 1 : Nc;
+        for (int j = jlo; j <= jhi; j++)
+            for (int i = ilo; i <= ihi; i++) {
+                if (ttype(f, g, i, j) == T_INACTIVE) continue;
+                int KI[2], KJ[2];
+                double wi[2], wj[2];
+                int ni = taps(i, g == G_U, Ilo, Ihi, KI, wi);
+                int nj = taps(j, g == G_V, Jlo, Jhi, KJ, wj);
+                double ws = 0.0;
+                for (int a = 0; a < nj; a++)
+                    for (int bb = 0; bb < ni; bb++)
+                        if (ttype(C, g, KI[bb], KJ[a]) != T_INACTIVE) ws += wj[a] * wi[bb];
+                if (!(ws > 0.0)) continue;
+                double y = r[iG(f, g, i, j)];
+                for (int a = 0; a < nj; a++)
+                    for (int bb = 0; bb < ni; bb++)
+                        if (ttype(C, g, KI[bb], KJ[a]) != T_INACTIVE)
+                            cH[iG(C, g, KI[bb], KJ[a])] += wj[a] * wi[bb] / ws * y;
+            }
+    }
+    cH[iXI(C)] += r[iXI(f)];
+}
+
+static void cycle_t_rec(ctx_t *c, int lev, double *lam, const double *cc)
+{
+    level_t *l = &c->lv[lev];
+    if (lev == c->L - 1) {
+        memcpy(lam, cc, sizeof(double) * l->n);
+        lu_solve(l->n, l->lut, l->pivt, lam);
+        return;
+    }
+    level_t *C = &c->lv[lev + 1];
+    or_smooth_t(c, lev, lam, cc, c->nu2);
+    or_residual_t(c, lev, lam, cc, l->r);
+    or_prolong_t(c, lev, l->r, C->b);
+    memset(C->x, 0, sizeof(double) * C->n);
+    for (int k = 0; k < c->gamma; k++) cycle_t_rec(c, lev + 1, C->x, C->b);
+    or_restrict_t(c, lev, C->x, lam);
+    or_smooth_t(c, lev, lam, cc, c->nu1);
+}
+
+/* one transposed cycle on level lev (the transpose of or_cycle from zero) */
+int or_cycle_t(void *vc, int lev, double *lam, const double *cc)
+{
+    ctx_t *c = (ctx_t *)vc;
+    int st = adjoint_prepare(c);
+    if (st != OR_OK) return st;
+    cycle_t_rec(c, lev, lam, cc);
+    return OR_OK;
+}
+
+/* the rows of M^T at inactive nodes: lam_k = c_k - (ghost-row terms) */
+static void fix_inactive_t(ctx_t *c, double *lam, const double *cc)
+{
+    level_t *l = &c->lv[0];
+    for (int k = 0; k < l->n - 1; k++) {
+        int t = k < l->nU ? l->tU[k] : k < l->nU + l->nV ? l->tV[k - l->nU] : l->tP[k - l->nU - l->nV];
+        if (t == T_INACTIVE) lam[k] += col_residual(l, k, lam, cc);
+    }
+}
+
+/* transposed cycles from lam until ||c - M^T lam||_inf <= tol */
+int or_solve_t(void *vc, double *lam, const double *cc, double tol, int max_cycles, double *hist, int *ncyc)
+{
+    ctx_t *c = (ctx_t *)vc;
+    int st = adjoint_prepare(c);
+    if (st != OR_OK) return st;
+    level_t *l = &c->lv[0];
+    fix_inactive_t(c, lam, cc);
+    double r0 = or_residual_t(c, 0, lam, cc, l->r);
+    hist[0] = r0;
+    *ncyc = 0;
+    if (r0 <= tol) return OR_OK;
+    for (int k = 1; k <= max_cycles; k++) {
+        cycle_t_rec(c, 0, lam, cc);
+        fix_inactive_t(c, lam, cc);
+        double rn = or_residual_t(c, 0, lam, cc, l->r);
+        hist[k] = rn;
+        *ncyc = k;
+        if (!(rn == rn) || rn > 1e6 * r0) return OR_DIVERGED;
+        if (rn <= tol) return OR_OK;
+    }
+    return OR_NOT_CONVERGED;
+}
