@@ -83,6 +83,8 @@ typedef struct gp_params {
                            boxes in one pass of shared-memory tiles (same iterate as the five
                            colour passes); 0: 512 for the FP32 cycles of the mixed mode and
                            never for FP64; negative: never */
+    int adjoint;        /* nonzero: carve the arrays of the adjoint solve (mg_solve_t and the
+                           gp_*_t calls; one FP64 vector per level and the ghost column lists) */
 } gp_params;
 
 typedef struct gp_report {
@@ -266,6 +268,45 @@ gp_status cn_step(gp_ctx *ctx, double *x, double *N1, double *N2, int step, cons
 gp_status gp_convective(gp_ctx *ctx, const double *x, double *out);
 gp_status gp_cn_rhs(gp_ctx *ctx, const double *xn, const double *Nh, const double *f, double dt, const double *bc,
                     const gp_body *body, const gp_walls *walls, double *b);
+
+/* ---- Adjoint of the linear solve: M^T lam = c.
+ *
+ * For a scalar function J of the solution x of M x = b, dJ/db = lam with
+ * M^T lam = dJ/dx; through the right-hand side of cn_step this gives the
+ * gradient with respect to the forcing (dt times the momentum entries of
+ * lam).  The solver is the transpose of the multigrid cycle: a cycle from
+ * zero is a linear map B of b whose stages (box solves, ghost Jacobi steps,
+ * the (xi, mean) update, the coarse-grid correction P B_H R) each add
+ * Q (b - M x); B^T is the cycle for M^T with the stages in reverse order and
+ * each Q transposed (transposed box matrices, cut colours 24..0 then full
+ * colours 4..0, ghost sweeps before the (xi, mean) step, post- before
+ * pre-relaxations, P^T as restriction, R^T as interpolation, the coarsest
+ * solve with the transposed inverse).  Rows of M^T at inactive nodes (only
+ * ghost rows reference those nodes) are solved exactly after each cycle.
+ * FP64 only.  All vectors are device pointers in the layout of the level
+ * (gp_vector_length); lam and c use the row slots of M (the xi slot holds
+ * the mean row's unknown).  The context must be created with
+ * gp_params.adjoint = 1 (else GP_INVALID); the first call after a geometry
+ * copies the ghost rows to the host once to list the columns they reference.
+ *
+ * gp_residual_t: r = c - M^T lam on level `level`, ||r||_inf into *norm_host
+ *                when not NULL (synchronises).
+ * gp_box_sweep_t, gp_scalar_update_t, gp_ghost_sweep_t, gp_smooth_t: the
+ *                transposed relaxation stages, in place on lam.
+ * gp_restrict_t: lam_fine += R^T y_coarse (R the restriction level -> level+1).
+ * gp_prolong_t:  c_coarse = P^T r_fine (P the interpolation level+1 -> level).
+ * gp_cycle_t:    one transposed cycle on the finest level, in place on lam.
+ * mg_solve_t:    transposed cycles from lam until ||c - M^T lam||_inf <= tol
+ *                (at most max_cycles); the report as for mg_solve. */
+gp_status gp_residual_t(gp_ctx *ctx, int level, const double *lam, const double *c, double *r, double *norm_host);
+gp_status gp_box_sweep_t(gp_ctx *ctx, int level, double *lam, const double *c);
+gp_status gp_scalar_update_t(gp_ctx *ctx, int level, double *lam, const double *c);
+gp_status gp_ghost_sweep_t(gp_ctx *ctx, int level, double *lam, const double *c);
+gp_status gp_smooth_t(gp_ctx *ctx, int level, double *lam, const double *c, int nu);
+gp_status gp_restrict_t(gp_ctx *ctx, int level, const double *y_coarse, double *lam_fine);
+gp_status gp_prolong_t(gp_ctx *ctx, int level, const double *r_fine, double *c_coarse);
+gp_status gp_cycle_t(gp_ctx *ctx, double *lam, const double *c);
+gp_status mg_solve_t(gp_ctx *ctx, double *lam, const double *c, double tol, gp_report *rep);
 
 /* Instrumentation (no counterpart in the paper; used by the benchmark).
  * gp_launch_count: kernels this context has launched so far.

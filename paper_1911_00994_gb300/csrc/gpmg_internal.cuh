@@ -98,6 +98,15 @@ struct Level {
     int h_ncut;
     int h_cutoff[26];
     int h_nlonely;
+    // adjoint (carved when gp_params.adjoint is set): the columns of M
+    // referenced by ghost-class rows, sorted, each with its (row node,
+    // weight) entries; the ghost-row part of M^T lam at those columns (0 at
+    // every other slot); the column-list index of each cut-box unknown
+    int *tl_node, *tl_ptr, *tl_src;
+    double *tl_w;
+    int tl_cap, h_tl_n;
+    double *gtd;
+    int *cut_tl;
 };
 
 struct Ctx {
@@ -149,6 +158,7 @@ struct Ctx {
     int geom_ok;
     int coarse_ok;
     double alpha_factored;
+    int adj_ok;            // adjoint column lists built for this geometry
     char msg[256];
 };
 
@@ -167,6 +177,41 @@ __device__ inline bool in_grid(int g, int N, int i, int j)
     if (g == G_U) return i >= 0 && i <= N && j >= -1 && j <= N;
     if (g == G_V) return i >= -1 && i <= N && j >= 0 && j <= N;
     return i >= 0 && i < N && j >= 0 && j < N;
+}
+
+// ------------------------------------------ grid transfers (Sects. 4.2, 4.3)
+__device__ inline bool same_class(uint8_t tc, uint8_t tf)
+{
+    if (tc == T_INTERNAL) return tf == T_INTERNAL;
+    return tf == T_GHOST || tf == T_WALL || tf == T_BOXGHOST;
+}
+
+__device__ inline uint8_t tget(const uint8_t *t, int g, int N, int P, int i, int j)
+{
+    if (!in_grid(g, N, i, j)) return T_INACTIVE;
+    return t[(long long)(j + 1) * P + (i + 1)];
+}
+
+// 1-D interpolation taps (see the oracle's description of the same rule)
+template <typename T> __device__ inline int taps(int k, bool aligned, int lo, int hi, int *K, T *w)
+{
+    bool even = (k % 2 == 0);
+    if (aligned) {
+        if (even) { K[0] = k / 2; w[0] = (T)1; return 1; }
+        K[0] = (k - 1) / 2; w[0] = (T)0.5;
+        K[1] = K[0] + 1; w[1] = (T)0.5;
+        return 2;
+    }
+    int Kc = even ? k / 2 : (k - 1) / 2;
+    int Ko = even ? Kc - 1 : Kc + 1;
+    if (Ko < lo || Ko > hi) {
+        K[0] = Kc; w[0] = (T)1.25;
+        K[1] = 2 * Kc - Ko; w[1] = (T)-0.25;
+        return 2;
+    }
+    K[0] = Kc; w[0] = (T)0.75;
+    K[1] = Ko; w[1] = (T)0.25;
+    return 2;
 }
 
 }  // namespace gpmg

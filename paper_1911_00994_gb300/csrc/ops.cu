@@ -47,12 +47,30 @@ __device__ inline double nanmax(double a, double b) { return (a != a || b != b) 
 
 // ---------------------------------------------------------------- residual
 
+// |v| as bits (sign cleared): for non-negative floats the integer order is
+// the numeric order and a NaN sorts above infinity, so an integer max is an
+// exact max norm that keeps NaN, without floating-point (or FP64) work
+template <typename T> struct AbsBits;
+template <> struct AbsBits<float> {
+    typedef unsigned int U;
+    __device__ static U of(float v) { return __float_as_uint(v) & 0x7fffffffu; }
+    __device__ static double value(U u) { return (double)__uint_as_float(u); }
+};
+template <> struct AbsBits<double> {
+    typedef unsigned long long U;
+    __device__ static U of(double v) { return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull; }
+    __device__ static double value(U u) { return __longlong_as_double((long long)u); }
+};
+
 // internal and inactive rows; ghost-class rows come from k_ghost_residual.
-// per block: [0] sum of p over internal cells, [1] max |r|
-template <typename T>
-__global__ void k_residual(LevelArgs<T> A, const T *x, const T *b, T *r, double *part)
+// r may be of a narrower type than the arithmetic (FP64 residual written as
+// the FP32 right-hand side of the next inner cycle).  per block: [0] sum of p
+// over internal cells, [1] max |r|
+template <typename T, typename R>
+__global__ void k_residual(LevelArgs<T> A, const T *x, const T *b, R *r, double *part)
 {
-    double psum = 0.0, rmax = 0.0;
+    T psum = 0;
+    typename AbsBits<T>::U rbits = 0;
     const long long nslot = (long long)(A.N + 2) * A.P;
     for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < nslot; s += (long long)gridDim.x * blockDim.x) {
         const T *u = x, *v = x + A.F, *p = x + 2 * A.F;
@@ -61,29 +79,29 @@ __global__ void k_residual(LevelArgs<T> A, const T *x, const T *b, T *r, double 
         if (tu == T_INTERNAL) {
             T Au = A.d * u[s] - A.a * (u[s + 1] + u[s - 1] + u[s + A.P] + u[s - A.P]) + A.q * (p[s] - p[s - 1]);
             T rr = b[s] - Au;
-            r[s] = rr;
-            rmax = nanmax(rmax, fabs((double)rr));
+            r[s] = (R)rr;
+            rbits = max(rbits, AbsBits<T>::of(rr));
         } else if (tu == T_INACTIVE) r[s] = 0;
         if (tv == T_INTERNAL) {
             long long sv = A.F + s;
             T Av = A.d * v[s] - A.a * (v[s + 1] + v[s - 1] + v[s + A.P] + v[s - A.P]) + A.q * (p[s] - p[s - A.P]);
             T rr = b[sv] - Av;
-            r[sv] = rr;
-            rmax = nanmax(rmax, fabs((double)rr));
+            r[sv] = (R)rr;
+            rbits = max(rbits, AbsBits<T>::of(rr));
         } else if (tv == T_INACTIVE) r[A.F + s] = 0;
         if (tp == T_INTERNAL) {
             long long sp = 2 * A.F + s;
             T Ac = A.q * (u[s + 1] - u[s] + v[s + A.P] - v[s]) - xi;
             T rr = b[sp] - Ac;
-            r[sp] = rr;
-            rmax = nanmax(rmax, fabs((double)rr));
-            psum += (double)p[s];
+            r[sp] = (R)rr;
+            rbits = max(rbits, AbsBits<T>::of(rr));
+            psum += p[s];
         } else if (tp == T_INACTIVE) r[2 * A.F + s] = 0;
     }
     // block reduction (fixed shape: deterministic)
     __shared__ double ss[256], sm[256];
-    ss[threadIdx.x] = psum;
-    sm[threadIdx.x] = rmax;
+    ss[threadIdx.x] = (double)psum;
+    sm[threadIdx.x] = AbsBits<T>::value(rbits);
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
         if (threadIdx.x < o) {
@@ -98,8 +116,8 @@ __global__ void k_residual(LevelArgs<T> A, const T *x, const T *b, T *r, double 
     }
 }
 
-template <typename T>
-__global__ void k_ghost_residual(GhostList gh, int nrows, const T *x, const T *b, T *r, unsigned long long *maxbits)
+template <typename T, typename R>
+__global__ void k_ghost_residual(GhostList gh, int nrows, const T *x, const T *b, R *r, unsigned long long *maxbits)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     double m = 0.0;
@@ -109,7 +127,7 @@ __global__ void k_ghost_residual(GhostList gh, int nrows, const T *x, const T *b
         int node = gh.node[k];
         T s = b[node];
         for (int q = 0; q < nst; q++) s -= w[(long long)q * gh.cap + k] * x[gh.st[(long long)q * gh.cap + k]];
-        r[node] = s;
+        r[node] = (R)s;
         m = fabs((double)s);
     }
     // warp max then one atomic per warp (max of non-negative doubles by bits)
@@ -119,8 +137,8 @@ __global__ void k_ghost_residual(GhostList gh, int nrows, const T *x, const T *b
 }
 
 // mean row (h^2 * sum of internal p) and the norm; one block
-template <typename T>
-__global__ void k_residual_final(const double *part, int nb, const T *b, T *r, long long imean, double h2,
+template <typename T, typename R>
+__global__ void k_residual_final(const double *part, int nb, const T *b, R *r, long long imean, double h2,
                                  unsigned long long *maxbits, double *out)
 {
     __shared__ double ss[256], sm[256];
@@ -141,7 +159,7 @@ __global__ void k_residual_final(const double *part, int nb, const T *b, T *r, l
     }
     if (threadIdx.x == 0) {
         double rm = (double)b[imean] - h2 * ss[0];
-        r[imean] = (T)rm;
+        r[imean] = (R)rm;
         double g = __longlong_as_double((long long)*maxbits);
         double nrm = nanmax(nanmax(sm[0], g), fabs(rm));
         out[0] = nrm;
@@ -625,23 +643,25 @@ template <typename T> __global__ void k_apply_list(T *x, const int *list, const 
 
 // ------------------------------------------------------- xi / mean pressure
 
+// per-thread sums in the arithmetic type (FP32 for FP32 sweeps: no FP64
+// work per cell), block sums in FP64
 template <typename T>
 __global__ void k_scalar_partial(LevelArgs<T> A, const T *x, const T *b, double *part)
 {
-    double s = 0.0, m = 0.0;
+    T s = 0, m = 0;
     const long long nslot = (long long)(A.N + 2) * A.P;
     for (long long sl = blockIdx.x * (long long)blockDim.x + threadIdx.x; sl < nslot;
          sl += (long long)gridDim.x * blockDim.x) {
         if (A.tP[sl] == T_INTERNAL) {
             const T *u = x, *v = x + A.F;
             T div = (u[sl + 1] - u[sl] + v[sl + A.P] - v[sl]) * A.q;
-            s += (double)(div - b[2 * A.F + sl]);
-            m += (double)x[2 * A.F + sl];
+            s += div - b[2 * A.F + sl];
+            m += x[2 * A.F + sl];
         }
     }
     __shared__ double ss[256], sm[256];
-    ss[threadIdx.x] = s;
-    sm[threadIdx.x] = m;
+    ss[threadIdx.x] = (double)s;
+    sm[threadIdx.x] = (double)m;
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
         if (threadIdx.x < o) {
@@ -717,18 +737,6 @@ template <typename T> __global__ void k_ghost_apply(GhostList gh, int nrows, T *
 
 // ---------------------------------------------------------------- transfers
 
-__device__ inline bool same_class(uint8_t tc, uint8_t tf)
-{
-    if (tc == T_INTERNAL) return tf == T_INTERNAL;
-    return tf == T_GHOST || tf == T_WALL || tf == T_BOXGHOST;
-}
-
-__device__ inline uint8_t tget(const uint8_t *t, int g, int N, int P, int i, int j)
-{
-    if (!in_grid(g, N, i, j)) return T_INACTIVE;
-    return t[(long long)(j + 1) * P + (i + 1)];
-}
-
 // Eq. (restop) where the whole stencil is of the coarse node's class,
 // otherwise the plain mean of the fine residuals of that class (Eq. restop5)
 template <typename T>
@@ -776,28 +784,6 @@ __global__ void k_restrict(int Nf, int Pf, long long Ff, const uint8_t *tUf, con
         bH[g * Fc + sc] = all ? sw : (cnt > 0 ? su / (T)cnt : (T)0);
     }
     if (row == 0 && col == 0) bH[3 * Fc] = r[3 * Ff];
-}
-
-// 1-D interpolation taps (see the oracle's description of the same rule)
-template <typename T> __device__ inline int taps(int k, bool aligned, int lo, int hi, int *K, T *w)
-{
-    bool even = (k % 2 == 0);
-    if (aligned) {
-        if (even) { K[0] = k / 2; w[0] = (T)1; return 1; }
-        K[0] = (k - 1) / 2; w[0] = (T)0.5;
-        K[1] = K[0] + 1; w[1] = (T)0.5;
-        return 2;
-    }
-    int Kc = even ? k / 2 : (k - 1) / 2;
-    int Ko = even ? Kc - 1 : Kc + 1;
-    if (Ko < lo || Ko > hi) {
-        K[0] = Kc; w[0] = (T)1.25;
-        K[1] = 2 * Kc - Ko; w[1] = (T)-0.25;
-        return 2;
-    }
-    K[0] = Kc; w[0] = (T)0.75;
-    K[1] = Ko; w[1] = (T)0.25;
-    return 2;
 }
 
 // bilinear interpolation over the active coarse nodes (weights renormalised)
@@ -1130,19 +1116,26 @@ static inline int red_blocks(const Level &l)
     return (int)(n < 1024 ? n : 1024);
 }
 
-template <typename T> void residual(Ctx *c, int lev, const T *x, const T *b, T *r)
+template <typename T, typename R> void residual_into(Ctx *c, int lev, const T *x, const T *b, R *r)
 {
     const Level &l = c->lv[lev];
     cudaStream_t st = c->stream;
     int nb = red_blocks(l);
     tmr_begin(c, KT_RESIDUAL, lev);
-    k_residual<T><<<nb, 256, 0, st>>>(level_args<T>(c, lev), x, b, r, c->part);
+    k_residual<T, R><<<nb, 256, 0, st>>>(level_args<T>(c, lev), x, b, r, c->part);
     tmr_end(c, KT_RESIDUAL, lev);
-    if (l.h_nrows > 0) k_ghost_residual<T><<<(l.h_nrows + 255) / 256, 256, 0, st>>>(l.gh, l.h_nrows, x, b, r, c->maxbits);
+    if (l.h_nrows > 0)
+        k_ghost_residual<T, R><<<(l.h_nrows + 255) / 256, 256, 0, st>>>(l.gh, l.h_nrows, x, b, r, c->maxbits);
     double h = c->prm.L / (double)l.N;
-    k_residual_final<T><<<1, 256, 0, st>>>(c->part, nb, b, r, 3 * l.F, h * h, c->maxbits, c->red);
+    k_residual_final<T, R><<<1, 256, 0, st>>>(c->part, nb, b, r, 3 * l.F, h * h, c->maxbits, c->red);
     c->launches += 2 + (l.h_nrows > 0);
 }
+
+template <typename T> void residual(Ctx *c, int lev, const T *x, const T *b, T *r) { residual_into<T, T>(c, lev, x, b, r); }
+
+// the FP64 residual of the finest level written as the FP32 right-hand side
+// of the next inner cycle (the scalars past the mean row are left as they are)
+void residual_to_float(Ctx *c, const double *x, const double *b, float *r) { residual_into<double, float>(c, 0, x, b, r); }
 
 // full boxes from `in` into `out`: with out != in the level is tiled and out
 // becomes a complete copy of the swept vector; with out == in the five colour

@@ -28,6 +28,7 @@ template <typename T> void zero_vec(Ctx *c, T *x, long long n);
 template <typename T> void zero_inactive(Ctx *c, int lev, T *x);
 template <typename T> void coarse_solve(Ctx *c, const T *b, T *x);
 void to_float(Ctx *c, const double *a, float *b, long long n);
+void residual_to_float(Ctx *c, const double *x, const double *b, float *r);
 void tmr_flush(Ctx *c);
 void tiles_init();
 void prepare_cuts(Ctx *c);
@@ -41,6 +42,17 @@ int cn_momentum_residual(Ctx *c, const double *x, const double *b, double *res, 
 void cn_extrapolate(Ctx *c, const double *Nn, const double *N1, const double *N2, double *Nh);
 void cn_copy(Ctx *c, const double *a, double *b, long long n);
 void add_float(Ctx *c, double *x, const float *e, long long n);
+int adjoint_prepare(Ctx *c);
+void residual_t(Ctx *c, int lev, const double *lam, const double *cc, double *r);
+void box_sweep_t(Ctx *c, int lev, double *lam, const double *cc);
+void scalar_update_t(Ctx *c, int lev, double *lam, const double *cc);
+void ghost_sweep_t(Ctx *c, int lev, double *lam, const double *cc);
+void smooth_t(Ctx *c, int lev, double *lam, const double *cc, int nu);
+void prolong_t(Ctx *c, int lev, const double *r, double *cH);
+void restrict_t(Ctx *c, int lev, const double *yH, double *lam);
+void cycle_t_rec(Ctx *c, int lev, double *lam, const double *cc);
+void fix_inactive_t(Ctx *c, double *lam, const double *cc);
+int solve_t(Ctx *c, double *lam, const double *cc, double tol, gp_report *rep);
 
 // ------------------------------------------------------------- workspace
 
@@ -149,6 +161,20 @@ static size_t carve(Ctx *c, char *base)
         l.lonely = cv.take<int>(l.lonely_cap);
         l.nlonely = cv.take<int>(1);
         l.nint = cv.take<int>(1);
+        if (p.adjoint) {
+            l.tl_cap = GH_ST * gc;
+            l.tl_node = cv.take<int>(l.tl_cap);
+            l.tl_ptr = cv.take<int>(l.tl_cap + 1);
+            l.tl_src = cv.take<int>(l.tl_cap);
+            l.tl_w = cv.take<double>(l.tl_cap);
+            l.gtd = cv.take<double>(l.VL);
+            l.cut_tl = cv.take<int>(5 * (size_t)cc);
+        } else {
+            l.tl_cap = 0;
+            l.tl_node = l.tl_ptr = l.tl_src = l.cut_tl = nullptr;
+            l.tl_w = l.gtd = nullptr;
+        }
+        l.h_tl_n = 0;
         long long nb = (long long)((l.P + 255) / 256) * (l.N + 2);
         long long need = 2 * nb + 3 * (l.N + 2) + 64 + 2 * l.lonely_cap;
         if (need > maxpart) maxpart = need;
@@ -225,14 +251,16 @@ static void solve_iteration(Ctx *c, int which, double *x, const double *b)
         return;
     }
     if (which == 1) {
-        to_float(c, l0.r, l0.bf, l0.VL);
+        // bf holds the FP64 residual of x rounded to FP32 (written by the
+        // previous residual)
         zero_vec<float>(c, l0.xf, l0.VL);
         cycle_rec<float>(c, 0, l0.xf, l0.bf);
         add_float(c, x, l0.xf, l0.VL);
+        residual_to_float(c, x, b, l0.bf);
     } else {
         cycle_rec<double>(c, 0, x, b);
+        residual<double>(c, 0, x, b, l0.r);
     }
-    residual<double>(c, 0, x, b, l0.r);
 }
 
 void graphs_reset(Ctx *c)
@@ -504,6 +532,7 @@ static gp_status geometry_finish(gp_ctx *ctx, const double *phi, int phi_fluid_p
     Ctx *c = &ctx->c;
     c->geom_ok = 0;
     c->coarse_ok = 0;
+    c->adj_ok = 0;
     c->msg[0] = 0;
     graphs_reset(c);
     int s = build_geometry_levels(c, phi, phi_fluid_positive);
@@ -679,7 +708,8 @@ gp_status mg_solve(gp_ctx *ctx, double *x, const double *b, double tol, gp_repor
     bool kry = c->prm.krylov != 0;
     zero_inactive<double>(c, 0, x);
     if (kry) krylov_init(c, x, b);
-    residual<double>(c, 0, x, b, l0.r);
+    if (mixed && !kry) residual_to_float(c, x, b, l0.bf);
+    else residual<double>(c, 0, x, b, l0.r);
     double nrm = 0.0;
     cudaMemcpyAsync(&nrm, c->red, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return check_cuda(ctx, "mg_solve");
@@ -800,6 +830,107 @@ gp_status cn_step(gp_ctx *ctx, double *x, double *N1, double *N2, int step, cons
     }
     gp_status cs = check_cuda(ctx, "cn_step");
     return cs != GP_OK ? cs : st;
+}
+
+// ------------------------------------------------------------- adjoint
+
+// common checks of the adjoint calls: geometry, coarse inverse and cut boxes
+// for the current alpha, column lists
+static gp_status adjoint_ready(gp_ctx *ctx, int level, bool need_coarse_level)
+{
+    if (!ctx || !ctx->c.geom_ok || level < 0 || level >= ctx->c.L || (need_coarse_level && level + 1 >= ctx->c.L))
+        return GP_INVALID;
+    gp_status es = ensure_coarse(ctx);
+    if (es != GP_OK) return es;
+    int st = adjoint_prepare(&ctx->c);
+    return (gp_status)st;
+}
+
+gp_status gp_residual_t(gp_ctx *ctx, int level, const double *lam, const double *c, double *r, double *norm_host)
+{
+    if (!lam || !c || !r) return GP_INVALID;
+    gp_status st = adjoint_ready(ctx, level, false);
+    if (st != GP_OK) return st;
+    Ctx *cx = &ctx->c;
+    residual_t(cx, level, lam, c, r);
+    if (norm_host) {
+        cudaMemcpyAsync(norm_host, cx->red + 4, sizeof(double), cudaMemcpyDeviceToHost, cx->stream);
+        if (cudaStreamSynchronize(cx->stream) != cudaSuccess) return check_cuda(ctx, "gp_residual_t");
+    }
+    return check_cuda(ctx, "gp_residual_t");
+}
+
+gp_status gp_box_sweep_t(gp_ctx *ctx, int level, double *lam, const double *c)
+{
+    if (!lam || !c) return GP_INVALID;
+    gp_status st = adjoint_ready(ctx, level, false);
+    if (st != GP_OK) return st;
+    box_sweep_t(&ctx->c, level, lam, c);
+    return check_cuda(ctx, "gp_box_sweep_t");
+}
+
+gp_status gp_scalar_update_t(gp_ctx *ctx, int level, double *lam, const double *c)
+{
+    if (!lam || !c) return GP_INVALID;
+    gp_status st = adjoint_ready(ctx, level, false);
+    if (st != GP_OK) return st;
+    scalar_update_t(&ctx->c, level, lam, c);
+    return check_cuda(ctx, "gp_scalar_update_t");
+}
+
+gp_status gp_ghost_sweep_t(gp_ctx *ctx, int level, double *lam, const double *c)
+{
+    if (!lam || !c) return GP_INVALID;
+    gp_status st = adjoint_ready(ctx, level, false);
+    if (st != GP_OK) return st;
+    ghost_sweep_t(&ctx->c, level, lam, c);
+    return check_cuda(ctx, "gp_ghost_sweep_t");
+}
+
+gp_status gp_smooth_t(gp_ctx *ctx, int level, double *lam, const double *c, int nu)
+{
+    if (!lam || !c || nu < 0) return GP_INVALID;
+    gp_status st = adjoint_ready(ctx, level, false);
+    if (st != GP_OK) return st;
+    smooth_t(&ctx->c, level, lam, c, nu);
+    return check_cuda(ctx, "gp_smooth_t");
+}
+
+gp_status gp_restrict_t(gp_ctx *ctx, int level, const double *y_coarse, double *lam_fine)
+{
+    if (!y_coarse || !lam_fine) return GP_INVALID;
+    gp_status st = adjoint_ready(ctx, level, true);
+    if (st != GP_OK) return st;
+    restrict_t(&ctx->c, level, y_coarse, lam_fine);
+    return check_cuda(ctx, "gp_restrict_t");
+}
+
+gp_status gp_prolong_t(gp_ctx *ctx, int level, const double *r_fine, double *c_coarse)
+{
+    if (!r_fine || !c_coarse) return GP_INVALID;
+    gp_status st = adjoint_ready(ctx, level, true);
+    if (st != GP_OK) return st;
+    prolong_t(&ctx->c, level, r_fine, c_coarse);
+    return check_cuda(ctx, "gp_prolong_t");
+}
+
+gp_status gp_cycle_t(gp_ctx *ctx, double *lam, const double *c)
+{
+    if (!lam || !c) return GP_INVALID;
+    gp_status st = adjoint_ready(ctx, 0, false);
+    if (st != GP_OK) return st;
+    cycle_t_rec(&ctx->c, 0, lam, c);
+    return check_cuda(ctx, "gp_cycle_t");
+}
+
+gp_status mg_solve_t(gp_ctx *ctx, double *lam, const double *c, double tol, gp_report *rep)
+{
+    if (!lam || !c || !(tol >= 0.0)) return GP_INVALID;
+    gp_status st = adjoint_ready(ctx, 0, false);
+    if (st != GP_OK) return st;
+    int s = solve_t(&ctx->c, lam, c, tol, rep);
+    gp_status cs = check_cuda(ctx, "mg_solve_t");
+    return cs != GP_OK ? cs : (gp_status)s;
 }
 
 }  // extern "C"

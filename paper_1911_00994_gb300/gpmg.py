@@ -27,7 +27,7 @@ class gp_params(ctypes.Structure):
                 ("gamma", ctypes.c_int), ("lam", ctypes.c_int), ("dtau", ctypes.c_double), ("snap", ctypes.c_double),
                 ("precision", ctypes.c_int), ("max_cycles", ctypes.c_int), ("cn_buffers", ctypes.c_int),
                 ("graphs", ctypes.c_int), ("band", ctypes.c_int), ("krylov", ctypes.c_int),
-                ("tile_min", ctypes.c_int)]
+                ("tile_min", ctypes.c_int), ("adjoint", ctypes.c_int)]
 
 
 class gp_report(ctypes.Structure):
@@ -102,6 +102,15 @@ SIGNATURES = [
                      _P(gp_cn_report)]),
     ("gp_convective", _I, [_VP, _VP, _VP]),
     ("gp_cn_rhs", _I, [_VP, _VP, _VP, _VP, _D, _VP, _P(gp_body), _P(gp_walls), _VP]),
+    ("gp_residual_t", _I, [_VP, _I, _VP, _VP, _VP, _P(_D)]),
+    ("gp_box_sweep_t", _I, [_VP, _I, _VP, _VP]),
+    ("gp_scalar_update_t", _I, [_VP, _I, _VP, _VP]),
+    ("gp_ghost_sweep_t", _I, [_VP, _I, _VP, _VP]),
+    ("gp_smooth_t", _I, [_VP, _I, _VP, _VP, _I]),
+    ("gp_restrict_t", _I, [_VP, _I, _VP, _VP]),
+    ("gp_prolong_t", _I, [_VP, _I, _VP, _VP]),
+    ("gp_cycle_t", _I, [_VP, _VP, _VP]),
+    ("mg_solve_t", _I, [_VP, _VP, _VP, _D, _P(gp_report)]),
     ("gp_launch_count", ctypes.c_int64, [_VP]),
     ("gp_timer_start", _I, [_VP, _I, _I]),
     ("gp_timer_stop", _I, [_VP, _P(ctypes.c_int64), _P(_D)]),
@@ -159,7 +168,7 @@ class Solver:
 
     def __init__(self, N, x0, y0, L, levels=None, alpha=None, nu1=2, nu2=1, gamma=1, lam=5, dtau=0.9,
                  snap=0.3, precision=GP_FP64, max_cycles=100, device="cuda", stream=None, cn_buffers=True,
-                 graphs=True, band=0, krylov=False, tile_min=0):
+                 graphs=True, band=0, krylov=False, tile_min=0, adjoint=False):
         import torch
         self.torch = torch
         self.L = lib()
@@ -178,6 +187,7 @@ class Solver:
         p.band = int(band)
         p.krylov = 1 if krylov else 0
         p.tile_min = int(tile_min)
+        p.adjoint = 1 if adjoint else 0
         self.prm = p
         nb = ctypes.c_size_t(0)
         st = self.L.gp_workspace_size(ctypes.byref(p), ctypes.byref(nb))
@@ -334,6 +344,49 @@ class Solver:
 
     def cycle(self, x, b):
         self._check(self.L.gp_cycle(self.ctx, _ptr(x), _ptr(b)), "gp_cycle")
+
+    # ---------------------------------------- adjoint (M^T lam = c)
+    def residual_t(self, lam, c, lev=0):
+        r = self.new_vec(lev)
+        nrm = ctypes.c_double(0.0)
+        self._check(self.L.gp_residual_t(self.ctx, lev, _ptr(lam), _ptr(c), _ptr(r), ctypes.byref(nrm)),
+                    "gp_residual_t")
+        return r, nrm.value
+
+    def box_sweep_t(self, lam, c, lev=0):
+        self._check(self.L.gp_box_sweep_t(self.ctx, lev, _ptr(lam), _ptr(c)), "gp_box_sweep_t")
+
+    def scalar_update_t(self, lam, c, lev=0):
+        self._check(self.L.gp_scalar_update_t(self.ctx, lev, _ptr(lam), _ptr(c)), "gp_scalar_update_t")
+
+    def ghost_sweep_t(self, lam, c, lev=0):
+        self._check(self.L.gp_ghost_sweep_t(self.ctx, lev, _ptr(lam), _ptr(c)), "gp_ghost_sweep_t")
+
+    def smooth_t(self, lam, c, nu=1, lev=0):
+        self._check(self.L.gp_smooth_t(self.ctx, lev, _ptr(lam), _ptr(c), nu), "gp_smooth_t")
+
+    def restrict_t(self, yH, lam, lev=0):
+        """lam += R^T yH (in place on lam, level lev)."""
+        self._check(self.L.gp_restrict_t(self.ctx, lev, _ptr(yH), _ptr(lam)), "gp_restrict_t")
+
+    def prolong_t(self, r, lev=0):
+        """P^T r on level lev + 1."""
+        out = self.new_vec(lev + 1)
+        self._check(self.L.gp_prolong_t(self.ctx, lev, _ptr(r), _ptr(out)), "gp_prolong_t")
+        return out
+
+    def cycle_t(self, lam, c):
+        self._check(self.L.gp_cycle_t(self.ctx, _ptr(lam), _ptr(c)), "gp_cycle_t")
+
+    def solve_t(self, lam, c, tol, hist=True):
+        rep = gp_report()
+        h = None
+        if hist:
+            h = (ctypes.c_double * (self.prm.max_cycles + 1))()
+            rep.hist_host = ctypes.cast(h, ctypes.POINTER(ctypes.c_double))
+        st = self.L.mg_solve_t(self.ctx, _ptr(lam), _ptr(c), tol, ctypes.byref(rep))
+        hist_arr = np.array(h[:rep.iterations + 1]) if hist else None
+        return st, rep, hist_arr
 
     # ------------------------------------------------ Crank-Nicolson step
     @staticmethod
