@@ -97,15 +97,30 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def kernel_source_sha1():
+    """sha1 of the source of the roofline kernel (the box constants, the box
+    solve and the tiled sweep in ops.cu): DRAM traffic measured by ncu stays
+    valid while this text is unchanged."""
+    src = open(os.path.join(ROOT, "paper_1911_00994_gb300", "csrc", "ops.cu")).read()
+    parts = []
+    a = src.index("template <typename T> struct BoxK")
+    parts.append(src[a:src.index("template <typename T> struct LevelArgs", a)])
+    a = src.index("template <typename T>\n__device__ __forceinline__ void box_core(")
+    parts.append(src[a:src.index("    p[0] += dp;\n}\n", a)])
+    a = src.index("template <typename T> struct TileGeom;")
+    b = src.index("k_box_tma(", a)
+    parts.append(src[a:src.index("\n}\n", b)])
+    return hashlib.sha1("".join(parts).encode()).hexdigest()
+
+
 def ncu_traffic(kernel):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
     was taken on the current kernel source."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             d = json.load(f)
-        src = open(os.path.join(ROOT, "paper_1911_00994_gb300", "csrc", "ops.cu"), "rb").read()
         e = d.get(kernel)
-        if e and e.get("ops_cu_sha1") == hashlib.sha1(src).hexdigest():
+        if e and e.get("kernel_source_sha1") == kernel_source_sha1():
             return e
     except Exception:
         pass
