@@ -87,6 +87,10 @@ def lib():
             L.or_prolong_t.argtypes = [vp, i, P(d), P(d)]
             L.or_cycle_t.argtypes = [vp, i, P(d), P(d)]
             L.or_solve_t.argtypes = [vp, P(d), P(d), d, i, P(d), P(i)]
+            L.or_convective_jt.argtypes = [vp, P(d), P(d), P(d)]
+            L.or_explicit_t.argtypes = [vp, P(d), P(d)]
+            L.or_cn_step_adjoint.argtypes = [vp, i, P(d), vp, d, P(d), d, P(d), d, i, P(d), P(d), P(d), P(d),
+                                             P(d), P(d), P(d)]
             L.or_convective.argtypes = [vp, P(d), P(d)]
             L.or_solve_krylov.argtypes = [vp, P(d), P(d), d, i, P(d), P(i)]
             L.or_cn_rhs.argtypes = [vp, P(d), P(d), vp, d, vp, P(d), P(d), P(d)]
@@ -316,6 +320,34 @@ class Oracle:
         nc = ctypes.c_int(0)
         st = self.L.or_solve_t(self.c, _p(lam2), _p(cc), tol, max_cycles, _p(hist), ctypes.byref(nc))
         return st, lam2, hist[:nc.value + 1]
+
+    def convective_jt(self, x, y):
+        """J_N(x)^T y (transpose of the linearised convective term at x)."""
+        out = np.zeros(self.n())
+        self.L.or_convective_jt(self.c, _p(np.ascontiguousarray(x, dtype=np.float64)),
+                                _p(np.ascontiguousarray(y, dtype=np.float64)), _p(out))
+        return out
+
+    def explicit_t(self, y):
+        """A^T y with A x = x + alpha lap x on the internal u, v rows."""
+        out = np.zeros(self.n())
+        self.L.or_explicit_t(self.c, _p(np.ascontiguousarray(y, dtype=np.float64)), _p(out))
+        return out
+
+    def cn_step_adjoint(self, step, xm, dt, xbar_next, nb, fbar, abar, f=None, body=(0, 0, 0, 0, 0), amp=1.0,
+                        walls=(0, 0, 0, 0), tol=1e-12, kmax=4):
+        """Backward pass of one CN step (see gpmg_oracle.c).  nb = [nb0, nb1,
+        nb2] and fbar are updated in place; returns (status, xbar_m, abar)."""
+        xbar_m = np.zeros(self.n())
+        ab = np.array([abar], dtype=np.float64)
+        f = self._opt(f)
+        st = self.L.or_cn_step_adjoint(self.c, step, _p(np.ascontiguousarray(xm, dtype=np.float64)),
+                                       None if f is None else f.ctypes.data,
+                                       dt, _p(np.array(body, dtype=np.float64)), amp,
+                                       _p(np.array(walls, dtype=np.float64)), tol, kmax,
+                                       _p(np.ascontiguousarray(xbar_next, dtype=np.float64)), _p(xbar_m),
+                                       _p(nb[0]), _p(nb[1]), _p(nb[2]), _p(fbar), _p(ab))
+        return st, xbar_m, float(ab[0])
 
     def solve(self, x, b, tol, max_cycles=50):
         x2 = np.array(x, dtype=np.float64)

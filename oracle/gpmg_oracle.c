@@ -1938,3 +1938,190 @@ int or_solve_t(void *vc, double *lam, const double *cc, double tol, int max_cycl
     }
     return OR_NOT_CONVERGED;
 }
+
+/* ------------------------------------------- adjoint of the CN step
+ *
+ * One CN step m (geometry of step m+1 built) maps x^m to x^(m+1) = M^-1 b with
+ * b = A x^m + dt E f - dt E Nh + a g on the rows of Eq. (spaceprob): A x =
+ * x + alpha lap x and E the internal momentum rows, g the rigid-body velocity
+ * on the Eq. (BCu) rows (a its amplitude), Nh the convective term of
+ * Eq. (extrUdU) (m >= 2: N(x^m) + N^(m-1)/2 - N^(m-2)/2 with the stored terms
+ * of the two previous steps) or of the mid-point Picard iteration
+ * (Eq. NSitconv) with a fixed number K of iterations (m = 0, 1: iterate k
+ * uses (N(x^m) + N(x^(k)))/2, x^(0) = x^m).  The backward pass applies the
+ * transposes in reverse: lam = M^-T xbar, fbar += dt E lam, abar += g.lam,
+ * xbar^m += A^T lam, and the convective term's adjoint goes to the stored
+ * term it came from; the adjoint of a stored term N(x^j) is turned into
+ * xbar^j by the transposed Jacobian when step j is processed (with that
+ * step's geometry), after all later steps have added to it. */
+
+static int internal_mom(const level_t *l, int k)
+{
+    if (k < l->nU) return l->tU[k] == T_INTERNAL;
+    if (k < l->nU + l->nV) return l->tV[k - l->nU] == T_INTERNAL;
+    return 0;
+}
+
+/* out += J_N(x)^T y: transpose of the linearised convective term at x (rows:
+ * internal u, v nodes; entries of y elsewhere are ignored) */
+void or_convective_jt(void *vc, const double *x, const double *y, double *out)
+{
+    ctx_t *c = (ctx_t *)vc;
+    level_t *l = &c->lv[0];
+    int N = l->N;
+    double h2 = 2.0 * l->h;
+    for (int j = 0; j < N; j++)
+        for (int i = 1; i < N; i++) {
+            if (ttype(l, G_U, i, j) != T_INTERNAL) continue;
+            double w = y[iU(l, i, j)];
+            double u = x[iU(l, i, j)];
+            double vb = 0.25 * (x[iV(l, i - 1, j)] + x[iV(l, i, j)] + x[iV(l, i - 1, j + 1)] + x[iV(l, i, j + 1)]);
+            double dudx = (x[iU(l, i + 1, j)] - x[iU(l, i - 1, j)]) / h2;
+            double dudy = (x[iU(l, i, j + 1)] - x[iU(l, i, j - 1)]) / h2;
+            out[iU(l, i, j)] += w * dudx;
+            out[iU(l, i + 1, j)] += w * u / h2;
+            out[iU(l, i - 1, j)] -= w * u / h2;
+            out[iU(l, i, j + 1)] += w * vb / h2;
+            out[iU(l, i, j - 1)] -= w * vb / h2;
+            double cv = 0.25 * w * dudy;
+            out[iV(l, i - 1, j)] += cv;
+            out[iV(l, i, j)] += cv;
+            out[iV(l, i - 1, j + 1)] += cv;
+            out[iV(l, i, j + 1)] += cv;
+        }
+    for (int j = 1; j < N; j++)
+        for (int i = 0; i < N; i++) {
+            if (ttype(l, G_V, i, j) != T_INTERNAL) continue;
+            double w = y[iV(l, i, j)];
+            double v = x[iV(l, i, j)];
+            double ub = 0.25 * (x[iU(l, i, j - 1)] + x[iU(l, i + 1, j - 1)] + x[iU(l, i, j)] + x[iU(l, i + 1, j)]);
+            double dvdx = (x[iV(l, i + 1, j)] - x[iV(l, i - 1, j)]) / h2;
+            double dvdy = (x[iV(l, i, j + 1)] - x[iV(l, i, j - 1)]) / h2;
+            out[iV(l, i, j)] += w * dvdy;
+            out[iV(l, i + 1, j)] += w * ub / h2;
+            out[iV(l, i - 1, j)] -= w * ub / h2;
+            out[iV(l, i, j + 1)] += w * v / h2;
+            out[iV(l, i, j - 1)] -= w * v / h2;
+            double cu = 0.25 * w * dvdx;
+            out[iU(l, i, j - 1)] += cu;
+            out[iU(l, i + 1, j - 1)] += cu;
+            out[iU(l, i, j)] += cu;
+            out[iU(l, i + 1, j)] += cu;
+        }
+}
+
+/* out += A^T y, A x = x + alpha lap x on the internal u, v rows */
+void or_explicit_t(void *vc, const double *y, double *out)
+{
+    ctx_t *c = (ctx_t *)vc;
+    level_t *l = &c->lv[0];
+    int N = l->N;
+    double a = c->alpha / (l->h * l->h);
+    for (int j = 0; j < N; j++)
+        for (int i = 1; i < N; i++) {
+            if (ttype(l, G_U, i, j) != T_INTERNAL) continue;
+            double w = y[iU(l, i, j)];
+            out[iU(l, i, j)] += (1.0 - 4.0 * a) * w;
+            out[iU(l, i + 1, j)] += a * w;
+            out[iU(l, i - 1, j)] += a * w;
+            out[iU(l, i, j + 1)] += a * w;
+            out[iU(l, i, j - 1)] += a * w;
+        }
+    for (int j = 1; j < N; j++)
+        for (int i = 0; i < N; i++) {
+            if (ttype(l, G_V, i, j) != T_INTERNAL) continue;
+            double w = y[iV(l, i, j)];
+            out[iV(l, i, j)] += (1.0 - 4.0 * a) * w;
+            out[iV(l, i + 1, j)] += a * w;
+            out[iV(l, i - 1, j)] += a * w;
+            out[iV(l, i, j + 1)] += a * w;
+            out[iV(l, i, j - 1)] += a * w;
+        }
+}
+
+#define OR_MAXPICARD 16
+
+/* Backward pass of CN step `step` (geometry of step+1 built, alpha set).
+ * xm: the state x^m; f: forcing (or NULL); body: the rigid-body motion at
+ * unit amplitude {U, V, omega, cx, cy}, amp its amplitude; walls: the box
+ * velocities (not scaled); kmax: the fixed Picard count of steps 0, 1.
+ * xbar_next = dL/dx^(m+1) (in); xbar_m += dL/dx^m through this step (the
+ * caller adds other paths); nb0, nb1, nb2: adjoints of the stored convective
+ * terms of steps m, m-1, m-2 (accumulated; nb0 is turned into xbar_m here);
+ * fbar += dL/df, *abar += dL/da. */
+int or_cn_step_adjoint(void *vc, int step, const double *xm, const double *f, double dt, const double *body,
+                       double amp, const double *walls, double tol, int kmax, const double *xbar_next, double *xbar_m,
+                       double *nb0, double *nb1, double *nb2, double *fbar, double *abar)
+{
+    ctx_t *c = (ctx_t *)vc;
+    if (!c->geom_ok || kmax < 1 || kmax > OR_MAXPICARD) return OR_INVALID;
+    level_t *l = &c->lv[0];
+    int n = l->n, st = OR_OK, nc = 0;
+    double *g = (double *)calloc(n, sizeof(double)), *zero = (double *)calloc(n, sizeof(double));
+    double *lam = (double *)calloc(n, sizeof(double)), *el = (double *)calloc(n, sizeof(double));
+    double *xb = (double *)malloc(sizeof(double) * n), *hist = (double *)malloc(sizeof(double) * 1001);
+    double nowalls[4] = {0, 0, 0, 0};
+    double bamp[5] = {amp * body[0], amp * body[1], amp * body[2], body[3], body[4]};
+    or_cn_rhs(c, zero, zero, NULL, dt, NULL, body, nowalls, g);
+    /* only the Eq. (BCu) rows carry the body velocity */
+    for (int k = 0; k < n; k++)
+        if (internal_mom(l, k)) g[k] = 0.0;
+    memcpy(xb, xbar_next, sizeof(double) * n);
+    double **X = NULL;
+    int K = step >= 2 ? 1 : kmax;
+    if (step < 2) {
+        /* the Picard iterates x^(1..K-1) of the forward step, recomputed */
+        X = (double **)calloc(K + 1, sizeof(double *));
+        double *Nn = (double *)malloc(sizeof(double) * n), *Nh = (double *)malloc(sizeof(double) * n);
+        double *b = (double *)malloc(sizeof(double) * n);
+        or_convective(c, xm, Nn);
+        memcpy(Nh, Nn, sizeof(double) * n);
+        X[0] = (double *)malloc(sizeof(double) * n);
+        memcpy(X[0], xm, sizeof(double) * n);
+        for (int k = 1; k < K && st == OR_OK; k++) {
+            X[k] = (double *)malloc(sizeof(double) * n);
+            memcpy(X[k], X[k - 1], sizeof(double) * n);
+            or_cn_rhs(c, xm, Nh, f, dt, NULL, bamp, walls, b);
+            st = or_solve(c, X[k], b, tol, 1000, hist, &nc);
+            or_convective(c, X[k], Nh);
+            for (int q = 0; q < n; q++) Nh[q] = 0.5 * (Nn[q] + Nh[q]);
+        }
+        free(Nn); free(Nh); free(b);
+    }
+    for (int k = K - 1; k >= 0 && st == OR_OK; k--) {
+        memset(lam, 0, sizeof(double) * n);
+        st = or_solve_t(c, lam, xb, tol, 1000, hist, &nc);
+        if (st != OR_OK) break;
+        for (int q = 0; q < n; q++) el[q] = internal_mom(l, q) ? lam[q] : 0.0;
+        double ga = 0.0;
+        for (int q = 0; q < n; q++) {
+            fbar[q] += dt * el[q];
+            ga += g[q] * lam[q];
+        }
+        *abar += ga;
+        or_explicit_t(c, lam, xbar_m);
+        if (step >= 2) {
+            for (int q = 0; q < n; q++) {
+                nb0[q] -= dt * el[q];
+                nb1[q] -= 0.5 * dt * el[q];
+                nb2[q] += 0.5 * dt * el[q];
+            }
+        } else if (k >= 1) {
+            for (int q = 0; q < n; q++) {
+                nb0[q] -= 0.5 * dt * el[q];
+                el[q] *= -0.5 * dt;
+            }
+            memset(xb, 0, sizeof(double) * n);
+            or_convective_jt(c, X[k], el, xb);
+        } else {
+            for (int q = 0; q < n; q++) nb0[q] -= dt * el[q];
+        }
+    }
+    if (st == OR_OK) or_convective_jt(c, xm, nb0, xbar_m);
+    if (X) {
+        for (int k = 0; k <= K; k++) free(X[k]);
+        free(X);
+    }
+    free(g); free(zero); free(lam); free(el); free(xb); free(hist);
+    return st;
+}
