@@ -146,6 +146,59 @@ def build_case(N, precision, device, stream, levels=None, krylov=False):
     return s, b
 
 
+def adjoint_rollout(dev, stream, steps=50, every=10, N=512):
+    """Config 4's adjoint: the orbiting circle (r = 0.25, orbit radius 0.2,
+    period 1) at Re = 100 on [-1, 1]^2, a rollout of `steps` CN steps from
+    rest, and the gradient of the kinetic energy on a 64 x 64 probe window
+    (u and v nodes with array indices i in [352, 416), j in [224, 288)) with
+    respect to the forcing (4 seeded Gaussian bumps, sigma = 0.1) and the
+    body-velocity amplitude, checkpoints every `every` steps.  dt = 0.3 h:
+    the paper bounds the step by h / max |u| and at dt = h the first steps'
+    Picard iteration diverges."""
+    import numpy as np
+    import torch
+    from paper_1911_00994_gb300 import gpmg
+    from paper_1911_00994_gb300 import workloads as W
+    from paper_1911_00994_gb300.rollout import Rollout
+    x0, L, Re = -1.0, 2.0, 100.0
+    dt = 0.3 * L / N
+    s = gpmg.Solver(N, x0, x0, L, alpha=dt / (2 * Re), band=3, adjoint=True, max_cycles=400, device=dev,
+                    stream=stream)
+    shape = dict(kind=gpmg.GP_CIRCLE, a=0.25, orbit_r=0.2, orbit_period=1.0)
+    st, body = s.geometry_shape(t=0.0, **shape)
+    if st:
+        raise RuntimeError("geometry failed: %s" % s.error())
+    t = s.types_flat()
+    g, i, j, X, Y = W.flat_coords(N, x0, x0, L)
+    rng = np.random.default_rng(1234)
+    f = np.zeros(len(t))
+    for _ in range(4):
+        while True:
+            c = rng.uniform(-0.9, 0.9, 2)
+            if np.hypot(c[0], c[1]) > 0.55:  # outside the orbit's reach
+                break
+        amp = rng.standard_normal(2)
+        bump = np.exp(-((X - c[0]) ** 2 + (Y - c[1]) ** 2) / (2 * 0.1 ** 2))
+        f += np.where(g == 0, amp[0] * bump, 0.0) + np.where(g == 1, amp[1] * bump, 0.0)
+    f = np.where(((g == 0) | (g == 1)) & (t == 1), f, 0.0)
+    w = (((g == 0) | (g == 1)) & (i >= 352) & (i < 416) & (j >= 224) & (j < 288)).astype(float)
+    fd, wd = s.to_device(f), s.to_device(w)
+    ro = Rollout(s, shape, dt, Re, steps, kmax=4, tol=1e-10, every=every)
+    torch.cuda.synchronize(dev)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    e[0].record(stream)
+    ro.forward(fd, 1.0)
+    e[1].record(stream)
+    e[2].record(stream)
+    loss, fbar, abar = ro.loss_and_gradient(fd, 1.0, wd)
+    e[3].record(stream)
+    torch.cuda.synchronize(dev)
+    fw, gr = e[0].elapsed_time(e[1]), e[2].elapsed_time(e[3])
+    return {"N": N, "steps": steps, "checkpoint_every": every, "dt": "0.3h", "Re": Re, "forward_ms": fw,
+            "loss_and_gradient_ms": gr, "gradient_over_forward": gr / fw, "loss": loss,
+            "dL_damp": abar, "dL_df_norm": float(fbar.norm())}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -291,6 +344,9 @@ def run_ours(args):
     g1.record(s64.stream)
     barrier()
     ms64 = g0.elapsed_time(g1)
+    del s64
+    torch.cuda.empty_cache()
+    adj = adjoint_rollout(dev, stream) if not args.no_adjoint else None
 
     if rank != 0:
         if dist:
@@ -319,6 +375,7 @@ def run_ours(args):
                  "steps": n64},
         "bicgstab_mixed": {"time_to_tol_ms": msk / nk, "iterations_per_step": kit / nk, "cycles_per_step": kc / nk,
                            "cycles_per_s": kc / (msk / 1e3), "steps": nk},
+        "adjoint_rollout_config4": adj,
         "roofline": {"kernel": "k_box_tma<float> (finest-level full-box sweep, five colours in one pass)", "bound": "hbm",
                      "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "peak_source": src, "avg_launch_ms": avg_ms, "launches": nbox,
@@ -413,6 +470,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--N", type=int, default=4096)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         args.steps = 2 if args.steps is None else args.steps

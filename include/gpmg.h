@@ -308,6 +308,28 @@ gp_status gp_prolong_t(gp_ctx *ctx, int level, const double *r_fine, double *c_c
 gp_status gp_cycle_t(gp_ctx *ctx, double *lam, const double *c);
 gp_status mg_solve_t(gp_ctx *ctx, double *lam, const double *c, double tol, gp_report *rep);
 
+/* Backward pass of one Crank-Nicolson step (the adjoint of cn_step with
+ * bc = NULL, a fixed number kmax of Picard iterations for steps 0 and 1,
+ * i.e. eps = 0).  The geometry of step+1 must be built (as for the forward
+ * step).  Step m maps x^m to x^(m+1) = M^-1 b, b = A x^m + dt E f - dt E Nh
+ * + amp g (A x = x + alpha lap x and E on the internal momentum rows, g the
+ * rigid-body velocity `body` at unit amplitude on the Eq. (BCu) rows, Nh the
+ * convective term of Eq. extrUdU or of the Picard iteration, Eq. NSitconv).
+ * Given xbar_next = dL/dx^(m+1) it adds to xbar_m the derivative through this
+ * step, to fbar dL/df (dt E lam summed over the step's solves), to *abar
+ * (host) dL/damp, and to nbar0/nbar1/nbar2 the adjoints of the stored
+ * convective terms of steps m, m-1, m-2; nbar0 is complete at this step and
+ * is turned into xbar_m through the transposed convective Jacobian (the
+ * caller then shifts nbar1 -> nbar0, nbar2 -> nbar1 and zeroes nbar2).  Each
+ * lam solves M^T lam = xbar by mg_solve_t to `tol`; Picard iterates are
+ * recomputed by mg_solve.  All vectors are finest-level device vectors;
+ * x_m, f (NULL: no forcing) and xbar_next are read only.  Needs
+ * gp_params.adjoint and cn_buffers; walls are the (unscaled) box velocities. */
+gp_status cn_step_adjoint(gp_ctx *ctx, int step, const double *x_m, const double *f, double dt, double Re,
+                          const gp_body *body, double amp, const gp_walls *walls, double tol, int kmax,
+                          const double *xbar_next, double *xbar_m, double *nbar0, double *nbar1, double *nbar2,
+                          double *fbar, double *abar);
+
 /* Instrumentation (no counterpart in the paper; used by the benchmark).
  * gp_launch_count: kernels this context has launched so far.
  * gp_timer_start: record CUDA events on the context stream around every

@@ -134,6 +134,109 @@ __global__ void k_copy(const double *a, double *b, long long n)
     if (k < n) b[k] = a[k];
 }
 
+// ------------------------------------------------- adjoint of the CN step
+
+// out += J_N(x)^T y on the u, v frames: the transpose of the linearised
+// convective term at x, as a gather over the rows that reference each node
+// (u rows at s, s +- 1, s +- P and the v rows whose averaged u holds u(s);
+// likewise for v).  y is read on internal u, v rows only.
+__global__ void k_convective_jt(int P, long long F, int R, double h, const uint8_t *tU, const uint8_t *tV,
+                                const double *x, const double *y, double *out)
+{
+    int col = blockIdx.x * blockDim.x + threadIdx.x;
+    int row = blockIdx.y;
+    if (col >= P) return;
+    const long long s = (long long)row * P + col, NS = (long long)R * P;
+    const double *u = x, *v = x + F, *yu = y, *yv = y + F;
+    const double h2 = 2.0 * h;
+    auto iu = [&](long long r) { return r >= 0 && r < NS && tU[r] == T_INTERNAL; };
+    auto iv = [&](long long r) { return r >= 0 && r < NS && tV[r] == T_INTERNAL; };
+    auto vbar = [&](long long r) { return 0.25 * (v[r - 1] + v[r] + v[r + P - 1] + v[r + P]); };
+    auto ubar = [&](long long r) { return 0.25 * (u[r - P] + u[r - P + 1] + u[r] + u[r + 1]); };
+    double su = 0.0, sv = 0.0;
+    if (iu(s)) su += yu[s] * ((u[s + 1] - u[s - 1]) / h2);
+    if (iu(s - 1)) su += yu[s - 1] * u[s - 1] / h2;
+    if (iu(s + 1)) su -= yu[s + 1] * u[s + 1] / h2;
+    if (iu(s - P)) su += yu[s - P] * vbar(s - P) / h2;
+    if (iu(s + P)) su -= yu[s + P] * vbar(s + P) / h2;
+    const long long rv[4] = {s + P, s + P - 1, s, s - 1};
+#pragma unroll
+    for (int q = 0; q < 4; q++)
+        if (iv(rv[q])) su += 0.25 * yv[rv[q]] * ((v[rv[q] + 1] - v[rv[q] - 1]) / h2);
+    if (iv(s)) sv += yv[s] * ((v[s + P] - v[s - P]) / h2);
+    if (iv(s - 1)) sv += yv[s - 1] * ubar(s - 1) / h2;
+    if (iv(s + 1)) sv -= yv[s + 1] * ubar(s + 1) / h2;
+    if (iv(s - P)) sv += yv[s - P] * v[s - P] / h2;
+    if (iv(s + P)) sv -= yv[s + P] * v[s + P] / h2;
+    const long long ru[4] = {s + 1, s, s - P + 1, s - P};
+#pragma unroll
+    for (int q = 0; q < 4; q++)
+        if (iu(ru[q])) sv += 0.25 * yu[ru[q]] * ((u[ru[q] + P] - u[ru[q] - P]) / h2);
+    out[s] += su;
+    out[F + s] += sv;
+}
+
+// out += A^T y, A x = x + alpha lap x on the internal u, v rows
+__global__ void k_explicit_t(int P, long long F, int R, double a, const uint8_t *tU, const uint8_t *tV,
+                             const double *y, double *out)
+{
+    int col = blockIdx.x * blockDim.x + threadIdx.x;
+    int row = blockIdx.y;
+    if (col >= P) return;
+    const long long s = (long long)row * P + col, NS = (long long)R * P;
+#pragma unroll
+    for (int g = 0; g < 2; g++) {
+        const uint8_t *t = g == 0 ? tU : tV;
+        const double *yy = y + g * F;
+        double acc = 0.0;
+        if (t[s] == T_INTERNAL) acc += (1.0 - 4.0 * a) * yy[s];
+        const long long nb[4] = {s + 1, s - 1, s + P, s - P};
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+            if (nb[q] >= 0 && nb[q] < NS && t[nb[q]] == T_INTERNAL) acc += a * yy[nb[q]];
+        out[g * F + s] += acc;
+    }
+}
+
+// el = lam on internal u, v rows (0 elsewhere on the u, v frames)
+__global__ void k_mask_mom(int P, long long F, const uint8_t *tU, const uint8_t *tV, const double *lam, double *el)
+{
+    int col = blockIdx.x * blockDim.x + threadIdx.x;
+    int row = blockIdx.y;
+    if (col >= P) return;
+    const long long s = (long long)row * P + col;
+    el[s] = tU[s] == T_INTERNAL ? lam[s] : 0.0;
+    el[F + s] = tV[s] == T_INTERNAL ? lam[F + s] : 0.0;
+}
+
+// acc_q += c_q el on the u, v frames for up to four (acc, c) pairs
+__global__ void k_axpy4(long long n, const double *el, double *a0, double c0, double *a1, double c1, double *a2,
+                        double c2, double *a3, double c3)
+{
+    long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const double e = el[k];
+    if (a0) a0[k] += c0 * e;
+    if (a1) a1[k] += c1 * e;
+    if (a2) a2[k] += c2 * e;
+    if (a3) a3[k] += c3 * e;
+}
+
+// out[0] = sum over ghost-class rows of g * lam (one block, fixed order)
+__global__ void k_dot_rows(const int *node, int n, const double *g, const double *lam, double *out)
+{
+    __shared__ double sh[256];
+    double s = 0.0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) s += g[node[k]] * lam[node[k]];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = sh[0];
+}
+
 // ------------------------------------------------------------- host side
 
 static dim3 fgrid(const Level &l) { return dim3((l.P + 255) / 256, l.N + 2); }
@@ -187,6 +290,43 @@ void cn_extrapolate(Ctx *c, const double *Nn, const double *N1, const double *N2
 void cn_copy(Ctx *c, const double *a, double *b, long long n)
 {
     k_copy<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(a, b, n);
+    c->launches++;
+}
+
+void cn_convective_jt(Ctx *c, const double *x, const double *y, double *out)
+{
+    const Level &l = c->lv[0];
+    k_convective_jt<<<fgrid(l), 256, 0, c->stream>>>(l.P, l.F, l.N + 2, l.h, l.tU, l.tV, x, y, out);
+    c->launches++;
+}
+
+void cn_explicit_t(Ctx *c, const double *y, double *out)
+{
+    const Level &l = c->lv[0];
+    k_explicit_t<<<fgrid(l), 256, 0, c->stream>>>(l.P, l.F, l.N + 2, c->prm.alpha / (l.h * l.h), l.tU, l.tV, y, out);
+    c->launches++;
+}
+
+void cn_mask_mom(Ctx *c, const double *lam, double *el)
+{
+    const Level &l = c->lv[0];
+    k_mask_mom<<<fgrid(l), 256, 0, c->stream>>>(l.P, l.F, l.tU, l.tV, lam, el);
+    c->launches++;
+}
+
+void cn_axpy4(Ctx *c, const double *el, double *a0, double c0, double *a1, double c1, double *a2, double c2,
+              double *a3, double c3)
+{
+    long long n = 2 * c->lv[0].F;
+    k_axpy4<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(n, el, a0, c0, a1, c1, a2, c2, a3, c3);
+    c->launches++;
+}
+
+// sum over the ghost-class rows of the finest level of g * lam (into out, device)
+void cn_dot_rows(Ctx *c, const double *g, const double *lam, double *out)
+{
+    const Level &l = c->lv[0];
+    k_dot_rows<<<1, 256, 0, c->stream>>>(l.gh.node, l.h_nrows, g, lam, out);
     c->launches++;
 }
 

@@ -26,6 +26,7 @@ enum RowKind : uint8_t { K_BCU = 0, K_EXTRAP = 1, K_COPY = 2, K_WALL = 3, K_BOXG
 constexpr int MAX_LEVELS = 16;
 constexpr int MAX_MARCH = 64;
 constexpr int NSCAL = 32;
+constexpr int ADJ_KMAX = 8;  // Picard iterations cn_step_adjoint can differentiate
 constexpr int GH_ST = 9;  // stencil slots per ghost row
 
 // error bits written by kernels into the context's device status word
@@ -159,6 +160,7 @@ struct Ctx {
     int coarse_ok;
     double alpha_factored;
     int adj_ok;            // adjoint column lists built for this geometry
+    double *adjv[12];      // finest-level vectors of cn_step_adjoint (lam, E lam, g, xbar, Picard iterates)
     char msg[256];
 };
 

@@ -53,6 +53,12 @@ void restrict_t(Ctx *c, int lev, const double *yH, double *lam);
 void cycle_t_rec(Ctx *c, int lev, double *lam, const double *cc);
 void fix_inactive_t(Ctx *c, double *lam, const double *cc);
 int solve_t(Ctx *c, double *lam, const double *cc, double tol, gp_report *rep);
+void cn_convective_jt(Ctx *c, const double *x, const double *y, double *out);
+void cn_explicit_t(Ctx *c, const double *y, double *out);
+void cn_mask_mom(Ctx *c, const double *lam, double *el);
+void cn_axpy4(Ctx *c, const double *el, double *a0, double c0, double *a1, double c1, double *a2, double c2,
+              double *a3, double c3);
+void cn_dot_rows(Ctx *c, const double *g, const double *lam, double *out);
 
 // ------------------------------------------------------------- workspace
 
@@ -195,6 +201,8 @@ static size_t carve(Ctx *c, char *base)
     c->err = cv.take<unsigned>(4);
     c->flag = cv.take<int>(4);
     for (int k = 0; k < 10; k++) c->kv[k] = p.krylov ? cv.take<double>(c->lv[0].VL) : nullptr;
+    for (int k = 0; k < 12; k++)
+        c->adjv[k] = (p.adjoint && p.cn_buffers && k < 4 + ADJ_KMAX - 1) ? cv.take<double>(c->lv[0].VL) : nullptr;
     c->ks = cv.take<double>(8);
     c->kpart = cv.take<double>(2 * 1024);
     const Level &lc = c->lv[L - 1];
@@ -931,6 +939,78 @@ gp_status mg_solve_t(gp_ctx *ctx, double *lam, const double *c, double tol, gp_r
     int s = solve_t(&ctx->c, lam, c, tol, rep);
     gp_status cs = check_cuda(ctx, "mg_solve_t");
     return cs != GP_OK ? cs : (gp_status)s;
+}
+
+gp_status cn_step_adjoint(gp_ctx *ctx, int step, const double *x_m, const double *f, double dt, double Re,
+                          const gp_body *body, double amp, const gp_walls *walls, double tol, int kmax,
+                          const double *xbar_next, double *xbar_m, double *nbar0, double *nbar1, double *nbar2,
+                          double *fbar, double *abar)
+{
+    if (!ctx || !x_m || !xbar_next || !xbar_m || !nbar0 || !nbar1 || !nbar2 || !fbar || !abar || step < 0 ||
+        !(dt > 0.0) || !(Re > 0.0) || !(tol >= 0.0))
+        return GP_INVALID;
+    Ctx *c = &ctx->c;
+    if (!c->adjv[0]) return fail(ctx, GP_INVALID, "cn_step_adjoint needs gp_params.adjoint and cn_buffers");
+    if (step < 2 && (kmax < 1 || kmax > ADJ_KMAX)) return fail(ctx, GP_INVALID, "kmax must be 1..8 for Picard steps");
+    if (!c->geom_ok) return fail(ctx, GP_INVALID, "geometry_build has not succeeded");
+    c->prm.alpha = dt / (2.0 * Re);
+    gp_status st = adjoint_ready(ctx, 0, false);
+    if (st != GP_OK) return st;
+    const Level &l0 = c->lv[0];
+    const long long VL = l0.VL;
+    gp_body unit = body ? *body : gp_body{0, 0, 0, 0, 0};
+    gp_body bamp = {amp * unit.U, amp * unit.V, amp * unit.omega, unit.cx, unit.cy};
+    gp_walls wl = walls ? *walls : gp_walls{0, 0, 0, 0};
+    const gp_walls nowalls = {0, 0, 0, 0};
+    double *lam = c->adjv[0], *el = c->adjv[1], *g = c->adjv[2], *xb = c->adjv[3];
+    // g: the rigid-body velocity at unit amplitude on the Eq. (BCu) rows
+    cudaMemsetAsync(el, 0, VL * sizeof(double), c->stream);
+    cn_rhs(c, el, el, nullptr, dt, nullptr, unit, nowalls, g);
+    cn_copy(c, xbar_next, xb, VL);
+    const int K = step >= 2 ? 1 : kmax;
+    const double *X[ADJ_KMAX];
+    X[0] = x_m;
+    if (step < 2) {
+        // the Picard iterates x^(1..K-1) of the forward step, recomputed
+        cn_convective(c, x_m, nullptr, c->cn_Nn, 0);
+        cn_copy(c, c->cn_Nn, c->cn_Nh, VL);
+        for (int k = 1; k < K; k++) {
+            double *xk = c->adjv[3 + k];
+            cn_copy(c, X[k - 1], xk, VL);
+            cn_rhs(c, x_m, c->cn_Nh, f, dt, nullptr, bamp, wl, c->cn_b);
+            st = mg_solve(ctx, xk, c->cn_b, tol, nullptr);
+            if (st != GP_OK) return st;
+            cn_convective(c, xk, c->cn_Nn, c->cn_Nh, 1);
+            X[k] = xk;
+        }
+    }
+    double ga = 0.0, acc = 0.0;
+    for (int k = K - 1; k >= 0; k--) {
+        cudaMemsetAsync(lam, 0, VL * sizeof(double), c->stream);
+        int s = solve_t(c, lam, xb, tol, nullptr);
+        if (s != GP_OK) return (gp_status)s;
+        cn_mask_mom(c, lam, el);
+        cn_dot_rows(c, g, lam, c->red + 7);
+        cudaMemcpyAsync(&ga, c->red + 7, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess) return check_cuda(ctx, "cn_step_adjoint");
+        acc += ga;
+        cn_explicit_t(c, lam, xbar_m);
+        if (step >= 2) {
+            cn_axpy4(c, el, fbar, dt, nbar0, -dt, nbar1, -0.5 * dt, nbar2, 0.5 * dt);
+        } else if (k >= 1) {
+            cn_axpy4(c, el, fbar, dt, nbar0, -0.5 * dt, nullptr, 0.0, nullptr, 0.0);
+            // the iterate's share: xbar^(k) = J_N(x^(k))^T (-dt/2 E lam)
+            cudaMemsetAsync(xb, 0, VL * sizeof(double), c->stream);
+            cudaMemsetAsync(c->cn_Nh, 0, VL * sizeof(double), c->stream);
+            cn_axpy4(c, el, c->cn_Nh, -0.5 * dt, nullptr, 0.0, nullptr, 0.0, nullptr, 0.0);
+            cn_convective_jt(c, X[k], c->cn_Nh, xb);
+        } else {
+            cn_axpy4(c, el, fbar, dt, nbar0, -dt, nullptr, 0.0, nullptr, 0.0);
+        }
+    }
+    cn_convective_jt(c, x_m, nbar0, xbar_m);
+    *abar += acc;
+    return check_cuda(ctx, "cn_step_adjoint");
 }
 
 }  // extern "C"

@@ -111,6 +111,8 @@ SIGNATURES = [
     ("gp_prolong_t", _I, [_VP, _I, _VP, _VP]),
     ("gp_cycle_t", _I, [_VP, _VP, _VP]),
     ("mg_solve_t", _I, [_VP, _VP, _VP, _D, _P(gp_report)]),
+    ("cn_step_adjoint", _I, [_VP, _I, _VP, _VP, _D, _D, _P(gp_body), _D, _P(gp_walls), _D, _I, _VP, _VP, _VP, _VP,
+                             _VP, _VP, _P(_D)]),
     ("gp_launch_count", ctypes.c_int64, [_VP]),
     ("gp_timer_start", _I, [_VP, _I, _I]),
     ("gp_timer_stop", _I, [_VP, _P(ctypes.c_int64), _P(_D)]),
@@ -387,6 +389,18 @@ class Solver:
         st = self.L.mg_solve_t(self.ctx, _ptr(lam), _ptr(c), tol, ctypes.byref(rep))
         hist_arr = np.array(h[:rep.iterations + 1]) if hist else None
         return st, rep, hist_arr
+
+    def cn_step_adjoint(self, step, xm, dt, Re, xbar_next, xbar_m, nb, fbar, f=None, body=(0, 0, 0, 0, 0), amp=1.0,
+                        walls=(0, 0, 0, 0), tol=1e-11, kmax=4):
+        """Backward pass of one CN step (see cn_step_adjoint in gpmg.h);
+        xbar_m, nb[0..2] and fbar are updated in place; returns dL/damp of
+        this step."""
+        bd, wl = gp_body(*body), gp_walls(*walls)
+        ab = ctypes.c_double(0.0)
+        self._check(self.L.cn_step_adjoint(self.ctx, step, _ptr(xm), self._opt(f), dt, Re, ctypes.byref(bd), amp,
+                                           ctypes.byref(wl), tol, kmax, _ptr(xbar_next), _ptr(xbar_m), _ptr(nb[0]),
+                                           _ptr(nb[1]), _ptr(nb[2]), _ptr(fbar), ctypes.byref(ab)), "cn_step_adjoint")
+        return ab.value
 
     # ------------------------------------------------ Crank-Nicolson step
     @staticmethod
