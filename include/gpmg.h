@@ -278,7 +278,7 @@ gp_status gp_cn_rhs(gp_ctx *ctx, const double *xn, const double *Nh, const doubl
  * zero is a linear map B of b whose stages (box solves, ghost Jacobi steps,
  * the (xi, mean) update, the coarse-grid correction P B_H R) each add
  * Q (b - M x); B^T is the cycle for M^T with the stages in reverse order and
- * each Q transposed (transposed box matrices, cut colours 24..0 then full
+ * each Q transposed (transposed box matrices, cut colours in reverse then full
  * colours 4..0, ghost sweeps before the (xi, mean) step, post- before
  * pre-relaxations, P^T as restriction, R^T as interpolation, the coarsest
  * solve with the transposed inverse).  Rows of M^T at inactive nodes (only

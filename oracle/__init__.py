@@ -87,6 +87,8 @@ def lib():
             L.or_prolong_t.argtypes = [vp, i, P(d), P(d)]
             L.or_cycle_t.argtypes = [vp, i, P(d), P(d)]
             L.or_solve_t.argtypes = [vp, P(d), P(d), d, i, P(d), P(i)]
+            L.or_cut_colours.argtypes = [vp, i, P(i)]
+            L.or_cut_colours.restype = i
             L.or_convective_jt.argtypes = [vp, P(d), P(d), P(d)]
             L.or_explicit_t.argtypes = [vp, P(d), P(d)]
             L.or_cn_step_adjoint.argtypes = [vp, i, P(d), vp, d, P(d), d, P(d), d, i, P(d), P(d), P(d), P(d),
@@ -320,6 +322,14 @@ class Oracle:
         nc = ctypes.c_int(0)
         st = self.L.or_solve_t(self.c, _p(lam2), _p(cc), tol, max_cycles, _p(hist), ctypes.byref(nc))
         return st, lam2, hist[:nc.value + 1]
+
+    def cut_colours(self, lev=0):
+        """(number of colours, colour of every cell j N + i or -1) of the cut
+        cells of level lev."""
+        Nl = self.N >> lev
+        out = np.zeros(Nl * Nl, dtype=np.int32)
+        nc = self.L.or_cut_colours(self.c, lev, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+        return nc, out
 
     def convective_jt(self, x, y):
         """J_N(x)^T y (transpose of the linearised convective term at x)."""

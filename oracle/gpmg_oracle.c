@@ -114,6 +114,9 @@ typedef struct {
     double *cval;
     double *lut;
     int *pivt;
+    /* colour of every cut cell (cell j N + i; -1 for other cells) */
+    int *cutcol;
+    int ncutcol;
 } level_t;
 
 typedef struct {
@@ -381,7 +384,7 @@ static void free_level(level_t *l)
 {
     free(l->tU); free(l->tV); free(l->tP); free(l->gid); free(l->prim); free(l->gh);
     free(l->lu); free(l->piv); free(l->x); free(l->b); free(l->r);
-    free(l->cptr); free(l->crow); free(l->cval); free(l->lut); free(l->pivt);
+    free(l->cptr); free(l->crow); free(l->cval); free(l->lut); free(l->pivt); free(l->cutcol);
     memset(l, 0, sizeof *l);
 }
 
@@ -731,6 +734,8 @@ int or_num_ghosts(void *vc, int lev) { return ((ctx_t *)vc)->lv[lev].ngh; }
 static int factor_coarsest(ctx_t *c);
 
 /* phi: (2N+1)^2 half lattice, row b (y) major, paper sign (phi > 0 in the object) */
+static int cut_colouring(ctx_t *c, int lev);
+
 int or_geometry(void *vc, const double *phi)
 {
     ctx_t *c = (ctx_t *)vc;
@@ -744,6 +749,8 @@ int or_geometry(void *vc, const double *phi)
         free(l->gh); l->gh = NULL; l->ngh = 0;
         if (!classify_level(c, k)) return OR_GEOMETRY;
     }
+    for (int k = 0; k < c->L; k++)
+        if (!cut_colouring(c, k)) return OR_GEOMETRY;
     int st = factor_coarsest(c);
     if (st != OR_OK) return st;
     c->geom_ok = 1;
@@ -999,6 +1006,104 @@ static int cut_cell(level_t *l, int i, int j)
            ttype(l, G_V, i, j) == T_GHOST || ttype(l, G_V, i, j + 1) == T_GHOST;
 }
 
+/* The unknowns of the box of cell (i, j): its faces that are internal or
+ * ghosts of the object, then p (as box_relax). */
+static int box_unknowns(level_t *l, int i, int j, int *gg, int *ii, int *jj, int *unk)
+{
+    const int fg[4] = {G_U, G_U, G_V, G_V};
+    const int fi[4] = {i, i + 1, i, i};
+    const int fj[4] = {j, j, j, j + 1};
+    int nu = 0;
+    for (int f = 0; f < 4; f++) {
+        int t = ttype(l, fg[f], fi[f], fj[f]);
+        if (t == T_INTERNAL || t == T_GHOST) {
+            gg[nu] = fg[f]; ii[nu] = fi[f]; jj[nu] = fj[f];
+            unk[nu] = iG(l, fg[f], fi[f], fj[f]);
+            nu++;
+        }
+    }
+    gg[nu] = G_P; ii[nu] = i; jj[nu] = j; unk[nu] = iP(l, i, j);
+    return nu + 1;
+}
+
+#define OR_MAXCUTCOL 64
+
+/* Colours of the cut cells: two cut boxes conflict when a row of one
+ * references an unknown of the other (their updates then depend on the order);
+ * cells are coloured in lexicographic order (j, then i), each with the
+ * smallest colour that no conflicting cell coloured before it has.  Boxes of
+ * one colour are then independent. */
+static int cut_colouring(ctx_t *c, int lev)
+{
+    level_t *l = &c->lv[lev];
+    int N = l->N, n = l->n;
+    free(l->cutcol);
+    l->cutcol = (int *)malloc(sizeof(int) * (size_t)N * N);
+    for (int k = 0; k < N * N; k++) l->cutcol[k] = -1;
+    int *cells = (int *)malloc(sizeof(int) * (size_t)N * N), nc = 0;
+    for (int j = 0; j < N; j++)
+        for (int i = 0; i < N; i++)
+            if (ttype(l, G_P, i, j) == T_INTERNAL && cut_cell(l, i, j)) cells[nc++] = j * N + i;
+    /* owners of every unknown (a face belongs to at most two boxes) */
+    int *own = (int *)malloc(sizeof(int) * 2 * (size_t)n);
+    for (int k = 0; k < 2 * n; k++) own[k] = -1;
+    int gg[5], ii[5], jj[5], unk[5];
+    for (int a = 0; a < nc; a++) {
+        int nu = box_unknowns(l, cells[a] % N, cells[a] / N, gg, ii, jj, unk);
+        for (int q = 0; q < nu; q++) {
+            int *o = own + 2 * (size_t)unk[q];
+            if (o[0] < 0) o[0] = a;
+            else o[1] = a;
+        }
+    }
+    /* conflict lists: for every referenced column, its owners */
+    int cap = 64, *nb = (int *)malloc(sizeof(int) * (size_t)nc * cap), *nnb = (int *)calloc(nc, sizeof(int));
+    int ok = 1;
+    for (int a = 0; a < nc && ok; a++) {
+        int nu = box_unknowns(l, cells[a] % N, cells[a] / N, gg, ii, jj, unk);
+        for (int q = 0; q < nu && ok; q++) {
+            row_t R;
+            get_row(c, lev, gg[q], ii[q], jj[q], &R);
+            for (int e = 0; e < R.n && ok; e++) {
+                if (R.col[e] >= n - 1) continue; /* xi: no box owns it */
+                for (int w = 0; w < 2; w++) {
+                    int bcell = own[2 * (size_t)R.col[e] + w];
+                    if (bcell < 0 || bcell == a) continue;
+                    /* add the edge both ways (once) */
+                    int pairs[2][2] = {{a, bcell}, {bcell, a}};
+                    for (int z = 0; z < 2; z++) {
+                        int x0 = pairs[z][0], y0 = pairs[z][1], dup = 0;
+                        for (int t = 0; t < nnb[x0]; t++)
+                            if (nb[(size_t)x0 * cap + t] == y0) { dup = 1; break; }
+                        if (dup) continue;
+                        if (nnb[x0] >= cap) { ok = 0; break; }
+                        nb[(size_t)x0 * cap + nnb[x0]++] = y0;
+                    }
+                }
+            }
+        }
+    }
+    int ncol = 0;
+    int *col = (int *)malloc(sizeof(int) * (nc > 0 ? nc : 1));
+    for (int a = 0; a < nc && ok; a++) {
+        unsigned long long used = 0ull;
+        for (int t = 0; t < nnb[a]; t++) {
+            int bcell = nb[(size_t)a * cap + t];
+            if (bcell < a) used |= 1ull << col[bcell];
+        }
+        int cc = 0;
+        while (cc < OR_MAXCUTCOL && (used >> cc & 1ull)) cc++;
+        if (cc >= OR_MAXCUTCOL) { ok = 0; break; }
+        col[a] = cc;
+        if (cc + 1 > ncol) ncol = cc + 1;
+        l->cutcol[cells[a]] = cc;
+    }
+    l->ncutcol = ncol;
+    free(cells); free(own); free(nb); free(nnb); free(col);
+    if (!ok) seterr(c, "cut-cell colouring exceeded its limits");
+    return ok;
+}
+
 static void shuffle(ctx_t *c, int *v, int n)
 {
     for (int k = n - 1; k > 0; k--) {
@@ -1009,9 +1114,9 @@ static void shuffle(ctx_t *c, int *v, int n)
 
 /* One box sweep over the internal cells: cells with no ghost border in five
  * colours (i + 3 j) mod 5, then cells with a ghost border (their boxes reach
- * up to four nodes through the ghost rows) in 25 colours (i mod 5, j mod 5);
- * boxes of one colour never touch each other's unknowns.  Then a point-Jacobi
- * update of internal faces that belong to no internal cell. */
+ * further through the ghost rows) in the colours of cut_colouring; boxes of
+ * one colour never touch each other's unknowns.  Then a point-Jacobi update
+ * of internal faces that belong to no internal cell. */
 void or_box_sweep(void *vc, int lev, double *x, const double *b)
 {
     ctx_t *c = (ctx_t *)vc;
@@ -1032,12 +1137,11 @@ void or_box_sweep(void *vc, int lev, double *x, const double *b)
             if (c->order_mode == 1) shuffle(c, cells, nc); /* random order inside a colour */
             for (int k = 0; k < nc; k++) box_relax(c, lev, x, b, cells[k] % N, cells[k] / N);
         }
-        for (int col = 0; col < 25; col++) {
+        for (int col = 0; col < l->ncutcol; col++) {
             int nc = 0;
             for (int j = 0; j < N; j++)
                 for (int i = 0; i < N; i++)
-                    if ((j % 5) * 5 + (i % 5) == col && ttype(l, G_P, i, j) == T_INTERNAL && cut_cell(l, i, j))
-                        cells[nc++] = j * N + i;
+                    if (l->cutcol[j * N + i] == col) cells[nc++] = j * N + i;
             if (c->order_mode == 1) shuffle(c, cells, nc);
             for (int k = 0; k < nc; k++) box_relax(c, lev, x, b, cells[k] % N, cells[k] / N);
         }
@@ -1682,8 +1786,9 @@ static void box_relax_t(ctx_t *c, int lev, double *lam, const double *cc, int i,
     for (int r = 0; r < nu; r++) lam[unk[r]] += rhs[r];
 }
 
-/* the transposed box sweep: the lonely faces, then the cut cells in colours
- * 24..0, then the other cells in colours 4..0 (colour-by-colour ordering) */
+/* the transposed box sweep: the lonely faces, then the cut cells in their
+ * colours in reverse, then the other cells in colours 4..0 (colour-by-colour
+ * ordering) */
 void or_box_sweep_t(void *vc, int lev, double *lam, const double *cc)
 {
     ctx_t *c = (ctx_t *)vc;
@@ -1714,11 +1819,10 @@ void or_box_sweep_t(void *vc, int lev, double *lam, const double *cc)
     for (int k = 0; k < cnt; k++) lam[idx[k]] += upd[k];
     free(idx);
     free(upd);
-    for (int col = 24; col >= 0; col--)
+    for (int col = l->ncutcol - 1; col >= 0; col--)
         for (int j = 0; j < N; j++)
             for (int i = 0; i < N; i++)
-                if ((j % 5) * 5 + (i % 5) == col && ttype(l, G_P, i, j) == T_INTERNAL && cut_cell(l, i, j))
-                    box_relax_t(c, lev, lam, cc, i, j);
+                if (l->cutcol[j * N + i] == col) box_relax_t(c, lev, lam, cc, i, j);
     for (int col = 4; col >= 0; col--)
         for (int j = 0; j < N; j++)
             for (int i = 0; i < N; i++)
@@ -2124,4 +2228,15 @@ int or_cn_step_adjoint(void *vc, int step, const double *xm, const double *f, do
     }
     free(g); free(zero); free(lam); free(el); free(xb); free(hist);
     return st;
+}
+
+/* colours of the cut cells of level lev (cell j N + i, -1 for other cells);
+ * returns the number of colours */
+int or_cut_colours(void *vc, int lev, int *out)
+{
+    ctx_t *c = (ctx_t *)vc;
+    level_t *l = &c->lv[lev];
+    if (!c->geom_ok || !l->cutcol) return -1;
+    memcpy(out, l->cutcol, sizeof(int) * (size_t)l->N * l->N);
+    return l->ncutcol;
 }

@@ -5,7 +5,7 @@
 // A cycle from x = 0 is a linear map B of b made of stages that each add
 // Q (b - M x); its transpose is the cycle for M^T with the stages in reverse
 // order and each Q transposed: ghost Jacobi sweeps before the (xi, mean)
-// step, the lonely faces, the cut boxes in colours 24..0, the full boxes in
+// step, the lonely faces, the cut boxes in reverse colour order, the full boxes in
 // colours 4..0, post- before pre-relaxations, P^T as restriction, R^T as
 // interpolation, and the coarsest solve with the transposed inverse.  Rows of
 // M^T at inactive nodes involve only ghost-row terms and are solved exactly
@@ -700,7 +700,7 @@ void box_sweep_t(Ctx *c, int lev, double *lam, const double *cc)
         k_apply_upd<<<nb, 128, 0, st>>>(l.lonely, c->part, l.h_nlonely, lam);
         c->launches += 2;
     }
-    for (int colour = 24; colour >= 0; colour--) {
+    for (int colour = l.cut.ncol - 1; colour >= 0; colour--) {
         int beg = l.h_cutoff[colour], end = l.h_cutoff[colour + 1];
         if (end <= beg) continue;
         k_box_cut_t<<<(end - beg + 127) / 128, 128, 0, st>>>(A, l, lam, cc, beg, end);

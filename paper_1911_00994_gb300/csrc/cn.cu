@@ -10,7 +10,8 @@
 
 namespace gpmg {
 
-// N = u . grad u at internal u and v nodes, zero on the other u, v slots.
+// N = u . grad u at internal u and v nodes, zero on every other slot of the
+// vector (the p frame and the scalars included).
 // mode 0: out = N(x); mode 1: out = (Nn + N(x)) / 2
 __global__ void k_convective(int P, long long F, double h, const uint8_t *tU, const uint8_t *tV, const double *x,
                              const double *Nn, double *out, int mode)
@@ -37,6 +38,8 @@ __global__ void k_convective(int P, long long F, double h, const uint8_t *tU, co
     }
     out[s] = nu;
     out[F + s] = nv;
+    out[2 * F + s] = 0.0;
+    if (row == 0 && col < NSCAL) out[3 * F + col] = 0.0;
 }
 
 // Nh = Nn + N1/2 - N2/2 on the u, v frames

@@ -747,6 +747,7 @@ int build_geometry_levels(Ctx *c, const double *phi_in, int phi_fluid_positive)
         cudaMemcpyAsync(&l.h_nint, l.nint, sizeof(int), cudaMemcpyDeviceToHost, st);
         if (cuda_fail(c, cudaStreamSynchronize(st), "geometry")) return GP_CUDA;
         l.h_ncut = l.h_cutoff[25];
+        l.cut.ncol = 25;  // recoloured once the rows of the cut boxes are prepared
         if (l.h_ncut > l.cut.cap) {
             snprintf(c->msg, sizeof c->msg, "level %d: %d cut cells exceed the capacity %d", lev, l.h_ncut, l.cut.cap);
             return GP_GEOMETRY;

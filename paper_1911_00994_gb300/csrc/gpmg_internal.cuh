@@ -26,6 +26,7 @@ enum RowKind : uint8_t { K_BCU = 0, K_EXTRAP = 1, K_COPY = 2, K_WALL = 3, K_BOXG
 constexpr int MAX_LEVELS = 16;
 constexpr int MAX_MARCH = 64;
 constexpr int NSCAL = 32;
+constexpr int MAX_CUTCOL = 64;  // colours of the cut boxes
 constexpr int ADJ_KMAX = 8;  // Picard iterations cn_step_adjoint can differentiate
 constexpr int GH_ST = 9;  // stencil slots per ghost row
 
@@ -56,11 +57,11 @@ struct GhostList {
     int cap;
 };
 
-// cut cells (internal cells with a ghost border) sorted by 25 colours
+// cut cells (internal cells with a ghost border) sorted by colour (recolour_cuts)
 constexpr int CUT_ST = 9;  // stencil entries per box row
 struct CutList {
     int *count;        // device [1]
-    int *off;          // device [26] colour offsets
+    int *off;          // device [MAX_CUTCOL + 1] colour offsets
     int *cell;         // slot of the cell (row * P + col)
     int *gface;        // [4][cap] ghost-list index of face W, E, S, N (or -1)
     // box rows prepared for the current alpha (k_cut_prepare): for row
@@ -74,6 +75,7 @@ struct CutList {
     double *minv;      // [25][cap]
     float *minvf;
     int cap;
+    int ncol;          // colours (the list is sorted by colour)
 };
 
 struct Level {
@@ -97,7 +99,7 @@ struct Level {
     int h_nghost;      // host copies after geometry_build
     int h_nrows;
     int h_ncut;
-    int h_cutoff[26];
+    int h_cutoff[MAX_CUTCOL + 1];
     int h_nlonely;
     // adjoint (carved when gp_params.adjoint is set): the columns of M
     // referenced by ghost-class rows, sorted, each with its (row node,

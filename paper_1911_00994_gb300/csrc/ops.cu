@@ -3,9 +3,13 @@
 // interpolation), in FP64 and FP32.
 #include <cuda.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <mutex>
+#include <unordered_map>
+#include <utility>
+#include <vector>
 
 #include "gpmg_internal.cuh"
 
@@ -13,10 +17,10 @@ namespace gpmg {
 
 // levels solved by the one-block smoother, ghost lists swept by one block,
 // and levels whose full boxes are swept by shared-memory tiles
-constexpr int SMALL_N = 64;
+constexpr int SMALL_N = 64;  // levels whose whole relaxation runs in one block
 constexpr int TILE_MIN_N = 512;  // default finest size swept by TMA tiles (gp_params.tile_min overrides)
 constexpr int GHOST_BLOCK_ROWS = 4096;
-constexpr int CUT_SPLIT = 64;  // cut boxes per colour above which each colour gets its own multi-block launch
+constexpr int CUT_SPLIT = 64;  // cut boxes per colour above which the cut sweep runs on a cluster of CTAs
 
 // constants of the box solves of one level (Sect. 4.1.1), reciprocals
 // precomputed so that a box needs no division
@@ -62,43 +66,102 @@ template <> struct AbsBits<double> {
     __device__ static double value(U u) { return __longlong_as_double((long long)u); }
 };
 
-// internal and inactive rows; ghost-class rows come from k_ghost_residual.
-// r may be of a narrower type than the arithmetic (FP64 residual written as
-// the FP32 right-hand side of the next inner cycle).  per block: [0] sum of p
-// over internal cells, [1] max |r|
+// 16-byte vector loads and stores of four consecutive slots (the slot is a
+// multiple of 4 and every frame starts 128-byte aligned)
+__device__ __forceinline__ void ld4(const float *p, float *o)
+{
+    float4 t = *(const float4 *)p;
+    o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+}
+__device__ __forceinline__ void ld4(const double *p, double *o)
+{
+    double2 a = *(const double2 *)p, c = *(const double2 *)(p + 2);
+    o[0] = a.x; o[1] = a.y; o[2] = c.x; o[3] = c.y;
+}
+__device__ __forceinline__ void st4(float *p, const float *o) { *(float4 *)p = make_float4(o[0], o[1], o[2], o[3]); }
+__device__ __forceinline__ void st4(double *p, const double *o)
+{
+    *(double2 *)p = make_double2(o[0], o[1]);
+    *(double2 *)(p + 2) = make_double2(o[2], o[3]);
+}
+__device__ __forceinline__ void ldt4(const uint8_t *p, uint8_t *o)
+{
+    uchar4 t = *(const uchar4 *)p;
+    o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+}
+
+// The residual of the internal rows (Eq. LS, Sect. 3.2) on four consecutive
+// slots per thread: one vector load per frame and neighbour row, all loads of
+// a quad issued before the arithmetic.  r may be of a narrower type than the
+// arithmetic (the FP64 residual written as the FP32 right-hand side of the
+// next inner cycle).  Per block: [0] sum of p over internal cells, [1] max |r|.  Slots that are not internal get 0 (the
+// ghost-class rows are written afterwards by k_ghost_residual); rows 0 and
+// N + 1 of the frames hold no internal row.
 template <typename T, typename R>
-__global__ void k_residual(LevelArgs<T> A, const T *x, const T *b, R *r, double *part)
+__global__ void __launch_bounds__(256) k_residual4(LevelArgs<T> A, const T *x, const T *b, R *r, double *part)
 {
     T psum = 0;
     typename AbsBits<T>::U rbits = 0;
-    const long long nslot = (long long)(A.N + 2) * A.P;
-    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < nslot; s += (long long)gridDim.x * blockDim.x) {
-        const T *u = x, *v = x + A.F, *p = x + 2 * A.F;
-        T xi = x[3 * A.F];
-        uint8_t tu = A.tU[s], tv = A.tV[s], tp = A.tP[s];
-        if (tu == T_INTERNAL) {
-            T Au = A.d * u[s] - A.a * (u[s + 1] + u[s - 1] + u[s + A.P] + u[s - A.P]) + A.q * (p[s] - p[s - 1]);
-            T rr = b[s] - Au;
-            r[s] = (R)rr;
-            rbits = max(rbits, AbsBits<T>::of(rr));
-        } else if (tu == T_INACTIVE) r[s] = 0;
-        if (tv == T_INTERNAL) {
-            long long sv = A.F + s;
-            T Av = A.d * v[s] - A.a * (v[s + 1] + v[s - 1] + v[s + A.P] + v[s - A.P]) + A.q * (p[s] - p[s - A.P]);
-            T rr = b[sv] - Av;
-            r[sv] = (R)rr;
-            rbits = max(rbits, AbsBits<T>::of(rr));
-        } else if (tv == T_INACTIVE) r[A.F + s] = 0;
-        if (tp == T_INTERNAL) {
-            long long sp = 2 * A.F + s;
-            T Ac = A.q * (u[s + 1] - u[s] + v[s + A.P] - v[s]) - xi;
-            T rr = b[sp] - Ac;
-            r[sp] = (R)rr;
-            rbits = max(rbits, AbsBits<T>::of(rr));
-            psum += p[s];
-        } else if (tp == T_INACTIVE) r[2 * A.F + s] = 0;
+    const int P = A.P;
+    const long long F = A.F, nq = (long long)(A.N + 2) * P / 4;
+    const T *u = x, *v = x + F, *p = x + 2 * F;
+    const T xi = x[3 * F];
+    for (long long qd = blockIdx.x * (long long)blockDim.x + threadIdx.x; qd < nq; qd += (long long)gridDim.x * blockDim.x) {
+        const long long s0 = 4 * qd;
+        const int row = (int)(s0 / P);
+        R ru[4] = {0, 0, 0, 0}, rv[4] = {0, 0, 0, 0}, rp[4] = {0, 0, 0, 0};
+        uint8_t tu[4], tv[4], tp[4];
+        ldt4(A.tU + s0, tu);
+        ldt4(A.tV + s0, tv);
+        ldt4(A.tP + s0, tp);
+        bool any = false;
+#pragma unroll
+        for (int q = 0; q < 4; q++) any |= tu[q] == T_INTERNAL || tv[q] == T_INTERNAL || tp[q] == T_INTERNAL;
+        if (any && row > 0 && row < A.N + 1) {
+            T uh[6], uU[4], uD[4], vh[6], vU[4], vD[4], ph[5], pD[4], bu[4], bv[4], bp[4];
+            ld4(u + s0, uh + 1);
+            uh[0] = u[s0 - 1];
+            uh[5] = u[s0 + 4];
+            ld4(u + s0 + P, uU);
+            ld4(u + s0 - P, uD);
+            ld4(v + s0, vh + 1);
+            vh[0] = v[s0 - 1];
+            vh[5] = v[s0 + 4];
+            ld4(v + s0 + P, vU);
+            ld4(v + s0 - P, vD);
+            ld4(p + s0, ph + 1);
+            ph[0] = p[s0 - 1];
+            ld4(p + s0 - P, pD);
+            ld4(b + s0, bu);
+            ld4(b + F + s0, bv);
+            ld4(b + 2 * F + s0, bp);
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                if (tu[q] == T_INTERNAL) {
+                    T Au = A.d * uh[q + 1] - A.a * (uh[q + 2] + uh[q] + uU[q] + uD[q]) + A.q * (ph[q + 1] - ph[q]);
+                    T rr = bu[q] - Au;
+                    ru[q] = (R)rr;
+                    rbits = max(rbits, AbsBits<T>::of(rr));
+                }
+                if (tv[q] == T_INTERNAL) {
+                    T Av = A.d * vh[q + 1] - A.a * (vh[q + 2] + vh[q] + vU[q] + vD[q]) + A.q * (ph[q + 1] - pD[q]);
+                    T rr = bv[q] - Av;
+                    rv[q] = (R)rr;
+                    rbits = max(rbits, AbsBits<T>::of(rr));
+                }
+                if (tp[q] == T_INTERNAL) {
+                    T Ac = A.q * (uh[q + 2] - uh[q + 1] + vU[q] - vh[q + 1]) - xi;
+                    T rr = bp[q] - Ac;
+                    rp[q] = (R)rr;
+                    rbits = max(rbits, AbsBits<T>::of(rr));
+                    psum += ph[q + 1];
+                }
+            }
+        }
+        st4(r + s0, ru);
+        st4(r + F + s0, rv);
+        st4(r + 2 * F + s0, rp);
     }
-    // block reduction (fixed shape: deterministic)
     __shared__ double ss[256], sm[256];
     ss[threadIdx.x] = (double)psum;
     sm[threadIdx.x] = AbsBits<T>::value(rbits);
@@ -598,24 +661,59 @@ template <typename T> __device__ __forceinline__ void box_cut_warp(T *x, const T
     if (lane < 5 && row >= 0) x[row] += d;
 }
 
-// one colour of the cut boxes, a warp per box, over as many blocks as needed
-template <typename T> __global__ void __launch_bounds__(256) k_box_cut_colour(T *x, const T *b, CutList cut, int beg, int end)
-{
-    const int k = beg + (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
-    if (k < end) box_cut_warp<T>(x, b, cut, k, threadIdx.x & 31);
-}
-
-// all 25 colours (i mod 5, j mod 5) of the cut boxes in one block of 32
+// all colours of the cut boxes in one block of 32
 // warps: the barrier between colours orders them; boxes of one colour are
 // independent
 template <typename T>
 __global__ void __launch_bounds__(1024) k_box_cut(LevelArgs<T> A, T *x, const T *b, CutList cut, GhostList gh)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int colour = 0; colour < 25; colour++) {
+    for (int colour = 0; colour < cut.ncol; colour++) {
         int beg = cut.off[colour], end = cut.off[colour + 1];
         for (int k = beg + warp; k < end; k += nw) box_cut_warp<T>(x, b, cut, k, lane);
         __syncthreads();
+    }
+}
+
+// ------------------------------------------------------- cluster kernels
+// The CTAs of a thread-block cluster are scheduled together and share a
+// hardware barrier, so phases that must follow one another (the colours of
+// the cut boxes) run in one launch over several SMs instead of one launch per
+// phase.  Ghost sweeps and whole small-level relaxations were measured slower
+// on a cluster (its SMs limit the memory parallelism of their gathers).
+constexpr int CL_CTAS = 8;        // CTAs per cluster (the portable maximum)
+constexpr int CL_THREADS = 1024;  // threads per CTA
+
+__device__ __forceinline__ unsigned cl_rank()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ unsigned cl_size()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+
+// every thread of the cluster: writes before it are seen by reads after it
+__device__ __forceinline__ void cl_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// all colours of the cut boxes, a warp per box over the whole cluster
+template <typename T> __global__ void __launch_bounds__(CL_THREADS) k_box_cut_cluster(T *x, const T *b, CutList cut)
+{
+    const int lane = threadIdx.x & 31;
+    const int wpc = blockDim.x >> 5;
+    const int gw = (int)cl_rank() * wpc + (threadIdx.x >> 5), nw = (int)cl_size() * wpc;
+    for (int colour = 0; colour < cut.ncol; colour++) {
+        const int beg = cut.off[colour], end = cut.off[colour + 1];
+        for (int k = beg + gw; k < end; k += nw) box_cut_warp<T>(x, b, cut, k, lane);
+        cl_sync();
     }
 }
 
@@ -649,15 +747,29 @@ template <typename T>
 __global__ void k_scalar_partial(LevelArgs<T> A, const T *x, const T *b, double *part)
 {
     T s = 0, m = 0;
-    const long long nslot = (long long)(A.N + 2) * A.P;
-    for (long long sl = blockIdx.x * (long long)blockDim.x + threadIdx.x; sl < nslot;
-         sl += (long long)gridDim.x * blockDim.x) {
-        if (A.tP[sl] == T_INTERNAL) {
-            const T *u = x, *v = x + A.F;
-            T div = (u[sl + 1] - u[sl] + v[sl + A.P] - v[sl]) * A.q;
-            s += div - b[2 * A.F + sl];
-            m += x[2 * A.F + sl];
-        }
+    const long long nq = (long long)(A.N + 2) * A.P / 4;
+    const T *u = x, *v = x + A.F, *p = x + 2 * A.F;
+    // four consecutive cells per thread, vector loads (internal cells lie in
+    // frame rows 1..N, so the loads one row up stay in the frame)
+    for (long long qd = blockIdx.x * (long long)blockDim.x + threadIdx.x; qd < nq; qd += (long long)gridDim.x * blockDim.x) {
+        const long long s0 = 4 * qd;
+        uint8_t tp[4];
+        ldt4(A.tP + s0, tp);
+        if (tp[0] != T_INTERNAL && tp[1] != T_INTERNAL && tp[2] != T_INTERNAL && tp[3] != T_INTERNAL) continue;
+        T uh[5], v4[4], vU[4], bc[4], p4[4];
+        ld4(u + s0, uh);
+        uh[4] = u[s0 + 4];
+        ld4(v + s0, v4);
+        ld4(v + s0 + A.P, vU);
+        ld4(b + 2 * A.F + s0, bc);
+        ld4(p + s0, p4);
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+            if (tp[q] == T_INTERNAL) {
+                T div = (uh[q + 1] - uh[q] + vU[q] - v4[q]) * A.q;
+                s += div - bc[q];
+                m += p4[q];
+            }
     }
     __shared__ double ss[256], sm[256];
     ss[threadIdx.x] = (double)s;
@@ -704,14 +816,23 @@ __global__ void k_scalar_final(const double *part, int nb, T *x, const T *b, lon
     }
 }
 
+// p += shift on internal and ghost cells, four consecutive slots per thread
 template <typename T> __global__ void k_pshift(LevelArgs<T> A, T *x, const double *shift)
 {
-    int col = blockIdx.x * blockDim.x + threadIdx.x;
+    int c0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
     int row = blockIdx.y;
-    if (col >= A.P) return;
-    long long s = (long long)row * A.P + col;
-    uint8_t t = A.tP[s];
-    if (t == T_INTERNAL || t == T_GHOST) x[2 * A.F + s] += (T)shift[0];
+    if (c0 >= A.P) return;
+    long long s0 = (long long)row * A.P + c0;
+    uint8_t t[4];
+    ldt4(A.tP + s0, t);
+    if (t[0] < T_INTERNAL && t[1] < T_INTERNAL && t[2] < T_INTERNAL && t[3] < T_INTERNAL) return;
+    T p4[4];
+    ld4(x + 2 * A.F + s0, p4);
+    const T sh = (T)shift[0];
+#pragma unroll
+    for (int q = 0; q < 4; q++)
+        if (t[q] == T_INTERNAL || t[q] == T_GHOST) p4[q] += sh;
+    st4(x + 2 * A.F + s0, p4);
 }
 
 // --------------------------------------------------------- ghost relaxation
@@ -786,44 +907,55 @@ __global__ void k_restrict(int Nf, int Pf, long long Ff, const uint8_t *tUf, con
     if (row == 0 && col == 0) bH[3 * Fc] = r[3 * Ff];
 }
 
-// bilinear interpolation over the active coarse nodes (weights renormalised)
-// added to every active fine node; y = x + P eH on every slot (y may be x)
+// Interpolation of the coarse correction (Sect. 4.3): bilinear over the active
+// coarse nodes around each fine node, weights renormalised (inactive coarse
+// nodes carry no value); y = x + P eH on every slot (y may be x).  Four
+// consecutive fine slots per thread: vector loads and stores of x, y and the
+// fine types, the row taps shared by the four slots.
 template <typename T>
-__global__ void k_prolong(int Nf, int Pf, long long Ff, const uint8_t *tUf, const uint8_t *tVf, const uint8_t *tPf,
-                          int Nc, int Pc, long long Fc, const uint8_t *tUc, const uint8_t *tVc, const uint8_t *tPc,
-                          const T *eH, const T *x, T *y)
+__global__ void __launch_bounds__(256) k_prolong4(int Nf, int Pf, long long Ff, const uint8_t *tUf, const uint8_t *tVf,
+                                                  const uint8_t *tPf, int Nc, int Pc, long long Fc, const uint8_t *tUc,
+                                                  const uint8_t *tVc, const uint8_t *tPc, const T *eH, const T *x, T *y)
 {
-    int col = blockIdx.x * blockDim.x + threadIdx.x;
-    int row = blockIdx.y;
-    if (col >= Pf) return;
-    int i = col - 1, j = row - 1;
-    long long sf = (long long)row * Pf + col;
+    const int c0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int row = blockIdx.y;
+    if (c0 >= Pf) return;
+    const int j = row - 1;
+    const long long s0 = (long long)row * Pf + c0;
+    if (row == 0 && c0 < NSCAL)
+        for (int q = 0; q < 4; q++) y[3 * Ff + c0 + q] = c0 + q == 0 ? x[3 * Ff] + eH[3 * Fc] : x[3 * Ff + c0 + q];
     const uint8_t *tf[3] = {tUf, tVf, tPf};
     const uint8_t *tc[3] = {tUc, tVc, tPc};
-    if (row == 0 && col < NSCAL) y[3 * Ff + col] = col == 0 ? x[3 * Ff] + eH[3 * Fc] : x[3 * Ff + col];
 #pragma unroll
     for (int g = 0; g < 3; g++) {
-        const long long k = g * Ff + sf;
-        if (!in_grid(g, Nf, i, j) || tf[g][sf] == T_INACTIVE) {
-            if (y != x) y[k] = x[k];
-            continue;
+        uint8_t tt[4];
+        T xv[4], out[4];
+        ldt4(tf[g] + s0, tt);
+        ld4(x + g * Ff + s0, xv);
+        const int Ilo = g == G_V ? -1 : 0, Ihi = g == G_P ? Nc - 1 : Nc;
+        const int Jlo = g == G_U ? -1 : 0, Jhi = g == G_P ? Nc - 1 : Nc;
+        int KJ[2];
+        T wj[2];
+        const int nj = taps<T>(j, g == G_V, Jlo, Jhi, KJ, wj);
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int i = c0 + q - 1;
+            out[q] = xv[q];
+            if (!in_grid(g, Nf, i, j) || tt[q] == T_INACTIVE) continue;
+            int KI[2];
+            T wi[2];
+            const int ni = taps<T>(i, g == G_U, Ilo, Ihi, KI, wi);
+            T sacc = 0, ws = 0;
+            for (int a = 0; a < nj; a++)
+                for (int bb = 0; bb < ni; bb++) {
+                    if (tget(tc[g], g, Nc, Pc, KI[bb], KJ[a]) == T_INACTIVE) continue;
+                    T w = wj[a] * wi[bb];
+                    sacc += w * eH[g * Fc + (long long)(KJ[a] + 1) * Pc + (KI[bb] + 1)];
+                    ws += w;
+                }
+            if (ws > (T)0) out[q] = xv[q] + (ws == (T)1 ? sacc : sacc / ws);
         }
-        int Ilo = g == G_V ? -1 : 0, Ihi = g == G_P ? Nc - 1 : Nc;
-        int Jlo = g == G_U ? -1 : 0, Jhi = g == G_P ? Nc - 1 : Nc;
-        int KI[2], KJ[2];
-        T wi[2], wj[2];
-        int ni = taps<T>(i, g == G_U, Ilo, Ihi, KI, wi);
-        int nj = taps<T>(j, g == G_V, Jlo, Jhi, KJ, wj);
-        T s = 0, ws = 0;
-        for (int a = 0; a < nj; a++)
-            for (int bb = 0; bb < ni; bb++) {
-                if (tget(tc[g], g, Nc, Pc, KI[bb], KJ[a]) == T_INACTIVE) continue;
-                T w = wj[a] * wi[bb];
-                s += w * eH[g * Fc + (long long)(KJ[a] + 1) * Pc + (KI[bb] + 1)];
-                ws += w;
-            }
-        if (ws > (T)0) y[k] = x[k] + (ws == (T)1 ? s : s / ws);
-        else if (y != x) y[k] = x[k];
+        st4(y + g * Ff + s0, out);
     }
 }
 
@@ -891,7 +1023,7 @@ __global__ void __launch_bounds__(1024) k_ghost_block(GhostList gh, int nrows, T
 }
 
 // nu relaxations (Algorithm relax) of a small level in one block: full boxes
-// by 5 colours, cut boxes by 25 colours, lonely faces, xi and the mean
+// by 5 colours, cut boxes by their colours, lonely faces, xi and the mean
 // pressure, lambda ghost sweeps; the same steps in the same order as the
 // multi-kernel path, with block barriers in place of kernel boundaries
 template <typename T>
@@ -913,7 +1045,7 @@ __global__ void __launch_bounds__(512) k_smooth_small(LevelArgs<T> A, T *x, cons
             }
             __syncthreads();
         }
-        for (int colour = 0; colour < 25; colour++) {
+        for (int colour = 0; colour < cut.ncol; colour++) {
             int beg = cut.off[colour], end = cut.off[colour + 1];
             for (int k = beg + threadIdx.x; k < end; k += blockDim.x) box_cut_pre<T>(x, b, cut, k);
             __syncthreads();
@@ -1094,6 +1226,131 @@ void prepare_cuts(Ctx *c)
     }
 }
 
+// one cluster of CL_CTAS CTAs of `threads` threads on the stream
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_cluster(cudaStream_t st, int threads, void (*kernel)(KArgs...), Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CL_CTAS, 1, 1);
+    cfg.blockDim = dim3(threads, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CL_CTAS;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+// Colours of the cut boxes: two boxes conflict when a row of one references
+// an unknown of the other (the unknowns of a box are its internal and ghost
+// faces and p; its rows are the prepared rows of k_cut_prepare).  Boxes in
+// slot order, i.e. lexicographic (j, i), take the smallest colour that no
+// conflicting box before them has; the list is then sorted by colour (slot
+// order inside a colour).  Needs prepared rows; the caller prepares again for
+// the new order.  Host work once per geometry (the rows are copied back).
+int recolour_cuts(Ctx *c)
+{
+    cudaStream_t st = c->stream;
+    for (int lev = 0; lev < c->L; lev++) {
+        Level &l = c->lv[lev];
+        const int n = l.h_ncut, cap = l.cut.cap;
+        if (n <= 0) {
+            l.cut.ncol = 0;
+            l.h_cutoff[0] = 0;
+            continue;
+        }
+        std::vector<int> cell(n), row((size_t)5 * n), sidx((size_t)5 * CUT_ST * n), gface((size_t)4 * n);
+        cudaMemcpyAsync(cell.data(), l.cut.cell, sizeof(int) * n, cudaMemcpyDeviceToHost, st);
+        for (int f = 0; f < 5; f++)
+            cudaMemcpyAsync(row.data() + (size_t)f * n, l.cut.row + (size_t)f * cap, sizeof(int) * n,
+                            cudaMemcpyDeviceToHost, st);
+        for (int e = 0; e < 5 * CUT_ST; e++)
+            cudaMemcpyAsync(sidx.data() + (size_t)e * n, l.cut.sidx + (size_t)e * cap, sizeof(int) * n,
+                            cudaMemcpyDeviceToHost, st);
+        for (int f = 0; f < 4; f++)
+            cudaMemcpyAsync(gface.data() + (size_t)f * n, l.cut.gface + (size_t)f * cap, sizeof(int) * n,
+                            cudaMemcpyDeviceToHost, st);
+        if (cudaStreamSynchronize(st) != cudaSuccess) {
+            snprintf(c->msg, sizeof c->msg, "cut colouring: %s", cudaGetErrorString(cudaGetLastError()));
+            return GP_CUDA;
+        }
+        // boxes in slot order; owners of every unknown (at most two boxes)
+        std::vector<int> ord(n);
+        for (int k = 0; k < n; k++) ord[k] = k;
+        std::sort(ord.begin(), ord.end(), [&](int a, int b) { return cell[a] < cell[b]; });
+        std::vector<int> rank(n);
+        for (int r = 0; r < n; r++) rank[ord[r]] = r;
+        std::unordered_map<int, std::pair<int, int>> own;
+        own.reserve((size_t)5 * n);
+        for (int k = 0; k < n; k++)
+            for (int f = 0; f < 5; f++) {
+                int u = row[(size_t)f * n + k];
+                if (u < 0) continue;
+                auto it = own.find(u);
+                if (it == own.end()) own.emplace(u, std::make_pair(rank[k], -1));
+                else it->second.second = rank[k];
+            }
+        std::vector<std::vector<int>> nb(n);
+        for (int k = 0; k < n; k++) {
+            const int a = rank[k];
+            for (int e = 0; e < 5 * CUT_ST; e++) {
+                auto it = own.find(sidx[(size_t)e * n + k]);
+                if (it == own.end()) continue;
+                const int bs[2] = {it->second.first, it->second.second};
+                for (int z = 0; z < 2; z++)
+                    if (bs[z] >= 0 && bs[z] != a) {
+                        nb[a].push_back(bs[z]);
+                        nb[bs[z]].push_back(a);
+                    }
+            }
+        }
+        std::vector<int> col(n, -1);
+        int ncol = 0;
+        for (int a = 0; a < n; a++) {
+            unsigned long long used = 0ull;
+            for (int b : nb[a])
+                if (b < a) used |= 1ull << col[b];
+            int cc = 0;
+            while (cc < MAX_CUTCOL && ((used >> cc) & 1ull)) cc++;
+            if (cc >= MAX_CUTCOL) {
+                snprintf(c->msg, sizeof c->msg, "level %d: cut boxes need more than %d colours", lev, MAX_CUTCOL);
+                return GP_GEOMETRY;
+            }
+            col[a] = cc;
+            ncol = std::max(ncol, cc + 1);
+        }
+        // the list sorted by (colour, slot)
+        std::vector<int> perm(n);
+        for (int r = 0; r < n; r++) perm[r] = r;
+        std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return col[a] < col[b]; });
+        std::vector<int> cell2(n), gface2((size_t)4 * n);
+        for (int q = 0; q < n; q++) {
+            const int k = ord[perm[q]];
+            cell2[q] = cell[k];
+            for (int f = 0; f < 4; f++) gface2[(size_t)f * n + q] = gface[(size_t)f * n + k];
+        }
+        for (int cc = 0; cc <= ncol; cc++) l.h_cutoff[cc] = 0;
+        for (int r = 0; r < n; r++) l.h_cutoff[col[r] + 1]++;
+        for (int cc = 0; cc < ncol; cc++) l.h_cutoff[cc + 1] += l.h_cutoff[cc];
+        l.cut.ncol = ncol;
+        cudaMemcpyAsync(l.cut.cell, cell2.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st);
+        for (int f = 0; f < 4; f++)
+            cudaMemcpyAsync(l.cut.gface + (size_t)f * cap, gface2.data() + (size_t)f * n, sizeof(int) * n,
+                            cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(l.cut.off, l.h_cutoff, sizeof(int) * (ncol + 1), cudaMemcpyHostToDevice, st);
+        // the host vectors must outlive the copies
+        if (cudaStreamSynchronize(st) != cudaSuccess) {
+            snprintf(c->msg, sizeof c->msg, "cut colouring: %s", cudaGetErrorString(cudaGetLastError()));
+            return GP_CUDA;
+        }
+    }
+    return GP_OK;
+}
+
 void tiles_init()
 {
     static bool done = false;
@@ -1122,7 +1379,7 @@ template <typename T, typename R> void residual_into(Ctx *c, int lev, const T *x
     cudaStream_t st = c->stream;
     int nb = red_blocks(l);
     tmr_begin(c, KT_RESIDUAL, lev);
-    k_residual<T, R><<<nb, 256, 0, st>>>(level_args<T>(c, lev), x, b, r, c->part);
+    k_residual4<T, R><<<nb, 256, 0, st>>>(level_args<T>(c, lev), x, b, r, c->part);
     tmr_end(c, KT_RESIDUAL, lev);
     if (l.h_nrows > 0)
         k_ghost_residual<T, R><<<(l.h_nrows + 255) / 256, 256, 0, st>>>(l.gh, l.h_nrows, x, b, r, c->maxbits);
@@ -1174,16 +1431,12 @@ template <typename T> static void box_pass(Ctx *c, int lev, const T *in, T *out,
     }
     T *x = out;
     int most = 0;  // largest colour of cut boxes
-    for (int colour = 0; colour < 25; colour++) most = max(most, l.h_cutoff[colour + 1] - l.h_cutoff[colour]);
+    for (int colour = 0; colour < l.cut.ncol; colour++) most = max(most, l.h_cutoff[colour + 1] - l.h_cutoff[colour]);
     if (most > CUT_SPLIT) {
         tmr_begin(c, KT_BOX_CUT, lev);
-        for (int colour = 0; colour < 25; colour++) {
-            int beg = l.h_cutoff[colour], end = l.h_cutoff[colour + 1];
-            if (end <= beg) continue;
-            k_box_cut_colour<T><<<(end - beg + 7) / 8, 256, 0, st>>>(x, b, l.cut, beg, end);
-            c->launches++;
-        }
+        launch_cluster(st, CL_THREADS, k_box_cut_cluster<T>, x, b, l.cut);
         tmr_end(c, KT_BOX_CUT, lev);
+        c->launches++;
     } else if (l.h_ncut > 0) {
         tmr_begin(c, KT_BOX_CUT, lev);
         k_box_cut<T><<<1, 1024, 0, st>>>(A, x, b, l.cut, l.gh);
@@ -1216,14 +1469,13 @@ template <typename T> void scalar_update(Ctx *c, int lev, T *x, const T *b)
     const Level &l = c->lv[lev];
     cudaStream_t st = c->stream;
     LevelArgs<T> A = level_args<T>(c, lev);
-    dim3 g = frame_grid(l);
     int nb = red_blocks(l);
     tmr_begin(c, KT_SCALAR, lev);
     k_scalar_partial<T><<<nb, 256, 0, st>>>(A, x, b, c->part);
     tmr_end(c, KT_SCALAR, lev);
     double h = c->prm.L / (double)l.N;
     k_scalar_final<T><<<1, 256, 0, st>>>(c->part, nb, x, b, 3 * l.F, h * h, l.nint, c->red + 1);
-    k_pshift<T><<<g, 256, 0, st>>>(A, x, c->red + 1);
+    k_pshift<T><<<dim3((l.P / 4 + 255) / 256, l.N + 2), 256, 0, st>>>(A, x, c->red + 1);
     c->launches += 3;
 }
 
@@ -1244,19 +1496,32 @@ template <typename T> void ghost_sweep(Ctx *c, int lev, T *x, const T *b)
 // level's other vector); the result ends in x.  Tiled levels alternate
 // between the two vectors, so an even count from x, or an odd count from the
 // other vector, needs no copy.
+// levels whose whole relaxation runs in one block, in place (a cluster of
+// CTAs was measured slower here than one block or than one launch per phase
+// over the whole GPU: its barriers cost more and its few SMs limit the memory
+// parallelism); tiled levels keep their ping-pong sweeps
+template <typename T> static bool one_kernel_level(Ctx *c, int lev)
+{
+    const Level &l = c->lv[lev];
+    return l.N <= SMALL_N && l.h_nlonely <= l.gh.cap && !tiled<T>(c, lev);
+}
+
 template <typename T> void smooth_from(Ctx *c, int lev, T *x, T *in, const T *b, int nu)
 {
     const Level &l = c->lv[lev];
     const bool tl = tiled<T>(c, lev);
-    if (in != x && (nu <= 0 || !tl || (l.N <= SMALL_N && l.h_nlonely <= l.gh.cap))) {
+    const bool one = one_kernel_level<T>(c, lev);
+    if (in != x && (nu <= 0 || !tl || one)) {
         copy_vec<T>(c, in, x, l.VL);
         in = x;
     }
     if (nu <= 0) return;
-    if (l.N <= SMALL_N && l.h_nlonely <= l.gh.cap) {
+    if (one) {
         double h = c->prm.L / (double)l.N;
+        tmr_begin(c, KT_BOX_FULL, lev);
         k_smooth_small<T><<<1, 512, 0, c->stream>>>(level_args<T>(c, lev), x, b, l.cut, l.gh, l.h_nrows, l.lonely,
                                                       l.h_nlonely, l.nint, h * h, (T)c->prm.dtau, c->prm.lambda, nu);
+        tmr_end(c, KT_BOX_FULL, lev);
         c->launches++;
         return;
     }
@@ -1285,8 +1550,7 @@ template <typename T> void smooth(Ctx *c, int lev, T *x, const T *b, int nu) { s
 // tiled sweeps end in x without a copy
 template <typename T> T *post_buffer(Ctx *c, int lev, T *x, int nu)
 {
-    const Level &l = c->lv[lev];
-    if (nu % 2 == 0 || !tiled<T>(c, lev) || (l.N <= SMALL_N && l.h_nlonely <= l.gh.cap)) return x;
+    if (nu % 2 == 0 || !tiled<T>(c, lev) || one_kernel_level<T>(c, lev)) return x;
     return tile_scratch<T>(c, lev);
 }
 
@@ -1303,9 +1567,9 @@ template <typename T> void restrict_level(Ctx *c, int lev, const T *r, T *bH)
 template <typename T> void prolong_to(Ctx *c, int lev, const T *eH, const T *x, T *y)
 {
     const Level &f = c->lv[lev], &C = c->lv[lev + 1];
-    dim3 g((f.P + 255) / 256, f.N + 2);
+    dim3 g((f.P / 4 + 255) / 256, f.N + 2);
     tmr_begin(c, KT_PROLONG, lev);
-    k_prolong<T><<<g, 256, 0, c->stream>>>(f.N, f.P, f.F, f.tU, f.tV, f.tP, C.N, C.P, C.F, C.tU, C.tV, C.tP, eH, x, y);
+    k_prolong4<T><<<g, 256, 0, c->stream>>>(f.N, f.P, f.F, f.tU, f.tV, f.tP, C.N, C.P, C.F, C.tU, C.tV, C.tP, eH, x, y);
     tmr_end(c, KT_PROLONG, lev);
     c->launches++;
 }

@@ -32,6 +32,7 @@ void residual_to_float(Ctx *c, const double *x, const double *b, float *r);
 void tmr_flush(Ctx *c);
 void tiles_init();
 void prepare_cuts(Ctx *c);
+int recolour_cuts(Ctx *c);
 void krylov_init(Ctx *c, double *x, const double *b);
 void krylov_iteration(Ctx *c, double *x, const double *b);
 int residual_static(Ctx *c, int lev, const double *x, const double *b, double *r, double *norm_host);
@@ -154,7 +155,7 @@ static size_t carve(Ctx *c, char *base)
         int cc = cut_cap(l.N);
         l.cut.cap = cc;
         l.cut.count = cv.take<int>(1);
-        l.cut.off = cv.take<int>(26);
+        l.cut.off = cv.take<int>(MAX_CUTCOL + 1);
         l.cut.cell = cv.take<int>(cc);
         l.cut.gface = cv.take<int>(4 * (size_t)cc);
         l.cut.row = cv.take<int>(5 * (size_t)cc);
@@ -548,6 +549,12 @@ static gp_status geometry_finish(gp_ctx *ctx, const double *phi, int phi_fluid_p
     gp_status cs = check_cuda(ctx, "geometry_build");
     if (cs != GP_OK) return cs;
     c->geom_ok = 1;
+    prepare_cuts(c);
+    s = recolour_cuts(c);
+    if (s != GP_OK) {
+        c->geom_ok = 0;
+        return (gp_status)s;
+    }
     prepare_cuts(c);
     s = build_coarse_inverse(c);
     if (s != GP_OK) {
