@@ -54,6 +54,9 @@ struct GhostList {
     double *th;        // [2][cap] theta
     double *upd;       // [cap] Jacobi update scratch
     float *updf;
+    double *acc;       // [2][cap] accumulated corrections of the fused sweeps (ping-pong)
+    float *accf;
+    int *strow;        // [GH_ST][cap] ghost-row index of each stencil node, or -1
     int cap;
 };
 

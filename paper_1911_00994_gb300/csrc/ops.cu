@@ -856,6 +856,42 @@ template <typename T> __global__ void k_ghost_apply(GhostList gh, int nrows, T *
     if (k < nrows) x[gh.node[k]] += gupd<T>(gh)[k];
 }
 
+// lambda Jacobi sweeps of Eq. (ghostrelax) with x fixed: after sweep s the
+// ghost-class values are x + d_s (d_0 = 0), and sweep s + 1 computes
+// d_(s+1) = d_s + dtau (b - B (x + d_s)) reading d_s of the referenced ghost
+// rows through strow; the last d is added to x by k_ghost_acc_apply.  The
+// iterates are those of the compute/apply pairs (up to rounding), in lambda + 1
+// launches instead of 2 lambda.
+template <typename T> __device__ inline T *gacc(const GhostList &gh);
+template <> __device__ inline double *gacc<double>(const GhostList &gh) { return gh.acc; }
+template <> __device__ inline float *gacc<float>(const GhostList &gh) { return gh.accf; }
+
+template <typename T>
+__global__ void k_ghost_acc_sweep(GhostList gh, int nrows, const T *x, const T *b, T dtau, int sweep)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nrows) return;
+    const T *w = gw<T>(gh);
+    const T *din = gacc<T>(gh) + (long long)(sweep & 1) * gh.cap;
+    T *dout = gacc<T>(gh) + (long long)((sweep + 1) & 1) * gh.cap;
+    int nst = gh.nst[k];
+    T s = b[gh.node[k]];
+    for (int q = 0; q < nst; q++) {
+        const long long e = (long long)q * gh.cap + k;
+        const int rr = gh.strow[e];
+        T xv = x[gh.st[e]];
+        if (sweep > 0 && rr >= 0) xv += din[rr];
+        s -= w[e] * xv;
+    }
+    dout[k] = (sweep > 0 ? din[k] : (T)0) + dtau * s;
+}
+
+template <typename T> __global__ void k_ghost_acc_apply(GhostList gh, int nrows, T *x, int sweeps)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < nrows) x[gh.node[k]] += gacc<T>(gh)[(long long)(sweeps & 1) * gh.cap + k];
+}
+
 // ---------------------------------------------------------------- transfers
 
 // Eq. (restop) where the whole stencil is of the coarse node's class,
@@ -1351,6 +1387,47 @@ int recolour_cuts(Ctx *c)
     return GP_OK;
 }
 
+// For every stencil entry of every ghost-class row, the index of the row
+// whose unknown it is (or -1): the fused ghost sweeps read the accumulated
+// correction of that row.  Host work once per geometry.
+int ghost_row_links(Ctx *c)
+{
+    cudaStream_t st = c->stream;
+    for (int lev = 0; lev < c->L; lev++) {
+        Level &l = c->lv[lev];
+        const int n = l.h_nrows, cap = l.gh.cap;
+        if (n <= 0) continue;
+        std::vector<int> node(n), sti((size_t)GH_ST * n), out((size_t)GH_ST * n, -1);
+        std::vector<uint8_t> nst(n);
+        cudaMemcpyAsync(node.data(), l.gh.node, sizeof(int) * n, cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(nst.data(), l.gh.nst, n, cudaMemcpyDeviceToHost, st);
+        for (int q = 0; q < GH_ST; q++)
+            cudaMemcpyAsync(sti.data() + (size_t)q * n, l.gh.st + (size_t)q * cap, sizeof(int) * n,
+                            cudaMemcpyDeviceToHost, st);
+        if (cudaStreamSynchronize(st) != cudaSuccess) {
+            snprintf(c->msg, sizeof c->msg, "ghost links: %s", cudaGetErrorString(cudaGetLastError()));
+            return GP_CUDA;
+        }
+        std::unordered_map<int, int> row;
+        row.reserve((size_t)n * 2);
+        for (int k = 0; k < n; k++) row.emplace(node[k], k);
+        for (int k = 0; k < n; k++)
+            for (int q = 0; q < nst[k]; q++) {
+                auto it = row.find(sti[(size_t)q * n + k]);
+                if (it != row.end()) out[(size_t)q * n + k] = it->second;
+            }
+        for (int q = 0; q < GH_ST; q++)
+            cudaMemcpyAsync(l.gh.strow + (size_t)q * cap, out.data() + (size_t)q * n, sizeof(int) * n,
+                            cudaMemcpyHostToDevice, st);
+        // the host vector must outlive the copies
+        if (cudaStreamSynchronize(st) != cudaSuccess) {
+            snprintf(c->msg, sizeof c->msg, "ghost links: %s", cudaGetErrorString(cudaGetLastError()));
+            return GP_CUDA;
+        }
+    }
+    return GP_OK;
+}
+
 void tiles_init()
 {
     static bool done = false;
@@ -1537,8 +1614,14 @@ template <typename T> void smooth_from(Ctx *c, int lev, T *x, T *in, const T *b,
             k_ghost_block<T><<<1, 1024, 0, c->stream>>>(l.gh, l.h_nrows, cur, b, (T)c->prm.dtau, c->prm.lambda);
             tmr_end(c, KT_GHOST, lev);
             c->launches++;
-        } else {
-            for (int k = 0; k < c->prm.lambda; k++) ghost_sweep<T>(c, lev, cur, b);
+        } else if (l.h_nrows > 0 && c->prm.lambda > 0) {
+            const int nb = (l.h_nrows + 255) / 256;
+            tmr_begin(c, KT_GHOST, lev);
+            for (int k = 0; k < c->prm.lambda; k++)
+                k_ghost_acc_sweep<T><<<nb, 256, 0, c->stream>>>(l.gh, l.h_nrows, cur, b, (T)c->prm.dtau, k);
+            k_ghost_acc_apply<T><<<nb, 256, 0, c->stream>>>(l.gh, l.h_nrows, cur, c->prm.lambda);
+            tmr_end(c, KT_GHOST, lev);
+            c->launches += c->prm.lambda + 1;
         }
     }
     if (cur != x) copy_vec<T>(c, cur, x, l.VL);

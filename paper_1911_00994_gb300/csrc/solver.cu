@@ -33,6 +33,7 @@ void tmr_flush(Ctx *c);
 void tiles_init();
 void prepare_cuts(Ctx *c);
 int recolour_cuts(Ctx *c);
+int ghost_row_links(Ctx *c);
 void krylov_init(Ctx *c, double *x, const double *b);
 void krylov_iteration(Ctx *c, double *x, const double *b);
 int residual_static(Ctx *c, int lev, const double *x, const double *b, double *r, double *norm_host);
@@ -152,6 +153,9 @@ static size_t carve(Ctx *c, char *base)
         g.th = cv.take<double>(2 * (size_t)gc);
         g.upd = cv.take<double>(gc);
         g.updf = cv.take<float>(gc);
+        g.acc = cv.take<double>(2 * (size_t)gc);
+        g.accf = cv.take<float>(2 * (size_t)gc);
+        g.strow = cv.take<int>((size_t)GH_ST * gc);
         int cc = cut_cap(l.N);
         l.cut.cap = cc;
         l.cut.count = cv.take<int>(1);
@@ -551,6 +555,7 @@ static gp_status geometry_finish(gp_ctx *ctx, const double *phi, int phi_fluid_p
     c->geom_ok = 1;
     prepare_cuts(c);
     s = recolour_cuts(c);
+    if (s == GP_OK) s = ghost_row_links(c);
     if (s != GP_OK) {
         c->geom_ok = 0;
         return (gp_status)s;

@@ -199,3 +199,21 @@ def test_graph_replay_matches_direct_launches(precision):
             out.append((s.to_flat(x), hist2))
     assert np.array_equal(out[0][0], out[1][0])
     assert np.array_equal(out[0][1], out[1][1])
+
+
+def test_large_level_relaxation_matches():
+    # a level whose ghost-class rows (the walls alone give 4 N) exceed one
+    # block's share: the box sweep, the (xi, mean) step and the fused ghost
+    # sweeps of the multi-launch path, N = 1024
+    o, s = pair("circle", 1024)
+    t = o.types(0)
+    x = W.random_flat(1024, t, 900)
+    b = W.random_flat(1024, t, 901) * 10
+    want = o.smooth(x, b, 1, 0)
+    xg = s.to_device(x)
+    s.smooth(xg, s.to_device(b), 1, 0)
+    assert rel(s.to_flat(xg), want) < 1e-11
+    want = o.ghost_sweep(x, b, 0)
+    xg = s.to_device(x)
+    s.ghost_sweep(xg, s.to_device(b), 0)
+    assert rel(s.to_flat(xg), want) < 1e-12
