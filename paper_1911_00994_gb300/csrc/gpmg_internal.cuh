@@ -28,6 +28,9 @@ constexpr int MAX_MARCH = 64;
 constexpr int NSCAL = 32;
 constexpr int MAX_CUTCOL = 64;  // colours of the cut boxes
 constexpr int ADJ_KMAX = 8;  // Picard iterations cn_step_adjoint can differentiate
+// box codes (one byte per cell): a full box (internal cell, no ghost face)
+// and which of its four faces are internal
+constexpr unsigned BOX_FULL = 1, BOX_W = 2, BOX_E = 4, BOX_S = 8, BOX_N = 16, BOX_ALL = 31;
 constexpr int GH_ST = 9;  // stencil slots per ghost row
 
 // error bits written by kernels into the context's device status word
@@ -88,6 +91,7 @@ struct Level {
     long long VL;      // vector length
     double h;
     uint8_t *tU, *tV, *tP;
+    uint8_t *bcode;    // [F] box code of each cell (BOX_FULL and its internal faces, or 0)
     uint8_t *prim;     // [3 * F] ghost referenced by an internal row
     uint8_t *done;     // [3 * F] ghost row computed (closure passes)
     double *x, *b, *r; // vectors owned by the context (coarse levels; r on all)

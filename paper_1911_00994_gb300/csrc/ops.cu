@@ -47,6 +47,37 @@ template <typename T> __device__ inline T *gupd(const GhostList &gh);
 template <> __device__ inline double *gupd<double>(const GhostList &gh) { return gh.upd; }
 template <> __device__ inline float *gupd<float>(const GhostList &gh) { return gh.updf; }
 
+// b - sum_q w_q x[st_q] of ghost-class row k (Eq. ghostrelax, Sect. 3.4):
+// every index and then every value of the row is loaded before the
+// arithmetic, which keeps the serial order q = 0, 1, ... (a plain loop over
+// the stencil would wait on each gather in turn).  With `acc`, the stencil
+// value of a node that is itself a ghost-class row is x + acc[that row].
+template <typename T, bool ACC>
+__device__ __forceinline__ T ghost_row_residual(const GhostList &gh, int k, const T *x, const T *b, const T *acc)
+{
+    const T *w = gw<T>(gh);
+    const int nst = gh.nst[k];
+    int idx[GH_ST], lnk[GH_ST];
+    T wv[GH_ST], xv[GH_ST];
+#pragma unroll
+    for (int q = 0; q < GH_ST; q++) {
+        const long long e = (long long)q * gh.cap + k;
+        idx[q] = q < nst ? gh.st[e] : 0;
+        lnk[q] = (ACC && q < nst) ? gh.strow[e] : -1;
+        wv[q] = q < nst ? w[e] : (T)0;
+    }
+#pragma unroll
+    for (int q = 0; q < GH_ST; q++) {
+        xv[q] = q < nst ? x[idx[q]] : (T)0;
+        if (ACC && lnk[q] >= 0) xv[q] += acc[lnk[q]];
+    }
+    T s = b[gh.node[k]];
+#pragma unroll
+    for (int q = 0; q < GH_ST; q++)
+        if (q < nst) s -= wv[q] * xv[q];
+    return s;
+}
+
 __device__ inline double nanmax(double a, double b) { return (a != a || b != b) ? (double)NAN : fmax(a, b); }
 
 // ---------------------------------------------------------------- residual
@@ -185,12 +216,8 @@ __global__ void k_ghost_residual(GhostList gh, int nrows, const T *x, const T *b
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     double m = 0.0;
     if (k < nrows) {
-        const T *w = gw<T>(gh);
-        int nst = gh.nst[k];
-        int node = gh.node[k];
-        T s = b[node];
-        for (int q = 0; q < nst; q++) s -= w[(long long)q * gh.cap + k] * x[gh.st[(long long)q * gh.cap + k]];
-        r[node] = (R)s;
+        const T s = ghost_row_residual<T, false>(gh, k, x, b, nullptr);
+        r[gh.node[k]] = (R)s;
         m = fabs((double)s);
     }
     // warp max then one atomic per warp (max of non-negative doubles by bits)
@@ -237,16 +264,16 @@ __global__ void k_residual_final(const double *part, int nb, const T *b, R *r, l
 // Box relaxation of one cell without ghost borders (Sect. 4.1.1): Schur
 // complement of the pressure unknown.  u, v, p point at the cell's slot in
 // arrays of row pitch `pitch` (global frames or a shared-memory tile); bu, bv,
-// bp at the cell's slot of the right-hand side.  Borders that are not
-// internal stay frozen.
-template <typename T>
+// bp at the cell's slot of the right-hand side.  W, E, S, Nn: the faces
+// that are internal (the others stay frozen); ALL: all four are.
+template <typename T, bool ALL = false>
 __device__ __forceinline__ void box_core(T *u, T *v, T *p, const int pitch, const T *bu, const T *bv, const T *bp,
-                                         const long long bpitch, const T xi, const uint8_t tW, const uint8_t tE,
-                                         const uint8_t tS, const uint8_t tN, const BoxK<T> &K)
+                                         const long long bpitch, const T xi, bool W, bool E, bool S, bool Nn,
+                                         const BoxK<T> &K)
 {
     const int Pp = pitch;
     const T a = K.a, d = K.d, q = K.q;
-    bool W = tW == T_INTERNAL, E = tE == T_INTERNAL, S = tS == T_INTERNAL, Nn = tN == T_INTERNAL;
+    if (ALL) W = E = S = Nn = true;
     T rW = 0, rE = 0, rS = 0, rN = 0;
     if (W) rW = bu[0] - (d * u[0] - a * (u[1] + u[-1] + u[Pp] + u[-Pp]) + q * (p[0] - p[-1]));
     if (E) rE = bu[1] - (d * u[1] - a * (u[2] + u[0] + u[1 + Pp] + u[1 - Pp]) + q * (p[1] - p[0]));
@@ -309,39 +336,39 @@ __device__ __forceinline__ void box_full_one(const LevelArgs<T> &A, T *x, const 
     if (A.tP[s] != T_INTERNAL) return;
     uint8_t tW = A.tU[s], tE = A.tU[s + 1], tS = A.tV[s], tN = A.tV[s + A.P];
     if (tW == T_GHOST || tE == T_GHOST || tS == T_GHOST || tN == T_GHOST) return;
-    box_core<T>(x + s, x + A.F + s, x + 2 * A.F + s, A.P, b + s, b + A.F + s, b + 2 * A.F + s, A.P, x[3 * A.F], tW, tE,
-                tS, tN, A.K);
+    box_core<T>(x + s, x + A.F + s, x + 2 * A.F + s, A.P, b + s, b + A.F + s, b + 2 * A.F + s, A.P, x[3 * A.F],
+                tW == T_INTERNAL, tE == T_INTERNAL, tS == T_INTERNAL, tN == T_INTERNAL, A.K);
 }
 
 // All five colours of the full boxes in one pass over the level.  Each
-// block owns TW x TH frame slots (all three frames).  One TMA copy brings the
+// block owns TH x TW frame slots (all three frames).  One TMA copy brings the
 // u, v, p frames of a (TH + 20) x LW window around them into shared memory
 // (10 slots above and below, 16 left, at least 10 right) and another the
-// three node-type frames.  Colour c relaxes the boxes within 2 (4 - c) + 1
-// cells below and 2 (4 - c) cells above the owned cells: a box reads only
-// values written by boxes at most two cells away, so the owned slots see the
-// same sequence of updates as the global colour-by-colour sweep (the extra
-// cell below gives the owned west and south faces the update of the box on
-// their far side).  The block then writes every owned slot, changed or not,
-// to the other vector y, so y is a complete copy of the swept x and no block
-// reads what another writes.
+// box codes of the same window.  Colour c relaxes the boxes within
+// 2 (4 - c) + 1 cells below and 2 (4 - c) cells above the owned cells: a box
+// reads only values written by boxes at most two cells away, so the owned
+// slots see the same sequence of updates as the global colour-by-colour
+// sweep (the extra cell below gives the owned west and south faces the update
+// of the box on their far side).  The boxes of one colour are numbered row by
+// row (M per row, every fifth cell) and dealt to the threads in that order.
+// The block then writes every owned slot, changed or not, to the other
+// vector y, so y is a complete copy of the swept x and no block reads what
+// another writes.
 template <typename T> struct TileGeom;
 template <> struct TileGeom<float> {
-    static constexpr int TW = 64, LW = 96;
+    static constexpr int TW = 64, LW = 96, TH = 64, THREADS = 512;
 };
 template <> struct TileGeom<double> {
-    static constexpr int TW = 32, LW = 64;
+    static constexpr int TW = 32, LW = 64, TH = 32, THREADS = 384;
 };
-constexpr int TT_H = 32;             // owned rows
 constexpr int TT_RLO = 10;           // rows loaded above (and below) the owned ones
-constexpr int TT_LH = TT_H + 2 * TT_RLO;
 constexpr int TT_CLO = 16;           // columns loaded left of the owned ones (TMA x offsets: multiples of 16 bytes)
 constexpr unsigned long long TT_WAIT_NS = 2000000000ull;  // bound on the wait for the tile copies
-constexpr int TT_THREADS = 384;
+template <typename T> __host__ __device__ constexpr int tt_lh() { return TileGeom<T>::TH + 2 * TT_RLO; }
 
 template <typename T> __host__ __device__ constexpr size_t tt_smem()
 {
-    return (size_t)3 * TT_LH * TileGeom<T>::LW * (sizeof(T) + 1) + 16;
+    return (size_t)tt_lh<T>() * TileGeom<T>::LW * (3 * sizeof(T) + 1) + 16;
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -385,6 +412,15 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        :
+        : "r"(smem_u32(dst)), "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
 template <typename T> struct Vec16;
 template <> struct Vec16<float> {
     using type = float4;
@@ -394,20 +430,18 @@ template <> struct Vec16<double> {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(TT_THREADS) k_box_tma(const __grid_constant__ CUtensorMap mx,
-                                                 const __grid_constant__ CUtensorMap mt, LevelArgs<T> A, const T *x,
-                                                 const T *b, T *y, unsigned *err)
+__global__ void __launch_bounds__(TileGeom<T>::THREADS) k_box_tma(const __grid_constant__ CUtensorMap mx,
+                                                           const __grid_constant__ CUtensorMap mc, LevelArgs<T> A,
+                                                           const T *x, const T *b, T *y, unsigned *err)
 {
-    constexpr int TW = TileGeom<T>::TW, LW = TileGeom<T>::LW, LH = TT_LH, FR = LH * LW;
+    constexpr int TW = TileGeom<T>::TW, LW = TileGeom<T>::LW, TH = TileGeom<T>::TH, LH = tt_lh<T>(), FR = LH * LW;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     T *su = (T *)smem_raw;
     T *sv = su + FR;
     T *sp = sv + FR;
-    uint8_t *tu = (uint8_t *)(sp + FR);
-    uint8_t *tv = tu + FR;
-    uint8_t *tp = tv + FR;
-    uint64_t *bar = (uint64_t *)(tp + FR);
-    const int c0 = blockIdx.x * TW, r0 = blockIdx.y * TT_H;
+    uint8_t *sc = (uint8_t *)(sp + FR);
+    uint64_t *bar = (uint64_t *)(sc + FR);
+    const int c0 = blockIdx.x * TW, r0 = blockIdx.y * TH;
     const int col0 = c0 - TT_CLO, row0 = r0 - TT_RLO;
     if (threadIdx.x == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
@@ -415,11 +449,11 @@ __global__ void __launch_bounds__(TT_THREADS) k_box_tma(const __grid_constant__ 
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        const unsigned bytes = (unsigned)(3 * FR * (sizeof(T) + 1));
+        const unsigned bytes = (unsigned)(FR * (3 * sizeof(T) + 1));
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                      : "memory");
         tma_load_3d(su, &mx, col0, row0, 0, bar);
-        tma_load_3d(tu, &mt, col0, row0, 0, bar);
+        tma_load_2d(sc, &mc, col0, row0, bar);
     }
     bool ok = __syncthreads_and(mbar_wait_bounded(bar, TT_WAIT_NS));
     if (!ok) {
@@ -436,24 +470,28 @@ __global__ void __launch_bounds__(TT_THREADS) k_box_tma(const __grid_constant__ 
     for (int colour = 0; colour < 5; colour++) {
         const int hi = 2 * (4 - colour), lo = hi + 1;
         const int ilo = max(c0 - 1 - lo, 0), ihi = min(c0 - 1 + TW + hi, A.N);
-        const int jlo = max(r0 - 1 - lo, 0), jhi = min(r0 - 1 + TT_H + hi, A.N);
-        // groups of 16 threads walk the rows; a group's threads take every
-        // fifth cell of the row (consecutive rows of one warp hit different
-        // shared-memory banks)
-        const int g16 = threadIdx.x >> 4, l16 = threadIdx.x & 15, ng = blockDim.x >> 4;
-        for (int j = jlo + g16; j < jhi; j += ng) {
-            const int i0 = ilo + ((colour - 3 * j - ilo) % 5 + 5) % 5;
-            const int lrow = (j + 1 - row0) * LW + 1 - col0;
-            const long long grow = (long long)(j + 1) * A.P + 1;
-            for (int i = i0 + 5 * l16; i < ihi; i += 80) {
-                const int ls = lrow + i;
-                if (tp[ls] != T_INTERNAL) continue;
-                const uint8_t tW = tu[ls], tE = tu[ls + 1], tS = tv[ls], tN = tv[ls + LW];
-                if (tW == T_GHOST || tE == T_GHOST || tS == T_GHOST || tN == T_GHOST) continue;
-                const long long gs = grow + i;
-                box_core<T>(su + ls, sv + ls, sp + ls, LW, b + gs, b + A.F + gs, b + 2 * A.F + gs, A.P, xi, tW, tE, tS,
-                            tN, A.K);
-            }
+        const int jlo = max(r0 - 1 - lo, 0), jhi = min(r0 - 1 + TH + hi, A.N);
+        if (ilo >= ihi || jlo >= jhi) continue;
+        // M boxes per row; k / M as (k * ceil(2^16 / M)) >> 16, exact for
+        // k < 2^16 / M (here k < 81 * 17 and M <= 17)
+        const int M = (ihi - ilo + 4) / 5, nslot = (jhi - jlo) * M;
+        const unsigned inv = (65536u + (unsigned)M - 1u) / (unsigned)M;
+        for (int k = threadIdx.x; k < nslot; k += TileGeom<T>::THREADS) {
+            const int jj = (int)(((unsigned)k * inv) >> 16), m = k - jj * M;
+            const int j = jlo + jj;
+            // first cell of colour (i + 3 j) mod 5 = colour at or after ilo
+            const int i = ilo + (int)((unsigned)(colour + (5 << 28) - 3 * j - ilo) % 5u) + 5 * m;
+            if (i >= ihi) continue;
+            const int ls = (j + 1 - row0) * LW + (i + 1 - col0);
+            const unsigned code = sc[ls];
+            if (!(code & BOX_FULL)) continue;
+            const long long gs = (long long)(j + 1) * A.P + (i + 1);
+            if (code == BOX_ALL)
+                box_core<T, true>(su + ls, sv + ls, sp + ls, LW, b + gs, b + A.F + gs, b + 2 * A.F + gs, A.P, xi,
+                                  true, true, true, true, A.K);
+            else
+                box_core<T>(su + ls, sv + ls, sp + ls, LW, b + gs, b + A.F + gs, b + 2 * A.F + gs, A.P, xi,
+                            code & BOX_W, code & BOX_E, code & BOX_S, code & BOX_N, A.K);
         }
         __syncthreads();
     }
@@ -461,7 +499,7 @@ __global__ void __launch_bounds__(TT_THREADS) k_box_tma(const __grid_constant__ 
     // multiples of 32 elements, so every row segment is whole vectors)
     using V = typename Vec16<T>::type;
     constexpr int VW = 16 / sizeof(T);
-    const int rows = min(TT_H, A.N + 2 - r0), vpr = min(TW, A.P - c0) / VW;
+    const int rows = min(TH, A.N + 2 - r0), vpr = min(TW, A.P - c0) / VW;
     const int per_frame = rows * vpr;
     for (int k = threadIdx.x; k < 3 * per_frame; k += blockDim.x) {
         const int f = k / per_frame, rem = k - f * per_frame;
@@ -471,6 +509,25 @@ __global__ void __launch_bounds__(TT_THREADS) k_box_tma(const __grid_constant__ 
         *dst = *src;
     }
     if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x < NSCAL) y[3 * A.F + threadIdx.x] = x[3 * A.F + threadIdx.x];
+}
+
+// Box code of every cell (one byte per slot): BOX_FULL for an internal cell
+// with no ghost face (a full box of Sect. 4.1.1), with BOX_W, BOX_E, BOX_S,
+// BOX_N for its internal faces; 0 for every other slot.  Once per geometry.
+__global__ void k_box_codes(int N, int P, long long F, const uint8_t *tU, const uint8_t *tV, const uint8_t *tP,
+                            uint8_t *code)
+{
+    const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (s >= F) return;
+    const int row = (int)(s / P), col = (int)(s - (long long)row * P);
+    uint8_t c = 0;
+    if (row >= 1 && row <= N && col >= 1 && col <= N && tP[s] == T_INTERNAL) {
+        const uint8_t tW = tU[s], tE = tU[s + 1], tS = tV[s], tN = tV[s + P];
+        if (tW != T_GHOST && tE != T_GHOST && tS != T_GHOST && tN != T_GHOST)
+            c = BOX_FULL | (tW == T_INTERNAL ? BOX_W : 0) | (tE == T_INTERNAL ? BOX_E : 0) |
+                (tS == T_INTERNAL ? BOX_S : 0) | (tN == T_INTERNAL ? BOX_N : 0);
+    }
+    code[s] = c;
 }
 
 template <typename T>
@@ -843,11 +900,7 @@ __global__ void k_ghost_update(GhostList gh, int nrows, const T *x, const T *b, 
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nrows) return;
-    const T *w = gw<T>(gh);
-    int nst = gh.nst[k];
-    T s = b[gh.node[k]];
-    for (int q = 0; q < nst; q++) s -= w[(long long)q * gh.cap + k] * x[gh.st[(long long)q * gh.cap + k]];
-    gupd<T>(gh)[k] = dtau * s;
+    gupd<T>(gh)[k] = dtau * ghost_row_residual<T, false>(gh, k, x, b, nullptr);
 }
 
 template <typename T> __global__ void k_ghost_apply(GhostList gh, int nrows, T *x)
@@ -871,18 +924,9 @@ __global__ void k_ghost_acc_sweep(GhostList gh, int nrows, const T *x, const T *
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nrows) return;
-    const T *w = gw<T>(gh);
     const T *din = gacc<T>(gh) + (long long)(sweep & 1) * gh.cap;
     T *dout = gacc<T>(gh) + (long long)((sweep + 1) & 1) * gh.cap;
-    int nst = gh.nst[k];
-    T s = b[gh.node[k]];
-    for (int q = 0; q < nst; q++) {
-        const long long e = (long long)q * gh.cap + k;
-        const int rr = gh.strow[e];
-        T xv = x[gh.st[e]];
-        if (sweep > 0 && rr >= 0) xv += din[rr];
-        s -= w[e] * xv;
-    }
+    const T s = sweep > 0 ? ghost_row_residual<T, true>(gh, k, x, b, din) : ghost_row_residual<T, false>(gh, k, x, b, nullptr);
     dout[k] = (sweep > 0 ? din[k] : (T)0) + dtau * s;
 }
 
@@ -1037,15 +1081,9 @@ __global__ void k_add_float(double *x, const float *e, long long n)
 template <typename T>
 __device__ __forceinline__ void ghost_sweeps_block(GhostList &gh, int nrows, T *x, const T *b, T dtau, int lambda)
 {
-    const T *w = gw<T>(gh);
     T *upd = gupd<T>(gh);
     for (int it = 0; it < lambda; it++) {
-        for (int k = threadIdx.x; k < nrows; k += blockDim.x) {
-            int nst = gh.nst[k];
-            T s = b[gh.node[k]];
-            for (int q = 0; q < nst; q++) s -= w[(long long)q * gh.cap + k] * x[gh.st[(long long)q * gh.cap + k]];
-            upd[k] = dtau * s;
-        }
+        for (int k = threadIdx.x; k < nrows; k += blockDim.x) upd[k] = dtau * ghost_row_residual<T, false>(gh, k, x, b, nullptr);
         __syncthreads();
         for (int k = threadIdx.x; k < nrows; k += blockDim.x) x[gh.node[k]] += upd[k];
         __syncthreads();
@@ -1225,18 +1263,18 @@ static EncodeTiledFn encode_fn()
     return fn;
 }
 
-// 3-D tensor map over the three frames of a level (x: column, y: frame row,
-// z: frame), box = the tile window of k_box_tma
+// tensor map over `nf` frames of a level (x: column, y: frame row, z:
+// frame when nf = 3), box = the tile window of k_box_tma
 static bool encode_frames(CUtensorMap *m, const void *base, CUtensorMapDataType dt, int esize, const Level &l,
-                          long long frame_stride_bytes, int LW)
+                          long long frame_stride_bytes, int nf, int LW, int LH)
 {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
-    cuuint64_t dims[3] = {(cuuint64_t)l.P, (cuuint64_t)(l.N + 2), 3};
+    cuuint64_t dims[3] = {(cuuint64_t)l.P, (cuuint64_t)(l.N + 2), (cuuint64_t)nf};
     cuuint64_t strides[2] = {(cuuint64_t)l.P * esize, (cuuint64_t)frame_stride_bytes};
-    cuuint32_t box[3] = {(cuuint32_t)LW, (cuuint32_t)TT_LH, 3};
+    cuuint32_t box[3] = {(cuuint32_t)LW, (cuuint32_t)LH, (cuuint32_t)nf};
     cuuint32_t es[3] = {1, 1, 1};
-    return fn(m, dt, 3, const_cast<void *>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+    return fn(m, dt, nf > 1 ? 3 : 2, const_cast<void *>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
            CUDA_SUCCESS;
 }
@@ -1249,8 +1287,7 @@ template <typename T> static bool tiled(Ctx *c, int lev)
     // units, where the halo boxes a tile recomputes cost more than the four
     // extra passes over memory they save
     int tmin = c->prm.tile_min != 0 ? c->prm.tile_min : sizeof(T) == 4 ? TILE_MIN_N : -1;
-    if (tmin < 0 || l.N < tmin || !tile_scratch<T>(c, lev) || !encode_fn()) return false;
-    return l.tV - l.tU == l.tP - l.tV;  // the type frames are equally spaced (one 3-D map)
+    return tmin >= 0 && l.N >= tmin && tile_scratch<T>(c, lev) && encode_fn();
 }
 
 void prepare_cuts(Ctx *c)
@@ -1387,6 +1424,15 @@ int recolour_cuts(Ctx *c)
     return GP_OK;
 }
 
+// box codes of every level (k_box_codes); once per geometry
+void box_codes(Ctx *c)
+{
+    for (int lev = 0; lev < c->L; lev++) {
+        const Level &l = c->lv[lev];
+        k_box_codes<<<(unsigned)((l.F + 255) / 256), 256, 0, c->stream>>>(l.N, l.P, l.F, l.tU, l.tV, l.tP, l.bcode);
+    }
+}
+
 // For every stencil entry of every ghost-class row, the index of the row
 // whose unknown it is (or -1): the fused ghost sweeps read the accumulated
 // correction of that row.  Host work once per geometry.
@@ -1481,14 +1527,14 @@ template <typename T> static void box_pass(Ctx *c, int lev, const T *in, T *out,
     LevelArgs<T> A = level_args<T>(c, lev);
     bool done = false;
     if (out != in) {
-        constexpr int TW = TileGeom<T>::TW, LW = TileGeom<T>::LW;
+        constexpr int TW = TileGeom<T>::TW, LW = TileGeom<T>::LW, TH = TileGeom<T>::TH;
         const CUtensorMapDataType dt = sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
-        CUtensorMap mx, mt;
-        if (encode_frames(&mx, in, dt, (int)sizeof(T), l, l.F * (long long)sizeof(T), LW) &&
-            encode_frames(&mt, l.tU, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, l, (long long)(l.tV - l.tU), LW)) {
-            dim3 gt((l.P + TW - 1) / TW, (l.N + 2 + TT_H - 1) / TT_H);
+        CUtensorMap mx, mc;
+        if (encode_frames(&mx, in, dt, (int)sizeof(T), l, l.F * (long long)sizeof(T), 3, LW, tt_lh<T>()) &&
+            encode_frames(&mc, l.bcode, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, l, l.F, 1, LW, tt_lh<T>())) {
+            dim3 gt((l.P + TW - 1) / TW, (l.N + 2 + TH - 1) / TH);
             tmr_begin(c, KT_BOX_FULL, lev);
-            k_box_tma<T><<<gt, TT_THREADS, tt_smem<T>(), st>>>(mx, mt, A, in, b, out, c->err);
+            k_box_tma<T><<<gt, TileGeom<T>::THREADS, tt_smem<T>(), st>>>(mx, mc, A, in, b, out, c->err);
             tmr_end(c, KT_BOX_FULL, lev);
             c->launches++;
             done = true;

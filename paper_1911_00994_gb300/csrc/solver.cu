@@ -34,6 +34,7 @@ void tiles_init();
 void prepare_cuts(Ctx *c);
 int recolour_cuts(Ctx *c);
 int ghost_row_links(Ctx *c);
+void box_codes(Ctx *c);
 void krylov_init(Ctx *c, double *x, const double *b);
 void krylov_iteration(Ctx *c, double *x, const double *b);
 int residual_static(Ctx *c, int lev, const double *x, const double *b, double *r, double *norm_host);
@@ -123,6 +124,7 @@ static size_t carve(Ctx *c, char *base)
         l.tU = cv.take<uint8_t>(l.F);
         l.tV = cv.take<uint8_t>(l.F);
         l.tP = cv.take<uint8_t>(l.F);
+        l.bcode = cv.take<uint8_t>(l.F);
         l.prim = cv.take<uint8_t>(3 * l.F);
         l.done = cv.take<uint8_t>(3 * l.F);
         l.r = cv.take<double>(l.VL);
@@ -553,6 +555,7 @@ static gp_status geometry_finish(gp_ctx *ctx, const double *phi, int phi_fluid_p
     gp_status cs = check_cuda(ctx, "geometry_build");
     if (cs != GP_OK) return cs;
     c->geom_ok = 1;
+    box_codes(c);
     prepare_cuts(c);
     s = recolour_cuts(c);
     if (s == GP_OK) s = ghost_row_links(c);
