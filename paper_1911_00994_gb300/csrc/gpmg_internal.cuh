@@ -31,6 +31,7 @@ constexpr int ADJ_KMAX = 8;  // Picard iterations cn_step_adjoint can differenti
 // box codes (one byte per cell): a full box (internal cell, no ghost face)
 // and which of its four faces are internal
 constexpr unsigned BOX_FULL = 1, BOX_W = 2, BOX_E = 4, BOX_S = 8, BOX_N = 16, BOX_ALL = 31;
+constexpr int NGRAPH = 4 + GP_MAX_INNER - 1;  // captured iteration kinds
 constexpr int GH_ST = 9;  // stencil slots per ghost row
 
 // error bits written by kernels into the context's device status word
@@ -154,11 +155,13 @@ struct Ctx {
     long long tmr_launches;
     // captured mg_solve iterations: [0] FP64 cycle + residual, [1] FP32 cycle
     // inside FP64 residual correction, [2] / [3] BiCGSTAB iteration with an
-    // FP64 / FP32 cycle; keyed by the iterate and rhs pointers
-    cudaGraphExec_t gexec[4];
-    const void *gx[4], *gb[4];
-    int gvalid[4];
-    long long glaunches[4];
+    // FP64 / FP32 cycle, [4 + k - 2] k FP32 cycles inside one FP64 residual
+    // correction; keyed by the iterate and rhs pointers
+    cudaGraphExec_t gexec[NGRAPH];
+    const void *gx[NGRAPH], *gb[NGRAPH];
+    int gvalid[NGRAPH];
+    long long glaunches[NGRAPH];
+    int inner_now;       // FP32 cycles of the next residual correction
     int graphs_off;
     // BiCGSTAB vectors (finest level): r, rh, p, -v, s, -t, y, z, 0, true residual
     double *kv[10];

@@ -3,6 +3,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -96,7 +97,8 @@ static int validate(const gp_params *p, char *msg, size_t nmsg)
         return 0;
     }
     if (!(p->L > 0.0) || !(p->alpha >= 0.0) || p->nu1 < 0 || p->nu2 < 0 || p->gamma < 1 || p->gamma > 2 ||
-        p->lambda < 0 || p->max_cycles < 1 || (p->precision != GP_FP64 && p->precision != GP_MIXED)) {
+        p->lambda < 0 || p->max_cycles < 1 || (p->precision != GP_FP64 && p->precision != GP_MIXED) ||
+        p->inner < 0 || p->inner > GP_MAX_INNER) {
         snprintf(msg, nmsg, "invalid solver parameters");
         return 0;
     }
@@ -267,9 +269,9 @@ static void solve_iteration(Ctx *c, int which, double *x, const double *b)
     }
     if (which == 1) {
         // bf holds the FP64 residual of x rounded to FP32 (written by the
-        // previous residual)
+        // previous residual); c->inner_now FP32 cycles on the correction
         zero_vec<float>(c, l0.xf, l0.VL);
-        cycle_rec<float>(c, 0, l0.xf, l0.bf);
+        for (int k = 0; k < c->inner_now; k++) cycle_rec<float>(c, 0, l0.xf, l0.bf);
         add_float(c, x, l0.xf, l0.VL);
         residual_to_float(c, x, b, l0.bf);
     } else {
@@ -280,7 +282,7 @@ static void solve_iteration(Ctx *c, int which, double *x, const double *b)
 
 void graphs_reset(Ctx *c)
 {
-    for (int w = 0; w < 4; w++)
+    for (int w = 0; w < NGRAPH; w++)
         if (c->gvalid[w]) {
             cudaGraphExecDestroy(c->gexec[w]);
             c->gvalid[w] = 0;
@@ -289,8 +291,10 @@ void graphs_reset(Ctx *c)
 
 // replay (capturing first if needed) one iteration as a CUDA graph; false
 // when graphs are unavailable here (then the caller launches directly)
-static bool run_graph(Ctx *c, int which, double *x, const double *b)
+static bool run_graph(Ctx *c, int which0, double *x, const double *b)
 {
+    // slot: the iteration kind, and for the FP32 corrections their cycle count
+    const int which = (which0 == 1 && c->inner_now > 1) ? 4 + c->inner_now - 2 : which0;
     if (!c->prm.graphs || c->graphs_off || c->stream == nullptr || c->tmr_kernel >= 0) return false;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(c->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
@@ -308,7 +312,7 @@ static bool run_graph(Ctx *c, int which, double *x, const double *b)
             c->graphs_off = 1;
             return false;
         }
-        solve_iteration(c, which, x, b);
+        solve_iteration(c, which0, x, b);
         long long per = c->launches - l0;  // kernels of one iteration
         c->launches = l0;
         cudaGraph_t g = nullptr;
@@ -744,13 +748,24 @@ gp_status mg_solve(gp_ctx *ctx, double *x, const double *b, double tol, gp_repor
         if (rep->hist_host) rep->hist_host[0] = r0;
     }
     gp_status st = GP_NOT_CONVERGED;
-    int k = 0;
+    int k = 0, cycles = 0;
+    // FP32 corrections: the first takes one cycle; each later one as many
+    // as the reduction per cycle of the previous correction (taken 10%
+    // faster, so that a correction rarely overshoots tol) predicts are still
+    // needed, at most `inner`
+    const bool multi = mixed && !kry;
+    const int inner_max = c->prm.inner > 0 ? c->prm.inner : 3;
+    double prev = r0;
+    c->inner_now = 1;
     if (!(r0 == r0)) st = GP_DIVERGED;
     else if (r0 <= tol) st = GP_OK;
     else
-        for (k = 1; k <= c->prm.max_cycles; k++) {
+        for (k = 1; cycles < c->prm.max_cycles; k++) {
             int which = (kry ? 2 : 0) + (mixed ? 1 : 0);
+            if (multi) c->inner_now = std::min(c->inner_now, c->prm.max_cycles - cycles);
             if (!run_graph(c, which, x, b)) solve_iteration(c, which, x, b);
+            const int done = kry ? 2 : multi ? c->inner_now : 1;
+            cycles += done;
             cudaMemcpyAsync(&nrm, c->red, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
             if (cudaStreamSynchronize(c->stream) != cudaSuccess) return check_cuda(ctx, "mg_solve");
             if (rep && rep->hist_host) rep->hist_host[k] = nrm;
@@ -762,13 +777,22 @@ gp_status mg_solve(gp_ctx *ctx, double *x, const double *b, double tol, gp_repor
                 st = GP_OK;
                 break;
             }
+            if (multi) {
+                const double rate = 0.9 * pow(nrm / prev, 1.0 / done);
+                int want = 1;
+                if (!(tol > 0.0)) want = inner_max;
+                else if (rate > 0.0 && rate < 1.0) want = (int)std::min(ceil(log(tol / nrm) / log(rate)), (double)inner_max);
+                c->inner_now = std::max(1, std::min(inner_max, want));
+                prev = nrm;
+            }
         }
-    if (k > c->prm.max_cycles) k = c->prm.max_cycles;
+    if (cycles >= c->prm.max_cycles && st == GP_NOT_CONVERGED) k--;
+    c->inner_now = 1;
     if (rep) {
         rep->iterations = k;
-        rep->cycles = kry ? 2 * k : k;
+        rep->cycles = cycles;
         rep->res = nrm;
-        rep->rho = (k > 0 && r0 > 0 && nrm > 0) ? pow(nrm / r0, 1.0 / k) : 0.0;
+        rep->rho = (cycles > 0 && r0 > 0 && nrm > 0) ? pow(nrm / r0, 1.0 / cycles) : 0.0;
         double xi = 0.0;
         cudaMemcpyAsync(&xi, x + 3 * l0.F, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
         cudaStreamSynchronize(c->stream);

@@ -37,3 +37,19 @@ def test_layout_helpers():
     m = gpmg.flat_to_vec(8)
     assert len(m) == 2 * 9 * 10 + 64 + 1
     assert len(set(m.tolist())) == len(m)
+
+
+def test_parameter_checks_on_the_host():
+    # gp_params_default and gp_workspace_size make no CUDA call: defaults,
+    # a workspace size, and GP_INVALID for an inner-cycle count out of range
+    L = gpmg.lib()
+    p = gpmg.gp_params()
+    assert L.gp_params_default(ctypes.byref(p), 64, -1.0, -1.0, 2.0) == 0
+    assert p.inner == 0 and p.precision == gpmg.GP_FP64 and p.nu1 == 2 and p.nu2 == 1
+    nb = ctypes.c_size_t(0)
+    assert L.gp_workspace_size(ctypes.byref(p), ctypes.byref(nb)) == 0 and nb.value > 0
+    for bad in (-1, 5):
+        p.inner = bad
+        assert L.gp_workspace_size(ctypes.byref(p), ctypes.byref(nb)) == 1
+    p.inner = 4
+    assert L.gp_workspace_size(ctypes.byref(p), ctypes.byref(nb)) == 0

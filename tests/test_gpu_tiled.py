@@ -88,3 +88,32 @@ def test_tiled_mixed_solve_matches_oracle(case, N):
     st2, rep2, h_g2 = s2.solve(xg2, s2.to_device(b), 1e-10)
     assert st2 == 0
     assert abs(len(h_g) - len(h_g2)) <= 1
+
+
+@pytest.mark.parametrize("case,N", [("flower5", 256), ("ellipse", 200)])
+def test_mixed_inner_cycles(case, N):
+    # several FP32 cycles per FP64 residual correction, their number predicted
+    # from the last correction's rate: the oracle's FP64 solution to the
+    # tolerance, at most one cycle more than one cycle per correction, and
+    # fewer FP64 residuals
+    shape, x0, L = CASES[case]
+    h = L / N
+    alpha = h / 2000.0 if case == "flower5" else h / 200.0
+    o, s1 = pair(case, N, alpha=alpha, precision=1, inner=1)
+    ex = W.taylor_green()
+    b, xe, t, gh = manufactured(o, ex)
+    st_o, x_o, h_o = o.solve(np.zeros_like(b), b, 1e-10, 200)
+    assert st_o == 0
+    x1 = s1.new_vec()
+    st1, rep1, h1 = s1.solve(x1, s1.to_device(b), 1e-10)
+    assert st1 == 0 and rep1.iterations == rep1.cycles
+    for inner in (2, 3, 4):
+        _, s3 = pair(case, N, alpha=alpha, precision=1, inner=inner)
+        x3 = s3.new_vec()
+        st3, rep3, h3 = s3.solve(x3, s3.to_device(b), 1e-10)
+        assert st3 == 0, s3.error()
+        assert rep3.res <= 1e-10 and h3[-1] <= 1e-10
+        assert rel(s3.to_flat(x3), x_o) <= 1e-8
+        assert rep3.cycles <= rep1.cycles + 1, (inner, rep3.cycles, rep1.cycles)
+        assert rep3.iterations < rep1.iterations
+        assert len(h3) == rep3.iterations + 1
