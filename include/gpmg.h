@@ -86,7 +86,7 @@ typedef struct gp_params {
     int adjoint;        /* nonzero: carve the arrays of the adjoint solve (mg_solve_t and the
                            gp_*_t calls; one FP64 vector per level and the ghost column lists) */
     int inner;          /* GP_MIXED without krylov: most FP32 cycles per FP64 residual correction
-                           (1..GP_MAX_INNER; 0: 3).  After the first correction mg_solve takes as
+                           (1..GP_MAX_INNER; 0: GP_MAX_INNER).  After the first correction mg_solve takes as
                            many as the last corrections' reduction rate predicts are still needed
                            to reach tol, so the cycle count stays that of one cycle per
                            correction while the FP64 residuals are fewer */

@@ -143,7 +143,7 @@ struct Ctx {
     int npart;
     double *red;        // small result area (device)
     unsigned long long *maxbits;
-    unsigned *err;      // device error word
+    unsigned *err;      // device error words: [0] geometry / coarse factorisation, [2] a tile copy wait ran out
     int *flag;          // device change flag
     double hostbuf[8];   // host staging for small device-to-host reads
     // instrumentation: kernels launched, and an optional event timer around

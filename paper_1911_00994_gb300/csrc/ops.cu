@@ -20,7 +20,8 @@ namespace gpmg {
 constexpr int SMALL_N = 64;  // levels whose whole relaxation runs in one block
 constexpr int TILE_MIN_N = 512;  // default finest size swept by TMA tiles (gp_params.tile_min overrides)
 constexpr int GHOST_BLOCK_ROWS = 4096;
-constexpr int CUT_SPLIT = 64;  // cut boxes per colour above which the cut sweep runs on a cluster of CTAs
+constexpr int CUT_SPLIT = 64;  // cut boxes per colour above which the cut sweep leaves a single block
+constexpr int CUT_COLOUR_LAUNCHES = 6;  // at most this many colours: one launch per colour, else one cluster
 
 // constants of the box solves of one level (Sect. 4.1.1), reciprocals
 // precomputed so that a box needs no division
@@ -37,6 +38,7 @@ template <typename T> struct LevelArgs {
     T q, a, d;          // 1/h, alpha/h^2, 1 + 4 alpha/h^2
     T h2;               // h^2
     const uint8_t *tU, *tV, *tP;
+    const uint8_t *bc;  // box codes
     BoxK<T> K;
 };
 
@@ -138,34 +140,36 @@ __global__ void __launch_bounds__(256) k_residual4(LevelArgs<T> A, const T *x, c
     const T *u = x, *v = x + F, *p = x + 2 * F;
     const T xi = x[3 * F];
     for (long long qd = blockIdx.x * (long long)blockDim.x + threadIdx.x; qd < nq; qd += (long long)gridDim.x * blockDim.x) {
-        const long long s0 = 4 * qd;
-        const int row = (int)(s0 / P);
+        // F < 2^31 (checked when the context is created), so slots fit an int
+        const int s0 = (int)(4 * qd);
+        const int row = s0 / P;
         R ru[4] = {0, 0, 0, 0}, rv[4] = {0, 0, 0, 0}, rp[4] = {0, 0, 0, 0};
         uint8_t tu[4], tv[4], tp[4];
         ldt4(A.tU + s0, tu);
         ldt4(A.tV + s0, tv);
         ldt4(A.tP + s0, tp);
-        bool any = false;
-#pragma unroll
-        for (int q = 0; q < 4; q++) any |= tu[q] == T_INTERNAL || tv[q] == T_INTERNAL || tp[q] == T_INTERNAL;
-        if (any && row > 0 && row < A.N + 1) {
-            T uh[6], uU[4], uD[4], vh[6], vU[4], vD[4], ph[5], pD[4], bu[4], bv[4], bp[4];
-            ld4(u + s0, uh + 1);
-            uh[0] = u[s0 - 1];
-            uh[5] = u[s0 + 4];
-            ld4(u + s0 + P, uU);
-            ld4(u + s0 - P, uD);
-            ld4(v + s0, vh + 1);
-            vh[0] = v[s0 - 1];
-            vh[5] = v[s0 + 4];
-            ld4(v + s0 + P, vU);
-            ld4(v + s0 - P, vD);
-            ld4(p + s0, ph + 1);
-            ph[0] = p[s0 - 1];
-            ld4(p + s0 - P, pD);
-            ld4(b + s0, bu);
-            ld4(b + F + s0, bv);
-            ld4(b + 2 * F + s0, bp);
+        // every load is issued before the types are tested: the neighbour
+        // rows and columns are clamped into the frame on its first and last
+        // rows, where no internal row is
+        const int up = row < A.N + 1 ? P : 0, dn = row > 0 ? P : 0, lf = s0 > 0 ? 1 : 0;
+        T uh[6], uU[4], uD[4], vh[6], vU[4], vD[4], ph[5], pD[4], bu[4], bv[4], bp[4];
+        ld4(u + s0, uh + 1);
+        uh[0] = u[s0 - lf];
+        uh[5] = u[s0 + 4];
+        ld4(u + s0 + up, uU);
+        ld4(u + s0 - dn, uD);
+        ld4(v + s0, vh + 1);
+        vh[0] = v[s0 - lf];
+        vh[5] = v[s0 + 4];
+        ld4(v + s0 + up, vU);
+        ld4(v + s0 - dn, vD);
+        ld4(p + s0, ph + 1);
+        ph[0] = p[s0 - lf];
+        ld4(p + s0 - dn, pD);
+        ld4(b + s0, bu);
+        ld4(b + F + s0, bv);
+        ld4(b + 2 * F + s0, bp);
+        if (row > 0 && row < A.N + 1) {
 #pragma unroll
             for (int q = 0; q < 4; q++) {
                 if (tu[q] == T_INTERNAL) {
@@ -329,15 +333,19 @@ __device__ __forceinline__ void box_core(T *u, T *v, T *p, const int pitch, cons
     p[0] += dp;
 }
 
+// the full box of cell (i, j), if it is one (box code BOX_FULL)
 template <typename T>
 __device__ __forceinline__ void box_full_one(const LevelArgs<T> &A, T *x, const T *b, int i, int j)
 {
-    long long s = (long long)(j + 1) * A.P + (i + 1);
-    if (A.tP[s] != T_INTERNAL) return;
-    uint8_t tW = A.tU[s], tE = A.tU[s + 1], tS = A.tV[s], tN = A.tV[s + A.P];
-    if (tW == T_GHOST || tE == T_GHOST || tS == T_GHOST || tN == T_GHOST) return;
-    box_core<T>(x + s, x + A.F + s, x + 2 * A.F + s, A.P, b + s, b + A.F + s, b + 2 * A.F + s, A.P, x[3 * A.F],
-                tW == T_INTERNAL, tE == T_INTERNAL, tS == T_INTERNAL, tN == T_INTERNAL, A.K);
+    const long long s = (long long)(j + 1) * A.P + (i + 1);
+    const unsigned code = A.bc[s];
+    if (!(code & BOX_FULL)) return;
+    if (code == BOX_ALL)
+        box_core<T, true>(x + s, x + A.F + s, x + 2 * A.F + s, A.P, b + s, b + A.F + s, b + 2 * A.F + s, A.P,
+                          x[3 * A.F], true, true, true, true, A.K);
+    else
+        box_core<T>(x + s, x + A.F + s, x + 2 * A.F + s, A.P, b + s, b + A.F + s, b + 2 * A.F + s, A.P, x[3 * A.F],
+                    code & BOX_W, code & BOX_E, code & BOX_S, code & BOX_N, A.K);
 }
 
 // All five colours of the full boxes in one pass over the level.  Each
@@ -774,6 +782,13 @@ template <typename T> __global__ void __launch_bounds__(CL_THREADS) k_box_cut_cl
     }
 }
 
+// the cut boxes [beg, end) of one colour, a warp per box over the whole GPU
+template <typename T> __global__ void __launch_bounds__(256) k_box_cut_colour(T *x, const T *b, CutList cut, int beg, int end)
+{
+    const int k = beg + (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (k < end) box_cut_warp<T>(x, b, cut, k, threadIdx.x & 31);
+}
+
 // internal faces with no internal cell: point Jacobi (compute, then apply)
 template <typename T>
 __global__ void k_lonely_update(LevelArgs<T> A, const T *x, const T *b, const int *list, int n, T *upd)
@@ -951,38 +966,49 @@ __global__ void k_restrict(int Nf, int Pf, long long Ff, const uint8_t *tUf, con
     int I = col - 1, J = row - 1;
     long long sc = (long long)row * Pc + col;
     const uint8_t *tf[3] = {tUf, tVf, tPf};
-    const uint8_t *tc[3] = {tUc, tVc, tPc};
+    const uint8_t tcg[3] = {tUc[sc], tVc[sc], tPc[sc]};
+    // every type and residual of the three stencils is loaded before the
+    // arithmetic (fine indices clamped into the frame; only nodes of the
+    // grid take part)
+    uint8_t tff[3][6];
+    T rv[3][6];
+    bool in[3][6];
+#pragma unroll
+    for (int g = 0; g < 3; g++)
+#pragma unroll
+        for (int k = 0; k < 6; k++) {
+            int di, dj;
+            if (g == G_U) { di = k % 3 - 1; dj = k / 3; }
+            else if (g == G_V) { di = k % 2; dj = k / 2 - 1; }
+            else { di = k % 2; dj = k / 2; }
+            const int fi = 2 * I + di, fj = 2 * J + dj;
+            in[g][k] = (g != G_P || k < 4) && in_grid(g, Nf, fi, fj);
+            const int ci = min(max(fi, -1), Nf), cj = min(max(fj, -1), Nf);
+            const long long sl = (long long)(cj + 1) * Pf + (ci + 1);
+            tff[g][k] = tf[g][sl];
+            rv[g][k] = r[g * Ff + sl];
+        }
+#pragma unroll
     for (int g = 0; g < 3; g++) {
-        uint8_t t = tc[g][sc];
-        if (t == T_INACTIVE) {
-            bH[g * Fc + sc] = 0;
-            continue;
+        const uint8_t t = tcg[g];
+        T out = 0;
+        if (t != T_INACTIVE) {
+            bool all = true;
+            int cnt = 0;
+            T sw = 0, su = 0;
+#pragma unroll
+            for (int k = 0; k < 6; k++) {
+                if (g == G_P && k >= 4) break;
+                const T wt = g == G_U ? (T)(k % 3 == 1 ? 0.25 : 0.125) : g == G_V ? (T)(k / 2 == 1 ? 0.25 : 0.125) : (T)0.25;
+                if (in[g][k] && same_class(t, tff[g][k])) {
+                    sw += wt * rv[g][k];
+                    su += rv[g][k];
+                    cnt++;
+                } else all = false;
+            }
+            out = all ? sw : (cnt > 0 ? su / (T)cnt : (T)0);
         }
-        int fi[6], fj[6], ns = 0;
-        T wt[6];
-        if (g == G_U) {
-            for (int dj = 0; dj <= 1; dj++)
-                for (int di = -1; di <= 1; di++) { fi[ns] = 2 * I + di; fj[ns] = 2 * J + dj; wt[ns] = (T)(di == 0 ? 0.25 : 0.125); ns++; }
-        } else if (g == G_V) {
-            for (int dj = -1; dj <= 1; dj++)
-                for (int di = 0; di <= 1; di++) { fi[ns] = 2 * I + di; fj[ns] = 2 * J + dj; wt[ns] = (T)(dj == 0 ? 0.25 : 0.125); ns++; }
-        } else {
-            for (int dj = 0; dj <= 1; dj++)
-                for (int di = 0; di <= 1; di++) { fi[ns] = 2 * I + di; fj[ns] = 2 * J + dj; wt[ns] = (T)0.25; ns++; }
-        }
-        bool all = true;
-        int cnt = 0;
-        T sw = 0, su = 0;
-        for (int k = 0; k < ns; k++) {
-            uint8_t tff = tget(tf[g], g, Nf, Pf, fi[k], fj[k]);
-            if (same_class(t, tff)) {
-                T v = r[g * Ff + (long long)(fj[k] + 1) * Pf + (fi[k] + 1)];
-                sw += wt[k] * v;
-                su += v;
-                cnt++;
-            } else all = false;
-        }
-        bH[g * Fc + sc] = all ? sw : (cnt > 0 ? su / (T)cnt : (T)0);
+        bH[g * Fc + sc] = out;
     }
     if (row == 0 && col == 0) bH[3 * Fc] = r[3 * Ff];
 }
@@ -1220,6 +1246,7 @@ template <typename T> LevelArgs<T> level_args(const Ctx *c, int lev)
     A.tU = l.tU;
     A.tV = l.tV;
     A.tP = l.tP;
+    A.bc = l.bcode;
     const double q = 1.0 / h, a = c->prm.alpha / (h * h), d = 1.0 + 4.0 * a;
     A.K.a = (T)a;
     A.K.d = (T)d;
@@ -1555,7 +1582,17 @@ template <typename T> static void box_pass(Ctx *c, int lev, const T *in, T *out,
     T *x = out;
     int most = 0;  // largest colour of cut boxes
     for (int colour = 0; colour < l.cut.ncol; colour++) most = max(most, l.h_cutoff[colour + 1] - l.h_cutoff[colour]);
-    if (most > CUT_SPLIT) {
+    if (most > CUT_SPLIT && l.cut.ncol <= CUT_COLOUR_LAUNCHES) {
+        // few colours with many boxes each: one launch per colour across the GPU
+        tmr_begin(c, KT_BOX_CUT, lev);
+        for (int colour = 0; colour < l.cut.ncol; colour++) {
+            const int beg = l.h_cutoff[colour], end = l.h_cutoff[colour + 1];
+            if (end <= beg) continue;
+            k_box_cut_colour<T><<<(end - beg + 7) / 8, 256, 0, st>>>(x, b, l.cut, beg, end);
+            c->launches++;
+        }
+        tmr_end(c, KT_BOX_CUT, lev);
+    } else if (most > CUT_SPLIT) {
         tmr_begin(c, KT_BOX_CUT, lev);
         launch_cluster(st, CL_THREADS, k_box_cut_cluster<T>, x, b, l.cut);
         tmr_end(c, KT_BOX_CUT, lev);

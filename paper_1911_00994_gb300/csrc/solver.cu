@@ -374,6 +374,15 @@ static gp_status ensure_coarse(gp_ctx *ctx)
 
 static bool level_ok(gp_ctx *ctx, int level) { return ctx && level >= 0 && level < ctx->c.L; }
 
+// why a solve diverged, when the bounded wait of a tile copy ran out
+static const char *wait_note(Ctx *c)
+{
+    unsigned e[4] = {0, 0, 0, 0};
+    cudaMemcpyAsync(e, c->err, sizeof e, cudaMemcpyDeviceToHost, c->stream);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return "";
+    return e[2] ? " (a tile copy wait ran out)" : "";
+}
+
 extern "C" {
 
 gp_status gp_params_default(gp_params *prm, int N, double x0, double y0, double L)
@@ -447,6 +456,7 @@ gp_status gp_create(gp_ctx **out, const gp_params *prm, void *workspace, size_t 
     coarse_maps_host(lc.N, lc.P, lc.F, maps.data(), maps.data() + c->nc, lc.VL);
     cudaError_t e = cudaMemcpyAsync(c->cmap, maps.data(), maps.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->maxbits, 0, 4 * sizeof(unsigned long long), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->err, 0, 4 * sizeof(unsigned), c->stream);
     for (int k = 0; k < c->L && e == cudaSuccess; k++) {
         Level &l = c->lv[k];
         e = cudaMemsetAsync(l.r, 0, l.VL * sizeof(double), c->stream);
@@ -754,7 +764,7 @@ gp_status mg_solve(gp_ctx *ctx, double *x, const double *b, double tol, gp_repor
     // faster, so that a correction rarely overshoots tol) predicts are still
     // needed, at most `inner`
     const bool multi = mixed && !kry;
-    const int inner_max = c->prm.inner > 0 ? c->prm.inner : 3;
+    const int inner_max = c->prm.inner > 0 ? c->prm.inner : GP_MAX_INNER;
     double prev = r0;
     c->inner_now = 1;
     if (!(r0 == r0)) st = GP_DIVERGED;
@@ -799,7 +809,7 @@ gp_status mg_solve(gp_ctx *ctx, double *x, const double *b, double tol, gp_repor
         rep->xi = xi;
     }
     if (st == GP_NOT_CONVERGED) snprintf(c->msg, sizeof c->msg, "not converged: %.3e after %d cycles", nrm, k);
-    if (st == GP_DIVERGED) snprintf(c->msg, sizeof c->msg, "diverged: %.3e (initial %.3e)", nrm, r0);
+    if (st == GP_DIVERGED) snprintf(c->msg, sizeof c->msg, "diverged: %.3e (initial %.3e)%s", nrm, r0, wait_note(c));
     gp_status cs = check_cuda(ctx, "mg_solve");
     return cs != GP_OK ? cs : st;
 }

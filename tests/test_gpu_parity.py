@@ -217,3 +217,4 @@ def test_large_level_relaxation_matches():
     xg = s.to_device(x)
     s.ghost_sweep(xg, s.to_device(b), 0)
     assert rel(s.to_flat(xg), want) < 1e-12
+
