@@ -105,7 +105,7 @@ def kernel_source_sha1():
     parts = []
     a = src.index("template <typename T> struct BoxK")
     parts.append(src[a:src.index("template <typename T> struct LevelArgs", a)])
-    a = src.index("template <typename T>\n__device__ __forceinline__ void box_core(")
+    a = src.index("__device__ __forceinline__ void box_solve(")
     parts.append(src[a:src.index("    p[0] += dp;\n}\n", a)])
     a = src.index("template <typename T> struct TileGeom;")
     b = src.index("k_box_tma(", a)

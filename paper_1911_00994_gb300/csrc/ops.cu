@@ -268,22 +268,22 @@ __global__ void k_residual_final(const double *part, int nb, const T *b, R *r, l
 // Box relaxation of one cell without ghost borders (Sect. 4.1.1): Schur
 // complement of the pressure unknown.  u, v, p point at the cell's slot in
 // arrays of row pitch `pitch` (global frames or a shared-memory tile); bu, bv,
-// bp at the cell's slot of the right-hand side.  W, E, S, Nn: the faces
-// that are internal (the others stay frozen); ALL: all four are.
+// bW, bE, bS, bN, bC: the right-hand side of the box's five rows.  W, E, S,
+// Nn: the faces that are internal (the others stay frozen); ALL: all four are.
 template <typename T, bool ALL = false>
-__device__ __forceinline__ void box_core(T *u, T *v, T *p, const int pitch, const T *bu, const T *bv, const T *bp,
-                                         const long long bpitch, const T xi, bool W, bool E, bool S, bool Nn,
-                                         const BoxK<T> &K)
+__device__ __forceinline__ void box_solve(T *u, T *v, T *p, const int pitch, const T bW, const T bE, const T bS,
+                                          const T bN, const T bC, const T xi, bool W, bool E, bool S, bool Nn,
+                                          const BoxK<T> &K)
 {
     const int Pp = pitch;
     const T a = K.a, d = K.d, q = K.q;
     if (ALL) W = E = S = Nn = true;
     T rW = 0, rE = 0, rS = 0, rN = 0;
-    if (W) rW = bu[0] - (d * u[0] - a * (u[1] + u[-1] + u[Pp] + u[-Pp]) + q * (p[0] - p[-1]));
-    if (E) rE = bu[1] - (d * u[1] - a * (u[2] + u[0] + u[1 + Pp] + u[1 - Pp]) + q * (p[1] - p[0]));
-    if (S) rS = bv[0] - (d * v[0] - a * (v[1] + v[-1] + v[Pp] + v[-Pp]) + q * (p[0] - p[-Pp]));
-    if (Nn) rN = bv[bpitch] - (d * v[Pp] - a * (v[Pp + 1] + v[Pp - 1] + v[2 * Pp] + v[0]) + q * (p[Pp] - p[0]));
-    T rC = bp[0] - (q * (u[1] - u[0] + v[Pp] - v[0]) - xi);
+    if (W) rW = bW - (d * u[0] - a * (u[1] + u[-1] + u[Pp] + u[-Pp]) + q * (p[0] - p[-1]));
+    if (E) rE = bE - (d * u[1] - a * (u[2] + u[0] + u[1 + Pp] + u[1 - Pp]) + q * (p[1] - p[0]));
+    if (S) rS = bS - (d * v[0] - a * (v[1] + v[-1] + v[Pp] + v[-Pp]) + q * (p[0] - p[-Pp]));
+    if (Nn) rN = bN - (d * v[Pp] - a * (v[Pp + 1] + v[Pp - 1] + v[2 * Pp] + v[0]) + q * (p[Pp] - p[0]));
+    T rC = bC - (q * (u[1] - u[0] + v[Pp] - v[0]) - xi);
     // eliminating the velocities leaves c1 dp = rC - c0 for the pressure;
     // each direction contributes to c0, and c1 depends only on which faces
     // take part
@@ -331,6 +331,15 @@ __device__ __forceinline__ void box_core(T *u, T *v, T *p, const int pitch, cons
     } else if (S) v[0] += fS * K.id;
     else if (Nn) v[Pp] += fN * K.id;
     p[0] += dp;
+}
+
+// the same with the right-hand side read at bu, bv, bp (bN at bv[bpitch])
+template <typename T, bool ALL = false>
+__device__ __forceinline__ void box_core(T *u, T *v, T *p, const int pitch, const T *bu, const T *bv, const T *bp,
+                                         const long long bpitch, const T xi, bool W, bool E, bool S, bool Nn,
+                                         const BoxK<T> &K)
+{
+    box_solve<T, ALL>(u, v, p, pitch, bu[0], bu[1], bv[0], bv[bpitch], bp[0], xi, W, E, S, Nn, K);
 }
 
 // the full box of cell (i, j), if it is one (box code BOX_FULL)
@@ -1462,41 +1471,42 @@ void box_codes(Ctx *c)
 
 // For every stencil entry of every ghost-class row, the index of the row
 // whose unknown it is (or -1): the fused ghost sweeps read the accumulated
-// correction of that row.  Host work once per geometry.
+// correction of that row.  Once per geometry, on the device: the rows are
+// scattered into a node -> row map over the level's vector (held in the
+// level's residual vector, free at this point), then read back per entry.
+__global__ void k_row_of_node(const int *node, int n, int *map)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) map[node[k]] = k;
+}
+
+__global__ void k_stencil_rows(GhostList gh, int n, const int *map)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int nst = gh.nst[k];
+    for (int q = 0; q < GH_ST; q++) {
+        const long long e = (long long)q * gh.cap + k;
+        gh.strow[e] = q < nst ? map[gh.st[e]] : -1;
+    }
+}
+
 int ghost_row_links(Ctx *c)
 {
     cudaStream_t st = c->stream;
     for (int lev = 0; lev < c->L; lev++) {
         Level &l = c->lv[lev];
-        const int n = l.h_nrows, cap = l.gh.cap;
+        const int n = l.h_nrows;
         if (n <= 0) continue;
-        std::vector<int> node(n), sti((size_t)GH_ST * n), out((size_t)GH_ST * n, -1);
-        std::vector<uint8_t> nst(n);
-        cudaMemcpyAsync(node.data(), l.gh.node, sizeof(int) * n, cudaMemcpyDeviceToHost, st);
-        cudaMemcpyAsync(nst.data(), l.gh.nst, n, cudaMemcpyDeviceToHost, st);
-        for (int q = 0; q < GH_ST; q++)
-            cudaMemcpyAsync(sti.data() + (size_t)q * n, l.gh.st + (size_t)q * cap, sizeof(int) * n,
-                            cudaMemcpyDeviceToHost, st);
-        if (cudaStreamSynchronize(st) != cudaSuccess) {
-            snprintf(c->msg, sizeof c->msg, "ghost links: %s", cudaGetErrorString(cudaGetLastError()));
-            return GP_CUDA;
-        }
-        std::unordered_map<int, int> row;
-        row.reserve((size_t)n * 2);
-        for (int k = 0; k < n; k++) row.emplace(node[k], k);
-        for (int k = 0; k < n; k++)
-            for (int q = 0; q < nst[k]; q++) {
-                auto it = row.find(sti[(size_t)q * n + k]);
-                if (it != row.end()) out[(size_t)q * n + k] = it->second;
-            }
-        for (int q = 0; q < GH_ST; q++)
-            cudaMemcpyAsync(l.gh.strow + (size_t)q * cap, out.data() + (size_t)q * n, sizeof(int) * n,
-                            cudaMemcpyHostToDevice, st);
-        // the host vector must outlive the copies
-        if (cudaStreamSynchronize(st) != cudaSuccess) {
-            snprintf(c->msg, sizeof c->msg, "ghost links: %s", cudaGetErrorString(cudaGetLastError()));
-            return GP_CUDA;
-        }
+        int *map = (int *)l.r;  // VL ints fit in the VL doubles of r
+        cudaMemsetAsync(map, 0xff, sizeof(int) * (size_t)l.VL, st);
+        k_row_of_node<<<(n + 255) / 256, 256, 0, st>>>(l.gh.node, n, map);
+        k_stencil_rows<<<(n + 255) / 256, 256, 0, st>>>(l.gh, n, map);
+    }
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        snprintf(c->msg, sizeof c->msg, "ghost links: %s", cudaGetErrorString(e));
+        return GP_CUDA;
     }
     return GP_OK;
 }
