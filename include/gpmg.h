@@ -70,7 +70,8 @@ typedef struct gp_params {
     double dtau;        /* fictitious time step of Eq. (ghostrelax) */
     double snap;        /* a node within snap*h of the boundary counts as external */
     int precision;      /* gp_precision */
-    int max_cycles;     /* cap for mg_solve */
+    int max_cycles;     /* cap for mg_solve: cycles of the FP32 corrections (GP_MIXED without krylov),
+                           iterations otherwise */
     int cn_buffers;     /* nonzero: carve the four finest-level vectors cn_step needs */
     int graphs;         /* nonzero: mg_solve replays each cycle as a captured CUDA graph
                            (needs a stream other than the legacy default stream) */

@@ -1,7 +1,8 @@
 // Exact solve on the coarsest grid (Sect. 4.3): the coarsest system is
 // assembled densely (flat unknown order: u block, v block, p block, xi) and
 // inverted once per geometry by Gauss-Jordan elimination with partial
-// pivoting; each cycle then applies the inverse with one GEMV.
+// pivoting (one launch per column); each cycle then applies the inverse with
+// one GEMV.
 #include <cmath>
 #include <cstdio>
 
@@ -67,68 +68,83 @@ __global__ void k_dense_mean_row(double *aug, int n, const int *cmap, long long 
     }
 }
 
-// pivot search in column k (first largest |a_rk|, r >= k), row swap and
-// scaling of the pivot row; one block
-__global__ void k_gj_pivot(double *aug, int n, int k, unsigned *err)
+// Gauss-Jordan elimination with partial pivoting, one launch per column and
+// no row exchanges or scaling: step k eliminates column k from every row
+// but the pivot row p_k (the unused row with the largest |a_ik|), which
+// keeps its place and scale.  Afterwards row p_k holds a_{p_k,k} in the left
+// half and a_{p_k,k} times row k of the inverse in the right half.  The
+// pivot of column k + 1 is chosen during step k from the updated column:
+// keys[k + 1] is the atomic maximum of (top 32 bits of |a_i,k+1|, ~i) over
+// the rows not yet used, so the first of equally large candidates wins.
+
+__device__ __forceinline__ unsigned long long pivot_key(double v, int i)
 {
-    __shared__ double bv[1024];
-    __shared__ int br[1024];
-    double best = -1.0;
-    int brow = k;
-    for (int r = k + threadIdx.x; r < n; r += blockDim.x) {
-        double v = fabs(aug[(long long)r * 2 * n + k]);
-        if (v > best) { best = v; brow = r; }
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(fabs(v));
+    return ((bits >> 32) << 32) | (unsigned long long)(0xffffffffu - (unsigned)i);
+}
+
+__device__ __forceinline__ int pivot_row(unsigned long long key) { return (int)(0xffffffffu - (unsigned)key); }
+
+// pivot of column 0
+__global__ void k_gj_first(const double *aug, int n, unsigned long long *keys)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        const unsigned long long key = pivot_key(aug[(long long)i * 2 * n], i);
+        if (key >> 32) atomicMax(keys, key);
     }
-    bv[threadIdx.x] = best;
-    br[threadIdx.x] = brow;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) {
-            double v2 = bv[threadIdx.x + o];
-            int r2 = br[threadIdx.x + o];
-            if (v2 > bv[threadIdx.x] || (v2 == bv[threadIdx.x] && r2 < br[threadIdx.x])) {
-                bv[threadIdx.x] = v2;
-                br[threadIdx.x] = r2;
-            }
-        }
-        __syncthreads();
-    }
-    int piv = br[0];
-    double pval = aug[(long long)piv * 2 * n + k];
-    if (!(bv[0] > 0.0)) {
-        if (threadIdx.x == 0) atomicOr(err, E_SINGULAR);
+}
+
+// step k over a 32-column x 8-row tile per block (a warp is 32 columns of one row)
+__global__ void __launch_bounds__(256) k_gj_step(double *aug, int n, int k, unsigned long long *keys, uint8_t *used,
+                                                 unsigned *err)
+{
+    const long long W = 2LL * n;
+    const int j = blockIdx.x * 32 + threadIdx.x, i = blockIdx.y * 8 + threadIdx.y;
+    if (blockIdx.x * 32 + 31 <= k) return;  // the whole tile lies in eliminated columns
+    const unsigned long long key = keys[k];
+    if (!(key >> 32)) {  // no nonzero candidate in column k
+        if (threadIdx.x == 0 && threadIdx.y == 0 && blockIdx.x == gridDim.x - 1 && blockIdx.y == 0)
+            atomicOr(err, E_SINGULAR);
         return;
     }
+    const int p = pivot_row(key);
+    __shared__ double s_rp;
+    __shared__ unsigned long long s_best[8];
+    if (threadIdx.x == 0 && threadIdx.y == 0) s_rp = 1.0 / aug[(long long)p * W + k];
     __syncthreads();
-    for (int c = threadIdx.x; c < 2 * n; c += blockDim.x) {
-        double a = aug[(long long)piv * 2 * n + c];
-        double b = aug[(long long)k * 2 * n + c];
-        aug[(long long)piv * 2 * n + c] = b;
-        aug[(long long)k * 2 * n + c] = a / pval;
+    unsigned long long cand = 0;
+    if (i < n && i != p && j > k && j < W) {
+        const double m = aug[(long long)i * W + k] * s_rp;
+        double v = aug[(long long)i * W + j];
+        if (m != 0.0) v -= m * aug[(long long)p * W + j];
+        aug[(long long)i * W + j] = v;
+        if (j == k + 1 && k + 1 < n && !used[i]) cand = pivot_key(v, i);
+    }
+    if (i == p && j == W - 1) used[p] = 1;
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long c2 = __shfl_xor_sync(0xffffffffu, cand, o);
+        cand = c2 > cand ? c2 : cand;
+    }
+    if (threadIdx.x == 0) s_best[threadIdx.y] = cand;
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        unsigned long long best = 0;
+        for (int y = 0; y < 8; y++) best = s_best[y] > best ? s_best[y] : best;
+        if (best >> 32) atomicMax(keys + k + 1, best);
     }
 }
 
-__global__ void k_gj_factors(const double *aug, int n, int k, double *fac)
+// row k of the inverse from the pivot row of column k
+__global__ void k_gj_extract(const double *aug, int n, const unsigned long long *keys, double *Minv, float *Minvf)
 {
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r < n) fac[r] = r == k ? 0.0 : aug[(long long)r * 2 * n + k];
-}
-
-__global__ void k_gj_eliminate(double *aug, int n, int k, const double *fac)
-{
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    int r = blockIdx.y;
-    if (c >= 2 * n || r == k) return;
-    double f = fac[r];
-    if (f != 0.0) aug[(long long)r * 2 * n + c] -= f * aug[(long long)k * 2 * n + c];
-}
-
-__global__ void k_gj_extract(const double *aug, int n, double *Minv, float *Minvf)
-{
-    long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (e >= (long long)n * n) return;
-    long long r = e / n, c = e % n;
-    double v = aug[r * 2 * n + n + c];
+    const long long r = e / n, c = e % n;
+    const unsigned long long key = keys[r];
+    // a singular matrix (flagged by the steps) leaves later keys empty
+    const int p = (key >> 32) ? pivot_row(key) : -1;
+    const double v = p >= 0 ? aug[(long long)p * 2 * n + n + c] / aug[(long long)p * 2 * n + r] : 0.0;
     Minv[e] = v;
     Minvf[e] = (float)v;
 }
@@ -192,14 +208,13 @@ int build_coarse_inverse(Ctx *c)
     if (l.h_nrows > 0) k_dense_ghost_rows<<<(l.h_nrows + 127) / 128, 128, 0, st>>>(c->aug, n, inv, l.gh, l.h_nrows);
     k_dense_mean_row<<<1, 1, 0, st>>>(c->aug, n, c->cmap, l.F, l.tP, h * h);
     cudaMemsetAsync(c->err, 0, sizeof(unsigned), st);
-    dim3 ge((2 * n + 255) / 256, n);
-    for (int k = 0; k < n; k++) {
-        k_gj_pivot<<<1, 1024, 0, st>>>(c->aug, n, k, c->err);
-        k_gj_factors<<<(n + 255) / 256, 256, 0, st>>>(c->aug, n, k, c->cvec);
-        k_gj_eliminate<<<ge, 256, 0, st>>>(c->aug, n, k, c->cvec);
-    }
+    cudaMemsetAsync(c->gjkeys, 0, sizeof(unsigned long long) * n, st);
+    cudaMemsetAsync(c->gjused, 0, n, st);
+    k_gj_first<<<(n + 255) / 256, 256, 0, st>>>(c->aug, n, c->gjkeys);
+    const dim3 ge((2 * n + 31) / 32, (n + 7) / 8), be(32, 8);
+    for (int k = 0; k < n; k++) k_gj_step<<<ge, be, 0, st>>>(c->aug, n, k, c->gjkeys, c->gjused, c->err);
     long long nn = (long long)n * n;
-    k_gj_extract<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(c->aug, n, c->Minv, c->Minvf);
+    k_gj_extract<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(c->aug, n, c->gjkeys, c->Minv, c->Minvf);
     unsigned herr = 0;
     cudaMemcpyAsync(&herr, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
     cudaError_t e = cudaStreamSynchronize(st);

@@ -134,6 +134,8 @@ struct Ctx {
     double *Minv;       // nc x nc
     float *Minvf;
     double *aug;        // nc x 2nc work for Gauss-Jordan
+    unsigned long long *gjkeys;  // nc pivot keys (|a| and row) of the Gauss-Jordan steps
+    uint8_t *gjused;    // nc flags: row already a pivot row
     int *cmap;          // flat index -> vector index on the coarsest level
     double *cvec;       // 2 * nc gather/scatter buffer
     float *cvecf;

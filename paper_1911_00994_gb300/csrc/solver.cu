@@ -220,6 +220,8 @@ static size_t carve(Ctx *c, char *base)
     c->Minv = cv.take<double>((size_t)nc * nc);
     c->Minvf = cv.take<float>((size_t)nc * nc);
     c->aug = cv.take<double>((size_t)nc * 2 * nc);
+    c->gjkeys = cv.take<unsigned long long>((size_t)nc);
+    c->gjused = cv.take<uint8_t>((size_t)nc);
     c->cmap = cv.take<int>((size_t)nc + lc.VL);
     c->cvec = cv.take<double>(2 * (size_t)nc + 8);
     c->cvecf = cv.take<float>(2 * (size_t)nc + 8);
@@ -770,7 +772,9 @@ gp_status mg_solve(gp_ctx *ctx, double *x, const double *b, double tol, gp_repor
     if (!(r0 == r0)) st = GP_DIVERGED;
     else if (r0 <= tol) st = GP_OK;
     else
-        for (k = 1; cycles < c->prm.max_cycles; k++) {
+        // max_cycles caps the cycles of the FP32 corrections and the
+        // iterations otherwise (a BiCGSTAB iteration applies two cycles)
+        for (k = 1; multi ? cycles < c->prm.max_cycles : k <= c->prm.max_cycles; k++) {
             int which = (kry ? 2 : 0) + (mixed ? 1 : 0);
             if (multi) c->inner_now = std::min(c->inner_now, c->prm.max_cycles - cycles);
             if (!run_graph(c, which, x, b)) solve_iteration(c, which, x, b);
@@ -796,7 +800,7 @@ gp_status mg_solve(gp_ctx *ctx, double *x, const double *b, double tol, gp_repor
                 prev = nrm;
             }
         }
-    if (cycles >= c->prm.max_cycles && st == GP_NOT_CONVERGED) k--;
+    if (st == GP_NOT_CONVERGED) k--;  // the loop ran out: k is one past the last iteration
     c->inner_now = 1;
     if (rep) {
         rep->iterations = k;
