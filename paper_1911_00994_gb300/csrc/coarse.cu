@@ -11,7 +11,8 @@
 namespace gpmg {
 
 // dense rows of internal and inactive nodes (ghost-class rows and the mean
-// row are written by the two kernels below); right half = identity
+// row are written by the two kernels below); right half zero (the
+// elimination fills it)
 __global__ void k_dense_rows(double *aug, int n, const int *cmap, const int *inv, int N, int P, long long F,
                              const uint8_t *tU, const uint8_t *tV, const uint8_t *tP, double q, double a, double d)
 {
@@ -19,7 +20,6 @@ __global__ void k_dense_rows(double *aug, int n, const int *cmap, const int *inv
     if (f >= n) return;
     double *row = aug + (long long)f * 2 * n;
     for (int c = 0; c < 2 * n; c++) row[c] = 0.0;
-    row[n + f] = 1.0;
     if (f == n - 1) return;  // mean row
     long long v = cmap[f];
     int g = (int)(v / F);
@@ -71,9 +71,13 @@ __global__ void k_dense_mean_row(double *aug, int n, const int *cmap, long long 
 // Gauss-Jordan elimination with partial pivoting, one launch per column and
 // no row exchanges or scaling: step k eliminates column k from every row
 // but the pivot row p_k (the unused row with the largest |a_ik|), which
-// keeps its place and scale.  Afterwards row p_k holds a_{p_k,k} in the left
-// half and a_{p_k,k} times row k of the inverse in the right half.  The
-// pivot of column k + 1 is chosen during step k from the updated column:
+// keeps its place and scale.  The right half is kept in pivot order: its
+// slot t holds column p_t of the transformed identity, which is the unit
+// column e_(p_t) until step t, so step k touches the n - k - 1 remaining
+// left columns and the k + 1 filled slots (n columns in all).  Afterwards
+// row p_k holds a_(p_k,k) in the left half, and row k of the inverse is
+// a_(p_k,k)^-1 times row p_k of the right half, slot t giving column p_t.
+// The pivot of column k + 1 is chosen during step k from the updated column:
 // keys[k + 1] is the atomic maximum of (top 32 bits of |a_i,k+1|, ~i) over
 // the rows not yet used, so the first of equally large candidates wins.
 
@@ -95,17 +99,17 @@ __global__ void k_gj_first(const double *aug, int n, unsigned long long *keys)
     }
 }
 
-// step k over a 32-column x 8-row tile per block (a warp is 32 columns of one row)
+// step k over a 128-column x 8-row tile per block (a warp covers 4 x 32
+// columns of one row, 32 consecutive ones per pass); column c < n - k - 1 is
+// left column k + 1 + c, the others are right-half slots c - (n - k - 1)
 __global__ void __launch_bounds__(256) k_gj_step(double *aug, int n, int k, unsigned long long *keys, uint8_t *used,
                                                  unsigned *err)
 {
     const long long W = 2LL * n;
-    const int j = blockIdx.x * 32 + threadIdx.x, i = blockIdx.y * 8 + threadIdx.y;
-    if (blockIdx.x * 32 + 31 <= k) return;  // the whole tile lies in eliminated columns
+    const int i = blockIdx.y * 8 + threadIdx.y;
     const unsigned long long key = keys[k];
     if (!(key >> 32)) {  // no nonzero candidate in column k
-        if (threadIdx.x == 0 && threadIdx.y == 0 && blockIdx.x == gridDim.x - 1 && blockIdx.y == 0)
-            atomicOr(err, E_SINGULAR);
+        if (threadIdx.x == 0 && threadIdx.y == 0 && blockIdx.x == 0 && blockIdx.y == 0) atomicOr(err, E_SINGULAR);
         return;
     }
     const int p = pivot_row(key);
@@ -114,14 +118,28 @@ __global__ void __launch_bounds__(256) k_gj_step(double *aug, int n, int k, unsi
     if (threadIdx.x == 0 && threadIdx.y == 0) s_rp = 1.0 / aug[(long long)p * W + k];
     __syncthreads();
     unsigned long long cand = 0;
-    if (i < n && i != p && j > k && j < W) {
-        const double m = aug[(long long)i * W + k] * s_rp;
-        double v = aug[(long long)i * W + j];
-        if (m != 0.0) v -= m * aug[(long long)p * W + j];
-        aug[(long long)i * W + j] = v;
-        if (j == k + 1 && k + 1 < n && !used[i]) cand = pivot_key(v, i);
+    const int nleft = n - k - 1;
+    if (i < n) {
+        const double m = i != p ? aug[(long long)i * W + k] * s_rp : 0.0;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int c = blockIdx.x * 128 + q * 32 + threadIdx.x;
+            if (c >= n) continue;
+            const long long j = c < nleft ? k + 1 + c : n + (c - nleft);  // element column
+            if (c < nleft || c - nleft < k) {
+                if (i != p) {
+                    double v = aug[(long long)i * W + j];
+                    if (m != 0.0) v -= m * aug[(long long)p * W + j];
+                    aug[(long long)i * W + j] = v;
+                    if (c == 0 && !used[i]) cand = pivot_key(v, i);
+                }
+            } else {
+                // slot k: the unit column e_p after this step's elimination
+                aug[(long long)i * W + j] = i == p ? 1.0 : -m;
+            }
+            if (i == p && c == n - 1) used[p] = 1;
+        }
     }
-    if (i == p && j == W - 1) used[p] = 1;
     for (int o = 16; o > 0; o >>= 1) {
         const unsigned long long c2 = __shfl_xor_sync(0xffffffffu, cand, o);
         cand = c2 > cand ? c2 : cand;
@@ -135,18 +153,23 @@ __global__ void __launch_bounds__(256) k_gj_step(double *aug, int n, int k, unsi
     }
 }
 
-// row k of the inverse from the pivot row of column k
+// row r of the inverse from the pivot row of column r: slot t gives column p_t
 __global__ void k_gj_extract(const double *aug, int n, const unsigned long long *keys, double *Minv, float *Minvf)
 {
     const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (e >= (long long)n * n) return;
-    const long long r = e / n, c = e % n;
-    const unsigned long long key = keys[r];
+    const long long r = e / n, t = e % n;
+    const unsigned long long kr = keys[r], kt = keys[t];
     // a singular matrix (flagged by the steps) leaves later keys empty
-    const int p = (key >> 32) ? pivot_row(key) : -1;
-    const double v = p >= 0 ? aug[(long long)p * 2 * n + n + c] / aug[(long long)p * 2 * n + r] : 0.0;
-    Minv[e] = v;
-    Minvf[e] = (float)v;
+    if (!(kr >> 32) || !(kt >> 32)) {
+        Minv[e] = 0.0;
+        Minvf[e] = 0.0f;
+        return;
+    }
+    const int p = pivot_row(kr), col = pivot_row(kt);
+    const double v = aug[(long long)p * 2 * n + n + t] / aug[(long long)p * 2 * n + r];
+    Minv[r * n + col] = v;
+    Minvf[r * n + col] = (float)v;
 }
 
 template <typename T> __global__ void k_gather(const T *b, const int *cmap, T *cv, int n)
@@ -196,6 +219,57 @@ void coarse_maps_host(int N, int P, long long F, int *cmap, int *inv, long long 
     for (int k = 0; k < f; k++) inv[cmap[k]] = k;
 }
 
+// the elimination of the assembled [M | I]: its arguments are fixed for the
+// context, so it is captured once as a CUDA graph and replayed for every
+// geometry
+static void gj_launches(Ctx *c)
+{
+    cudaStream_t st = c->stream;
+    const int n = c->nc;
+    cudaMemsetAsync(c->err, 0, sizeof(unsigned), st);
+    cudaMemsetAsync(c->gjkeys, 0, sizeof(unsigned long long) * n, st);
+    cudaMemsetAsync(c->gjused, 0, n, st);
+    k_gj_first<<<(n + 255) / 256, 256, 0, st>>>(c->aug, n, c->gjkeys);
+    const dim3 ge((n + 127) / 128, (n + 7) / 8), be(32, 8);
+    for (int k = 0; k < n; k++) k_gj_step<<<ge, be, 0, st>>>(c->aug, n, k, c->gjkeys, c->gjused, c->err);
+    const long long nn = (long long)n * n;
+    k_gj_extract<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(c->aug, n, c->gjkeys, c->Minv, c->Minvf);
+}
+
+// replay the captured elimination; false when graphs are unavailable here
+static bool gj_graph(Ctx *c)
+{
+    if (!c->prm.graphs || c->graphs_off || c->stream == nullptr) return false;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(c->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return false;
+    }
+    if (!c->gj_exec) {
+        if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        gj_launches(c);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&c->gj_exec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            c->gj_exec = nullptr;
+            return false;
+        }
+    }
+    if (cudaGraphLaunch(c->gj_exec, c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        cudaGraphExecDestroy(c->gj_exec);
+        c->gj_exec = nullptr;
+        return false;
+    }
+    return true;
+}
+
 int build_coarse_inverse(Ctx *c)
 {
     cudaStream_t st = c->stream;
@@ -207,14 +281,7 @@ int build_coarse_inverse(Ctx *c)
     k_dense_rows<<<(n + 127) / 128, 128, 0, st>>>(c->aug, n, c->cmap, inv, l.N, l.P, l.F, l.tU, l.tV, l.tP, q, a, d);
     if (l.h_nrows > 0) k_dense_ghost_rows<<<(l.h_nrows + 127) / 128, 128, 0, st>>>(c->aug, n, inv, l.gh, l.h_nrows);
     k_dense_mean_row<<<1, 1, 0, st>>>(c->aug, n, c->cmap, l.F, l.tP, h * h);
-    cudaMemsetAsync(c->err, 0, sizeof(unsigned), st);
-    cudaMemsetAsync(c->gjkeys, 0, sizeof(unsigned long long) * n, st);
-    cudaMemsetAsync(c->gjused, 0, n, st);
-    k_gj_first<<<(n + 255) / 256, 256, 0, st>>>(c->aug, n, c->gjkeys);
-    const dim3 ge((2 * n + 31) / 32, (n + 7) / 8), be(32, 8);
-    for (int k = 0; k < n; k++) k_gj_step<<<ge, be, 0, st>>>(c->aug, n, k, c->gjkeys, c->gjused, c->err);
-    long long nn = (long long)n * n;
-    k_gj_extract<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(c->aug, n, c->gjkeys, c->Minv, c->Minvf);
+    if (!gj_graph(c)) gj_launches(c);
     unsigned herr = 0;
     cudaMemcpyAsync(&herr, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
     cudaError_t e = cudaStreamSynchronize(st);

@@ -136,6 +136,7 @@ struct Ctx {
     double *aug;        // nc x 2nc work for Gauss-Jordan
     unsigned long long *gjkeys;  // nc pivot keys (|a| and row) of the Gauss-Jordan steps
     uint8_t *gjused;    // nc flags: row already a pivot row
+    cudaGraphExec_t gj_exec;  // the captured Gauss-Jordan elimination (null until first used)
     int *cmap;          // flat index -> vector index on the coarsest level
     double *cvec;       // 2 * nc gather/scatter buffer
     float *cvecf;

@@ -488,6 +488,7 @@ gp_status gp_destroy(gp_ctx *ctx)
     if (ctx->c.tmr_ready)
         for (int k = 0; k < 2 * 512; k++) cudaEventDestroy(ctx->c.tmr_ev[k]);
     graphs_reset(&ctx->c);
+    if (ctx->c.gj_exec) cudaGraphExecDestroy(ctx->c.gj_exec);
     delete ctx;
     return GP_OK;
 }
