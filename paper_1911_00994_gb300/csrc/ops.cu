@@ -18,6 +18,7 @@ namespace gpmg {
 // levels solved by the one-block smoother, ghost lists swept by one block,
 // and levels whose full boxes are swept by shared-memory tiles
 constexpr int SMALL_N = 64;  // levels whose whole relaxation runs in one block
+constexpr size_t SMALL_STAGE_BYTES = 200 * 1024;  // x and b of such a level staged in shared memory up to this size
 constexpr int TILE_MIN_N = 512;  // default finest size swept by TMA tiles (gp_params.tile_min overrides)
 constexpr int GHOST_BLOCK_ROWS = 4096;
 constexpr int CUT_SPLIT = 64;  // cut boxes per colour above which the cut sweep leaves a single block
@@ -1136,10 +1137,26 @@ __global__ void __launch_bounds__(1024) k_ghost_block(GhostList gh, int nrows, T
 // pressure, lambda ghost sweeps; the same steps in the same order as the
 // multi-kernel path, with block barriers in place of kernel boundaries
 template <typename T>
-__global__ void __launch_bounds__(512) k_smooth_small(LevelArgs<T> A, T *x, const T *b, CutList cut, GhostList gh,
+__global__ void __launch_bounds__(512) k_smooth_small(LevelArgs<T> A, T *xg, const T *bg, CutList cut, GhostList gh,
                                                          int nrows, const int *lonely, int nlonely, const int *nint,
-                                                         double h2, T dtau, int lambda, int nu)
+                                                         double h2, T dtau, int lambda, int nu, long long vl, int staged)
 {
+    // with `staged`, x and b (vl slots each) are copied into shared memory,
+    // relaxed there, and x is copied back: every access of the many short
+    // steps is a shared-memory one instead of an L2 round trip
+    extern __shared__ __align__(16) unsigned char small_smem[];
+    T *x = xg;
+    const T *b = bg;
+    if (staged) {
+        T *xs = (T *)small_smem, *bs = xs + vl;
+        for (long long k = threadIdx.x; k < vl; k += blockDim.x) {
+            xs[k] = xg[k];
+            bs[k] = bg[k];
+        }
+        __syncthreads();
+        x = xs;
+        b = bs;
+    }
     __shared__ double ss[1024], sm[1024];
     __shared__ double shift;
     const int N = A.N;
@@ -1207,6 +1224,10 @@ __global__ void __launch_bounds__(512) k_smooth_small(LevelArgs<T> A, T *x, cons
         }
         __syncthreads();
         ghost_sweeps_block<T>(gh, nrows, x, b, dtau, lambda);
+    }
+    if (staged) {
+        __syncthreads();
+        for (long long k = threadIdx.x; k < vl; k += blockDim.x) xg[k] = x[k];
     }
 }
 
@@ -1517,6 +1538,8 @@ void tiles_init()
     if (done) return;
     cudaFuncSetAttribute(k_box_tma<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tt_smem<double>());
     cudaFuncSetAttribute(k_box_tma<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tt_smem<float>());
+    cudaFuncSetAttribute(k_smooth_small<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMALL_STAGE_BYTES);
+    cudaFuncSetAttribute(k_smooth_small<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMALL_STAGE_BYTES);
     done = true;
 }
 
@@ -1689,8 +1712,11 @@ template <typename T> void smooth_from(Ctx *c, int lev, T *x, T *in, const T *b,
     if (one) {
         double h = c->prm.L / (double)l.N;
         tmr_begin(c, KT_BOX_FULL, lev);
-        k_smooth_small<T><<<1, 512, 0, c->stream>>>(level_args<T>(c, lev), x, b, l.cut, l.gh, l.h_nrows, l.lonely,
-                                                      l.h_nlonely, l.nint, h * h, (T)c->prm.dtau, c->prm.lambda, nu);
+        const size_t stage = 2 * sizeof(T) * (size_t)l.VL;
+        const int staged = stage <= SMALL_STAGE_BYTES;
+        k_smooth_small<T><<<1, 512, staged ? stage : 0, c->stream>>>(
+            level_args<T>(c, lev), x, b, l.cut, l.gh, l.h_nrows, l.lonely, l.h_nlonely, l.nint, h * h,
+            (T)c->prm.dtau, c->prm.lambda, nu, l.VL, staged);
         tmr_end(c, KT_BOX_FULL, lev);
         c->launches++;
         return;
