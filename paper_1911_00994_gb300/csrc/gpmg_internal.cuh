@@ -93,6 +93,7 @@ struct Level {
     double h;
     uint8_t *tU, *tV, *tP;
     uint8_t *bcode;    // [F] box code of each cell (BOX_FULL and its internal faces, or 0)
+    uint8_t *pcode;    // [3 F] prolongation code of each node (from the next coarser level; not on the coarsest)
     uint8_t *prim;     // [3 * F] ghost referenced by an internal row
     uint8_t *done;     // [3 * F] ghost row computed (closure passes)
     double *x, *b, *r; // vectors owned by the context (coarse levels; r on all)

@@ -1023,15 +1023,50 @@ __global__ void k_restrict(int Nf, int Pf, long long Ff, const uint8_t *tUf, con
     if (row == 0 && col == 0) bH[3 * Fc] = r[3 * Ff];
 }
 
+// Prolongation code of every fine node (one byte per slot and grid, once per
+// geometry): PRO_ON when the node is in its grid and active (it receives
+// x + P e), PRO_ALL when besides every coarse node of its interpolation
+// stencil is active, so that the weights sum to 1 and no type needs looking
+// up during the cycle.
+constexpr uint8_t PRO_ON = 1, PRO_ALL = 2;
+
+__global__ void k_prolong_codes(int Nf, int Pf, long long Ff, const uint8_t *tUf, const uint8_t *tVf,
+                                const uint8_t *tPf, int Nc, int Pc, const uint8_t *tUc, const uint8_t *tVc,
+                                const uint8_t *tPc, uint8_t *code)
+{
+    const int col = blockIdx.x * blockDim.x + threadIdx.x, row = blockIdx.y, g = blockIdx.z;
+    if (col >= Pf) return;
+    const long long s = (long long)row * Pf + col;
+    const uint8_t *tf = g == G_U ? tUf : g == G_V ? tVf : tPf;
+    const uint8_t *tc = g == G_U ? tUc : g == G_V ? tVc : tPc;
+    const int i = col - 1, j = row - 1;
+    uint8_t c = 0;
+    if (in_grid(g, Nf, i, j) && tf[s] != T_INACTIVE) {
+        c = PRO_ON;
+        const int Ilo = g == G_V ? -1 : 0, Ihi = g == G_P ? Nc - 1 : Nc;
+        const int Jlo = g == G_U ? -1 : 0, Jhi = g == G_P ? Nc - 1 : Nc;
+        int KI[2], KJ[2];
+        double wi[2], wj[2];
+        const int ni = taps<double>(i, g == G_U, Ilo, Ihi, KI, wi);
+        const int nj = taps<double>(j, g == G_V, Jlo, Jhi, KJ, wj);
+        bool all = true;
+        for (int a = 0; a < nj; a++)
+            for (int bb = 0; bb < ni; bb++) all = all && tget(tc, g, Nc, Pc, KI[bb], KJ[a]) != T_INACTIVE;
+        if (all) c |= PRO_ALL;
+    }
+    code[g * Ff + s] = c;
+}
+
 // Interpolation of the coarse correction (Sect. 4.3): bilinear over the active
 // coarse nodes around each fine node, weights renormalised (inactive coarse
 // nodes carry no value); y = x + P eH on every slot (y may be x).  Four
 // consecutive fine slots per thread: vector loads and stores of x, y and the
-// fine types, the row taps shared by the four slots.
+// fine prolongation codes, the row taps shared by the four slots.  Nodes
+// whose stencil is wholly active (PRO_ALL) skip the coarse type lookups.
 template <typename T>
-__global__ void __launch_bounds__(256) k_prolong4(int Nf, int Pf, long long Ff, const uint8_t *tUf, const uint8_t *tVf,
-                                                  const uint8_t *tPf, int Nc, int Pc, long long Fc, const uint8_t *tUc,
-                                                  const uint8_t *tVc, const uint8_t *tPc, const T *eH, const T *x, T *y)
+__global__ void __launch_bounds__(256) k_prolong4(int Nf, int Pf, long long Ff, const uint8_t *pcode, int Nc, int Pc,
+                                                  long long Fc, const uint8_t *tUc, const uint8_t *tVc,
+                                                  const uint8_t *tPc, const T *eH, const T *x, T *y)
 {
     const int c0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
     const int row = blockIdx.y;
@@ -1040,33 +1075,40 @@ __global__ void __launch_bounds__(256) k_prolong4(int Nf, int Pf, long long Ff, 
     const long long s0 = (long long)row * Pf + c0;
     if (row == 0 && c0 < NSCAL)
         for (int q = 0; q < 4; q++) y[3 * Ff + c0 + q] = c0 + q == 0 ? x[3 * Ff] + eH[3 * Fc] : x[3 * Ff + c0 + q];
-    const uint8_t *tf[3] = {tUf, tVf, tPf};
     const uint8_t *tc[3] = {tUc, tVc, tPc};
 #pragma unroll
     for (int g = 0; g < 3; g++) {
-        uint8_t tt[4];
+        uint8_t pc[4];
         T xv[4], out[4];
-        ldt4(tf[g] + s0, tt);
+        ldt4(pcode + g * Ff + s0, pc);
         ld4(x + g * Ff + s0, xv);
         const int Ilo = g == G_V ? -1 : 0, Ihi = g == G_P ? Nc - 1 : Nc;
         const int Jlo = g == G_U ? -1 : 0, Jhi = g == G_P ? Nc - 1 : Nc;
         int KJ[2];
         T wj[2];
         const int nj = taps<T>(j, g == G_V, Jlo, Jhi, KJ, wj);
+        const T *e = eH + g * Fc;
 #pragma unroll
         for (int q = 0; q < 4; q++) {
             const int i = c0 + q - 1;
             out[q] = xv[q];
-            if (!in_grid(g, Nf, i, j) || tt[q] == T_INACTIVE) continue;
+            if (!(pc[q] & PRO_ON)) continue;
             int KI[2];
             T wi[2];
             const int ni = taps<T>(i, g == G_U, Ilo, Ihi, KI, wi);
             T sacc = 0, ws = 0;
+            if (pc[q] & PRO_ALL) {
+                for (int a = 0; a < nj; a++)
+                    for (int bb = 0; bb < ni; bb++)
+                        sacc += (wj[a] * wi[bb]) * e[(long long)(KJ[a] + 1) * Pc + (KI[bb] + 1)];
+                out[q] = xv[q] + sacc;
+                continue;
+            }
             for (int a = 0; a < nj; a++)
                 for (int bb = 0; bb < ni; bb++) {
                     if (tget(tc[g], g, Nc, Pc, KI[bb], KJ[a]) == T_INACTIVE) continue;
                     T w = wj[a] * wi[bb];
-                    sacc += w * eH[g * Fc + (long long)(KJ[a] + 1) * Pc + (KI[bb] + 1)];
+                    sacc += w * e[(long long)(KJ[a] + 1) * Pc + (KI[bb] + 1)];
                     ws += w;
                 }
             if (ws > (T)0) out[q] = xv[q] + (ws == (T)1 ? sacc : sacc / ws);
@@ -1481,12 +1523,18 @@ int recolour_cuts(Ctx *c)
     return GP_OK;
 }
 
-// box codes of every level (k_box_codes); once per geometry
+// box codes of every level and prolongation codes of every level but the
+// coarsest (k_box_codes, k_prolong_codes); once per geometry
 void box_codes(Ctx *c)
 {
     for (int lev = 0; lev < c->L; lev++) {
         const Level &l = c->lv[lev];
         k_box_codes<<<(unsigned)((l.F + 255) / 256), 256, 0, c->stream>>>(l.N, l.P, l.F, l.tU, l.tV, l.tP, l.bcode);
+        if (lev + 1 < c->L) {
+            const Level &C = c->lv[lev + 1];
+            k_prolong_codes<<<dim3((l.P + 127) / 128, l.N + 2, 3), 128, 0, c->stream>>>(
+                l.N, l.P, l.F, l.tU, l.tV, l.tP, C.N, C.P, C.tU, C.tV, C.tP, l.pcode);
+        }
     }
 }
 
@@ -1771,7 +1819,7 @@ template <typename T> void prolong_to(Ctx *c, int lev, const T *eH, const T *x, 
     const Level &f = c->lv[lev], &C = c->lv[lev + 1];
     dim3 g((f.P / 4 + 255) / 256, f.N + 2);
     tmr_begin(c, KT_PROLONG, lev);
-    k_prolong4<T><<<g, 256, 0, c->stream>>>(f.N, f.P, f.F, f.tU, f.tV, f.tP, C.N, C.P, C.F, C.tU, C.tV, C.tP, eH, x, y);
+    k_prolong4<T><<<g, 256, 0, c->stream>>>(f.N, f.P, f.F, f.pcode, C.N, C.P, C.F, C.tU, C.tV, C.tP, eH, x, y);
     tmr_end(c, KT_PROLONG, lev);
     c->launches++;
 }

@@ -127,6 +127,7 @@ static size_t carve(Ctx *c, char *base)
         l.tV = cv.take<uint8_t>(l.F);
         l.tP = cv.take<uint8_t>(l.F);
         l.bcode = cv.take<uint8_t>(l.F);
+        l.pcode = k + 1 < L ? cv.take<uint8_t>(3 * l.F) : nullptr;
         l.prim = cv.take<uint8_t>(3 * l.F);
         l.done = cv.take<uint8_t>(3 * l.F);
         l.r = cv.take<double>(l.VL);
