@@ -82,7 +82,7 @@ typedef struct gp_params {
                            cycle (two cycles per iteration), same stopping test */
     int tile_min;       /* levels with at least this many cells per side sweep their full
                            boxes in one pass of shared-memory tiles (same iterate as the five
-                           colour passes); 0: 512 for the FP32 cycles of the mixed mode and
+                           colour passes); 0: 128 for the FP32 cycles of the mixed mode and
                            never for FP64; negative: never */
     int adjoint;        /* nonzero: carve the arrays of the adjoint solve (mg_solve_t and the
                            gp_*_t calls; one FP64 vector per level and the ghost column lists) */

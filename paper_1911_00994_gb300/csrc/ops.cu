@@ -19,8 +19,8 @@ namespace gpmg {
 // and levels whose full boxes are swept by shared-memory tiles
 constexpr int SMALL_N = 64;  // levels whose whole relaxation runs in one block
 constexpr size_t SMALL_STAGE_BYTES = 200 * 1024;  // x and b of such a level staged in shared memory up to this size
-constexpr int TILE_MIN_N = 512;  // default finest size swept by TMA tiles (gp_params.tile_min overrides)
-constexpr int GHOST_BLOCK_ROWS = 4096;
+constexpr int TILE_MIN_N = 128;  // default smallest FP32 level swept by TMA tiles (gp_params.tile_min overrides)
+constexpr int GHOST_BLOCK_ROWS = 1024;  // at most this many ghost-class rows: the lambda sweeps in one block
 constexpr int CUT_SPLIT = 64;  // cut boxes per colour above which the cut sweep leaves a single block
 constexpr int CUT_COLOUR_LAUNCHES = 6;  // at most this many colours: one launch per colour, else one cluster
 
