@@ -792,6 +792,17 @@ static int read_norm(Ctx *c, double *out)
 }
 
 // transposed cycles from lam until ||c - M^T lam||_inf <= tol
+// one iteration of the adjoint solve: a transposed cycle, the inactive rows
+// fixed, the transposed residual and its norm (replayed as a CUDA graph)
+void transposed_iteration(Ctx *c, double *lam, const double *cc)
+{
+    cycle_t_rec(c, 0, lam, cc);
+    fix_inactive_t(c, lam, cc);
+    residual_t(c, 0, lam, cc, c->lv[0].r);
+}
+
+bool run_graph(Ctx *c, int which, double *x, const double *b);
+
 int solve_t(Ctx *c, double *lam, const double *cc, double tol, gp_report *rep)
 {
     Level &l0 = c->lv[0];
@@ -809,9 +820,7 @@ int solve_t(Ctx *c, double *lam, const double *cc, double tol, gp_report *rep)
     int k = 0, status = GP_NOT_CONVERGED;
     if (r0 <= tol) status = GP_OK;
     for (k = 1; status == GP_NOT_CONVERGED && k <= c->prm.max_cycles; k++) {
-        cycle_t_rec(c, 0, lam, cc);
-        fix_inactive_t(c, lam, cc);
-        residual_t(c, 0, lam, cc, l0.r);
+        if (!run_graph(c, GRAPH_T, lam, cc)) transposed_iteration(c, lam, cc);
         st = read_norm(c, &rn);
         if (st != GP_OK) return st;
         if (rep) {

@@ -36,6 +36,7 @@ void prepare_cuts(Ctx *c);
 int recolour_cuts(Ctx *c);
 int ghost_row_links(Ctx *c);
 void box_codes(Ctx *c);
+void transposed_iteration(Ctx *c, double *lam, const double *cc);
 void krylov_init(Ctx *c, double *x, const double *b);
 void krylov_iteration(Ctx *c, double *x, const double *b);
 int residual_static(Ctx *c, int lev, const double *x, const double *b, double *r, double *norm_host);
@@ -266,6 +267,10 @@ template <typename T> void cycle_rec(Ctx *c, int lev, T *x, const T *b)
 static void solve_iteration(Ctx *c, int which, double *x, const double *b)
 {
     Level &l0 = c->lv[0];
+    if (which == GRAPH_T) {
+        transposed_iteration(c, x, b);
+        return;
+    }
     if (which >= 2) {
         krylov_iteration(c, x, b);
         return;
@@ -294,7 +299,7 @@ void graphs_reset(Ctx *c)
 
 // replay (capturing first if needed) one iteration as a CUDA graph; false
 // when graphs are unavailable here (then the caller launches directly)
-static bool run_graph(Ctx *c, int which0, double *x, const double *b)
+bool run_graph(Ctx *c, int which0, double *x, const double *b)
 {
     // slot: the iteration kind, and for the FP32 corrections their cycle count
     const int which = (which0 == 1 && c->inner_now > 1) ? 4 + c->inner_now - 2 : which0;
