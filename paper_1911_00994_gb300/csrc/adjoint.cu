@@ -373,32 +373,32 @@ __global__ void k_box_full_t(TArgs A, double *lam, const double *cc, const doubl
 
 // one colour of the cut boxes on M^T: residuals of the transposed rows at the
 // box unknowns (ghost-row parts summed on the fly: ghost unknowns of this
-// colour change), the transposed stored inverse
+// colour change), the transposed stored inverse.  Eight lanes per box: lane
+// f < 5 computes row f's residual, then its correction from the five
+// residuals of the group (warp shuffles), in the serial order.
 __global__ void k_box_cut_t(TArgs A, Level l, double *lam, const double *cc, int beg, int end)
 {
-    int k = beg + blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= end) return;
+    const int lane = threadIdx.x & 31, f = lane & 7;
+    const int k = beg + (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 3);
+    const bool valid = k < end && f < 5;
     const CutList &cut = l.cut;
-    double r[5];
-    int row[5];
-#pragma unroll
-    for (int f = 0; f < 5; f++) {
-        row[f] = cut.row[(long long)f * cut.cap + k];
-        r[f] = 0.0;
-        if (row[f] >= 0) {
-            const int g = (int)(row[f] / A.F);
-            const long long s = row[f] - g * A.F;
-            r[f] = cc[row[f]] - colt_struct(A, lam, g, s) - ghost_part(l, l.cut_tl[(long long)f * cut.cap + k], lam);
+    int row = -1;
+    double r = 0.0;
+    if (valid) {
+        row = cut.row[(long long)f * cut.cap + k];
+        if (row >= 0) {
+            const int g = (int)(row / A.F);
+            const long long s = row - g * A.F;
+            r = cc[row] - colt_struct(A, lam, g, s) - ghost_part(l, l.cut_tl[(long long)f * cut.cap + k], lam);
         }
     }
+    double d = 0.0;
 #pragma unroll
-    for (int f = 0; f < 5; f++) {
-        if (row[f] < 0) continue;
-        double d = 0.0;
-#pragma unroll
-        for (int c = 0; c < 5; c++) d += cut.minv[(long long)(c * 5 + f) * cut.cap + k] * r[c];
-        lam[row[f]] += d;
+    for (int c = 0; c < 5; c++) {
+        const double rc = __shfl_sync(0xffffffffu, r, (lane & ~7) + c);
+        if (valid) d += cut.minv[(long long)(c * 5 + f) * cut.cap + k] * rc;
     }
+    if (valid && row >= 0) lam[row] += d;
 }
 
 // lonely internal faces on M^T: point Jacobi with the diagonal d
@@ -419,16 +419,14 @@ __global__ void k_lonely_t(TArgs A, const int *list, int n, const double *lam, c
 // interpolation taps reach it (fine offsets -2..3 from 2I, 2J cover the
 // aligned, staggered and extrapolated taps), with the fine node's
 // renormalised weight
-__global__ void k_prolong_t(int Nf, int Pf, long long Ff, const uint8_t *tUf, const uint8_t *tVf, const uint8_t *tPf,
-                            int Nc, int Pc, long long Fc, const uint8_t *tUc, const uint8_t *tVc, const uint8_t *tPc,
-                            const double *r, double *cH)
+__global__ void k_prolong_t(int Nf, int Pf, long long Ff, const uint8_t *pcode, int Nc, int Pc, long long Fc,
+                            const uint8_t *tUc, const uint8_t *tVc, const uint8_t *tPc, const double *r, double *cH)
 {
     int col = blockIdx.x * blockDim.x + threadIdx.x;
     int row = blockIdx.y;
     if (col >= Pc) return;
     const int I = col - 1, J = row - 1;
     const long long sc = (long long)row * Pc + col;
-    const uint8_t *tf[3] = {tUf, tVf, tPf};
     const uint8_t *tc[3] = {tUc, tVc, tPc};
     if (row == 0 && col < NSCAL) cH[3 * Fc + col] = col == 0 ? r[3 * Ff] : 0.0;
 #pragma unroll
@@ -443,7 +441,9 @@ __global__ void k_prolong_t(int Nf, int Pf, long long Ff, const uint8_t *tUf, co
         for (int dj = -2; dj <= 3; dj++)
             for (int di = -2; di <= 3; di++) {
                 const int i = 2 * I + di, j = 2 * J + dj;
-                if (tget(tf[g], g, Nf, Pf, i, j) == T_INACTIVE) continue;
+                // the fine node's prolongation code (0 outside its grid)
+                const uint8_t pc = in_grid(g, Nf, i, j) ? pcode[g * Ff + (long long)(j + 1) * Pf + (i + 1)] : 0;
+                if (!(pc & PRO_ON)) continue;
                 int KI[2], KJ[2];
                 double wi[2], wj[2];
                 int ni = taps<double>(i, g == G_U, Ilo, Ihi, KI, wi);
@@ -451,7 +451,8 @@ __global__ void k_prolong_t(int Nf, int Pf, long long Ff, const uint8_t *tUf, co
                 double ws = 0.0, w = 0.0;
                 for (int a = 0; a < nj; a++)
                     for (int bb = 0; bb < ni; bb++) {
-                        if (tget(tc[g], g, Nc, Pc, KI[bb], KJ[a]) == T_INACTIVE) continue;
+                        // a wholly active stencil needs no type lookups (its weights sum to 1)
+                        if (!(pc & PRO_ALL) && tget(tc[g], g, Nc, Pc, KI[bb], KJ[a]) == T_INACTIVE) continue;
                         ws += wj[a] * wi[bb];
                         if (KI[bb] == I && KJ[a] == J) w += wj[a] * wi[bb];
                     }
@@ -516,14 +517,23 @@ __global__ void k_restrict_t(int Nf, int Pf, long long Ff, const uint8_t *tUf, c
     }
 }
 
-// y = M^T x for a dense row-major n x n matrix, one thread per output
-__global__ void k_gemv_t(const double *M, const double *x, double *y, int n)
+// y = M^T x for a dense row-major n x n matrix: a block per 32 columns, its
+// 32 thread rows take every 32nd matrix row (coalesced along the columns)
+// and the 32 partial sums of a column are added in a fixed tree order
+__global__ void __launch_bounds__(1024) k_gemv_t(const double *M, const double *x, double *y, int n)
 {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= n) return;
+    __shared__ double part[32][33];
+    const int c = blockIdx.x * 32 + threadIdx.x;
     double s = 0.0;
-    for (int r = 0; r < n; r++) s += M[(long long)r * n + c] * x[r];
-    y[c] = s;
+    if (c < n)
+        for (int r = threadIdx.y; r < n; r += 32) s += M[(long long)r * n + c] * x[r];
+    part[threadIdx.y][threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 16; o > 0; o >>= 1) {
+        if (threadIdx.y < o) part[threadIdx.y][threadIdx.x] += part[threadIdx.y + o][threadIdx.x];
+        __syncthreads();
+    }
+    if (threadIdx.y == 0 && c < n) y[c] = part[0][threadIdx.x];
 }
 
 __global__ void k_gather_d(const double *b, const int *cmap, double *cv, int n)
@@ -703,7 +713,7 @@ void box_sweep_t(Ctx *c, int lev, double *lam, const double *cc)
     for (int colour = l.cut.ncol - 1; colour >= 0; colour--) {
         int beg = l.h_cutoff[colour], end = l.h_cutoff[colour + 1];
         if (end <= beg) continue;
-        k_box_cut_t<<<(end - beg + 127) / 128, 128, 0, st>>>(A, l, lam, cc, beg, end);
+        k_box_cut_t<<<(end - beg + 15) / 16, 128, 0, st>>>(A, l, lam, cc, beg, end);
         c->launches++;
     }
     gtd_update(c, lev, lam);
@@ -728,8 +738,8 @@ void smooth_t(Ctx *c, int lev, double *lam, const double *cc, int nu)
 void prolong_t(Ctx *c, int lev, const double *r, double *cH)
 {
     const Level &f = c->lv[lev], &C = c->lv[lev + 1];
-    k_prolong_t<<<dim3((C.P + 255) / 256, C.N + 2), 256, 0, c->stream>>>(f.N, f.P, f.F, f.tU, f.tV, f.tP, C.N, C.P, C.F,
-                                                                          C.tU, C.tV, C.tP, r, cH);
+    k_prolong_t<<<dim3((C.P + 255) / 256, C.N + 2), 256, 0, c->stream>>>(f.N, f.P, f.F, f.pcode, C.N, C.P, C.F, C.tU,
+                                                                          C.tV, C.tP, r, cH);
     c->launches++;
 }
 
@@ -750,7 +760,7 @@ void coarse_solve_t(Ctx *c, const double *cc, double *lam)
     int n = c->nc;
     k_zero_d<<<(unsigned)((l.VL + 255) / 256), 256, 0, st>>>(lam, l.VL);
     k_gather_d<<<(n + 255) / 256, 256, 0, st>>>(cc, c->cmap, c->cvec, n);
-    k_gemv_t<<<(n + 127) / 128, 128, 0, st>>>(c->Minv, c->cvec, c->cvec + n, n);
+    k_gemv_t<<<(n + 31) / 32, dim3(32, 32), 0, st>>>(c->Minv, c->cvec, c->cvec + n, n);
     k_scatter_d<<<(n + 255) / 256, 256, 0, st>>>(c->cvec + n, c->cmap, lam, n);
     c->launches += 4;
 }

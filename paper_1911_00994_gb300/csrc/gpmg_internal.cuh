@@ -31,6 +31,9 @@ constexpr int ADJ_KMAX = 8;  // Picard iterations cn_step_adjoint can differenti
 // box codes (one byte per cell): a full box (internal cell, no ghost face)
 // and which of its four faces are internal
 constexpr unsigned BOX_FULL = 1, BOX_W = 2, BOX_E = 4, BOX_S = 8, BOX_N = 16, BOX_ALL = 31;
+// prolongation codes (one byte per node and grid): the node is active and in
+// its grid; every coarse node of its interpolation stencil is active too
+constexpr uint8_t PRO_ON = 1, PRO_ALL = 2;
 constexpr int GRAPH_T = 4 + GP_MAX_INNER - 1;  // captured kind: one transposed cycle and its residual
 constexpr int NGRAPH = GRAPH_T + 1;            // captured iteration kinds
 constexpr int GH_ST = 9;  // stencil slots per ghost row

@@ -1028,7 +1028,6 @@ __global__ void k_restrict(int Nf, int Pf, long long Ff, const uint8_t *tUf, con
 // x + P e), PRO_ALL when besides every coarse node of its interpolation
 // stencil is active, so that the weights sum to 1 and no type needs looking
 // up during the cycle.
-constexpr uint8_t PRO_ON = 1, PRO_ALL = 2;
 
 __global__ void k_prolong_codes(int Nf, int Pf, long long Ff, const uint8_t *tUf, const uint8_t *tVf,
                                 const uint8_t *tPf, int Nc, int Pc, const uint8_t *tUc, const uint8_t *tVc,
