@@ -146,7 +146,7 @@ def build_case(N, precision, device, stream, levels=None, krylov=False, inner=0)
     return s, b
 
 
-def adjoint_rollout(dev, stream, steps=50, every=10, N=512):
+def adjoint_rollout(dev, stream, steps=50, every=10, N=512, krylov=True):
     """Config 4's adjoint: the orbiting circle (r = 0.25, orbit radius 0.2,
     period 1) at Re = 100 on [-1, 1]^2, a rollout of `steps` CN steps from
     rest, and the gradient of the kinetic energy on a 64 x 64 probe window
@@ -154,7 +154,8 @@ def adjoint_rollout(dev, stream, steps=50, every=10, N=512):
     respect to the forcing (4 seeded Gaussian bumps, sigma = 0.1) and the
     body-velocity amplitude, checkpoints every `every` steps.  dt = 0.3 h:
     the paper bounds the step by h / max |u| and at dt = h the first steps'
-    Picard iteration diverges."""
+    Picard iteration diverges.  The forward and adjoint solves use BiCGSTAB
+    preconditioned by one (transposed) cycle unless `krylov` is false."""
     import numpy as np
     import torch
     from paper_1911_00994_gb300 import gpmg
@@ -163,7 +164,7 @@ def adjoint_rollout(dev, stream, steps=50, every=10, N=512):
     x0, L, Re = -1.0, 2.0, 100.0
     dt = 0.3 * L / N
     s = gpmg.Solver(N, x0, x0, L, alpha=dt / (2 * Re), band=3, adjoint=True, max_cycles=400, device=dev,
-                    stream=stream)
+                    stream=stream, krylov=krylov)
     shape = dict(kind=gpmg.GP_CIRCLE, a=0.25, orbit_r=0.2, orbit_period=1.0)
     st, body = s.geometry_shape(t=0.0, **shape)
     if st:
@@ -194,7 +195,9 @@ def adjoint_rollout(dev, stream, steps=50, every=10, N=512):
     e[3].record(stream)
     torch.cuda.synchronize(dev)
     fw, gr = e[0].elapsed_time(e[1]), e[2].elapsed_time(e[3])
-    return {"N": N, "steps": steps, "checkpoint_every": every, "dt": "0.3h", "Re": Re, "forward_ms": fw,
+    return {"N": N, "steps": steps, "checkpoint_every": every, "dt": "0.3h", "Re": Re,
+            "solver": "BiCGSTAB, one (transposed) V(2,1) cycle per preconditioner" if krylov else "V(2,1) cycles",
+            "forward_ms": fw,
             "loss_and_gradient_ms": gr, "gradient_over_forward": gr / fw, "loss": loss,
             "dL_damp": abar, "dL_df_norm": float(fbar.norm())}
 

@@ -812,13 +812,23 @@ void transposed_iteration(Ctx *c, double *lam, const double *cc)
 }
 
 bool run_graph(Ctx *c, int which, double *x, const double *b);
+void krylov_init_t(Ctx *c, double *lam, const double *cc);
+void krylov_iteration_t(Ctx *c, double *lam, const double *cc);
 
+// the adjoint solve: plain transposed cycles, or (gp_params.krylov)
+// BiCGSTAB preconditioned by one transposed cycle; the same stopping test
+// on the transposed residual
 int solve_t(Ctx *c, double *lam, const double *cc, double tol, gp_report *rep)
 {
     Level &l0 = c->lv[0];
+    const bool kry = c->prm.krylov != 0;
     double r0 = 0.0, rn = 0.0;
-    fix_inactive_t(c, lam, cc);
-    residual_t(c, 0, lam, cc, l0.r);
+    if (kry) {
+        krylov_init_t(c, lam, cc);
+    } else {
+        fix_inactive_t(c, lam, cc);
+        residual_t(c, 0, lam, cc, l0.r);
+    }
     int st = read_norm(c, &r0);
     if (st != GP_OK) return st;
     if (rep) {
@@ -830,11 +840,16 @@ int solve_t(Ctx *c, double *lam, const double *cc, double tol, gp_report *rep)
     int k = 0, status = GP_NOT_CONVERGED;
     if (r0 <= tol) status = GP_OK;
     for (k = 1; status == GP_NOT_CONVERGED && k <= c->prm.max_cycles; k++) {
-        if (!run_graph(c, GRAPH_T, lam, cc)) transposed_iteration(c, lam, cc);
+        if (kry) {
+            if (!run_graph(c, GRAPH_KT, lam, cc)) krylov_iteration_t(c, lam, cc);
+        } else if (!run_graph(c, GRAPH_T, lam, cc)) {
+            transposed_iteration(c, lam, cc);
+        }
         st = read_norm(c, &rn);
         if (st != GP_OK) return st;
         if (rep) {
-            rep->cycles = rep->iterations = k;
+            rep->iterations = k;
+            rep->cycles = kry ? 2 * k : k;
             if (rep->hist_host) rep->hist_host[k] = rn;
         }
         if (!(rn == rn) || rn > 1e6 * r0) status = GP_DIVERGED;

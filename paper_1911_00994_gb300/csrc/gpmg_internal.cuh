@@ -35,7 +35,8 @@ constexpr unsigned BOX_FULL = 1, BOX_W = 2, BOX_E = 4, BOX_S = 8, BOX_N = 16, BO
 // its grid; every coarse node of its interpolation stencil is active too
 constexpr uint8_t PRO_ON = 1, PRO_ALL = 2;
 constexpr int GRAPH_T = 4 + GP_MAX_INNER - 1;  // captured kind: one transposed cycle and its residual
-constexpr int NGRAPH = GRAPH_T + 1;            // captured iteration kinds
+constexpr int GRAPH_KT = GRAPH_T + 1;          // captured kind: one BiCGSTAB iteration of the adjoint solve
+constexpr int NGRAPH = GRAPH_KT + 1;           // captured iteration kinds
 constexpr int GH_ST = 9;  // stencil slots per ghost row
 
 // error bits written by kernels into the context's device status word
@@ -164,8 +165,8 @@ struct Ctx {
     // captured mg_solve iterations: [0] FP64 cycle + residual, [1] FP32 cycle
     // inside FP64 residual correction, [2] / [3] BiCGSTAB iteration with an
     // FP64 / FP32 cycle, [4 + k - 2] k FP32 cycles inside one FP64 residual
-    // correction, [GRAPH_T] an iteration of the adjoint solve; keyed by the
-    // iterate and rhs pointers
+    // correction, [GRAPH_T] / [GRAPH_KT] an iteration of the plain / BiCGSTAB
+    // adjoint solve; keyed by the iterate and rhs pointers
     cudaGraphExec_t gexec[NGRAPH];
     const void *gx[NGRAPH], *gb[NGRAPH];
     int gvalid[NGRAPH];

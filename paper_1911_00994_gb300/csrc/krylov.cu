@@ -1,6 +1,7 @@
 // Krylov acceleration of the multigrid solve: BiCGSTAB on M x = b,
 // preconditioned on the right by one multigrid cycle from zero (FP64 cycle,
-// or FP32 cycle on an FP64 vector in the mixed mode).  The stopping test is
+// or FP32 cycle on an FP64 vector in the mixed mode), and on the adjoint
+// system M^T lam = c with the transposed cycle.  The stopping test is
 // the true residual ||b - M x||_inf after every iteration, as for the plain
 // cycles.  All scalars stay on the device; one iteration is a fixed sequence
 // of launches that mg_solve replays as a CUDA graph.
@@ -12,6 +13,9 @@
 namespace gpmg {
 
 template <typename T> void residual(Ctx *c, int lev, const T *x, const T *b, T *r);
+void residual_t(Ctx *c, int lev, const double *lam, const double *cc, double *r);
+void cycle_t_rec(Ctx *c, int lev, double *lam, const double *cc);
+void fix_inactive_t(Ctx *c, double *lam, const double *cc);
 template <typename T> void cycle_rec(Ctx *c, int lev, T *x, const T *b);
 template <typename T> void zero_vec(Ctx *c, T *x, long long n);
 void to_float(Ctx *c, const double *a, float *b, long long n);
@@ -182,8 +186,51 @@ void krylov_init(Ctx *c, double *x, const double *b)
     c->launches += 2;
 }
 
+// The same iteration on the adjoint system M^T lam = c: the operator is the
+// transposed residual, the preconditioner one transposed cycle from zero
+// followed by the exact solve of the inactive rows (as every iteration of
+// the plain adjoint solve ends); the true residual's norm lands in
+// c->red[4].  `adj` selects this form.
+static void apply_op(Ctx *c, bool adj, const double *y, const double *zero, double *out)
+{
+    if (adj) residual_t(c, 0, y, zero, out);  // out = -M^T y
+    else residual<double>(c, 0, y, zero, out);  // out = -M y
+}
+
+static void precondition_any(Ctx *c, bool adj, const double *v, double *y)
+{
+    if (!adj) {
+        precondition(c, v, y);
+        return;
+    }
+    zero_vec<double>(c, y, c->lv[0].VL);
+    cycle_t_rec(c, 0, y, v);
+    fix_inactive_t(c, y, v);
+}
+
+// r = c - M^T lam, rh = r, p = vn = 0, scalars 1
+void krylov_init_t(Ctx *c, double *lam, const double *cc)
+{
+    Level &l0 = c->lv[0];
+    long long n = l0.VL;
+    fix_inactive_t(c, lam, cc);
+    residual_t(c, 0, lam, cc, c->kv[0]);
+    k_copy_vec<<<vblocks(n), 256, 0, c->stream>>>(c->kv[0], c->kv[1], n);
+    zero_vec<double>(c, c->kv[2], n);
+    zero_vec<double>(c, c->kv[3], n);
+    k_bicg_init<<<1, 32, 0, c->stream>>>(c->ks);
+    c->launches += 2;
+}
+
+static void bicg_iteration(Ctx *c, bool adj, double *x, const double *b);
+
 // one BiCGSTAB iteration and the true residual of x (norm in c->red[0])
-void krylov_iteration(Ctx *c, double *x, const double *b)
+void krylov_iteration(Ctx *c, double *x, const double *b) { bicg_iteration(c, false, x, b); }
+
+// one BiCGSTAB iteration on M^T lam = c (norm in c->red[4])
+void krylov_iteration_t(Ctx *c, double *lam, const double *cc) { bicg_iteration(c, true, lam, cc); }
+
+static void bicg_iteration(Ctx *c, bool adj, double *x, const double *b)
 {
     Level &l0 = c->lv[0];
     long long n = l0.VL;
@@ -193,17 +240,18 @@ void krylov_iteration(Ctx *c, double *x, const double *b)
     dot(c, rh, r, nullptr, nullptr, n);
     k_bicg_beta<<<1, 256, 0, c->stream>>>(c->kpart, c->kpart_n, c->ks);
     k_bicg_p<<<vb, 256, 0, c->stream>>>(p, r, vn, c->ks, n);
-    precondition(c, p, y);
-    residual<double>(c, 0, y, zero, vn);  // vn = -M y
+    precondition_any(c, adj, p, y);
+    apply_op(c, adj, y, zero, vn);  // vn = -M y (or -M^T y)
     dot(c, rh, vn, nullptr, nullptr, n);
     k_bicg_alpha<<<1, 256, 0, c->stream>>>(c->kpart, c->kpart_n, c->ks);
     k_bicg_s<<<vb, 256, 0, c->stream>>>(s, r, vn, c->ks, n);
-    precondition(c, s, z);
-    residual<double>(c, 0, z, zero, tn);  // tn = -M z
+    precondition_any(c, adj, s, z);
+    apply_op(c, adj, z, zero, tn);  // tn = -M z (or -M^T z)
     dot(c, tn, s, tn, tn, n);
     k_bicg_omega<<<1, 256, 0, c->stream>>>(c->kpart, c->kpart_n, c->ks);
     k_bicg_xr<<<vb, 256, 0, c->stream>>>(x, r, y, z, s, tn, c->ks, n);
-    residual<double>(c, 0, x, b, rt);
+    if (adj) residual_t(c, 0, x, b, rt);
+    else residual<double>(c, 0, x, b, rt);
     c->launches += 6;
 }
 

@@ -39,6 +39,7 @@ void box_codes(Ctx *c);
 void transposed_iteration(Ctx *c, double *lam, const double *cc);
 void krylov_init(Ctx *c, double *x, const double *b);
 void krylov_iteration(Ctx *c, double *x, const double *b);
+void krylov_iteration_t(Ctx *c, double *lam, const double *cc);
 int residual_static(Ctx *c, int lev, const double *x, const double *b, double *r, double *norm_host);
 void cn_convective(Ctx *c, const double *x, const double *Nn, double *out, int mode);
 void cn_rhs(Ctx *c, const double *xn, const double *Nh, const double *f, double dt, const double *bc, const gp_body &body,
@@ -269,6 +270,10 @@ static void solve_iteration(Ctx *c, int which, double *x, const double *b)
     Level &l0 = c->lv[0];
     if (which == GRAPH_T) {
         transposed_iteration(c, x, b);
+        return;
+    }
+    if (which == GRAPH_KT) {
+        krylov_iteration_t(c, x, b);
         return;
     }
     if (which >= 2) {

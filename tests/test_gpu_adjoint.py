@@ -99,6 +99,27 @@ def test_adjoint_solve_matches_oracle(case, N):
         assert rel(s.to_flat(lg), ref) <= 1e-9
 
 
+@pytest.mark.parametrize("case,N", [("circle", 32), ("flower5", 128), ("ellipse", 128)])
+def test_adjoint_krylov_matches_oracle(case, N):
+    # BiCGSTAB on M^T lam = c preconditioned by one transposed cycle: the
+    # oracle's adjoint solution (and at 32^2 the dense transpose solve), two
+    # cycles per iteration, fewer cycles than the plain transposed cycles
+    o, s = pair(case, N, krylov=True)
+    cc = np.random.default_rng(9).standard_normal(o.n())
+    st_o, lam_o, h_o = o.solve_t(np.zeros(o.n()), cc, 1e-11, 200)
+    assert st_o == 0
+    lg = s.new_vec()
+    st, rep, h_g = s.solve_t(lg, s.to_device(cc), 1e-11)
+    assert st == 0, s.error()
+    assert rep.cycles == 2 * rep.iterations and len(h_g) == rep.iterations + 1
+    assert rep.res <= 1e-11
+    assert rel(s.to_flat(lg), lam_o) <= 1e-9
+    assert rep.cycles < len(h_o) - 1
+    if N == 32:
+        A = o.dense_matrix(0)
+        assert rel(s.to_flat(lg), np.linalg.solve(A.T, cc)) <= 1e-9
+
+
 def test_forcing_gradient_matches_finite_differences():
     # J(f) = sum over a probe window of u^2 and v^2 after one extrapolated CN
     # step (Eq. extrUdU; the right-hand side is affine in f: dt f on internal

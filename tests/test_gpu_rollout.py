@@ -112,12 +112,12 @@ def bumps(N, types, scale):
 AMP = 0.3
 
 
-def make_rollout(N, steps, every):
+def make_rollout(N, steps, every, krylov=False):
     from paper_1911_00994_gb300 import gpmg
     from paper_1911_00994_gb300.rollout import Rollout
     dt = 0.3 * LEN / N
     s = gpmg.Solver(N, X0, X0, LEN, levels=levels_for(N), alpha=dt / (2 * RE), band=3, adjoint=True,
-                    max_cycles=400)
+                    max_cycles=400, krylov=krylov)
     shape = dict(kind=gpmg.GP_CIRCLE, a=0.25, orbit_r=0.2, orbit_period=1.0)
     st, body = s.geometry_shape(t=0.0, **shape)
     assert st == 0, s.error()
@@ -136,6 +136,24 @@ def test_checkpoints_do_not_change_the_gradient():
     L0, f0, a0 = ro.loss_and_gradient(f, AMP, w)
     assert L3 == L0 and a3 == a0
     assert np.array_equal(s.to_flat(f3), s.to_flat(f0))
+
+
+def test_krylov_rollout_gradient_matches_plain_cycles():
+    # BiCGSTAB for the forward and the adjoint solves (both to 1e-10): the
+    # same loss and gradient as the plain cycles, to the solves' tolerance
+    N, steps = 64, 7
+    out = []
+    for kry in (False, True):
+        s, ro = make_rollout(N, steps, 3, krylov=kry)
+        t = s.types_flat()
+        f = s.to_device(bumps(N, t, 0.1))
+        w = s.to_device(window(N, len(t)))
+        L, fb, ab = ro.loss_and_gradient(f, AMP, w)
+        out.append((L, s.to_flat(fb), ab))
+    (L0, f0, a0), (L1, f1, a1) = out
+    assert abs(L1 - L0) <= 1e-8 * abs(L0)
+    assert abs(a1 - a0) <= 1e-6 * abs(a0)
+    assert np.abs(f1 - f0).max() <= 1e-6 * np.abs(f0).max()
 
 
 def test_rollout_gradient_matches_finite_differences():
