@@ -1623,7 +1623,6 @@ int or_solve_krylov(void *vc, double *x, const double *b, double tol, int maxit,
     double *r = calloc(n, sizeof(double)), *rh = calloc(n, sizeof(double)), *p = calloc(n, sizeof(double));
     double *v = calloc(n, sizeof(double)), *s = calloc(n, sizeof(double)), *t = calloc(n, sizeof(double));
     double *y = calloc(n, sizeof(double)), *z = calloc(n, sizeof(double)), *zero = calloc(n, sizeof(double));
-    double *tr = calloc(n, sizeof(double));
     zero_inactive(c, 0, x);
     double r0 = or_residual(c, 0, x, b, r);
     memcpy(rh, r, sizeof(double) * n);
@@ -1650,13 +1649,16 @@ int or_solve_krylov(void *vc, double *x, const double *b, double tol, int maxit,
             x[k] += alpha * y[k] + omega * z[k];
             r[k] = s[k] - omega * t[k];
         }
-        double rt = or_residual(c, 0, x, b, tr);
+        // residual replacement: the recurrence continues from the true
+        // residual b - M x, so that rounding accumulated in the recurrence
+        // cannot hold the true residual above the tolerance
+        double rt = or_residual(c, 0, x, b, r);
         hist[it] = rt;
         *nit = it;
         if (!(rt == rt) || rt > 1e6 * r0) st = OR_DIVERGED;
         else if (rt <= tol) st = OR_OK;
     }
-    free(r); free(rh); free(p); free(v); free(s); free(t); free(y); free(z); free(zero); free(tr);
+    free(r); free(rh); free(p); free(v); free(s); free(t); free(y); free(z); free(zero);
     return st;
 }
 

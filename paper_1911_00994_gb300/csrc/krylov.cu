@@ -1,7 +1,8 @@
 // Krylov acceleration of the multigrid solve: BiCGSTAB on M x = b,
 // preconditioned on the right by one multigrid cycle from zero (FP64 cycle,
 // or FP32 cycle on an FP64 vector in the mixed mode), and on the adjoint
-// system M^T lam = c with the transposed cycle.  The stopping test is
+// system M^T lam = c with the transposed cycle.  Every iteration ends with
+// the true residual, which also replaces the recurrence's residual.  The stopping test is
 // the true residual ||b - M x||_inf after every iteration, as for the plain
 // cycles.  All scalars stay on the device; one iteration is a fixed sequence
 // of launches that mg_solve replays as a CUDA graph.
@@ -235,7 +236,7 @@ static void bicg_iteration(Ctx *c, bool adj, double *x, const double *b)
     Level &l0 = c->lv[0];
     long long n = l0.VL;
     double *r = c->kv[0], *rh = c->kv[1], *p = c->kv[2], *vn = c->kv[3], *s = c->kv[4], *tn = c->kv[5];
-    double *y = c->kv[6], *z = c->kv[7], *zero = c->kv[8], *rt = c->kv[9];
+    double *y = c->kv[6], *z = c->kv[7], *zero = c->kv[8];
     int vb = vblocks(n);
     dot(c, rh, r, nullptr, nullptr, n);
     k_bicg_beta<<<1, 256, 0, c->stream>>>(c->kpart, c->kpart_n, c->ks);
@@ -250,8 +251,11 @@ static void bicg_iteration(Ctx *c, bool adj, double *x, const double *b)
     dot(c, tn, s, tn, tn, n);
     k_bicg_omega<<<1, 256, 0, c->stream>>>(c->kpart, c->kpart_n, c->ks);
     k_bicg_xr<<<vb, 256, 0, c->stream>>>(x, r, y, z, s, tn, c->ks, n);
-    if (adj) residual_t(c, 0, x, b, rt);
-    else residual<double>(c, 0, x, b, rt);
+    // residual replacement: the recurrence continues from the true residual
+    // b - M x (whose norm is the stopping test), so that rounding accumulated
+    // in the recurrence cannot hold the true residual above the tolerance
+    if (adj) residual_t(c, 0, x, b, r);
+    else residual<double>(c, 0, x, b, r);
     c->launches += 6;
 }
 

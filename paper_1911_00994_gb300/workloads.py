@@ -218,3 +218,76 @@ def random_flat(N: int, types: np.ndarray, seed: int, scale: float = 1.0) -> np.
     out[types.astype(int) == INACTIVE] = 0.0
     out[-1] = rng.standard_normal() * scale
     return out
+
+
+def div_free_flat(N: int, x0: float, y0: float, L: float, types: np.ndarray, seed: int, amp: float = 0.1,
+                  modes: int = 6) -> np.ndarray:
+    """A seeded velocity field that is discretely divergence-free on the MAC
+    grid (config 5's initial state): u and v are the centred differences of a
+    smooth random stream function psi (sum of `modes` plane waves with
+    wave numbers pi * (1..4)) across each face, u = (psi(x, y + h/2) -
+    psi(x, y - h/2)) / h and v = -(psi(x + h/2, y) - psi(x - h/2, y)) / h, so
+    the divergence of every cell telescopes to zero.  Scaled so that
+    max |u|, |v| = amp; pressure, xi and inactive nodes are 0."""
+    rng = np.random.default_rng(seed)
+    kx = np.pi * rng.integers(1, 5, modes) * rng.choice([-1, 1], modes)
+    ky = np.pi * rng.integers(1, 5, modes) * rng.choice([-1, 1], modes)
+    c = rng.standard_normal(modes)
+    ph = rng.uniform(0.0, 2 * np.pi, modes)
+
+    def psi(x, y):
+        s = np.zeros_like(x)
+        for m in range(modes):
+            s += c[m] * np.sin(kx[m] * x + ky[m] * y + ph[m])
+        return s
+
+    h = L / N
+    g, i, j, x, y = flat_coords(N, x0, y0, L)
+    out = np.zeros(g.size)
+    mu, mv = g == 0, g == 1
+    out[mu] = (psi(x[mu], y[mu] + h / 2) - psi(x[mu], y[mu] - h / 2)) / h
+    out[mv] = -(psi(x[mv] + h / 2, y[mv]) - psi(x[mv] - h / 2, y[mv])) / h
+    out[types.astype(int) == INACTIVE] = 0.0
+    out[-1] = 0.0
+    peak = np.abs(out[mu | mv]).max()
+    return out * (amp / peak if peak > 0 else 0.0)
+
+
+def div_free_device(N: int, x0: float, L: float, P: int, seed: int, amp: float = 0.1, modes: int = 6, device=None):
+    """div_free_flat's field (same seeded stream function) built directly in
+    the device vector layout with torch: three frames of (N + 2) rows x P
+    (node (i, j) at (j + 1) P + i + 1), then 32 scalars; pressure, xi and the
+    frame padding 0.  Unlike div_free_flat it does not zero inactive nodes
+    (the solver does) and scales by the maximum over every node.  For the
+    full-size cases, where the flat host arrays would be large."""
+    import torch
+    rng = np.random.default_rng(seed)
+    kx = np.pi * rng.integers(1, 5, modes) * rng.choice([-1, 1], modes)
+    ky = np.pi * rng.integers(1, 5, modes) * rng.choice([-1, 1], modes)
+    c = rng.standard_normal(modes)
+    ph = rng.uniform(0.0, 2 * np.pi, modes)
+    h = L / N
+    F = (N + 2) * P
+    out = torch.zeros(3 * F + 32, dtype=torch.float64, device=device)
+    rows = torch.arange(N + 2, dtype=torch.float64, device=device).view(-1, 1)
+    cols = torch.arange(P, dtype=torch.float64, device=device).view(1, -1)
+
+    def psi(x, y):
+        s = torch.zeros(torch.broadcast_shapes(x.shape, y.shape), dtype=torch.float64, device=device)
+        for m in range(modes):
+            s += float(c[m]) * torch.sin(float(kx[m]) * x + float(ky[m]) * y + float(ph[m]))
+        return s
+
+    xu, yu = x0 + (cols - 1) * h, x0 + (rows - 0.5) * h      # u(i, j) at (i h, (j + 1/2) h)
+    u = (psi(xu, yu + h / 2) - psi(xu, yu - h / 2)) / h
+    u[:, 0] = 0.0
+    u[:, N + 2:] = 0.0                                        # i in [0, N]
+    xv, yv = x0 + (cols - 0.5) * h, x0 + (rows - 1) * h      # v(i, j) at ((i + 1/2) h, j h)
+    v = -(psi(xv + h / 2, yv) - psi(xv - h / 2, yv)) / h
+    v[0, :] = 0.0                                             # j in [0, N]
+    v[:, N + 2:] = 0.0                                        # i in [-1, N]
+    peak = max(float(u.abs().max()), float(v.abs().max()))
+    scale = amp / peak if peak > 0 else 0.0
+    out[:F] = (u * scale).reshape(-1)
+    out[F:2 * F] = (v * scale).reshape(-1)
+    return out
