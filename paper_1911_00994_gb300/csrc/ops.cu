@@ -1596,18 +1596,35 @@ template <typename T> static void copy_vec(Ctx *c, const T *a, T *b, long long n
     c->launches++;
 }
 
-// blocks of the reduction kernels: enough to fill the GPU, at most 1024
-static inline int red_blocks(const Level &l)
+// blocks of 256 threads of `kernel` that are resident on the device at once
+template <typename K> static int resident_blocks(K kernel)
 {
-    long long n = (l.F + 255) / 256;
-    return (int)(n < 1024 ? n : 1024);
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, 0) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    return sms * per_sm;
+}
+
+// blocks of a grid-stride reduction kernel: one block per 256 threads' worth
+// of slots, at most one wave of resident blocks (every block then loops the
+// same number of times and no partial second wave trails)
+template <typename K> static int red_blocks(const Level &l, K kernel, int &cache)
+{
+    if (cache <= 0) cache = resident_blocks(kernel);
+    const long long n = (l.F + 255) / 256;
+    return (int)(n < cache ? n : cache);
 }
 
 template <typename T, typename R> void residual_into(Ctx *c, int lev, const T *x, const T *b, R *r)
 {
     const Level &l = c->lv[lev];
     cudaStream_t st = c->stream;
-    int nb = red_blocks(l);
+    static int resident = 0;
+    int nb = red_blocks(l, k_residual4<T, R>, resident);
     tmr_begin(c, KT_RESIDUAL, lev);
     k_residual4<T, R><<<nb, 256, 0, st>>>(level_args<T>(c, lev), x, b, r, c->part);
     tmr_end(c, KT_RESIDUAL, lev);
@@ -1709,7 +1726,8 @@ template <typename T> void scalar_update(Ctx *c, int lev, T *x, const T *b)
     const Level &l = c->lv[lev];
     cudaStream_t st = c->stream;
     LevelArgs<T> A = level_args<T>(c, lev);
-    int nb = red_blocks(l);
+    static int resident = 0;
+    int nb = red_blocks(l, k_scalar_partial<T>, resident);
     tmr_begin(c, KT_SCALAR, lev);
     k_scalar_partial<T><<<nb, 256, 0, st>>>(A, x, b, c->part);
     tmr_end(c, KT_SCALAR, lev);
