@@ -542,7 +542,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "V-cycles/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": dict(workload(N), precision="fp32 V-cycles in fp64 residual correction (up to 4 per correction)",
+        "config": dict(workload(N), precision="fp32 V-cycles in fp64 residual correction (up to 8 per correction)",
                        levels=levels,
                        l2="inputs larger than L2 (each vector %.0f MB)" % (8 * gpmg.vec_len(N) / 1e6),
                        parallelism="replicas" if world > 1 else "single GPU"),

@@ -93,7 +93,7 @@ typedef struct gp_params {
                            correction while the FP64 residuals are fewer */
 } gp_params;
 
-#define GP_MAX_INNER 4
+#define GP_MAX_INNER 8
 
 typedef struct gp_report {
     int cycles;          /* multigrid cycles done */

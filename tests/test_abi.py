@@ -48,8 +48,8 @@ def test_parameter_checks_on_the_host():
     assert p.inner == 0 and p.precision == gpmg.GP_FP64 and p.nu1 == 2 and p.nu2 == 1
     nb = ctypes.c_size_t(0)
     assert L.gp_workspace_size(ctypes.byref(p), ctypes.byref(nb)) == 0 and nb.value > 0
-    for bad in (-1, 5):
+    for bad in (-1, 9):
         p.inner = bad
         assert L.gp_workspace_size(ctypes.byref(p), ctypes.byref(nb)) == 1
-    p.inner = 4
+    p.inner = 8
     assert L.gp_workspace_size(ctypes.byref(p), ctypes.byref(nb)) == 0
