@@ -293,6 +293,20 @@ def largest_solve(dev, stream, N=8192, steps=2):
     return out
 
 
+def combine_over_ranks(ms, cycles, device, dist):
+    """Timing of a replicated run (one independent solve per rank): the
+    slowest rank's time and the cycles of all ranks, on every rank."""
+    if not dist:
+        return ms, float(cycles)
+    import torch
+    import torch.distributed as tdist
+    tmax = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    tsum = torch.tensor([float(cycles)], dtype=torch.float64, device=device)
+    tdist.all_reduce(tmax, op=tdist.ReduceOp.MAX)
+    tdist.all_reduce(tsum, op=tdist.ReduceOp.SUM)
+    return float(tmax[0]), float(tsum[0])
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -359,16 +373,7 @@ def run_ours(args):
         x.zero_()
         s.solve(x, b, TOL, hist=False)
     nbox, box_ms = s.timer_stop()
-    # max over ranks
-    t = torch.tensor([ms, float(cycles)], dtype=torch.float64, device=dev)
-    if dist:
-        import torch.distributed as tdist
-        tmax = t.clone()
-        tdist.all_reduce(tmax[:1], op=tdist.ReduceOp.MAX)
-        tdist.all_reduce(t[1:], op=tdist.ReduceOp.SUM)
-        ms_all, cycles_all = float(tmax[0]), float(t[1])
-    else:
-        ms_all, cycles_all = ms, float(cycles)
+    ms_all, cycles_all = combine_over_ranks(ms, cycles, dev, dist)
     value = cycles_all / (ms_all / 1e3)
 
     # ---- end to end through the public API with host buffers: every step
