@@ -147,7 +147,7 @@ def build_case(N, precision, device, stream, levels=None, krylov=False, inner=0)
 
 
 def adjoint_rollout(dev, stream, steps=50, every=10, N=512, krylov=True):
-    """Config 4's adjoint: the orbiting circle (r = 0.25, orbit radius 0.2,
+    """Adjoint rollout of the orbiting circle (r = 0.25, orbit radius 0.2,
     period 1) at Re = 100 on [-1, 1]^2, a rollout of `steps` CN steps from
     rest, and the gradient of the kinetic energy on a 64 x 64 probe window
     (u and v nodes with array indices i in [352, 416), j in [224, 288)) with
@@ -203,7 +203,7 @@ def adjoint_rollout(dev, stream, steps=50, every=10, N=512, krylov=True):
 
 
 def moving_ellipse(dev, stream, steps=20, warm=4, N=1024):
-    """Config 2's moving body: the ellipse with semi-axes 0.4 and 0.2 on
+    """The moving ellipse with semi-axes 0.4 and 0.2 on
     [-1, 1]^2, translating on a circle of radius 0.3 with period 1, Re = 100,
     from rest; the ghost-point geometry is rebuilt every step.  dt = 0.3 h
     (the paper's time-step bound; see the rollout above).  BiCGSTAB
@@ -247,7 +247,7 @@ def moving_ellipse(dev, stream, steps=20, warm=4, N=1024):
 
 
 def largest_solve(dev, stream, N=8192, steps=2):
-    """Config 5, the largest single solve: the seven-petal flower
+    """The largest single solve: the seven-petal flower
     r = 0.5 + 0.1 sin(7 theta) on [-1, 1]^2 at 8192^2 (201 M unknowns),
     Re = 500, dt = h, the CN system of a seeded divergence-free velocity of
     amplitude 0.1 (explicit convective term), solved to ||r||_inf <= 1e-10
@@ -282,7 +282,7 @@ def largest_solve(dev, stream, N=8192, steps=2):
             x.copy_(xn)
             st, rep, _ = s.solve(x, b, TOL, hist=False)
             if st:
-                raise RuntimeError("config 5 solve failed: %s" % s.error())
+                raise RuntimeError("8192^2 flower solve failed: %s" % s.error())
             cyc += rep.cycles
         e1.record(stream)
         torch.cuda.synchronize(dev)
@@ -561,9 +561,9 @@ def run_ours(args):
                                            "steps": n1},
         "bicgstab_mixed": {"time_to_tol_ms": msk / nk, "iterations_per_step": kit / nk, "cycles_per_step": kc / nk,
                            "cycles_per_s": kc / (msk / 1e3), "steps": nk},
-        "adjoint_rollout_config4": adj,
-        "moving_ellipse_config2": mov,
-        "largest_solve_config5": big,
+        "adjoint_rollout_orbiting_circle_512": adj,
+        "moving_ellipse_1024": mov,
+        "largest_solve_flower7_8192": big,
         "roofline": {"kernel": "k_box_tma<float> (finest-level full-box sweep, five colours in one pass)", "bound": "hbm",
                      "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "peak_source": src, "avg_launch_ms": avg_ms, "launches": nbox,

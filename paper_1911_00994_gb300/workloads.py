@@ -35,7 +35,7 @@ def half_lattice(N: int, x0: float, y0: float, L: float):
 
 
 def circle(R: float, xc: float = 0.0, yc: float = 0.0):
-    """Disc of radius R: phi = R - r (config 1: R = 0.5)."""
+    """Disc of radius R: phi = R - r."""
     return lambda X, Y: R - np.hypot(X - xc, Y - yc)
 
 
@@ -223,7 +223,8 @@ def random_flat(N: int, types: np.ndarray, seed: int, scale: float = 1.0) -> np.
 def div_free_flat(N: int, x0: float, y0: float, L: float, types: np.ndarray, seed: int, amp: float = 0.1,
                   modes: int = 6) -> np.ndarray:
     """A seeded velocity field that is discretely divergence-free on the MAC
-    grid (config 5's initial state): u and v are the centred differences of a
+    grid (the initial state of the 8192^2 seven-petal-flower solve): u and v
+    are the centred differences of a
     smooth random stream function psi (sum of `modes` plane waves with
     wave numbers pi * (1..4)) across each face, u = (psi(x, y + h/2) -
     psi(x, y - h/2)) / h and v = -(psi(x + h/2, y) - psi(x - h/2, y)) / h, so

@@ -11,11 +11,11 @@ from paper_1911_00994_gb300 import workloads as W
 
 CASES = {
     # name: (shape, x0, L)
-    "circle": (W.circle(0.5), -1.0, 2.0),                           # config 1 body
-    "circle_off": (W.circle(0.25, 0.2, 0.0), -1.0, 2.0),            # config 4 body at t = 0
-    "ellipse": (W.ellipse(0.4, 0.2, 0.3, 0.0), -1.0, 2.0),          # config 2 body at t = 0
-    "flower5": (W.flower(0.2, 0.05, 5, 0.5, 0.5), 0.0, 1.0),        # config 3 body
-    "flower7": (W.flower(0.5, 0.1, 7), -1.0, 2.0),                  # config 5 body
+    "circle": (W.circle(0.5), -1.0, 2.0),                           # the 32^2 manufactured case
+    "circle_off": (W.circle(0.25, 0.2, 0.0), -1.0, 2.0),            # the orbiting circle at t = 0
+    "ellipse": (W.ellipse(0.4, 0.2, 0.3, 0.0), -1.0, 2.0),          # the orbiting ellipse at t = 0
+    "flower5": (W.flower(0.2, 0.05, 5, 0.5, 0.5), 0.0, 1.0),        # the cavity's five-petal flower
+    "flower7": (W.flower(0.5, 0.1, 7), -1.0, 2.0),                  # the seven-petal flower
     "nobody": (lambda X, Y: -1.0 + 0.0 * X, -1.0, 2.0),             # empty box
 }
 

@@ -1,7 +1,7 @@
 """Crank-Nicolson step (Sect. 2) on the GPU against the oracle: convective
 term, right-hand side, and whole steps (mid-point Picard for steps 0 and 1,
-extrapolation from step 2) of config 1 (circle r = 0.5 on [-1, 1]^2, 32^2,
-Re = 1, dt = h, Taylor-Green velocity with the forcing that keeps it steady).
+extrapolation from step 2) of the 32^2 manufactured case (circle r = 0.5 on
+[-1, 1]^2, Re = 1, dt = h, Taylor-Green velocity with the forcing that keeps it steady).
 """
 import numpy as np
 import pytest
@@ -58,7 +58,7 @@ def test_convective_and_rhs_match(case, N):
         assert rel(got, want) < 1e-13
 
 
-def test_config1_cn_steps_match_oracle():
+def test_circle32_cn_steps_match_oracle():
     Re = 1.0
     o, s, dt = setup("circle", 32, Re)
     N, x0, L = 32, -1.0, 2.0

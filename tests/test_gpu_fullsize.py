@@ -2,14 +2,14 @@
 captured graphs, the default cycle), each checked with the oracle's residual
 of the solution the GPU returns.  The oracle assembles its own system from
 the same level set, so the check does not involve the GPU's operator.
-- config 3: 4096^2 lid-driven cavity with the five-petal flower, mixed and
+- the 4096^2 lid-driven cavity with the five-petal flower, mixed and
   FP64 cycles to 1e-10;
-- config 5: 8192^2 seven-petal flower, a CN system from a seeded
+- the 8192^2 seven-petal flower, a CN system from a seeded
   divergence-free velocity, BiCGSTAB mixed and FP64;
-- config 2: the moving ellipse at 1024^2 after three CN steps, BiCGSTAB
+- the orbiting 0.4 x 0.2 ellipse at 1024^2 after three CN steps, BiCGSTAB
   mixed.
 The mixed and FP64 solutions agree to the tolerance the solves reach; with
-plain cycles (config 3) the two paths take the same number of cycles."""
+plain cycles (the cavity) the two paths take the same number of cycles."""
 import numpy as np
 import pytest
 
@@ -33,7 +33,7 @@ def oracle_residual(N, x0, L, alpha, phi, x, b):
     return o, nrm
 
 
-def test_config3_4096_solutions_have_oracle_residual_below_tol():
+def test_cavity_flower5_4096_solutions_have_oracle_residual_below_tol():
     import torch
     from paper_1911_00994_gb300 import gpmg
     N, x0, L = 4096, 0.0, 1.0
@@ -64,7 +64,7 @@ def test_config3_4096_solutions_have_oracle_residual_below_tol():
     assert cycles[gpmg.GP_MIXED] == cycles[gpmg.GP_FP64]
 
 
-def test_config5_8192_cn_system_has_oracle_residual_below_tol():
+def test_flower7_8192_cn_system_has_oracle_residual_below_tol():
     import torch
     from paper_1911_00994_gb300 import gpmg
     N, x0, L, Re = 8192, -1.0, 2.0, 500.0
@@ -100,7 +100,7 @@ def test_config5_8192_cn_system_has_oracle_residual_below_tol():
     assert cycles[gpmg.GP_MIXED] <= 3 * cycles[gpmg.GP_FP64]
 
 
-def test_config2_1024_moving_ellipse_step_has_oracle_residual_below_tol():
+def test_moving_ellipse_1024_step_has_oracle_residual_below_tol():
     import torch
     from paper_1911_00994_gb300 import gpmg
     N, x0, L, Re = 1024, -1.0, 2.0, 100.0

@@ -1,6 +1,6 @@
 """BiCGSTAB preconditioned by one multigrid cycle on the GPU against the
-oracle's BiCGSTAB, and on the bodies where plain V-cycles diverge (config 2's
-ellipse, config 5's seven-petal flower)."""
+oracle's BiCGSTAB, and on the bodies where plain V-cycles diverge (the
+0.4 x 0.2 ellipse, the seven-petal flower)."""
 import numpy as np
 import pytest
 

@@ -1,5 +1,5 @@
 """Moving bodies (Sect. 3.4): the device level set of a rigidly moving test
-body against the closed form, and Crank-Nicolson steps of config 4's body
+body against the closed form, and Crank-Nicolson steps of the orbiting circle
 (circle r = 0.25 on an orbit of radius 0.2, period 1) with the geometry
 rebuilt every step, against the oracle."""
 import numpy as np

@@ -136,7 +136,7 @@ def test_cycle_history_matches(case, N, ah2):
         assert abs(ng - no) <= 1e-6 * no
 
 
-def test_config1_solve_matches_oracle():
+def test_circle32_solve_matches_oracle():
     # circle r = 0.5, 32 x 32 on [-1, 1]^2, Re = 1, dt = h: alpha = h / 2;
     # Taylor-Green manufactured solution, solved to ||r||_inf <= 1e-12
     o, s = pair("circle", 32)

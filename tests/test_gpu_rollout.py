@@ -1,5 +1,5 @@
 """Adjoint of a rollout of Crank-Nicolson steps around the orbiting circle
-(config 4's body: r = 0.25, orbit radius 0.2, period 1, Re = 100) on the GPU:
+(the orbiting circle: r = 0.25, orbit radius 0.2, period 1, Re = 100) on the GPU:
 the gradient of a windowed kinetic energy with respect to the forcing and the
 body-velocity amplitude, against the oracle's adjoint (same geometry arrays),
 against central differences of the forward rollout, and with and without

@@ -3,8 +3,8 @@ NSCN1, extrUdU, NSitconv with a fixed number of Picard iterations) against
 the oracle's forward step: the transposed convective Jacobian against exact
 central differences of the convective term (quadratic in x), the transposed
 explicit diffusion against the right-hand side, and the gradient of a
-windowed kinetic energy after a short rollout of the moving circle (config 4
-body) with respect to the forcing and the boundary-velocity amplitude
+windowed kinetic energy after a short rollout of the orbiting circle (r = 0.25,
+orbit radius 0.2) with respect to the forcing and the boundary-velocity amplitude
 against central differences of the forward rollout."""
 import numpy as np
 import pytest

@@ -127,8 +127,8 @@ def test_assembled_matrix_matches_residual():
     assert np.abs(r - (b - A @ x)).max() < 1e-12 * np.abs(b).max() * 100
 
 
-def test_multigrid_equals_direct_config1():
-    # config 1: circle r = 0.5, 32 x 32 on [-1, 1]^2, Re = 1, dt = h -> alpha = h / 2
+def test_multigrid_equals_direct_circle32():
+    # circle r = 0.5, 32 x 32 on [-1, 1]^2, Re = 1, dt = h -> alpha = h / 2
     o, phi, st = make_oracle("circle", 32)
     ex = W.taylor_green()
     b, xe, t, gh = manufactured(o, ex)
@@ -284,7 +284,7 @@ def test_coarse_solve_matches_library_solve():
 
 def test_krylov_equals_direct_solve():
     # BiCGSTAB preconditioned by one cycle reaches the dense solution of the
-    # assembled system (config 1)
+    # assembled system (the 32^2 circle)
     o, phi, st = make_oracle("circle", 32)
     ex = W.taylor_green()
     b, xe, t, gh = manufactured(o, ex)
