@@ -17,6 +17,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -127,14 +128,14 @@ def ncu_traffic(kernel):
     return None
 
 
-def build_case(N, precision, device, stream, levels=None, krylov=False, inner=0):
+def build_case(N, precision, device, stream, levels=None, krylov=False, inner=0, gamma=1, alpha=None):
     import torch
     from paper_1911_00994_gb300 import gpmg
     from paper_1911_00994_gb300 import workloads as W
     h = 1.0 / N
-    alpha = h / (2.0 * 1000.0)
+    alpha = h / (2.0 * 1000.0) if alpha is None else alpha
     s = gpmg.Solver(N, 0.0, 0.0, 1.0, levels=levels, alpha=alpha, precision=precision, device=device,
-                    max_cycles=200, stream=stream, krylov=krylov, inner=inner)
+                    max_cycles=200, stream=stream, krylov=krylov, inner=inner, gamma=gamma)
     phi = torch.from_numpy(W.phi_half_lattice(W.flower(0.2, 0.05, 5, 0.5, 0.5), N, 0.0, 0.0, 1.0)).to(device)
     st = s.geometry(phi, 0)
     if st:
@@ -290,6 +291,46 @@ def largest_solve(dev, stream, N=8192, steps=2):
         out[name] = {"time_to_tol_ms": ms, "cycles_per_step": cyc / steps, "cycles_per_s": cyc / steps / (ms / 1e3)}
         del s, x
         torch.cuda.empty_cache()
+    return out
+
+
+def cycle_ablation(dev, stream, tol, barrier, cases=((256, 8.0), (1024, 0.512), (4096, 2.048))):
+    """V(2,1) against W(2,1) cycles (the W-cycle is the one the paper adopts,
+    Sect. 4, and its convergence factor is reported for W-cycles, Sect. 5), both
+    mixed precision, on the cavity-with-flower system at N^2 with
+    alpha / h^2 as given (1024^2 and 4096^2: Re = 1000, dt = h): cycles, the
+    geometric-mean residual reduction per cycle and the time to the tolerance
+    (the second of two solves), or the failure.  A W-cycle visits level l
+    2^l times, so its coarse levels cost far more launches."""
+    import torch
+    from paper_1911_00994_gb300 import gpmg
+    out = []
+    for N, ah2 in cases:
+        row = {"N": N, "alpha_over_h2": ah2}
+        for name, gamma in (("V", 1), ("W", 2)):
+            s, b = build_case(N, gpmg.GP_MIXED, dev, stream, gamma=gamma, alpha=ah2 / N ** 2)
+            x = s.new_vec()
+            st, rep, _ = s.solve(x, b, tol, hist=False)
+            r = {"levels": s.levels}
+            if st == 0:
+                barrier()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                x.zero_()
+                e0.record(stream)
+                st, rep, _ = s.solve(x, b, tol, hist=False)
+                e1.record(stream)
+                barrier()
+                r["time_to_tol_ms"] = e0.elapsed_time(e1)
+            else:
+                # every replica solves the same system, so all of them take this branch
+                barrier()
+                barrier()
+            r.update({"status": "ok" if st == 0 else "failed: %s" % s.error(), "cycles": rep.cycles,
+                      "rho": rep.rho if math.isfinite(rep.rho) else None})
+            row[name] = r
+            del s
+            torch.cuda.empty_cache()
+        out.append(row)
     return out
 
 
@@ -525,6 +566,7 @@ def run_ours(args):
     ms1 = h0.elapsed_time(h1)
     del s1
     torch.cuda.empty_cache()
+    wcy = cycle_ablation(dev, stream, TOL, barrier) if not args.no_wcycle else None
     adj = adjoint_rollout(dev, stream) if not args.no_adjoint else None
     mov = moving_ellipse(dev, stream) if not args.no_moving else None
     big = largest_solve(dev, stream) if not args.no_large else None
@@ -559,6 +601,7 @@ def run_ours(args):
         "mixed_one_cycle_per_correction": {"time_to_tol_ms": ms1 / n1, "cycles_per_step": c1 / n1,
                                            "corrections_per_step": it1 / n1, "cycles_per_s": c1 / (ms1 / 1e3),
                                            "steps": n1},
+        "v_and_w_cycles_flower_cavity": wcy,
         "bicgstab_mixed": {"time_to_tol_ms": msk / nk, "iterations_per_step": kit / nk, "cycles_per_step": kc / nk,
                            "cycles_per_s": kc / (msk / 1e3), "steps": nk},
         "adjoint_rollout_orbiting_circle_512": adj,
@@ -661,6 +704,7 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-moving", action="store_true")
     ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--no-wcycle", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         args.steps = 2 if args.steps is None else args.steps

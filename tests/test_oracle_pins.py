@@ -13,6 +13,12 @@ not by the oracle itself.
 * Bilinear prolongation is exact for linear fields.
 * Multicolour box ordering is race free: a random order inside each colour
   gives a bitwise identical iterate.
+* W-cycle (the cycle Sect. 4 adopts): with two levels it is the V-cycle
+  bitwise (the coarse problem is solved exactly, so a second visit changes
+  nothing); on more levels it is the pre-smoothing, restriction, two coarse
+  cycles (from zero, then from the first's result), prolongation and
+  post-smoothing composed from the pinned pieces; it converges to the dense
+  solution.
 """
 import numpy as np
 import pytest
@@ -270,6 +276,58 @@ def test_colour_order_is_race_free():
     y2 = o2.box_sweep(x, b)
     assert np.array_equal(y1, y2)
     assert not np.array_equal(y1, x)
+
+
+def test_w_cycle_on_two_levels_is_the_v_cycle():
+    ex = W.taylor_green()
+    out = []
+    for gamma in (1, 2):
+        o, phi, st = make_oracle("flower5", 64, levels=2, gamma=gamma)
+        assert st == 0
+        b, xe, t, gh = manufactured(o, ex)
+        x = W.random_flat(64, t, 21)
+        for _ in range(2):
+            st, x = o.cycle(x, b)
+            assert st == 0
+        out.append(x)
+    assert np.array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("gamma", [1, 2])
+def test_cycle_composed_from_its_pieces(gamma):
+    # Sect. 4: nu1 relaxations, the residual restricted, the coarse residual
+    # equation by gamma coarse cycles from a zero error (each from the last
+    # one's result), the error prolonged and added, nu2 relaxations
+    o, phi, st = make_oracle("flower5", 128, alpha=2.0 / 128 ** 2, levels=4, gamma=gamma)
+    assert st == 0
+    ex = W.taylor_green()
+    b, xe, t, gh = manufactured(o, ex)
+    x0 = W.random_flat(128, t, 22)
+    st, xc = o.cycle(x0, b)
+    assert st == 0
+    x = o.smooth(x0, b, 2, 0)
+    r, _ = o.residual(x, b, 0)
+    bH = o.restrict(r, 0)
+    eH = np.zeros(o.n(1))
+    for _ in range(gamma):
+        st, eH = o.cycle(eH, bH, 1)
+    x = o.prolong(eH, x, 0)
+    x = o.smooth(x, b, 1, 0)
+    assert np.array_equal(x, xc)
+    if gamma == 2:
+        # one coarse cycle instead of two gives another iterate
+        st, e1 = o.cycle(np.zeros(o.n(1)), bH, 1)
+        assert not np.array_equal(e1, eH)
+
+
+def test_w_cycles_converge_to_the_dense_solution():
+    o, phi, st = make_oracle("circle", 32, gamma=2)
+    ex = W.taylor_green()
+    b, xe, t, gh = manufactured(o, ex)
+    st, xd = o.dense_solve(b)
+    st, xw, hw = o.solve(np.zeros_like(b), b, 1e-12, 60)
+    assert st == 0
+    assert np.abs(xw - xd).max() / np.abs(xd).max() <= 1e-10
 
 
 def test_coarse_solve_matches_library_solve():
