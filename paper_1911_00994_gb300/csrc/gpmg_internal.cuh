@@ -38,6 +38,10 @@ constexpr int GRAPH_T = 4 + GP_MAX_INNER - 1;  // captured kind: one transposed 
 constexpr int GRAPH_KT = GRAPH_T + 1;          // captured kind: one BiCGSTAB iteration of the adjoint solve
 constexpr int NGRAPH = GRAPH_KT + 1;           // captured iteration kinds
 constexpr int GH_ST = 9;  // stencil slots per ghost row
+// fused ghost sweeps: each block owns GC_OWN consecutive ghost-class rows and
+// relaxes them together with every row they reach through at most lambda - 1
+// stencil links (their closure, at most GC_CAP rows)
+constexpr int GC_OWN = 128, GC_CAP = 512, GC_THREADS = 256;
 
 // error bits written by kernels into the context's device status word
 enum ErrBits : unsigned {
@@ -66,6 +70,9 @@ struct GhostList {
     double *acc;       // [2][cap] accumulated corrections of the fused sweeps (ping-pong)
     float *accf;
     int *strow;        // [GH_ST][cap] ghost-row index of each stencil node, or -1
+    int *cl_row;       // [cap / GC_OWN + 1][GC_CAP] rows of each block's closure, ascending
+    int16_t *cl_lnk;   // [cap / GC_OWN + 1][GH_ST][GC_CAP] closure position of each stencil node's row, or -1
+    int *cl_n;         // [cap / GC_OWN + 1] closure size of each block (-1: above GC_CAP)
     int cap;
 };
 
@@ -115,6 +122,7 @@ struct Level {
     int h_ncut;
     int h_cutoff[MAX_CUTCOL + 1];
     int h_nlonely;
+    int h_fused;       // the lambda ghost sweeps run as one launch over the row closures
     // adjoint (carved when gp_params.adjoint is set): the columns of M
     // referenced by ghost-class rows, sorted, each with its (row node,
     // weight) entries; the ghost-row part of M^T lam at those columns (0 at

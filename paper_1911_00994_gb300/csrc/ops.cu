@@ -961,6 +961,76 @@ template <typename T> __global__ void k_ghost_acc_apply(GhostList gh, int nrows,
     if (k < nrows) x[gh.node[k]] += gacc<T>(gh)[(long long)(sweeps & 1) * gh.cap + k];
 }
 
+// The lambda sweeps of k_ghost_acc_sweep in one launch (Eq. ghostrelax with x
+// fixed).  Block q owns rows [q GC_OWN, (q + 1) GC_OWN) and relaxes them with
+// their closure (every row within lambda - 1 stencil links) in shared memory:
+// after sweep s a row at link distance h is exact for s <= lambda - h, so the
+// owned rows end with exactly the iterate of the one-sweep-per-launch form, and
+// a link that leaves the closure (distance lambda) counts as zero.  Each row
+// repeats that form's arithmetic in the same order (no correction added in the
+// first sweep), so both give the same bits.  The owned rows' corrections go
+// where k_ghost_acc_apply reads them after lambda sweeps; no block writes x.
+template <typename T>
+__global__ void __launch_bounds__(GC_THREADS) k_ghost_fused(GhostList gh, int nrows, const T *x, const T *b, T dtau,
+                                                             int lambda)
+{
+    constexpr int RPT = GC_CAP / GC_THREADS;
+    __shared__ T dsh[2][GC_CAP];
+    const int n = gh.cl_n[blockIdx.x];
+    const int lo = blockIdx.x * GC_OWN, hi = min(lo + GC_OWN, nrows);
+    const int *grow = gh.cl_row + (long long)blockIdx.x * GC_CAP;
+    const int16_t *glnk = gh.cl_lnk + (long long)blockIdx.x * GH_ST * GC_CAP;
+    const T *w = gw<T>(gh);
+    int kr[RPT], nst[RPT], lnk[RPT][GH_ST];
+    T wv[RPT][GH_ST], xv[RPT][GH_ST], bv[RPT];
+#pragma unroll
+    for (int r = 0; r < RPT; r++) {
+        const int c = threadIdx.x + r * GC_THREADS;
+        const bool valid = c < n;
+        const int k = valid ? grow[c] : 0;
+        kr[r] = valid ? k : -1;
+        nst[r] = valid ? gh.nst[k] : 0;
+        int idx[GH_ST];
+#pragma unroll
+        for (int q = 0; q < GH_ST; q++) {
+            const long long e = (long long)q * gh.cap + k;
+            idx[q] = q < nst[r] ? gh.st[e] : 0;
+            lnk[r][q] = q < nst[r] ? (int)glnk[q * GC_CAP + c] : -1;
+            wv[r][q] = q < nst[r] ? w[e] : (T)0;
+        }
+#pragma unroll
+        for (int q = 0; q < GH_ST; q++) xv[r][q] = q < nst[r] ? x[idx[q]] : (T)0;
+        bv[r] = valid ? b[gh.node[k]] : (T)0;
+        if (valid) dsh[0][c] = (T)0;
+    }
+    __syncthreads();
+    int cur = 0;
+    for (int s = 0; s < lambda; s++) {
+#pragma unroll
+        for (int r = 0; r < RPT; r++) {
+            if (kr[r] < 0) continue;
+            const int c = threadIdx.x + r * GC_THREADS;
+            T xs[GH_ST];
+#pragma unroll
+            for (int q = 0; q < GH_ST; q++) {
+                xs[q] = xv[r][q];
+                if (s > 0 && lnk[r][q] >= 0) xs[q] += dsh[cur][lnk[r][q]];
+            }
+            T res = bv[r];
+#pragma unroll
+            for (int q = 0; q < GH_ST; q++)
+                if (q < nst[r]) res -= wv[r][q] * xs[q];
+            dsh[cur ^ 1][c] = dsh[cur][c] + dtau * res;
+        }
+        __syncthreads();
+        cur ^= 1;
+    }
+    T *dout = gacc<T>(gh) + (long long)(lambda & 1) * gh.cap;
+#pragma unroll
+    for (int r = 0; r < RPT; r++)
+        if (kr[r] >= lo && kr[r] < hi) dout[kr[r]] = dsh[cur][threadIdx.x + r * GC_THREADS];
+}
+
 // ---------------------------------------------------------------- transfers
 
 // Eq. (restop) where the whole stencil is of the coarse node's class,
@@ -1559,6 +1629,106 @@ __global__ void k_stencil_rows(GhostList gh, int n, const int *map)
     }
 }
 
+// The closure of each block of GC_OWN ghost-class rows for k_ghost_fused:
+// the rows within lambda - 1 stencil links (breadth first over a bitmap of
+// the level's rows in shared memory), listed in ascending order, and for
+// each stencil entry of each listed row the list position of the entry's row
+// (or -1 when that row is outside the closure or no row).  cl_n = -1 when the
+// closure has more than GC_CAP rows.  Once per geometry.
+__global__ void __launch_bounds__(GC_THREADS) k_ghost_closure(GhostList gh, int n, int lambda)
+{
+    extern __shared__ unsigned cl_smem[];
+    const int words = (n + 31) >> 5;
+    unsigned *cur = cl_smem, *nxt = cl_smem + words;
+    int *rows = (int *)(nxt + words);  // GC_CAP
+    int *scan = rows + GC_CAP;         // GC_THREADS + 1
+    const int lo = blockIdx.x * GC_OWN, hi = min(lo + GC_OWN, n);
+    for (int wd = threadIdx.x; wd < words; wd += blockDim.x) {
+        unsigned m = 0;
+        for (int bit = 0; bit < 32; bit++) {
+            const int r = (wd << 5) + bit;
+            if (r >= lo && r < hi) m |= 1u << bit;
+        }
+        cur[wd] = m;
+        nxt[wd] = m;
+    }
+    __syncthreads();
+    for (int hop = 1; hop < lambda; hop++) {
+        for (int wd = threadIdx.x; wd < words; wd += blockDim.x) {
+            unsigned m = cur[wd];
+            while (m) {
+                const int r = (wd << 5) + __ffs(m) - 1;
+                m &= m - 1;
+                const int ns = gh.nst[r];
+                for (int q = 0; q < ns && q < GH_ST; q++) {
+                    const int l = gh.strow[(long long)q * gh.cap + r];
+                    if (l >= 0 && l < n) atomicOr(&nxt[l >> 5], 1u << (l & 31));
+                }
+            }
+        }
+        __syncthreads();
+        for (int wd = threadIdx.x; wd < words; wd += blockDim.x) cur[wd] = nxt[wd];
+        __syncthreads();
+    }
+    // ascending list: each thread lists a contiguous run of words at the
+    // offset of an exclusive scan of the runs' counts
+    const int per = (words + blockDim.x - 1) / blockDim.x;
+    const int w0 = min((int)threadIdx.x * per, words), w1 = min(w0 + per, words);
+    int cnt = 0;
+    for (int wd = w0; wd < w1; wd++) cnt += __popc(cur[wd]);
+    scan[threadIdx.x] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int t = 0; t < (int)blockDim.x; t++) {
+            const int v = scan[t];
+            scan[t] = acc;
+            acc += v;
+        }
+        scan[blockDim.x] = acc;
+    }
+    __syncthreads();
+    const int total = scan[blockDim.x];
+    if (total > GC_CAP) {
+        if (threadIdx.x == 0) gh.cl_n[blockIdx.x] = -1;
+        return;
+    }
+    int pos = scan[threadIdx.x];
+    for (int wd = w0; wd < w1; wd++) {
+        unsigned m = cur[wd];
+        while (m) {
+            rows[pos++] = (wd << 5) + __ffs(m) - 1;
+            m &= m - 1;
+        }
+    }
+    __syncthreads();
+    int *grow = gh.cl_row + (long long)blockIdx.x * GC_CAP;
+    int16_t *glnk = gh.cl_lnk + (long long)blockIdx.x * GH_ST * GC_CAP;
+    for (int ci = threadIdx.x; ci < total; ci += blockDim.x) {
+        const int r = rows[ci];
+        grow[ci] = r;
+        const int ns = gh.nst[r];
+        for (int q = 0; q < GH_ST; q++) {
+            int loc = -1;
+            const int l = q < ns ? gh.strow[(long long)q * gh.cap + r] : -1;
+            if (l >= 0 && l < n && ((cur[l >> 5] >> (l & 31)) & 1u)) {
+                int a = 0, z = total - 1;
+                while (a < z) {
+                    const int mid = (a + z) >> 1;
+                    if (rows[mid] < l) a = mid + 1;
+                    else z = mid;
+                }
+                loc = a;
+            }
+            glnk[q * GC_CAP + ci] = (int16_t)loc;
+        }
+    }
+    if (threadIdx.x == 0) gh.cl_n[blockIdx.x] = total;
+}
+
+static size_t closure_smem(int n) { return 2 * sizeof(unsigned) * (size_t)((n + 31) / 32) + sizeof(int) * (GC_CAP + GC_THREADS + 1); }
+constexpr size_t CLOSURE_SMEM_MAX = 200 * 1024;
+
 int ghost_row_links(Ctx *c)
 {
     cudaStream_t st = c->stream;
@@ -1571,10 +1741,35 @@ int ghost_row_links(Ctx *c)
         k_row_of_node<<<(n + 255) / 256, 256, 0, st>>>(l.gh.node, n, map);
         k_stencil_rows<<<(n + 255) / 256, 256, 0, st>>>(l.gh, n, map);
     }
-    const cudaError_t e = cudaGetLastError();
+    // closures for the fused sweeps of the levels above the one-block size
+    // (lambda > 1; one sweep needs no closure)
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_ghost_closure, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CLOSURE_SMEM_MAX);
+        attr = true;
+    }
+    std::vector<std::vector<int>> hn(c->L);
+    for (int lev = 0; lev < c->L; lev++) {
+        Level &l = c->lv[lev];
+        l.h_fused = 0;
+        const int n = l.h_nrows;
+        if (n <= GHOST_BLOCK_ROWS || c->prm.lambda <= 1 || closure_smem(n) > CLOSURE_SMEM_MAX) continue;
+        const int nblk = (n + GC_OWN - 1) / GC_OWN;
+        k_ghost_closure<<<nblk, GC_THREADS, closure_smem(n), st>>>(l.gh, n, c->prm.lambda);
+        hn[lev].resize(nblk);
+        cudaMemcpyAsync(hn[lev].data(), l.gh.cl_n, sizeof(int) * nblk, cudaMemcpyDeviceToHost, st);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         snprintf(c->msg, sizeof c->msg, "ghost links: %s", cudaGetErrorString(e));
         return GP_CUDA;
+    }
+    for (int lev = 0; lev < c->L; lev++) {
+        if (hn[lev].empty()) continue;
+        bool ok = true;
+        for (int v : hn[lev]) ok = ok && v >= 0;
+        c->lv[lev].h_fused = ok ? 1 : 0;
     }
     return GP_OK;
 }
@@ -1801,11 +1996,18 @@ template <typename T> void smooth_from(Ctx *c, int lev, T *x, T *in, const T *b,
         } else if (l.h_nrows > 0 && c->prm.lambda > 0) {
             const int nb = (l.h_nrows + 255) / 256;
             tmr_begin(c, KT_GHOST, lev);
-            for (int k = 0; k < c->prm.lambda; k++)
-                k_ghost_acc_sweep<T><<<nb, 256, 0, c->stream>>>(l.gh, l.h_nrows, cur, b, (T)c->prm.dtau, k);
+            if (l.h_fused) {
+                k_ghost_fused<T><<<(l.h_nrows + GC_OWN - 1) / GC_OWN, GC_THREADS, 0, c->stream>>>(
+                    l.gh, l.h_nrows, cur, b, (T)c->prm.dtau, c->prm.lambda);
+                c->launches += 1;
+            } else {
+                for (int k = 0; k < c->prm.lambda; k++)
+                    k_ghost_acc_sweep<T><<<nb, 256, 0, c->stream>>>(l.gh, l.h_nrows, cur, b, (T)c->prm.dtau, k);
+                c->launches += c->prm.lambda;
+            }
             k_ghost_acc_apply<T><<<nb, 256, 0, c->stream>>>(l.gh, l.h_nrows, cur, c->prm.lambda);
             tmr_end(c, KT_GHOST, lev);
-            c->launches += c->prm.lambda + 1;
+            c->launches += 1;
         }
     }
     if (cur != x) copy_vec<T>(c, cur, x, l.VL);

@@ -163,6 +163,10 @@ static size_t carve(Ctx *c, char *base)
         g.acc = cv.take<double>(2 * (size_t)gc);
         g.accf = cv.take<float>(2 * (size_t)gc);
         g.strow = cv.take<int>((size_t)GH_ST * gc);
+        const size_t ncl = (size_t)gc / GC_OWN + 1;
+        g.cl_row = cv.take<int>(ncl * GC_CAP);
+        g.cl_lnk = cv.take<int16_t>(ncl * GH_ST * GC_CAP);
+        g.cl_n = cv.take<int>(ncl);
         int cc = cut_cap(l.N);
         l.cut.cap = cc;
         l.cut.count = cv.take<int>(1);
