@@ -107,7 +107,7 @@ def test_mixed_inner_cycles(case, N):
     x1 = s1.new_vec()
     st1, rep1, h1 = s1.solve(x1, s1.to_device(b), 1e-10)
     assert st1 == 0 and rep1.iterations == rep1.cycles
-    for inner in (2, 3, 4):
+    for inner in (2, 4, 8):
         _, s3 = pair(case, N, alpha=alpha, precision=1, inner=inner)
         x3 = s3.new_vec()
         st3, rep3, h3 = s3.solve(x3, s3.to_device(b), 1e-10)
