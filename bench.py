@@ -114,14 +114,14 @@ def kernel_source_sha1():
     return hashlib.sha1("".join(parts).encode()).hexdigest()
 
 
-def ncu_traffic(kernel):
+def ncu_traffic(kernel, N):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
-    was taken on the current kernel source."""
+    was taken on the current kernel source and on an N x N finest level."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             d = json.load(f)
         e = d.get(kernel)
-        if e and e.get("kernel_source_sha1") == kernel_source_sha1():
+        if e and e.get("kernel_source_sha1") == kernel_source_sha1() and e.get("N") == N:
             return e
     except Exception:
         pass
@@ -584,7 +584,7 @@ def run_ours(args):
     bytes_per_launch = N * N * (9 * 4 + 1.0)
     avg_ms = box_ms / max(1, nbox)
     achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
-    tr = ncu_traffic("k_box_tma<float>")
+    tr = ncu_traffic("k_box_tma<float>", N)
     line = {
         "metric": METRIC, "value": value, "unit": "V-cycles/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True, "scaling": "weak",
