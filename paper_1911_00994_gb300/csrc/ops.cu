@@ -967,8 +967,8 @@ template <typename T> __global__ void k_ghost_acc_apply(GhostList gh, int nrows,
 // after sweep s a row at link distance h is exact for s <= lambda - h, so the
 // owned rows end with exactly the iterate of the one-sweep-per-launch form, and
 // a link that leaves the closure (distance lambda) counts as zero.  Each row
-// repeats that form's arithmetic in the same order (no correction added in the
-// first sweep), so both give the same bits.  The owned rows' corrections go
+// repeats that form's expressions in the same order (no correction added in
+// the first sweep).  The owned rows' corrections go
 // where k_ghost_acc_apply reads them after lambda sweeps; no block writes x.
 template <typename T>
 __global__ void __launch_bounds__(GC_THREADS) k_ghost_fused(GhostList gh, int nrows, const T *x, const T *b, T dtau,
