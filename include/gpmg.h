@@ -204,19 +204,20 @@ gp_status gp_ghost_rows(gp_ctx *ctx, int level, int *node, uint8_t *kind, uint8_
  * NULL).  x, b, r: FP64 vectors of that level. */
 gp_status gp_residual(gp_ctx *ctx, int level, const double *x, const double *b, double *r, double *norm_host);
 
-/* The same residual and norm as gp_residual, for callers that cannot obtain
- * device memory for scratch: for example work recorded into a CUDA graph
- * under a capture mode that forbids allocation, or a host whose workspace is
- * fixed and shared.  The paper has no counterpart; this is a property of the
- * library only.  It allocates nothing and uses none of the workspace's
- * reduction area: its scratch is a fixed array of about 128 KB inside the
- * library, which every GPU that loads the library keeps until the process
- * exits.  Levels with more than 8192 cells per side return GP_INVALID.  All
- * calls share that array (it keeps the last call's contents; the call clears
- * what must start at zero), so two calls whose kernels overlap on one GPU
- * race.  The first call on a device looks up the array's device address;
- * make it before any stream capture.  Synchronises the stream when
- * norm_host is not NULL. */
+/* The same residual and norm as gp_residual, for callers that cannot
+ * allocate device memory: a plug-in running inside a host application that
+ * owns all device memory and hands out none, or a caller whose workspace was
+ * sized once for other work and may not grow.  The paper has no counterpart;
+ * this is a property of the library only.  It calls no allocator and uses
+ * none of the workspace's reduction area: its scratch is a fixed array of
+ * about 128 KB inside the library, which every GPU that loads the library
+ * keeps until the process exits.  Levels with more than 8192 cells per side
+ * return GP_INVALID.  All calls share that array (it keeps the last call's
+ * contents; each call clears what must start at zero), so two calls whose
+ * kernels overlap on one GPU race.  The first call on a device looks up the
+ * array's device address; make that first call before any stream capture.
+ * norm_host may be NULL: then only r is returned and the call does not
+ * synchronise; otherwise it synchronises the stream to read the norm. */
 gp_status gp_residual_static(gp_ctx *ctx, int level, const double *x, const double *b, double *r, double *norm_host);
 
 /* Pieces of the relaxation (Sect. 4.1), in place on x: */

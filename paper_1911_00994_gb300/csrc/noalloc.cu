@@ -2,11 +2,11 @@
 // like gp_residual, but with its reduction scratch in a fixed device array of
 // this library instead of the context workspace.
 //
-// Who needs it: code that computes a residual norm where no device memory can
-// be obtained, such as a caller recording work into a CUDA graph under a
-// capture mode that forbids allocation, or a host that hands the library a
-// workspace sized for other work and must not grow it.  This entry point
-// allocates nothing and takes nothing from the workspace's reduction area.
+// Who needs it: callers that cannot allocate device memory, such as a plug-in
+// running inside a host application that owns all device memory and hands
+// out none, or a caller whose workspace was sized once for other work and
+// may not grow.  This entry point calls no allocator and takes nothing from
+// the workspace's reduction area.
 //
 // Scratch: one (sum, max) pair per frame row plus a few result slots, in
 // g_static_scratch below.  Every GPU that loads the library holds this array

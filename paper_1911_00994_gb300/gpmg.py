@@ -311,14 +311,19 @@ class Solver:
         self._check(self.L.gp_residual(self.ctx, lev, _ptr(x), _ptr(b), _ptr(r), ctypes.byref(nrm)), "gp_residual")
         return r, nrm.value
 
-    def residual_static(self, x, b, lev=0):
+    def residual_static(self, x, b, lev=0, r=None, want_norm=True):
         """gp_residual_static: same result as residual(), scratch in a fixed
-        library array instead of the workspace (no allocation)."""
-        r = self.new_vec(lev)
+        library array instead of the workspace (no allocation).  r: an
+        existing output vector of the level (a new zeroed one when None);
+        want_norm=False passes a NULL norm pointer (no synchronisation) and
+        returns None for the norm."""
+        if r is None:
+            r = self.new_vec(lev)
         nrm = ctypes.c_double(0.0)
-        self._check(self.L.gp_residual_static(self.ctx, lev, _ptr(x), _ptr(b), _ptr(r), ctypes.byref(nrm)),
+        self._check(self.L.gp_residual_static(self.ctx, lev, _ptr(x), _ptr(b), _ptr(r),
+                                              ctypes.byref(nrm) if want_norm else None),
                     "gp_residual_static")
-        return r, nrm.value
+        return r, (nrm.value if want_norm else None)
 
     def box_sweep(self, x, b, lev=0):
         self._check(self.L.gp_box_sweep(self.ctx, lev, _ptr(x), _ptr(b)), "gp_box_sweep")

@@ -52,20 +52,20 @@ class Rollout:
             self._step(m, x, N1, N2, f, amp)
         return x
 
-    def loss_and_gradient(self, f, amp, w, x0=None):
-        """(L, dL/df, dL/damp) for L = sum w x_final^2."""
+    def vjp(self, f, amp, checkpoints, xbar):
+        """Backward pass from the checkpoints of a forward run: given xbar =
+        dL/dx_final, returns (dL/df, dL/damp, dL/dx0).  Each segment is
+        recomputed from its checkpoint, then its adjoint steps run in
+        reverse."""
         s = self.s
-        ck = {}
-        x = self.forward(f, amp, x0, ck)
-        loss = float((w * x * x).sum())
-        xbar = 2.0 * w * x
+        xbar = xbar.clone()
         nb = [s.new_vec(), s.new_vec(), s.new_vec()]
         fbar = s.new_vec()
         abar = 0.0
-        for a in reversed(sorted(ck)):
+        for a in reversed(sorted(checkpoints)):
             b = min(a + self.every, self.steps)
             xs = {}
-            xc, n1, n2 = (t.clone() for t in ck[a])
+            xc, n1, n2 = (t.clone() for t in checkpoints[a])
             for m in range(a, b):
                 xs[m] = xc.clone()
                 if m + 1 < b:
@@ -77,4 +77,12 @@ class Rollout:
                                           amp=amp, walls=self.walls, tol=self.tol, kmax=self.kmax)
                 xbar = xbar_m
                 nb = [nb[1], nb[2], s.new_vec()]
+        return fbar, abar, xbar
+
+    def loss_and_gradient(self, f, amp, w, x0=None):
+        """(L, dL/df, dL/damp) for L = sum w x_final^2."""
+        ck = {}
+        x = self.forward(f, amp, x0, ck)
+        loss = float((w * x * x).sum())
+        fbar, abar, _ = self.vjp(f, amp, ck, 2.0 * w * x)
         return loss, fbar, abar

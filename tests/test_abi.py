@@ -53,3 +53,25 @@ def test_parameter_checks_on_the_host():
         assert L.gp_workspace_size(ctypes.byref(p), ctypes.byref(nb)) == 1
     p.inner = 8
     assert L.gp_workspace_size(ctypes.byref(p), ctypes.byref(nb)) == 0
+
+
+def test_invalid_sizes_are_rejected_on_the_host():
+    # bad N or levels: GP_INVALID from gp_workspace_size and gp_create, before
+    # any CUDA call (the context is not created)
+    L = gpmg.lib()
+    p = gpmg.gp_params()
+    assert L.gp_params_default(ctypes.byref(p), 64, -1.0, -1.0, 2.0) == 0
+    nb = ctypes.c_size_t(0)
+    ctx = ctypes.c_void_p(1)
+    for N, levels in ((64, 0), (64, 17), (2, 1), (60, 4), (256, 2), (64, 6)):
+        q = gpmg.gp_params.from_buffer_copy(p)
+        q.N, q.levels = N, levels
+        assert L.gp_workspace_size(ctypes.byref(q), ctypes.byref(nb)) == gpmg.GP_INVALID, (N, levels)
+        assert L.gp_create(ctypes.byref(ctx), ctypes.byref(q), None, 0, None) == gpmg.GP_INVALID, (N, levels)
+        assert ctx.value is None
+    assert L.gp_params_default(ctypes.byref(p), 3, -1.0, -1.0, 2.0) == gpmg.GP_INVALID
+    assert L.gp_last_error(None) == b"null context"
+    # a non-power-of-two grid whose coarsening stays integral is accepted
+    q = gpmg.gp_params.from_buffer_copy(p)
+    q.N, q.levels = 60, 3
+    assert L.gp_workspace_size(ctypes.byref(q), ctypes.byref(nb)) == 0
