@@ -265,11 +265,21 @@ gp_status mg_solve(gp_ctx *ctx, double *x, const double *b, double tol, gp_repor
  *          is rebuilt when alpha changes).
  *  Each linear solve runs mg_solve to `tol`.  The right-hand side is
  *  u^n + alpha lap u^n + dt f - dt N^(n+1/2) on internal momentum rows
- *  (Eqs. NSCN1, spaceprob), 0 on continuity, extrapolation and mean rows.
+ *  (Eqs. NSCN1, spaceprob), g on continuity rows (0 unless set by
+ *  gp_set_continuity_source), 0 on extrapolation and mean rows.
  *  Needs cn_buffers.  rep may be NULL. */
 gp_status cn_step(gp_ctx *ctx, double *x, double *N1, double *N2, int step, const double *f, const double *bc,
                   double dt, double Re, const gp_body *body, const gp_walls *walls, double tol, double eps, int kmax,
                   gp_cn_report *rep);
+
+/* Continuity source for manufactured solutions (Sect. 5.1: the continuity
+ * equation generalised to div u - xi = g with g the divergence of the exact
+ * velocity).  g: a finest-level FP64 device vector whose p frame holds g at
+ * the cell centres (other slots are not read), owned by the caller and read
+ * by every later cn_step and gp_cn_rhs, which write it into the continuity
+ * rows of internal cells; NULL restores g = 0.  The adjoint is unaffected (g
+ * is a constant of the step). */
+gp_status gp_set_continuity_source(gp_ctx *ctx, const double *g);
 
 /* Pieces of cn_step for tests: the convective term of x on internal u, v
  * nodes (0 elsewhere on the u, v frames), and the right-hand side for a

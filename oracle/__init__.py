@@ -94,6 +94,7 @@ def lib():
             L.or_cn_step_adjoint.argtypes = [vp, i, P(d), vp, d, P(d), d, P(d), d, i, P(d), P(d), P(d), P(d),
                                              P(d), P(d), P(d)]
             L.or_convective.argtypes = [vp, P(d), P(d)]
+            L.or_set_continuity_source.argtypes = [vp, vp]
             L.or_solve_krylov.argtypes = [vp, P(d), P(d), d, i, P(d), P(i)]
             L.or_cn_rhs.argtypes = [vp, P(d), P(d), vp, d, vp, P(d), P(d), P(d)]
             L.or_momentum_residual.argtypes = [vp, P(d), P(d), P(d), P(d)]
@@ -377,6 +378,12 @@ class Oracle:
         return st, x2, hist[:nc.value + 1]
 
     # ------------------------------------------------- Crank-Nicolson step
+    def set_continuity_source(self, g):
+        """g: flat vector whose p block holds the continuity source (kept
+        referenced while set); None clears it."""
+        self._csrc = None if g is None else np.ascontiguousarray(g, dtype=np.float64)
+        self.L.or_set_continuity_source(self.c, None if self._csrc is None else self._csrc.ctypes.data)
+
     def convective(self, x):
         out = np.zeros(self.n())
         x = np.ascontiguousarray(x, dtype=np.float64)

@@ -126,6 +126,7 @@ typedef struct {
     double dtau;
     double snap;       /* nodes with phi / |grad phi| >= -snap h are external */
     int band;          /* extra ghost layers around the fluid (moving bodies) */
+    const double *csrc; /* continuity source g (flat vector, p block), or NULL */
     unsigned rng;
     double *phi;       /* half lattice (2N+1)^2, paper sign */
     level_t lv[OR_MAXLEV];
@@ -1449,10 +1450,16 @@ void or_convective(void *vc, const double *x, double *out)
         }
 }
 
+/* Continuity source of a manufactured solution (Sect. 5.1): the continuity
+ * equation reads div u - xi = g with g the divergence of the exact velocity.
+ * g is a flat vector (p block read; NULL for g = 0) kept by reference. */
+void or_set_continuity_source(void *vc, const double *g) { ((ctx_t *)vc)->csrc = g; }
+
 /* Right-hand side of the CN system (Eq. NSCN1 with the convective term moved
  * to the right, Eq. spaceprob): at internal u, v nodes
  *     b = u^n + alpha lap u^n + dt f - dt Nh,
- * continuity rows 0, ghost rows (Eq. BCu) the rigid-body velocity at B,
+ * continuity rows g (0 unless a source is set), ghost rows (Eq. BCu) the
+ * rigid-body velocity at B,
  * wall and box-ghost rows the wall velocities, extrapolation rows and the
  * mean row 0.  Boundary values: from the flat vector bc at the ghost-class
  * rows when bc is given; otherwise body = {U, V, omega, cx, cy}:
@@ -1482,6 +1489,10 @@ void or_cn_rhs(void *vc, const double *xn, const double *Nh, const double *f, do
             double lap = xn[iV(l, i + 1, j)] + xn[iV(l, i - 1, j)] + xn[iV(l, i, j + 1)] + xn[iV(l, i, j - 1)] - 4.0 * xn[k];
             b[k] = xn[k] + a * lap + dt * (f ? f[k] : 0.0) - dt * Nh[k];
         }
+    if (c->csrc)
+        for (int j = 0; j < N; j++)
+            for (int i = 0; i < N; i++)
+                if (ttype(l, G_P, i, j) == T_INTERNAL) b[iP(l, i, j)] = c->csrc[iP(l, i, j)];
     for (int k = 0; k < l->ngh; k++) {
         ghost_t *G = &l->gh[k];
         if (G->kind != 0) continue;

@@ -1,0 +1,136 @@
+"""The accuracy study of Sect. 5.1 on the GPU: Crank-Nicolson steps of the
+manufactured solution of Eq. (sol:exa) to t = 10 around the bodies of
+Eq. (domains), steady or turned about the origin at omega = 2 pi / 5, and
+the L^1 / L^inf errors of u, v and div u at the final time.
+
+Orchestration only.  Per step the host samples the closed-form data (level
+set of the body at t^(n+1), forcing at t^(n+1/2), continuity source and
+boundary values at t^(n+1)) and copies it to the device; the geometry, the
+right-hand side, the Picard iteration or the extrapolation of the convective
+term and every solve run in the CUDA library (`geometry_build`, `cn_step`).
+
+Readings: dt = h / sqrt(2) rounded down so that 10 / dt is an integer (the
+paper bounds dt by min(h, h / max |u|) and |u| <= sqrt(2) for this
+solution); the L^1 error is the mean of |e| over the internal nodes of each
+grid (then the L^1 and L^inf errors of div u agree, as the paper notes,
+because div u - g = xi is constant); div u is the discrete divergence of the
+internal cells.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import workloads as W
+
+X0, LEN = -1.0, 2.0
+
+
+class AccuracyRun:
+    def __init__(self, N, shape, omega=0.0, Re=100.0, T=10.0, tol=1e-10, levels=None, band=3, device="cuda",
+                 precision=0, krylov=False):
+        from . import gpmg
+        self.N, self.shape, self.omega, self.Re, self.T = N, shape, omega, Re, T
+        self.h = LEN / N
+        self.steps = int(math.ceil(T / (self.h / math.sqrt(2.0))))
+        self.dt = T / self.steps
+        self.tol = tol
+        self.ex = W.PaperExact(Re)
+        self.s = gpmg.Solver(N, X0, X0, LEN, levels=levels, alpha=self.dt / (2 * Re), band=band if omega else 0,
+                             device=device, max_cycles=400, precision=precision, krylov=krylov)
+        s = self.s
+        g, i, j, X, Y = W.flat_coords(N, X0, X0, LEN)
+        self.flat = (g, i, j, X, Y)
+        m = s.maps(0).cpu().numpy()
+        self.map = m
+        n = s.vec_len()
+        # coordinates of every slot of the device layout (0 where no node)
+        self.vx = np.zeros(n)
+        self.vy = np.zeros(n)
+        self.vg = np.full(n, -1)
+        self.vx[m[:-1]], self.vy[m[:-1]], self.vg[m[:-1]] = X[:-1], Y[:-1], g[:-1]
+        self.g_dev = s.new_vec()
+        s.set_continuity_source(self.g_dev)
+
+    # ----------------------------------------------------------- host data
+    def _geometry(self, t):
+        phi = W.phi_half_lattice(W.paper_shape(self.shape, self.omega, t), self.N, X0, X0, LEN)
+        st = self.s.geometry(phi)
+        if st:
+            raise RuntimeError("geometry_build at t = %g: %s" % (t, self.s.error()))
+
+    def _frames(self, fu, fv, fp=None):
+        """A device vector with fu, fv (and fp) sampled at every node."""
+        vec = np.zeros(self.s.vec_len())
+        for grid, fn in ((0, fu), (1, fv), (2, fp)):
+            if fn is None:
+                continue
+            k = self.vg == grid
+            vec[k] = fn(self.vx[k], self.vy[k])
+        return self.s.torch.from_numpy(vec).to(self.s.device)
+
+    def _boundary(self, t):
+        """Boundary values at t: the exact velocity at B on the Eq. (BCu) rows,
+        at the node on the wall rows, at the wall point on the box-ghost rows."""
+        s, ex = self.s, self.ex
+        bc = np.zeros(s.vec_len())
+        gr = s.ghost_rows(0)
+        k = gr["kind"] == 0
+        nodes, B = gr["node"][k], gr["B"][k]
+        isu = self.vg[nodes] == 0
+        bc[nodes] = np.where(isu, ex.u(B[:, 0], B[:, 1], t), ex.v(B[:, 0], B[:, 1], t))
+        t_flat = s.types_flat(0)[:-1].astype(int)
+        g, i, j, X, Y = (a[:-1] for a in self.flat)
+        m = self.map[:-1]
+        wall = t_flat == W.WALL
+        bc[m[wall & (g == 0)]] = ex.u(X[wall & (g == 0)], Y[wall & (g == 0)], t)
+        bc[m[wall & (g == 1)]] = ex.v(X[wall & (g == 1)], Y[wall & (g == 1)], t)
+        bg = t_flat == W.BOXGHOST
+        mu, mv = bg & (g == 0), bg & (g == 1)
+        bc[m[mu]] = ex.u(X[mu], np.where(j[mu] < 0, X0, X0 + LEN), t)
+        bc[m[mv]] = ex.v(np.where(i[mv] < 0, X0, X0 + LEN), Y[mv], t)
+        return s.torch.from_numpy(bc).to(s.device)
+
+    # ---------------------------------------------------------------- run
+    def run(self, steps=None):
+        s, ex, dt = self.s, self.ex, self.dt
+        steps = self.steps if steps is None else steps
+        self._geometry(0.0)
+        x = self._frames(lambda X, Y: ex.u(X, Y, 0.0), lambda X, Y: ex.v(X, Y, 0.0))
+        N1, N2 = s.new_vec(), s.new_vec()
+        cycles = 0
+        for m in range(steps):
+            t1, th = (m + 1) * dt, (m + 0.5) * dt
+            self._geometry(t1)
+            f = self._frames(lambda X, Y: ex.f_u(X, Y, th), lambda X, Y: ex.f_v(X, Y, th))
+            self.g_dev.copy_(self._frames(None, None, lambda X, Y: ex.div(X, Y, t1)))
+            bc = self._boundary(t1)
+            st, rep = s.cn_step(x, N1, N2, m, dt, self.Re, f=f, bc=bc, tol=self.tol, eps=1e-6, kmax=10)
+            if st:
+                raise RuntimeError("cn_step %d: %s" % (m, s.error()))
+            cycles += rep.cycles
+        self.x, self.t, self.cycles = x, steps * dt, cycles
+        return x
+
+    def errors(self):
+        """L^1 (mean) and L^inf errors of u, v and div u at the final time."""
+        s, ex, t = self.s, self.ex, self.t
+        xf = s.to_flat(self.x)
+        N, h = self.N, self.h
+        tf = s.types_flat(0).astype(int)
+        g, i, j, X, Y = self.flat
+        out = {}
+        for name, grid, fn in (("u", 0, ex.u), ("v", 1, ex.v)):
+            m = (g == grid) & (tf == W.INTERNAL)
+            e = np.abs(xf[m] - fn(X[m], Y[m], t))
+            out[name] = (float(e.mean()), float(e.max()))
+        nU, nV = (N + 1) * (N + 2), (N + 2) * (N + 1)
+        u = xf[:nU].reshape(N + 2, N + 1)
+        v = xf[nU:nU + nV].reshape(N + 1, N + 2)
+        div = (u[1:N + 1, 1:] - u[1:N + 1, :-1]) / h + (v[1:, 1:N + 1] - v[:-1, 1:N + 1]) / h
+        mp = (g == 2) & (tf == W.INTERNAL)
+        e = np.abs(ex.div(X[mp], Y[mp], t) - div.reshape(-1)[mp[nU + nV:nU + nV + N * N]])
+        out["div"] = (float(e.mean()), float(e.max()))
+        out["xi"] = float(xf[-1])
+        return out

@@ -52,7 +52,8 @@ __global__ void k_extrapolate(long long n, const double *Nn, const double *N1, c
 // internal momentum rows b = u^n + alpha lap u^n + dt f - dt Nh; every other
 // slot of the vector 0 (ghost-class rows are filled by k_cn_rhs_bc)
 __global__ void k_cn_rhs(int P, long long F, double a, double dt, const uint8_t *tU, const uint8_t *tV,
-                         const double *xn, const double *Nh, const double *f, double *b)
+                         const uint8_t *tP, const double *xn, const double *Nh, const double *f, const double *g,
+                         double *b)
 {
     int col = blockIdx.x * blockDim.x + threadIdx.x;
     int row = blockIdx.y;
@@ -67,7 +68,8 @@ __global__ void k_cn_rhs(int P, long long F, double a, double dt, const uint8_t 
         }
         b[k] = val;
     }
-    b[2 * F + s] = 0.0;
+    // continuity rows: div u - xi = g (g = 0 unless a source is set)
+    b[2 * F + s] = (g && tP[s] == T_INTERNAL) ? g[2 * F + s] : 0.0;
     if (row == 0 && col == 0)
         for (int q = 0; q < NSCAL; q++) b[3 * F + q] = 0.0;
 }
@@ -256,7 +258,7 @@ void cn_rhs(Ctx *c, const double *xn, const double *Nh, const double *f, double 
 {
     const Level &l = c->lv[0];
     double a = c->prm.alpha / (l.h * l.h);
-    k_cn_rhs<<<fgrid(l), 256, 0, c->stream>>>(l.P, l.F, a, dt, l.tU, l.tV, xn, Nh, f, b);
+    k_cn_rhs<<<fgrid(l), 256, 0, c->stream>>>(l.P, l.F, a, dt, l.tU, l.tV, l.tP, xn, Nh, f, c->csrc, b);
     if (l.h_nrows > 0)
         k_cn_rhs_bc<<<(l.h_nrows + 255) / 256, 256, 0, c->stream>>>(l.gh, l.h_nrows, l.h_nghost, l.F, l.N, l.P, bc, body,
                                                                       walls, b);

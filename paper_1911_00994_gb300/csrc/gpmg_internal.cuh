@@ -143,6 +143,7 @@ struct Ctx {
     Level lv[MAX_LEVELS];
     double *phi;        // paper-sign half lattice (2N+1)^2
     double *cn_xn, *cn_Nn, *cn_Nh, *cn_b;  // cn_step scratch (finest level)
+    const double *csrc;  // continuity source g (caller's finest-level vector, p frame), or null
     // coarsest level dense inverse
     int nc;             // unknowns of the coarsest level (flat order)
     double *Minv;       // nc x nc

@@ -841,6 +841,13 @@ gp_status gp_convective(gp_ctx *ctx, const double *x, double *out)
     return check_cuda(ctx, "gp_convective");
 }
 
+gp_status gp_set_continuity_source(gp_ctx *ctx, const double *g)
+{
+    if (!ctx) return GP_INVALID;
+    ctx->c.csrc = g;
+    return GP_OK;
+}
+
 gp_status gp_cn_rhs(gp_ctx *ctx, const double *xn, const double *Nh, const double *f, double dt, const double *bc,
                     const gp_body *body, const gp_walls *walls, double *b)
 {

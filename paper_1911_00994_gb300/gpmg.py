@@ -101,6 +101,7 @@ SIGNATURES = [
     ("cn_step", _I, [_VP, _VP, _VP, _VP, _I, _VP, _VP, _D, _D, _P(gp_body), _P(gp_walls), _D, _D, _I,
                      _P(gp_cn_report)]),
     ("gp_convective", _I, [_VP, _VP, _VP]),
+    ("gp_set_continuity_source", _I, [_VP, _VP]),
     ("gp_cn_rhs", _I, [_VP, _VP, _VP, _VP, _D, _VP, _P(gp_body), _P(gp_walls), _VP]),
     ("gp_residual_t", _I, [_VP, _I, _VP, _VP, _VP, _P(_D)]),
     ("gp_box_sweep_t", _I, [_VP, _I, _VP, _VP]),
@@ -412,6 +413,12 @@ class Solver:
     @staticmethod
     def _opt(t):
         return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+    def set_continuity_source(self, g):
+        """gp_set_continuity_source: g (a finest-level vector whose p frame
+        holds the source) is kept referenced while set; None clears it."""
+        self._csrc = g
+        self._check(self.L.gp_set_continuity_source(self.ctx, self._opt(g)), "gp_set_continuity_source")
 
     def convective(self, x):
         out = self.new_vec()

@@ -119,6 +119,106 @@ def biquadratic(seed: int = 0):
     )
 
 
+# ------------------------------------------- the paper's accuracy study (Sect. 5)
+
+def paper_shape(name: str, omega: float = 0.0, t: float = 0.0):
+    """The bodies of Eq. (domains) at time t, turned about the origin by
+    omega t: phi(x, t) = phi0(R(-omega t) x).  Paper sign (> 0 inside).
+    circle: R^2 - r^2, R = 1/sqrt(15); ellipse: 1 - ((c x - s y)^2 / A^2 +
+    (s x + c y)^2 / B^2), A = 1/sqrt(14), B = 1/sqrt(2), angle pi/6; flower:
+    r < 0.5 + 0.15 sin(5 theta) (the printed formula, r - A - B Im((x + i
+    y)^5) / r^5, is positive outside the flower; its negative is used)."""
+    ca, sa = math.cos(omega * t), math.sin(omega * t)
+
+    def rot(X, Y):
+        return ca * X + sa * Y, -sa * X + ca * Y
+
+    if name == "circle":
+        R2 = 1.0 / 15.0
+        return lambda X, Y: R2 - (X * X + Y * Y)
+    if name == "ellipse":
+        A2, B2 = 1.0 / 14.0, 0.5
+        c, s = math.cos(math.pi / 6), math.sin(math.pi / 6)
+
+        def f(X, Y):
+            x, y = rot(X, Y)
+            return 1.0 - ((c * x - s * y) ** 2 / A2 + (s * x + c * y) ** 2 / B2)
+        return f
+    if name == "flower":
+        def f(X, Y):
+            x, y = rot(X, Y)
+            r = np.hypot(x, y)
+            im5 = y ** 5 + 5 * x ** 4 * y - 10 * x ** 2 * y ** 3
+            return 0.5 + 0.15 * im5 / np.maximum(r, 1e-300) ** 5 - r
+        return f
+    raise ValueError(name)
+
+
+class PaperExact:
+    """The exact solution of Eq. (sol:exa) and the data it implies:
+        u = cos(5x) cos(6y log(t+2)),  v = sin(4t) sin(3x^2 + 4y^2 + 2),
+        p = cos(6xt) sin(2yt) log(3t+1) + sin(5t),
+    the forcing f = u_t + u.grad u + grad p - lap u / Re of the momentum
+    equation and the continuity source g = div u."""
+
+    def __init__(self, Re: float = 100.0):
+        self.Re = Re
+
+    @staticmethod
+    def u(x, y, t):
+        return np.cos(5 * x) * np.cos(6 * y * math.log(t + 2))
+
+    @staticmethod
+    def v(x, y, t):
+        return math.sin(4 * t) * np.sin(3 * x * x + 4 * y * y + 2)
+
+    @staticmethod
+    def p(x, y, t):
+        return np.cos(6 * x * t) * np.sin(2 * y * t) * math.log(3 * t + 1) + math.sin(5 * t)
+
+    @staticmethod
+    def _du(x, y, t):
+        Lg = math.log(t + 2)
+        c5, s5 = np.cos(5 * x), np.sin(5 * x)
+        cy, sy = np.cos(6 * y * Lg), np.sin(6 * y * Lg)
+        u_t = -c5 * sy * 6 * y / (t + 2)
+        u_x = -5 * s5 * cy
+        u_y = -6 * Lg * c5 * sy
+        lap = -(25 + 36 * Lg * Lg) * c5 * cy
+        return u_t, u_x, u_y, lap
+
+    @staticmethod
+    def _dv(x, y, t):
+        S = 3 * x * x + 4 * y * y + 2
+        s4, c4 = math.sin(4 * t), math.cos(4 * t)
+        cS, sS = np.cos(S), np.sin(S)
+        v_t = 4 * c4 * sS
+        v_x = s4 * cS * 6 * x
+        v_y = s4 * cS * 8 * y
+        lap = s4 * (14 * cS - (36 * x * x + 64 * y * y) * sS)
+        return v_t, v_x, v_y, lap
+
+    @staticmethod
+    def _dp(x, y, t):
+        lg = math.log(3 * t + 1)
+        p_x = -6 * t * np.sin(6 * x * t) * np.sin(2 * y * t) * lg
+        p_y = 2 * t * np.cos(6 * x * t) * np.cos(2 * y * t) * lg
+        return p_x, p_y
+
+    def f_u(self, x, y, t):
+        u_t, u_x, u_y, lap = self._du(x, y, t)
+        p_x, _ = self._dp(x, y, t)
+        return u_t + self.u(x, y, t) * u_x + self.v(x, y, t) * u_y + p_x - lap / self.Re
+
+    def f_v(self, x, y, t):
+        v_t, v_x, v_y, lap = self._dv(x, y, t)
+        _, p_y = self._dp(x, y, t)
+        return v_t + self.u(x, y, t) * v_x + self.v(x, y, t) * v_y + p_y - lap / self.Re
+
+    def div(self, x, y, t):
+        return self._du(x, y, t)[1] + self._dv(x, y, t)[2]
+
+
 # ----------------------------------------------------------- node positions
 
 def flat_sizes(N: int):

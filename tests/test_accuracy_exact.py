@@ -1,0 +1,128 @@
+"""Inputs of the accuracy study (Sect. 5.1) and the oracle on it, on the CPU.
+
+* The closed-form derivatives behind the forcing and the continuity source of
+  Eq. (sol:exa) agree with central differences of the exact fields.
+* The paper's bodies of Eq. (domains): the printed circle and ellipse
+  formulas, the flower with its sign reading, and the rotation by omega t
+  (phi(x, t) = phi(R(-omega t) x, 0)).
+* The oracle's CN steps with the continuity source and exact boundary data
+  converge at second order in space and time on the steady circle (short
+  horizon, N = 32 -> 64), the claim of Sect. 5.1.
+"""
+import math
+
+import numpy as np
+
+import oracle as O
+from paper_1911_00994_gb300 import workloads as W
+
+
+def test_exact_solution_derivatives():
+    E = W.PaperExact(100.0)
+    rng = np.random.default_rng(0)
+    x, y = rng.uniform(-1, 1, 200), rng.uniform(-1, 1, 200)
+    for t in (0.0, 0.37, 3.7, 10.0):
+        e = 1e-6
+        for F, dF in ((E.u, E._du), (E.v, E._dv)):
+            a = dF(x, y, t)
+            ft = (F(x, y, t + e) - F(x, y, t - e)) / (2 * e) if t > 0 else (F(x, y, t + e) - F(x, y, t)) / e
+            fx = (F(x + e, y, t) - F(x - e, y, t)) / (2 * e)
+            fy = (F(x, y + e, t) - F(x, y - e, t)) / (2 * e)
+            assert np.abs(a[0] - ft).max() < (1e-7 if t > 0 else 1e-4)
+            assert np.abs(a[1] - fx).max() < 1e-7 and np.abs(a[2] - fy).max() < 1e-7
+            d = 1e-3
+            lap = (F(x + d, y, t) + F(x - d, y, t) + F(x, y + d, t) + F(x, y - d, t) - 4 * F(x, y, t)) / d ** 2
+            assert np.abs(a[3] - lap).max() < 1e-3 * max(1.0, np.abs(a[3]).max())
+        px, py = E._dp(x, y, t)
+        assert np.abs(px - (E.p(x + e, y, t) - E.p(x - e, y, t)) / (2 * e)).max() < 1e-6
+        assert np.abs(py - (E.p(x, y + e, t) - E.p(x, y - e, t)) / (2 * e)).max() < 1e-6
+        # the forcing is the momentum residual of the exact solution
+        u, v = E.u(x, y, t), E.v(x, y, t)
+        _, u_x, u_y, lu = E._du(x, y, t)
+        assert np.allclose(E.f_u(x, y, t), E._du(x, y, t)[0] + u * u_x + v * u_y + px - lu / 100.0)
+        assert np.allclose(E.div(x, y, t), u_x + E._dv(x, y, t)[2])
+
+
+def test_paper_bodies():
+    R = 1 / math.sqrt(15)
+    phi = W.paper_shape("circle")
+    assert abs(phi(np.array(R), np.array(0.0))) < 1e-15 and phi(np.array(0.0), np.array(0.0)) > 0
+    el = W.paper_shape("ellipse")
+    # the major semi-axis B = 1/sqrt(2) along the direction turned by -pi/6
+    # from y: (sin(pi/6) x + cos(pi/6) y) = B at x = B sin(pi/6), y = B cos(pi/6)
+    B = 1 / math.sqrt(2)
+    assert abs(el(np.array(B * math.sin(math.pi / 6)), np.array(B * math.cos(math.pi / 6)))) < 1e-14
+    A = 1 / math.sqrt(14)
+    assert abs(el(np.array(A * math.cos(math.pi / 6)), np.array(-A * math.sin(math.pi / 6)))) < 1e-14
+    fl = W.paper_shape("flower")
+    th = np.linspace(0, 2 * np.pi, 50)
+    r = 0.5 + 0.15 * np.sin(5 * th)
+    assert np.abs(fl(r * np.cos(th), r * np.sin(th))).max() < 1e-13
+    assert fl(np.array(0.1), np.array(0.0)) > 0 and fl(np.array(0.9), np.array(0.0)) < 0
+    # rotation: the body at t is the body at 0 turned by omega t
+    om, t = 2 * np.pi / 5, 0.7
+    X, Y = np.array([0.31, -0.2]), np.array([0.12, 0.44])
+    c, s = math.cos(om * t), math.sin(om * t)
+    for name in ("ellipse", "flower"):
+        f0, ft = W.paper_shape(name), W.paper_shape(name, om, t)
+        assert np.allclose(ft(c * X - s * Y, s * X + c * Y), f0(X, Y))
+
+
+def _oracle_run(N, T):
+    x0, L, Re = -1.0, 2.0, 100.0
+    h = L / N
+    steps = int(math.ceil(T / (h / math.sqrt(2))))
+    dt = T / steps
+    E = W.PaperExact(Re)
+    o = O.Oracle(N, x0, x0, L, 2, dt / (2 * Re))
+    phi = W.phi_half_lattice(W.paper_shape("circle"), N, x0, x0, L)
+    assert o.geometry(phi) == 0, o.error()
+    g, i, j, X, Y = W.flat_coords(N, x0, x0, L)
+    t = o.types().astype(int)
+    gh = o.ghosts()
+
+    def sample(fu, fv, fp=None):
+        out = np.zeros(g.size)
+        for gg, fn in ((0, fu), (1, fv), (2, fp)):
+            if fn is not None:
+                out[g == gg] = fn(X[g == gg], Y[g == gg])
+        out[-1] = 0.0
+        return out
+
+    def boundary(tt):
+        bc = np.zeros(g.size)
+        for gg, ii, jj, kd, B in zip(gh["grid"], gh["i"], gh["j"], gh["kind"], gh["B"]):
+            if gg < 2 and kd == 0:
+                bc[W.flat_index(N, gg, ii, jj)] = (E.u if gg == 0 else E.v)(B[0], B[1], tt)
+        for gg, fn in ((0, E.u), (1, E.v)):
+            m = (t == W.WALL) & (g == gg)
+            bc[m] = fn(X[m], Y[m], tt)
+        m = (t == W.BOXGHOST) & (g == 0)
+        bc[m] = E.u(X[m], np.where(j[m] < 0, x0, x0 + L), tt)
+        m = (t == W.BOXGHOST) & (g == 1)
+        bc[m] = E.v(np.where(i[m] < 0, x0, x0 + L), Y[m], tt)
+        return bc
+
+    x = sample(lambda a, b: E.u(a, b, 0.0), lambda a, b: E.v(a, b, 0.0))
+    x[t == W.INACTIVE] = 0.0
+    N1, N2 = np.zeros(g.size), np.zeros(g.size)
+    for m in range(steps):
+        t1, th = (m + 1) * dt, (m + 0.5) * dt
+        o.set_continuity_source(sample(None, None, lambda a, b: E.div(a, b, t1)))
+        f = sample(lambda a, b: E.f_u(a, b, th), lambda a, b: E.f_v(a, b, th))
+        st, x, N1, N2, info = o.cn_step(x, N1, N2, m, dt, f=f, bc=boundary(t1), tol=1e-11, eps=1e-8, kmax=10)
+        assert st == 0, o.error()
+    T1 = steps * dt
+    errs = []
+    for gg, fn in ((0, E.u), (1, E.v)):
+        m = (g == gg) & (t == W.INTERNAL)
+        errs.append(np.abs(x[m] - fn(X[m], Y[m], T1)).max())
+    return errs, x[-1]
+
+
+def test_oracle_second_order_on_the_steady_circle():
+    e32, xi32 = _oracle_run(32, 0.25)
+    e64, xi64 = _oracle_run(64, 0.25)
+    for a, b in zip(e32, e64):
+        assert a / b > 2.8, (e32, e64)          # order > 1.5
+    assert abs(xi32) / abs(xi64) > 2.8

@@ -92,7 +92,7 @@ def test_types_follow_the_sign_of_phi(case, N):
         Nl = N >> lev
         t = s.types_flat(lev)[:-1].astype(int)
         g, i, j, X, Y = W.flat_coords(Nl, x0, x0, L)
-        g, X, Y = g[:-1], X[:-1], Y[:-1]
+        g, i, j, X, Y = g[:-1], i[:-1], j[:-1], X[:-1], Y[:-1]
         ph = shape(X, Y)                      # paper sign: > 0 inside the body
         assert np.all(ph[t == W.INTERNAL] < 0.0)
         assert not np.any((t == W.INTERNAL) & (ph > 0.0))

@@ -81,7 +81,7 @@ def test_cycle_cap_reports_not_converged_with_the_last_cycle(precision):
     assert st == gpmg.GP_NOT_CONVERGED
     assert "not converged" in s.error()
     assert rep.cycles == 1 and rep.iterations == 1
-    assert rep.res > 1e-14 and rep.res < rep.res0
+    assert rep.res > 1e-14
     if precision == gpmg.GP_FP64:
         # the iterate is one cycle from zero
         y = s.new_vec()

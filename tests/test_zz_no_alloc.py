@@ -47,8 +47,11 @@ def test_static_scratch_residual_matches_workspace_residual_and_oracle():
         free0 = torch.cuda.mem_get_info()[0]
         r_st, n_st = s.residual_static(x, b, r=r_out)
         torch.cuda.synchronize()
-        assert torch.cuda.memory_allocated() == mem0, call
+        # nothing allocated: torch's allocator holds no more memory and the
+        # device's free memory is unchanged (a cudaMalloc would lower it)
+        assert torch.cuda.memory_allocated() <= mem0, call
         assert torch.cuda.mem_get_info()[0] == free0, call
+        assert r_st is r_out
         a, c = r_st.cpu().numpy(), r_ws.cpu().numpy()
         # every slot of the three frames and the mean row written (the 31
         # trailing scalar slots are padding), equal to the workspace residual
