@@ -247,6 +247,58 @@ def moving_ellipse(dev, stream, steps=20, warm=4, N=1024):
     return out
 
 
+def cavity_cn_steps(dev, stream, N=4096, warm=10, steps=5):
+    """Crank-Nicolson steps of the lid-driven cavity with the five-petal
+    flower (the headline system's problem) at N^2, Re = 1000, dt = h, from
+    rest: `warm` untimed steps (steps 0 and 1 by the mid-point Picard
+    iteration, later ones extrapolated), then `steps` timed steps, each
+    `cn_step` warm-started from the previous state with the extrapolated
+    convective term, solved to ||r||_inf <= 1e-10.  FP64 and mixed.  The
+    right-hand side work of a step (convective term and Eq. NSCN1's
+    right-hand side, the same kernels cn_step launches) is timed apart on
+    the same stream; the rest of the step is the solve."""
+    import torch
+    from paper_1911_00994_gb300 import gpmg
+    Re, h = 1000.0, 1.0 / N
+    dt = h
+    out = {"N": N, "Re": Re, "dt": "h", "warm_steps": warm, "timed_steps": steps, "tol": TOL,
+           "solver": "V(2,1) cycles"}
+    for name, prec in (("mixed", gpmg.GP_MIXED), ("fp64", gpmg.GP_FP64)):
+        s, _ = build_case(N, prec, dev, stream)
+        walls = (0.0, 1.0, 0.0, 0.0)
+        x, N1, N2 = s.new_vec(), s.new_vec(), s.new_vec()
+        for m in range(warm):
+            st, rep = s.cn_step(x, N1, N2, m, dt, Re, walls=walls, tol=TOL, eps=1e-6, kmax=10)
+            if st:
+                raise RuntimeError("cavity cn_step %d: %s" % (m, s.error()))
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        cyc = 0
+        for m in range(warm, warm + steps):
+            st, rep = s.cn_step(x, N1, N2, m, dt, Re, walls=walls, tol=TOL, eps=1e-6, kmax=10)
+            if st:
+                raise RuntimeError("cavity cn_step %d: %s" % (m, s.error()))
+            cyc += rep.cycles
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / steps
+        # the right-hand side work of one extrapolated step, on its own
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(steps):
+            Nn = s.convective(x)
+            b = s.cn_rhs(x, Nn, dt, walls=walls)
+        f1.record(stream)
+        torch.cuda.synchronize(dev)
+        rhs_ms = f0.elapsed_time(f1) / steps
+        out[name] = {"cn_step_ms": ms, "rhs_ms": rhs_ms, "solve_ms": ms - rhs_ms, "cycles_per_step": cyc / steps,
+                     "cycles_per_s": cyc / steps / (ms / 1e3)}
+        del s, x, N1, N2
+        torch.cuda.empty_cache()
+    return out
+
+
 def largest_solve(dev, stream, N=8192, steps=2):
     """The largest single solve: the seven-petal flower
     r = 0.5 + 0.1 sin(7 theta) on [-1, 1]^2 at 8192^2 (201 M unknowns),
@@ -570,6 +622,7 @@ def run_ours(args):
     adj = adjoint_rollout(dev, stream) if not args.no_adjoint else None
     mov = moving_ellipse(dev, stream) if not args.no_moving else None
     big = largest_solve(dev, stream) if not args.no_large else None
+    cav = cavity_cn_steps(dev, stream, N=N) if not args.no_cavity else None
 
     if rank != 0:
         if dist:
@@ -607,6 +660,7 @@ def run_ours(args):
         "adjoint_rollout_orbiting_circle_512": adj,
         "moving_ellipse_1024": mov,
         "largest_solve_flower7_8192": big,
+        "cavity_cn_steps": cav,
         "roofline": {"kernel": "k_box_tma<float> (finest-level full-box sweep, five colours in one pass)", "bound": "hbm",
                      "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "peak_source": src, "avg_launch_ms": avg_ms, "launches": nbox,
@@ -623,9 +677,9 @@ def run_ours(args):
     return line
 
 
-def cpu_baseline(N):
-    """The oracle, as it stands, timed on the host: one V-cycle of the same
-    system (geometry built outside the timed region)."""
+def _oracle_case(N, threads=1):
+    """The oracle on the benchmark's system (geometry built, lid right-hand
+    side), with `threads` host threads (the OpenMP build when > 1)."""
     import numpy as np
 
     import oracle as O
@@ -634,46 +688,56 @@ def cpu_baseline(N):
     lev = 1
     while (N >> lev) >= 16:
         lev += 1
-    o = O.Oracle(N, 0.0, 0.0, 1.0, lev, h / 2000.0)
+    o = O.Oracle(N, 0.0, 0.0, 1.0, lev, h / 2000.0, threads=threads)
     st = o.geometry(W.phi_half_lattice(W.flower(0.2, 0.05, 5, 0.5, 0.5), N, 0.0, 0.0, 1.0))
     if st:
-        return {"value": None, "error": o.error()}
+        return o, None
     b = np.zeros(o.n())
     g, i, j, X, Y = W.flat_coords(N, 0.0, 0.0, 1.0)
     t = o.types()
     b[(g == 0) & (j == N) & (t == W.BOXGHOST)] = 1.0
-    x = np.zeros_like(b)
-    t0 = time.perf_counter()
-    st, x = o.cycle(x, b)
-    dt = time.perf_counter() - t0
-    return {"value": 1.0 / dt, "unit": "V-cycles/s", "cores": 1, "kind": "oracle",
-            "sample": "one V(2,1) cycle of the %dx%d system from zero (FP64, single thread; geometry excluded)" % (N, N),
-            "seconds": dt}
+    return o, b
+
+
+def cpu_baseline(N):
+    """The oracle, as it stands, timed on the host: one V-cycle of the same
+    system (geometry built outside the timed region), on every host core (the
+    OpenMP build: boxes of one colour and row-wise loops in parallel, same
+    iterate as one thread), and on one thread."""
+    import numpy as np
+    cores = os.cpu_count() or 1
+    out = None
+    for threads in ((cores, 1) if cores > 1 else (1,)):
+        o, b = _oracle_case(N, threads)
+        if b is None:
+            return {"value": None, "error": o.error()}
+        x = np.zeros_like(b)
+        t0 = time.perf_counter()
+        st, x = o.cycle(x, b)
+        dt = time.perf_counter() - t0
+        entry = {"value": 1.0 / dt, "unit": "V-cycles/s", "cores": o.threads, "kind": "oracle",
+                 "sample": "one V(2,1) cycle of the %dx%d system from zero (FP64, %d thread%s; geometry excluded)"
+                           % (N, N, o.threads, "s" if o.threads > 1 else ""),
+                 "seconds": dt}
+        if out is None:
+            out = entry
+        else:
+            out["single_thread"] = entry
+    return out
 
 
 def run_reference(args):
-    """--impl reference: the CPU oracle on the same system, one V-cycle per step."""
+    """--impl reference: the CPU oracle on the same system, one V-cycle per
+    step, on every host core (the OpenMP build)."""
     import numpy as np
-
-    import oracle as O
-    from paper_1911_00994_gb300 import workloads as W
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return None
     N = args.N
-    h = 1.0 / N
-    lev = 1
-    while (N >> lev) >= 16:
-        lev += 1
-    o = O.Oracle(N, 0.0, 0.0, 1.0, lev, h / 2000.0)
-    st = o.geometry(W.phi_half_lattice(W.flower(0.2, 0.05, 5, 0.5, 0.5), N, 0.0, 0.0, 1.0))
-    if st:
+    o, b = _oracle_case(N, os.cpu_count() or 1)
+    if b is None:
         print(json.dumps({"impl": "reference", "unavailable": "oracle geometry failed: " + o.error()}))
         return None
-    b = np.zeros(o.n())
-    g, i, j, X, Y = W.flat_coords(N, 0.0, 0.0, 1.0)
-    t = o.types()
-    b[(g == 0) & (j == N) & (t == W.BOXGHOST)] = 1.0
     x = np.zeros_like(b)
     for _ in range(args.warmup):
         st, x = o.cycle(x, b)
@@ -686,8 +750,9 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload(N),
-            "cpu_baseline": {"value": value, "unit": "V-cycles/s", "cores": 1, "kind": "oracle",
-                             "sample": "one V(2,1) cycle per step of the %dx%d system (FP64, single thread)" % (N, N)},
+            "cpu_baseline": {"value": value, "unit": "V-cycles/s", "cores": o.threads, "kind": "oracle",
+                             "sample": "one V(2,1) cycle per step of the %dx%d system (FP64, %d host threads)"
+                                       % (N, N, o.threads)},
             "e2e": {"value": value, "unit": "V-cycles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return line
@@ -705,6 +770,7 @@ def main():
     ap.add_argument("--no-moving", action="store_true")
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--no-wcycle", action="store_true")
+    ap.add_argument("--no-cavity", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         args.steps = 2 if args.steps is None else args.steps

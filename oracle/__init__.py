@@ -25,28 +25,33 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "gpmg_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
 _lock = threading.Lock()
 _lib = None
+_lib_omp = None
 
 INACTIVE, INTERNAL, GHOST, WALL, BOXGHOST = 0, 1, 2, 3, 4
 OK, INVALID, GEOMETRY, SINGULAR, NOT_CONVERGED, DIVERGED = range(6)
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle into oracle/liboracle.so (gcc, -ffp-contract=off)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + ".%d.tmp" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
-                               "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+def build(force: bool = False, omp: bool = False) -> str:
+    """Compile the oracle into oracle/liboracle.so (gcc, -ffp-contract=off);
+    omp=True: the OpenMP build liboracle_omp.so (same source, same iterates;
+    used only for the multi-core CPU baseline)."""
+    out = _LIB_OMP if omp else _LIB
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        tmp = out + ".%d.tmp" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared"] +
+                              (["-fopenmp"] if omp else []) + ["-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, out)
+    return out
 
 
-def lib():
-    global _lib
+def lib(omp: bool = False):
+    global _lib, _lib_omp
     with _lock:
-        if _lib is None:
-            L = ctypes.CDLL(build())
+        if (_lib_omp if omp else _lib) is None:
+            L = ctypes.CDLL(build(omp=omp))
             vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
             P = ctypes.POINTER
             L.or_create.restype = vp
@@ -99,8 +104,13 @@ def lib():
             L.or_cn_rhs.argtypes = [vp, P(d), P(d), vp, d, vp, P(d), P(d), P(d)]
             L.or_momentum_residual.argtypes = [vp, P(d), P(d), P(d), P(d)]
             L.or_cn_step.argtypes = [vp, P(d), P(d), P(d), i, vp, vp, d, P(d), P(d), d, d, i, P(d)]
-            _lib = L
-    return _lib
+            L.or_set_threads.argtypes = [i]
+            L.or_set_threads.restype = i
+            if omp:
+                _lib_omp = L
+            else:
+                _lib = L
+    return _lib_omp if omp else _lib
 
 
 def _p(a, ct=ctypes.c_double):
@@ -138,8 +148,9 @@ class Oracle:
     grids (N, N/2, ...), alpha = dt / (2 Re)."""
 
     def __init__(self, N, x0, y0, L, levels, alpha, nu1=2, nu2=1, gamma=1, lam=5, dtau=0.9,
-                 ghost_mode=0, order_mode=0, seed=12345, snap=0.3, band=0):
-        self.L = lib()
+                 ghost_mode=0, order_mode=0, seed=12345, snap=0.3, band=0, threads=1):
+        self.L = lib(omp=threads > 1)
+        self.threads = self.L.or_set_threads(threads) if threads > 1 else 1
         self.N, self.x0, self.y0, self.len, self.levels, self.alpha = N, x0, y0, L, levels, alpha
         self.h = L / N
         self.c = self.L.or_create(N, x0, y0, L, levels, alpha)

@@ -6,6 +6,12 @@
  * leg of the benchmark may load this library.  It shares no code, header,
  * table or helper with the CUDA path.
  *
+ * Built serially by default.  The benchmark's multi-core CPU baseline builds
+ * it a second time with OpenMP: the only parallel loops are the boxes of one
+ * colour (independent by construction) and row-wise loops whose rows write
+ * disjoint outputs (residual, restriction, interpolation), so the iterate is
+ * bitwise the same for any thread count; every sum stays serial.
+ *
  * Everything is written the direct way: every equation of the linear system
  * is produced by one function (get_row) that lists its coefficients, and the
  * residual, the assembled matrix, the box relaxation and the ghost relaxation
@@ -68,6 +74,9 @@
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define OR_MAXLEV 16
 #define OR_MAXMARCH 64
@@ -670,6 +679,18 @@ static double row_residual(const row_t *R, const double *x, double b)
 
 /* ----------------------------------------------------------------- public */
 
+/* threads of the OpenMP build (1 in the serial build); returns the count in use */
+int or_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
 void *or_create(int N, double x0, double y0, double len, int levels, double alpha)
 {
     if (N < 4 || levels < 1 || levels > OR_MAXLEV) return NULL;
@@ -804,19 +825,22 @@ double or_residual(void *vc, int lev, const double *x, const double *b, double *
     ctx_t *c = (ctx_t *)vc;
     level_t *l = &c->lv[lev];
     int N = l->N;
-    row_t R;
     double mx = 0.0;
     for (int g = 0; g < 3; g++) {
         int ilo = g == G_V ? -1 : 0, ihi = g == G_P ? N - 1 : N;
         int jlo = g == G_U ? -1 : 0, jhi = g == G_P ? N - 1 : N;
+#pragma omp parallel for schedule(static)
         for (int j = jlo; j <= jhi; j++)
             for (int i = ilo; i <= ihi; i++) {
+                row_t R;
                 int k = iG(l, g, i, j);
                 get_row(c, lev, g, i, j, &R);
-                double v = row_residual(&R, x, b[k]);
-                r[k] = v;
-                if (fabs(v) > mx || v != v) mx = v != v ? NAN : fabs(v);
+                r[k] = row_residual(&R, x, b[k]);
             }
+    }
+    for (int k = 0; k < l->n - 1; k++) {
+        double v = r[k];
+        if (fabs(v) > mx || v != v) mx = v != v ? NAN : fabs(v);
     }
     /* mean row, Eq. (midpoint) scaled by h^2 */
     double s = 0.0;
@@ -1136,6 +1160,9 @@ void or_box_sweep(void *vc, int lev, double *x, const double *b)
                     if ((i + 3 * j) % 5 == col && ttype(l, G_P, i, j) == T_INTERNAL && !cut_cell(l, i, j))
                         cells[nc++] = j * N + i;
             if (c->order_mode == 1) shuffle(c, cells, nc); /* random order inside a colour */
+            /* boxes of one colour are independent: any order, or several
+             * threads, give the same iterate */
+#pragma omp parallel for schedule(static)
             for (int k = 0; k < nc; k++) box_relax(c, lev, x, b, cells[k] % N, cells[k] / N);
         }
         for (int col = 0; col < l->ncutcol; col++) {
@@ -1144,6 +1171,7 @@ void or_box_sweep(void *vc, int lev, double *x, const double *b)
                 for (int i = 0; i < N; i++)
                     if (l->cutcol[j * N + i] == col) cells[nc++] = j * N + i;
             if (c->order_mode == 1) shuffle(c, cells, nc);
+#pragma omp parallel for schedule(static)
             for (int k = 0; k < nc; k++) box_relax(c, lev, x, b, cells[k] % N, cells[k] / N);
         }
     }
@@ -1259,6 +1287,7 @@ void or_restrict(void *vc, int lev, const double *r, double *bH)
     for (int g = 0; g < 3; g++) {
         int ilo = g == G_V ? -1 : 0, ihi = g == G_P ? Nc - 1 : Nc;
         int jlo = g == G_U ? -1 : 0, jhi = g == G_P ? Nc - 1 : Nc;
+#pragma omp parallel for schedule(static)
         for (int J = jlo; J <= jhi; J++)
             for (int I = ilo; I <= ihi; I++) {
                 int tc = ttype(C, g, I, J);
@@ -1340,6 +1369,7 @@ void or_prolong(void *vc, int lev, const double *eH, double *x)
         int jlo = g == G_U ? -1 : 0, jhi = g == G_P ? N - 1 : N;
         int Ilo = g == G_V ? -1 : 0, Ihi = g == G_P ? Nc - 1 : Nc;
         int Jlo = g == G_U ? -1 : 0, Jhi = g == G_P ? Nc - 1 : Nc;
+#pragma omp parallel for schedule(static)
         for (int j = jlo; j <= jhi; j++)
             for (int i = ilo; i <= ihi; i++) {
                 if (ttype(f, g, i, j) == T_INACTIVE) continue;
@@ -1922,6 +1952,7 @@ void or_restrict_t(void *vc, int lev, const double *yH, double *lam)
     for (int g = 0; g < 3; g++) {
         int ilo = g == G_V ? -1 : 0, ihi = g == G_P ? Nc - 1 : Nc;
         int jlo = g == G_U ? -1 : 0, jhi = g == G_P ? Nc - 1 : Nc;
+#pragma omp parallel for schedule(static)
         for (int J = jlo; J <= jhi; J++)
             for (int I = ilo; I <= ihi; I++) {
                 int tc = ttype(C, g, I, J);
@@ -1972,6 +2003,7 @@ void or_prolong_t(void *vc, int lev, const double *r, double *cH)
         int jlo = g == G_U ? -1 : 0, jhi = g == G_P ? N - 1 : N;
         int Ilo = g == G_V ? -1 : 0, Ihi = g == G_P ? Nc - 1 : Nc;
         int Jlo = g == G_U ? -1 : 0, Jhi = g == G_P ? Nc - 1 : Nc;
+#pragma omp parallel for schedule(static)
         for (int j = jlo; j <= jhi; j++)
             for (int i = ilo; i <= ihi; i++) {
                 if (ttype(f, g, i, j) == T_INACTIVE) continue;

@@ -490,21 +490,16 @@ __global__ void __launch_bounds__(TileGeom<T>::THREADS) k_box_tma(const __grid_c
         const int ilo = max(c0 - 1 - lo, 0), ihi = min(c0 - 1 + TW + hi, A.N);
         const int jlo = max(r0 - 1 - lo, 0), jhi = min(r0 - 1 + TH + hi, A.N);
         if (ilo >= ihi || jlo >= jhi) continue;
-        // Slots are (t, column): WR = width rounded up to whole warps, slot
-        // s -> column ilo + s % WR and the t = s / WR-th box of the colour in
-        // that column (rows j = 2 (colour - i) mod 5 plus multiples of 5).
-        // The 32 lanes of a warp share t and take 32 consecutive columns, so
-        // with LW a multiple of 32 their shared-memory words lie in 32
-        // different banks, whatever rows they sit on.  s / WR is computed as
-        // ((s >> 5) * ceil(2^16 / (WR / 32))) >> 16, exact for s < 2^16.
-        const int WR = (ihi - ilo + 31) & ~31, nt = (jhi - jlo + 4) / 5, nslot = WR * nt;
-        const unsigned wq = (unsigned)(WR >> 5), inv = (65536u + wq - 1u) / wq;
+        // M boxes per row; k / M as (k * ceil(2^16 / M)) >> 16, exact for
+        // k < 2^16 / M (here k < 81 * 17 and M <= 17)
+        const int M = (ihi - ilo + 4) / 5, nslot = (jhi - jlo) * M;
+        const unsigned inv = (65536u + (unsigned)M - 1u) / (unsigned)M;
         for (int k = threadIdx.x; k < nslot; k += TileGeom<T>::THREADS) {
-            const int t = (int)((((unsigned)k >> 5) * inv) >> 16);
-            const int i = ilo + (k - t * WR);
+            const int jj = (int)(((unsigned)k * inv) >> 16), m = k - jj * M;
+            const int j = jlo + jj;
+            // first cell of colour (i + 3 j) mod 5 = colour at or after ilo
+            const int i = ilo + (int)((unsigned)(colour + (5 << 28) - 3 * j - ilo) % 5u) + 5 * m;
             if (i >= ihi) continue;
-            const int j = jlo + (int)((unsigned)(2 * colour - 2 * i - jlo + (5 << 26)) % 5u) + 5 * t;
-            if (j >= jhi) continue;
             const int ls = (j + 1 - row0) * LW + (i + 1 - col0);
             const unsigned code = sc[ls];
             if (!(code & BOX_FULL)) continue;

@@ -149,7 +149,8 @@ def paper_shape(name: str, omega: float = 0.0, t: float = 0.0):
             x, y = rot(X, Y)
             r = np.hypot(x, y)
             im5 = y ** 5 + 5 * x ** 4 * y - 10 * x ** 2 * y ** 3
-            return 0.5 + 0.15 * im5 / np.maximum(r, 1e-300) ** 5 - r
+            rs = np.where(r > 0, r, 1.0)
+            return 0.5 + 0.15 * np.where(r > 0, im5 / rs ** 5, 0.0) - r
         return f
     raise ValueError(name)
 

@@ -126,3 +126,30 @@ def test_oracle_second_order_on_the_steady_circle():
     for a, b in zip(e32, e64):
         assert a / b > 2.8, (e32, e64)          # order > 1.5
     assert abs(xi32) / abs(xi64) > 2.8
+
+
+def test_transcribed_paper_tables_are_consistent():
+    # the golden file holds the paper's printed errors and orders; the
+    # orders recomputed from the errors, log(e1 / e2) / log(N2 / N1), agree
+    # with the printed ones to their two decimals (a transcription slip in
+    # either would break this)
+    import json
+    import os
+    d = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "accuracy_tables.json")))
+    tests = [k for k in d if not k.startswith("_")]
+    assert len(tests) == 6
+    for k in tests:
+        Ns = sorted(d[k]["errors"], key=int)
+        assert Ns == ["60", "72", "87", "104", "125", "150", "180"]
+        for a, b in zip(Ns, Ns[1:]):
+            for q in ("u", "v", "div"):
+                for n in range(2):
+                    e1, e2 = d[k]["errors"][a][q][n], d[k]["errors"][b][q][n]
+                    got = math.log(e1 / e2) / math.log(int(b) / int(a))
+                    printed = d[k]["orders"][b][q][n]
+                    # three-digit errors: the recomputed order carries about
+                    # +-0.06 of rounding at these N ratios
+                    assert abs(got - printed) < 0.08, (k, b, q, n, got, printed)
+        # div u - g = xi is constant: equal L1 and Linf errors of div u
+        for N in Ns:
+            assert d[k]["errors"][N]["div"][0] == d[k]["errors"][N]["div"][1]

@@ -350,3 +350,19 @@ def test_krylov_equals_direct_solve():
     st, xk, hist = o.solve_krylov(np.zeros_like(b), b, 1e-12, 60)
     assert st == 0
     assert np.abs(xk - xd).max() / np.abs(xd).max() <= 1e-10
+
+
+def test_openmp_build_gives_the_same_iterate():
+    # the multi-core CPU baseline's build: parallel loops only over
+    # independent boxes of one colour and over rows with disjoint outputs,
+    # so one V-cycle is bitwise that of the serial build
+    o1, phi, st = make_oracle("flower5", 128)
+    o4 = O.Oracle(128, 0.0, 0.0, 1.0, o1.levels, o1.alpha, threads=4)
+    assert o4.geometry(phi) == 0 and o4.threads == 4
+    t = o1.types()
+    b = W.random_flat(128, t, 3)
+    x = W.random_flat(128, t, 4)
+    _, x1 = o1.cycle(x, b)
+    _, x4 = o4.cycle(x, b)
+    assert np.array_equal(x1, x4)
+    assert np.array_equal(o1.residual(x1, b)[0], o4.residual(x4, b)[0])
