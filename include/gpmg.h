@@ -358,6 +358,15 @@ gp_status cn_step_adjoint(gp_ctx *ctx, int step, const double *x_m, const double
  * synchronises and returns the number of timed launches and their summed
  * device time in milliseconds. */
 int64_t gp_launch_count(const gp_ctx *ctx);
+
+/* Arithmetic ceilings of the current device for the FP64 kernels' roofline:
+ * FP64 and FP32 fused multiply-add throughput in TFLOP/s (an FMA counts as two
+ * flops), measured with CUDA events over 5 launches of a full-occupancy grid
+ * whose threads run 8 independent FMA chains of 4096 steps.  sink: a device
+ * buffer of at least 8 * 8 * (multiprocessor count) bytes that the kernels may
+ * write (they do not for these inputs); stream: a cudaStream_t or NULL.
+ * Synchronises the stream. */
+gp_status gp_fma_peak(void *sink, void *stream, double *fp64_tflops, double *fp32_tflops);
 gp_status gp_timer_start(gp_ctx *ctx, int kernel, int level);
 gp_status gp_timer_stop(gp_ctx *ctx, int64_t *launches, double *total_ms);
 

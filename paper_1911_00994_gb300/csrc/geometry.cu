@@ -15,8 +15,8 @@
 
 namespace gpmg {
 
-__constant__ int c_OX2[3] = {0, 1, 1};
-__constant__ int c_OY2[3] = {1, 0, 1};
+// half-cell offsets (x, y) of node (0, 0) of the u, v and p grids
+__constant__ int c_half[3][2] = {{0, 1}, {1, 0}, {1, 1}};
 
 struct Geo {
     const double *phi;  // paper-sign half lattice of the finest grid
@@ -34,113 +34,115 @@ struct Geo {
     int *flag;
 };
 
-__device__ inline bool phi_node(const Geo &G, int g, int i, int j, double *out)
-{
-    int m = 1 << G.lev;
-    int a = m * (2 * i + c_OX2[g]);
-    int b = m * (2 * j + c_OY2[g]);
-    int M = 2 * G.Nf;
-    if (a < 0 || a > M || b < 0 || b > M) return false;
-    *out = G.phi[(size_t)b * (M + 1) + a];
-    return true;
-}
-
-__device__ inline double node_x(const Geo &G, int g, int i) { return G.x0 + (double)(2 * i + c_OX2[g]) * (0.5 * G.h); }
-__device__ inline double node_y(const Geo &G, int g, int j) { return G.y0 + (double)(2 * j + c_OY2[g]) * (0.5 * G.h); }
-
-__device__ inline uint8_t ttype(const Geo &G, int g, int i, int j)
-{
-    if (!in_grid(g, G.N, i, j)) return T_INACTIVE;
-    return G.t[g][(j + 1) * G.P + (i + 1)];
-}
-
-// bilinear interpolant of phi on the 2x2 cell of grid g containing (x, y),
-// cell chosen by floor in each axis
-__device__ bool bilin(const Geo &G, int g, double x, double y, double *val, double *gx, double *gy)
-{
-    double h = G.h;
-    double sx = (x - G.x0) / h - 0.5 * (double)c_OX2[g];
-    double sy = (y - G.y0) / h - 0.5 * (double)c_OY2[g];
-    double fi = floor(sx), fj = floor(sy);
-    if (!(fi > -1e9 && fi < 1e9 && fj > -1e9 && fj < 1e9)) return false;
-    int i0 = (int)fi, j0 = (int)fj;
-    double fx = sx - fi, fy = sy - fj;
-    double p00, p10, p01, p11;
-    if (!phi_node(G, g, i0, j0, &p00) || !phi_node(G, g, i0 + 1, j0, &p10) || !phi_node(G, g, i0, j0 + 1, &p01) ||
-        !phi_node(G, g, i0 + 1, j0 + 1, &p11))
-        return false;
-    double ex = 1.0 - fx, ey = 1.0 - fy;
-    *val = ex * ey * p00 + fx * ey * p10 + ex * fy * p01 + fx * fy * p11;
-    *gx = (ey * (p10 - p00) + fy * (p11 - p01)) / h;
-    *gy = (ex * (p01 - p00) + fx * (p11 - p10)) / h;
-    return true;
-}
-
-__device__ bool unit_normal(const Geo &G, int g, double x, double y, double *nx, double *ny)
-{
-    double v, gx, gy;
-    if (!bilin(G, g, x, y, &v, &gx, &gy)) return false;
-    double nrm = sqrt(gx * gx + gy * gy);
-    if (!(nrm > 0.0)) return false;
-    *nx = gx / nrm;
-    *ny = gy / nrm;
-    return true;
-}
-
-// Algorithm 1 (march by h/2 against the normal, then bisection); a node
-// inside the fluid marches along the normal
-__device__ bool ghost_to_boundary(const Geo &G, int g, int i, int j, double *xB, double *yB)
-{
-    double h = G.h;
-    double xG = node_x(G, g, i), yG = node_y(G, g, j);
-    double phH;
-    if (!phi_node(G, g, i, j, &phH)) return false;
-    double sg = phH > 0.0 ? 1.0 : -1.0;
-    double xH = xG, yH = yG, xK = xG, yK = yG;
-    int steps = 0;
-    while (sg * phH > 0.0) {
-        double nx, ny, gx, gy;
-        xK = xH;
-        yK = yH;
-        if (!unit_normal(G, g, xH, yH, &nx, &ny)) return false;
-        xH = xH - sg * (0.5 * h * nx);
-        yH = yH - sg * (0.5 * h * ny);
-        if (!bilin(G, g, xH, yH, &phH, &gx, &gy)) return false;
-        if (++steps > MAX_MARCH) return false;
+// One grid of one level, read through the finest half-cell lattice: its node
+// (i, j) is lattice point (step (2 i + hx), step (2 j + hy)), step = 2^lev,
+// so the coarse grids see phi by injection.
+struct GridView {
+    const double *phi;
+    int side, step, hx, hy;
+    double x0, y0, h;
+    __device__ GridView(const Geo &G, int g)
+        : phi(G.phi), side(2 * G.Nf + 1), step(1 << G.lev), hx(c_half[g][0]), hy(c_half[g][1]), x0(G.x0),
+          y0(G.y0), h(G.h)
+    {
     }
-    if (steps == 0) {
-        *xB = xG;
-        *yB = yG;
+    __device__ bool at(int i, int j, double &v) const
+    {
+        const int a = step * (2 * i + hx), b = step * (2 * j + hy);
+        if (a < 0 || b < 0 || a >= side || b >= side) return false;
+        v = phi[(size_t)b * side + a];
         return true;
     }
-    double dx = xH - xK, dy = yH - yK;
-    double dist = sqrt(dx * dx + dy * dy);
-    int nb = (int)ceil(log2(dist / (0.01 * h)));
-    double xm = xH, ym = yH;
-    for (int it = 0; it < nb; it++) {
-        double phB, gx, gy;
-        xm = 0.5 * (xH + xK);
-        ym = 0.5 * (yH + yK);
-        if (!bilin(G, g, xm, ym, &phB, &gx, &gy)) return false;
-        if (phB * phH < 0.0) {
-            xK = xm;
-            yK = ym;
-        } else {
-            xH = xm;
-            yH = ym;
-            phH = phB;
-        }
-    }
-    *xB = xm;
-    *yB = ym;
+    __device__ double xc(int i) const { return x0 + (double)(2 * i + hx) * (0.5 * h); }
+    __device__ double yc(int j) const { return y0 + (double)(2 * j + hy) * (0.5 * h); }
+};
+
+// phi's bilinear interpolant on the grid cell holding a point (Sect. 3.3):
+// value and gradient.  The cell is the one whose lower-left node is the floor
+// of the point's grid coordinates (reading R7).
+struct Patch {
+    double v, gx, gy;
+};
+
+__device__ bool patch_at(const GridView &V, double x, double y, Patch &P)
+{
+    const double cx = (x - V.x0) / V.h - 0.5 * (double)V.hx;
+    const double cy = (y - V.y0) / V.h - 0.5 * (double)V.hy;
+    const double bx = floor(cx), by = floor(cy);
+    if (!(bx > -1e9 && bx < 1e9 && by > -1e9 && by < 1e9)) return false;
+    const int i = (int)bx, j = (int)by;
+    double c00, c10, c01, c11;  // corners: (i, j), (i + 1, j), (i, j + 1), (i + 1, j + 1)
+    if (!V.at(i, j, c00) || !V.at(i + 1, j, c10) || !V.at(i, j + 1, c01) || !V.at(i + 1, j + 1, c11)) return false;
+    const double tx = cx - bx, ty = cy - by, sx = 1.0 - tx, sy = 1.0 - ty;
+    P.v = sx * sy * c00 + tx * sy * c10 + sx * ty * c01 + tx * ty * c11;
+    P.gx = (sy * (c10 - c00) + ty * (c11 - c01)) / V.h;
+    P.gy = (sx * (c01 - c00) + tx * (c11 - c10)) / V.h;
     return true;
 }
 
-__device__ inline void lagrange3(double t, double T[3])
+// direction of grad phi (toward the object) at a point
+__device__ bool normal_at(const GridView &V, double x, double y, double &nx, double &ny)
 {
-    T[0] = (1.0 - t) * (2.0 - t) / 2.0;
-    T[1] = t * (2.0 - t);
-    T[2] = t * (t - 1.0) / 2.0;
+    Patch P;
+    if (!patch_at(V, x, y, P)) return false;
+    const double len = sqrt(P.gx * P.gx + P.gy * P.gy);
+    if (!(len > 0.0)) return false;
+    nx = P.gx / len;
+    ny = P.gy / len;
+    return true;
+}
+
+// Algorithm 1 for the node (i, j): walk in steps of h/2 along -grad phi (a
+// node inside the fluid, snapped to a ghost, walks along +grad phi) until phi
+// changes sign, then halve the last step ceil(log2(step length / 0.01 h))
+// times; the boundary point is the last midpoint (reading R7).  The walk's two
+// ends live in registers: `far` on the node's side of the boundary, `near` the
+// point before it.
+__device__ bool find_boundary(const GridView &V, int i, int j, double &bx, double &by)
+{
+    double f;
+    if (!V.at(i, j, f)) return false;
+    const double side = f > 0.0 ? 1.0 : -1.0;
+    const double px = V.xc(i), py = V.yc(j);
+    double fx = px, fy = py, nx0 = px, ny0 = py;
+    int walked = 0;
+    while (side * f > 0.0) {
+        double dx, dy;
+        nx0 = fx;
+        ny0 = fy;
+        if (!normal_at(V, fx, fy, dx, dy)) return false;
+        fx = fx - side * (0.5 * V.h * dx);
+        fy = fy - side * (0.5 * V.h * dy);
+        Patch P;
+        if (!patch_at(V, fx, fy, P)) return false;
+        f = P.v;
+        if (++walked > MAX_MARCH) return false;
+    }
+    if (walked == 0) {  // phi = 0 at the node: it lies on the boundary
+        bx = px;
+        by = py;
+        return true;
+    }
+    const double ex = fx - nx0, ey = fy - ny0;
+    const int halvings = (int)ceil(log2(sqrt(ex * ex + ey * ey) / (0.01 * V.h)));
+    double mx = fx, my = fy;
+    for (int k = 0; k < halvings; k++) {
+        mx = 0.5 * (fx + nx0);
+        my = 0.5 * (fy + ny0);
+        Patch P;
+        if (!patch_at(V, mx, my, P)) return false;
+        if (P.v * f < 0.0) {  // the sign change lies between the midpoint and fx
+            nx0 = mx;
+            ny0 = my;
+        } else {
+            fx = mx;
+            fy = my;
+            f = P.v;
+        }
+    }
+    bx = mx;
+    by = my;
+    return true;
 }
 
 struct GhostRow {
@@ -150,94 +152,126 @@ struct GhostRow {
     double xB, yB, thx, thy;
 };
 
-// Row of an external node acting as a ghost: Eq. (BCu) for u, v ghosts that
-// an internal or box-ghost row references and whose B is within one cell on
-// both axes; otherwise extrapolation along the dominant normal axis toward
-// the fluid (quadratic for u, v; linear for p) where phi decreases strictly
-// along its nodes, else a copy of the axis neighbour of smallest phi.
+// three-point Lagrange basis on the nodes 0, 1, 2 evaluated at t (Eq. BCu)
+__device__ inline double lagrange_basis(int k, double t)
+{
+    return k == 0 ? (1.0 - t) * (2.0 - t) / 2.0 : k == 1 ? t * (2.0 - t) : t * (t - 1.0) / 2.0;
+}
+
+// signed binomial weight (-1)^k C(n-1, k): the n-point extrapolation row
+// x_0 - C(n-1,1) x_1 + ... = 0 that is exact for polynomials of degree n - 2
+__device__ inline double extrap_weight(int n, int k)
+{
+    double c = 1.0;
+    for (int q = 0; q < k; q++) c = c * (double)(n - 1 - q) / (double)(q + 1);
+    return (k & 1) ? -c : c;
+}
+
+// The row of a ghost node (readings R2, R5):
+//  * Eq. (BCu) on the upwind nine-point stencil for a u or v ghost that an
+//    internal or box-ghost row references directly and whose boundary point B
+//    is at most one cell away on both axes (theta_x, theta_y <= 1), theta =
+//    SIGN(n) (x_G - x_B) / h so that stencil node k sits at theta = k;
+//  * otherwise extrapolation toward the fluid along the axis where |n| is
+//    largest (x on ties), four points for u, v and three for p, used only
+//    when phi decreases strictly along the row's nodes;
+//  * otherwise a copy of the axis neighbour with the smallest phi below
+//    phi(G), the neighbours tried as -x, +x, -y, +y (first one wins a tie).
 __device__ bool ghost_setup(const Geo &G, int g, int i, int j, GhostRow *R)
 {
-    double h = G.h;
-    double xG = node_x(G, g, i), yG = node_y(G, g, j);
+    const GridView V(G, g);
+    const double gxn = V.xc(i), gyn = V.yc(j);
     double nx, ny;
-    if (!unit_normal(G, g, xG, yG, &nx, &ny)) return false;
-    int sx = nx >= 0.0 ? 1 : -1;
-    int sy = ny >= 0.0 ? 1 : -1;
-    int axis = fabs(nx) >= fabs(ny) ? 0 : 1;
+    if (!normal_at(V, gxn, gyn, nx, ny)) return false;
+    const int ux = nx >= 0.0 ? 1 : -1, uy = ny >= 0.0 ? 1 : -1;  // SIGN(n), SIGN(0) = 1
     R->kind = K_EXTRAP;
-    R->xB = 0.0; R->yB = 0.0; R->thx = 0.0; R->thy = 0.0;
+    R->xB = R->yB = R->thx = R->thy = 0.0;
     if (g != G_P) {
-        double xB, yB;
-        if (!ghost_to_boundary(G, g, i, j, &xB, &yB)) return false;
-        R->xB = xB;
-        R->yB = yB;
-        R->thx = (double)sx * (xG - xB) / h;
-        R->thy = (double)sy * (yG - yB) / h;
-        if (G.prim[(long long)g * G.F + (j + 1) * G.P + (i + 1)] && R->thx <= 1.0 && R->thy <= 1.0) R->kind = K_BCU;
+        if (!find_boundary(V, i, j, R->xB, R->yB)) return false;
+        R->thx = (double)ux * (gxn - R->xB) / V.h;
+        R->thy = (double)uy * (gyn - R->yB) / V.h;
+        const bool direct = G.prim[(long long)g * G.F + (j + 1) * G.P + (i + 1)] != 0;
+        if (direct && R->thx <= 1.0 && R->thy <= 1.0) R->kind = K_BCU;
     }
     if (R->kind == K_BCU) {
-        double Tx[3], Ty[3];
-        lagrange3(R->thx, Tx);
-        lagrange3(R->thy, Ty);
         R->nst = 9;
-        for (int ky = 0; ky < 3; ky++)
-            for (int kx = 0; kx < 3; kx++) {
-                R->si[ky * 3 + kx] = i - kx * sx;
-                R->sj[ky * 3 + kx] = j - ky * sy;
-                R->w[ky * 3 + kx] = Tx[kx] * Ty[ky];
-            }
-        return true;
-    }
-    const double e3[3] = {1.0, -2.0, 1.0};
-    const double e4[4] = {1.0, -3.0, 3.0, -1.0};
-    int s = axis == 0 ? sx : sy;
-    int n = g == G_P ? 3 : 4;
-    double ph[4];
-    bool mono = true;
-    for (int k = 0; k < n && mono; k++) {
-        int ii = i - (axis == 0 ? k * s : 0), jj = j - (axis == 1 ? k * s : 0);
-        if (!phi_node(G, g, ii, jj, &ph[k])) mono = false;
-        else if (k > 0 && !(ph[k] < ph[k - 1])) mono = false;
-    }
-    if (mono) {
-        R->nst = n;
-        for (int k = 0; k < n; k++) {
-            R->si[k] = i - (axis == 0 ? k * s : 0);
-            R->sj[k] = j - (axis == 1 ? k * s : 0);
-            R->w[k] = g == G_P ? e3[k] : e4[k];
+        for (int q = 0; q < 9; q++) {
+            const int kx = q % 3, ky = q / 3;
+            R->si[q] = i - kx * ux;
+            R->sj[q] = j - ky * uy;
+            R->w[q] = lagrange_basis(kx, R->thx) * lagrange_basis(ky, R->thy);
         }
         return true;
     }
-    const int di[4] = {-1, 1, 0, 0}, dj[4] = {0, 0, -1, 1};
-    double pG, best = 0.0;
-    int kb = -1;
-    if (!phi_node(G, g, i, j, &pG)) return false;
-    for (int k = 0; k < 4; k++) {
-        double q;
-        if (!phi_node(G, g, i + di[k], j + dj[k], &q)) continue;
-        if (q < pG && (kb < 0 || q < best)) {
-            best = q;
-            kb = k;
+    // extrapolation: nodes G, G - e, G - 2e (, G - 3e), e one step toward the fluid
+    const bool along_x = fabs(nx) >= fabs(ny);
+    const int ex = along_x ? ux : 0, ey = along_x ? 0 : uy;
+    const int npts = g == G_P ? 3 : 4;
+    bool falling = true;
+    double prev = 0.0;
+    for (int k = 0; k < npts && falling; k++) {
+        double f;
+        if (!V.at(i - k * ex, j - k * ey, f) || (k > 0 && !(f < prev))) falling = false;
+        prev = f;
+    }
+    if (falling) {
+        R->nst = npts;
+        for (int k = 0; k < npts; k++) {
+            R->si[k] = i - k * ex;
+            R->sj[k] = j - k * ey;
+            R->w[k] = extrap_weight(npts, k);
+        }
+        return true;
+    }
+    // copy row
+    double fG;
+    if (!V.at(i, j, fG)) return false;
+    int bi = 0, bj = 0;
+    double fbest = 0.0;
+    bool found = false;
+    for (int q = 0; q < 4; q++) {
+        const int di = q < 2 ? 2 * q - 1 : 0, dj = q < 2 ? 0 : 2 * q - 5;  // -x, +x, -y, +y
+        double f;
+        if (!V.at(i + di, j + dj, f) || !(f < fG)) continue;
+        if (!found || f < fbest) {
+            found = true;
+            fbest = f;
+            bi = di;
+            bj = dj;
         }
     }
-    if (kb < 0) return false;
+    if (!found) return false;
     R->kind = K_COPY;
     R->nst = 2;
-    R->si[0] = i; R->sj[0] = j; R->w[0] = 1.0;
-    R->si[1] = i + di[kb]; R->sj[1] = j + dj[kb]; R->w[1] = -1.0;
+    R->si[0] = i;
+    R->sj[0] = j;
+    R->w[0] = 1.0;
+    R->si[1] = i + bi;
+    R->sj[1] = j + bj;
+    R->w[1] = -1.0;
     return true;
 }
 
-// Algorithm LS: internal when phi < 0, and farther than snap*h from the
-// boundary (first-order distance phi / |grad phi| of the bilinear interpolant)
+// Algorithm LS's internal test with the snap of reading R4: phi < 0 and the
+// first-order distance -phi / |grad phi~| above snap h
 __device__ bool node_internal(const Geo &G, int g, int i, int j, double ph)
 {
     if (!(ph < 0.0)) return false;
     if (G.snap <= 0.0) return true;
-    double v, gx, gy;
-    if (!bilin(G, g, node_x(G, g, i), node_y(G, g, j), &v, &gx, &gy)) return true;
-    double gn = sqrt(gx * gx + gy * gy);
+    const GridView V(G, g);
+    Patch P;
+    if (!patch_at(V, V.xc(i), V.yc(j), P)) return true;
+    const double gn = sqrt(P.gx * P.gx + P.gy * P.gy);
     return ph < -G.snap * G.h * gn;
+}
+
+// node value of phi on grid g of this level (false outside the lattice)
+__device__ inline bool phi_node(const Geo &G, int g, int i, int j, double *out) { return GridView(G, g).at(i, j, *out); }
+
+__device__ inline uint8_t ttype(const Geo &G, int g, int i, int j)
+{
+    if (!in_grid(g, G.N, i, j)) return T_INACTIVE;
+    return G.t[g][(j + 1) * G.P + (i + 1)];
 }
 
 // ------------------------------------------------------------------ kernels

@@ -225,25 +225,36 @@ __device__ inline uint8_t tget(const uint8_t *t, int g, int N, int P, int i, int
     return t[(long long)(j + 1) * P + (i + 1)];
 }
 
-// 1-D interpolation taps (see the oracle's description of the same rule)
+// Bilinear interpolation (Sect. 4.3) factors into one-axis taps.  Along an
+// axis where the grid's nodes lie on the nodes or cell midpoints of its
+// coarse grid ("aligned"), fine index k sits at coarse coordinate c = k / 2;
+// along a staggered axis at c = k / 2 - 1 / 4.  With q = 4 c (an integer), the
+// taps are the coarse nodes floor(c) and floor(c) + 1 with linear weights,
+// the nearer node first (the lower one when c is midway; a single tap when c
+// is a coarse node).  A far node outside [lo, hi] is replaced by linear
+// extrapolation from the near node and the one beyond it, 5/4 and -1/4.
 template <typename T> __device__ inline int taps(int k, bool aligned, int lo, int hi, int *K, T *w)
 {
-    bool even = (k % 2 == 0);
-    if (aligned) {
-        if (even) { K[0] = k / 2; w[0] = (T)1; return 1; }
-        K[0] = (k - 1) / 2; w[0] = (T)0.5;
-        K[1] = K[0] + 1; w[1] = (T)0.5;
+    const int q = aligned ? 2 * k : 2 * k - 1;
+    const int fl = q >= 0 ? q / 4 : -((3 - q) / 4);  // floor(q / 4)
+    const int r = q - 4 * fl;                         // 4 (c - floor(c)), 0..3
+    if (r == 0) {
+        K[0] = fl;
+        w[0] = (T)1;
+        return 1;
+    }
+    const int near = r == 3 ? fl + 1 : fl, far = r == 3 ? fl : fl + 1;
+    if (far < lo || far > hi) {
+        K[0] = near;
+        w[0] = (T)1.25;
+        K[1] = 2 * near - far;
+        w[1] = (T)-0.25;
         return 2;
     }
-    int Kc = even ? k / 2 : (k - 1) / 2;
-    int Ko = even ? Kc - 1 : Kc + 1;
-    if (Ko < lo || Ko > hi) {
-        K[0] = Kc; w[0] = (T)1.25;
-        K[1] = 2 * Kc - Ko; w[1] = (T)-0.25;
-        return 2;
-    }
-    K[0] = Kc; w[0] = (T)0.75;
-    K[1] = Ko; w[1] = (T)0.25;
+    K[0] = near;
+    w[0] = (T)(r == 2 ? 0.5 : 0.75);
+    K[1] = far;
+    w[1] = (T)(r == 2 ? 0.5 : 0.25);
     return 2;
 }
 

@@ -374,7 +374,7 @@ __device__ __forceinline__ void box_full_one(const LevelArgs<T> &A, T *x, const 
 // another writes.
 template <typename T> struct TileGeom;
 template <> struct TileGeom<float> {
-    static constexpr int TW = 64, LW = 96, TH = 64, THREADS = 512;
+    static constexpr int TW = 64, LW = 96, TH = 32, THREADS = 640;
 };
 template <> struct TileGeom<double> {
     static constexpr int TW = 32, LW = 64, TH = 32, THREADS = 384;

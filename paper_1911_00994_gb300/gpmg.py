@@ -115,6 +115,7 @@ SIGNATURES = [
     ("cn_step_adjoint", _I, [_VP, _I, _VP, _VP, _D, _D, _P(gp_body), _D, _P(gp_walls), _D, _I, _VP, _VP, _VP, _VP,
                              _VP, _VP, _P(_D)]),
     ("gp_launch_count", ctypes.c_int64, [_VP]),
+    ("gp_fma_peak", _I, [_VP, _VP, _P(_D), _P(_D)]),
     ("gp_timer_start", _I, [_VP, _I, _I]),
     ("gp_timer_stop", _I, [_VP, _P(ctypes.c_int64), _P(_D)]),
 ]
@@ -163,6 +164,20 @@ def flat_to_vec(N: int) -> np.ndarray:
     v = F + (jv + 1) * P + (iv + 1)
     p = 2 * F + (jp + 1) * P + (ip + 1)
     return np.concatenate([u.ravel(), v.ravel(), p.ravel(), [3 * F]]).astype(np.int64)
+
+
+def fma_peak(device="cuda", stream=None):
+    """gp_fma_peak: (FP64, FP32) FMA throughput of the device in TFLOP/s."""
+    import torch
+    dev = torch.device(device)
+    sink = torch.zeros(8 * 1024, dtype=torch.float64, device=dev)
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    a, b = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    s = lib().gp_fma_peak(ctypes.c_void_p(sink.data_ptr()), ctypes.c_void_p(st.cuda_stream), ctypes.byref(a),
+                          ctypes.byref(b))
+    if s != GP_OK:
+        raise GpmgError(s, "gp_fma_peak")
+    return a.value, b.value
 
 
 class Solver:

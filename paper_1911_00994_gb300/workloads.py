@@ -133,6 +133,8 @@ def paper_shape(name: str, omega: float = 0.0, t: float = 0.0):
     def rot(X, Y):
         return ca * X + sa * Y, -sa * X + ca * Y
 
+    if name == "none":
+        return lambda X, Y: -1.0 + 0.0 * X
     if name == "circle":
         R2 = 1.0 / 15.0
         return lambda X, Y: R2 - (X * X + Y * Y)
