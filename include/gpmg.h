@@ -182,6 +182,27 @@ gp_status geometry_build_shape(gp_ctx *ctx, const gp_shape *shape, double t, gp_
  * the paper sign, copied to phi_out (device). */
 gp_status gp_level_set(gp_ctx *ctx, double *phi_out);
 
+/* Level-set transport for deforming bodies (Sect. 3.1).  phi: the (2N+1)^2
+ * half-cell lattice of the context's finest grid (the layout geometry_build
+ * reads, spacing dx = h/2), FP64, in place.  work: caller-owned device
+ * scratch, 2 (2N+1)^2 doubles for the reinitialisation, (2N+1)^2 for the
+ * advection.  Beyond the lattice border phi is taken equal to its border
+ * value.  Both return GP_INVALID for bad arguments and are asynchronous on the
+ * context stream (no synchronisation).
+ *
+ * gp_levelset_reinit: `iters` forward-Euler steps in the fictitious time mu
+ *   of Eq. (sdf), d phi / d mu = S (1 - |grad phi|), from the current phi
+ *   (phi0), S = phi0 / sqrt(phi0^2 + dx^2) and |grad phi| by Godunov's upwind
+ *   rule; dtau <= dx (GP_INVALID above), dx / 2 is the usual choice.  The
+ *   zero level set stays put to a fraction of dx and phi becomes the signed
+ *   distance within about iters * dtau of it.
+ * gp_levelset_advect: `steps` first-order upwind steps of
+ *   phi_t + w . grad phi = 0 with the velocity (wx, wy) given on the same
+ *   lattice; stable for dt (|wx| + |wy|) <= dx (the caller's bound). */
+gp_status gp_levelset_reinit(gp_ctx *ctx, double *phi, double *work, int iters, double dtau);
+gp_status gp_levelset_advect(gp_ctx *ctx, double *phi, double *work, const double *wx, const double *wy, double dt,
+                             int steps);
+
 /* Level information: cells per side, vector length, mesh size. */
 gp_status gp_level_info(const gp_ctx *ctx, int level, int *N, int64_t *len, double *h);
 

@@ -1038,7 +1038,7 @@ __global__ void __launch_bounds__(GC_THREADS) k_ghost_fused(GhostList gh, int nr
 template <typename T>
 __global__ void k_restrict(int Nf, int Pf, long long Ff, const uint8_t *tUf, const uint8_t *tVf, const uint8_t *tPf,
                            int Nc, int Pc, long long Fc, const uint8_t *tUc, const uint8_t *tVc, const uint8_t *tPc,
-                           const T *r, T *bH)
+                           const T *r, T *bH, T *xz)
 {
     int col = blockIdx.x * blockDim.x + threadIdx.x;
     int row = blockIdx.y;
@@ -1089,8 +1089,13 @@ __global__ void k_restrict(int Nf, int Pf, long long Ff, const uint8_t *tUf, con
             out = all ? sw : (cnt > 0 ? su / (T)cnt : (T)0);
         }
         bH[g * Fc + sc] = out;
+        if (xz) xz[g * Fc + sc] = (T)0;  // the coarse iterate starts from zero
     }
-    if (row == 0 && col == 0) bH[3 * Fc] = r[3 * Ff];
+    if (row == 0 && col == 0) {
+        bH[3 * Fc] = r[3 * Ff];
+        if (xz)
+            for (int q = 0; q < NSCAL; q++) xz[3 * Fc + q] = (T)0;
+    }
 }
 
 // Prolongation code of every fine node (one byte per slot and grid, once per
@@ -2023,12 +2028,15 @@ template <typename T> T *post_buffer(Ctx *c, int lev, T *x, int nu)
     return tile_scratch<T>(c, lev);
 }
 
-template <typename T> void restrict_level(Ctx *c, int lev, const T *r, T *bH)
+// restriction into bH; with xz non-null the same launch also zeroes the
+// coarse iterate xz (every slot of its frames and scalars)
+template <typename T> void restrict_level(Ctx *c, int lev, const T *r, T *bH, T *xz)
 {
     const Level &f = c->lv[lev], &C = c->lv[lev + 1];
     dim3 g((C.P + 255) / 256, C.N + 2);
     tmr_begin(c, KT_RESTRICT, lev);
-    k_restrict<T><<<g, 256, 0, c->stream>>>(f.N, f.P, f.F, f.tU, f.tV, f.tP, C.N, C.P, C.F, C.tU, C.tV, C.tP, r, bH);
+    k_restrict<T><<<g, 256, 0, c->stream>>>(f.N, f.P, f.F, f.tU, f.tV, f.tP, C.N, C.P, C.F, C.tU, C.tV, C.tP, r, bH,
+                                             xz);
     tmr_end(c, KT_RESTRICT, lev);
     c->launches++;
 }
@@ -2078,7 +2086,7 @@ void add_float(Ctx *c, double *x, const float *e, long long n)
     template void smooth_from<T>(Ctx *, int, T *, T *, const T *, int);         \
     template T *post_buffer<T>(Ctx *, int, T *, int);                           \
     template void prolong_to<T>(Ctx *, int, const T *, const T *, T *);         \
-    template void restrict_level<T>(Ctx *, int, const T *, T *);                \
+    template void restrict_level<T>(Ctx *, int, const T *, T *, T *);           \
     template void prolong_level<T>(Ctx *, int, const T *, T *);                 \
     template void zero_vec<T>(Ctx *, T *, long long);                           \
     template void zero_inactive<T>(Ctx *, int, T *);

@@ -20,7 +20,7 @@ template <typename T> void box_sweep(Ctx *c, int lev, T *x, const T *b);
 template <typename T> void scalar_update(Ctx *c, int lev, T *x, const T *b);
 template <typename T> void ghost_sweep(Ctx *c, int lev, T *x, const T *b);
 template <typename T> void smooth(Ctx *c, int lev, T *x, const T *b, int nu);
-template <typename T> void restrict_level(Ctx *c, int lev, const T *r, T *bH);
+template <typename T> void restrict_level(Ctx *c, int lev, const T *r, T *bH, T *xz);
 template <typename T> void prolong_level(Ctx *c, int lev, const T *eH, T *x);
 template <typename T> void prolong_to(Ctx *c, int lev, const T *eH, const T *x, T *y);
 template <typename T> void smooth_from(Ctx *c, int lev, T *x, T *in, const T *b, int nu);
@@ -41,6 +41,8 @@ void krylov_init(Ctx *c, double *x, const double *b);
 void krylov_iteration(Ctx *c, double *x, const double *b);
 void krylov_iteration_t(Ctx *c, double *lam, const double *cc);
 int residual_static(Ctx *c, int lev, const double *x, const double *b, double *r, double *norm_host);
+int levelset_reinit(Ctx *c, double *phi, double *work, int iters, double dtau);
+int levelset_advect(Ctx *c, double *phi, double *work, const double *wx, const double *wy, double dt, int steps);
 void cn_convective(Ctx *c, const double *x, const double *Nn, double *out, int mode);
 void cn_rhs(Ctx *c, const double *xn, const double *Nh, const double *f, double dt, const double *bc, const gp_body &body,
             const gp_walls &walls, double *b);
@@ -259,8 +261,7 @@ template <typename T> void cycle_rec(Ctx *c, int lev, T *x, const T *b)
     T *r = Vecs<T>::r(c, lev);
     residual<T>(c, lev, x, b, r);
     T *xH = Vecs<T>::x(c, lev + 1), *bH = Vecs<T>::b(c, lev + 1);
-    restrict_level<T>(c, lev, r, bH);
-    zero_vec<T>(c, xH, c->lv[lev + 1].VL);
+    restrict_level<T>(c, lev, r, bH, xH);  // also zeroes xH
     for (int k = 0; k < c->prm.gamma; k++) cycle_rec<T>(c, lev + 1, xH, bH);
     T *y = post_buffer<T>(c, lev, x, c->prm.nu2);
     prolong_to<T>(c, lev, xH, x, y);
@@ -682,6 +683,19 @@ gp_status gp_residual(gp_ctx *ctx, int level, const double *x, const double *b, 
     return check_cuda(ctx, "gp_residual");
 }
 
+gp_status gp_levelset_reinit(gp_ctx *ctx, double *phi, double *work, int iters, double dtau)
+{
+    if (!ctx || !phi || !work || iters < 0 || !(dtau > 0.0)) return GP_INVALID;
+    return (gp_status)levelset_reinit(&ctx->c, phi, work, iters, dtau);
+}
+
+gp_status gp_levelset_advect(gp_ctx *ctx, double *phi, double *work, const double *wx, const double *wy, double dt,
+                             int steps)
+{
+    if (!ctx || !phi || !work || !wx || !wy || steps < 0 || !(dt > 0.0)) return GP_INVALID;
+    return (gp_status)levelset_advect(&ctx->c, phi, work, wx, wy, dt, steps);
+}
+
 gp_status gp_residual_static(gp_ctx *ctx, int level, const double *x, const double *b, double *r, double *norm_host)
 {
     if (!level_ok(ctx, level) || !ctx->c.geom_ok || !x || !b || !r) return GP_INVALID;
@@ -723,7 +737,7 @@ gp_status gp_smooth(gp_ctx *ctx, int level, double *x, const double *b, int nu)
 gp_status gp_restrict(gp_ctx *ctx, int level, const double *r_fine, double *b_coarse)
 {
     if (!ctx || level < 0 || level + 1 >= ctx->c.L || !ctx->c.geom_ok || !r_fine || !b_coarse) return GP_INVALID;
-    restrict_level<double>(&ctx->c, level, r_fine, b_coarse);
+    restrict_level<double>(&ctx->c, level, r_fine, b_coarse, nullptr);
     return check_cuda(ctx, "gp_restrict");
 }
 

@@ -116,6 +116,8 @@ SIGNATURES = [
                              _VP, _VP, _P(_D)]),
     ("gp_launch_count", ctypes.c_int64, [_VP]),
     ("gp_fma_peak", _I, [_VP, _VP, _P(_D), _P(_D)]),
+    ("gp_levelset_reinit", _I, [_VP, _VP, _VP, _I, _D]),
+    ("gp_levelset_advect", _I, [_VP, _VP, _VP, _VP, _VP, _D, _I]),
     ("gp_timer_start", _I, [_VP, _I, _I]),
     ("gp_timer_stop", _I, [_VP, _P(ctypes.c_int64), _P(_D)]),
 ]
@@ -428,6 +430,24 @@ class Solver:
     @staticmethod
     def _opt(t):
         return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+    def levelset_reinit(self, phi, iters, dtau):
+        """gp_levelset_reinit in place on a (2N+1)^2 FP64 device lattice."""
+        n = (2 * self.N + 1) ** 2
+        work = self.torch.empty(2 * n, dtype=self.torch.float64, device=self.device)
+        work.record_stream(self.stream)
+        self._check(self.L.gp_levelset_reinit(self.ctx, _ptr(phi), _ptr(work), int(iters), float(dtau)),
+                    "gp_levelset_reinit")
+        return phi
+
+    def levelset_advect(self, phi, wx, wy, dt, steps):
+        """gp_levelset_advect in place; wx, wy on the same lattice."""
+        n = (2 * self.N + 1) ** 2
+        work = self.torch.empty(n, dtype=self.torch.float64, device=self.device)
+        work.record_stream(self.stream)
+        self._check(self.L.gp_levelset_advect(self.ctx, _ptr(phi), _ptr(work), _ptr(wx), _ptr(wy), float(dt),
+                                              int(steps)), "gp_levelset_advect")
+        return phi
 
     def set_continuity_source(self, g):
         """gp_set_continuity_source: g (a finest-level vector whose p frame
