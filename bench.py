@@ -694,7 +694,7 @@ def run_ours(args):
     mov = moving_ellipse(dev, stream) if not args.no_moving else None
     big = largest_solve(dev, stream) if not args.no_large else None
     cav = cavity_cn_steps(dev, stream, N=N) if not args.no_cavity else None
-    acc = accuracy_study() if not args.no_accuracy else None
+    acc = accuracy_study() if args.accuracy else None
 
     if rank != 0:
         if dist:
@@ -845,7 +845,7 @@ def main():
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--no-wcycle", action="store_true")
     ap.add_argument("--no-cavity", action="store_true")
-    ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--accuracy", action="store_true", help="add the Sect. 5.1 accuracy study (about 3.5 min)")
     args = ap.parse_args()
     if args.impl == "reference":
         args.steps = 2 if args.steps is None else args.steps
