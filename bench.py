@@ -691,7 +691,7 @@ def run_ours(args):
     torch.cuda.empty_cache()
     wcy = cycle_ablation(dev, stream, TOL, barrier) if not args.no_wcycle else None
     adj = adjoint_rollout(dev, stream) if not args.no_adjoint else None
-    mov = moving_ellipse(dev, stream) if not args.no_moving else None
+    mov = moving_ellipse(dev, stream, steps=args.moving_steps, warm=args.moving_warm) if not args.no_moving else None
     big = largest_solve(dev, stream) if not args.no_large else None
     cav = cavity_cn_steps(dev, stream, N=N) if not args.no_cavity else None
     acc = accuracy_study() if args.accuracy else None
@@ -842,6 +842,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-moving", action="store_true")
+    ap.add_argument("--moving-steps", type=int, default=20, help="timed steps of the moving ellipse (the config: 200)")
+    ap.add_argument("--moving-warm", type=int, default=4, help="untimed steps before them (the config: 0, from rest)")
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--no-wcycle", action="store_true")
     ap.add_argument("--no-cavity", action="store_true")
