@@ -603,7 +603,7 @@ def run_ours(args):
            "copies": "pinned host buffers, second stream, double-buffered device staging (overlapped with the solve)",
            "serial": {"value": scycles / (serial_ms / 1e3), "ms_per_step": serial_ms / args.steps,
                       "copies": "same stream, before and after each solve"}}
-    del sb, sx, so
+    del sb, so
 
     levels = s.levels
     del s
