@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "gpmg_internal.cuh"
+#include <nvtx3/nvToolsExt.h>
 
 namespace gpmg {
 
@@ -365,6 +366,13 @@ struct gp_ctx {
     Ctx c;
 };
 
+// an NVTX range around each entry point (and each solver iteration), for
+// profilers' timelines; no effect without a profiler attached
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
+
 static gp_status fail(gp_ctx *ctx, gp_status s, const char *m)
 {
     if (ctx) snprintf(ctx->c.msg, sizeof ctx->c.msg, "%s", m);
@@ -552,12 +560,14 @@ static gp_status geometry_finish(gp_ctx *ctx, const double *phi, int phi_fluid_p
 
 gp_status geometry_build(gp_ctx *ctx, const double *phi, int phi_fluid_positive)
 {
+    Range nvtx_range("geometry_build");
     if (!ctx || !phi) return GP_INVALID;
     return geometry_finish(ctx, phi, phi_fluid_positive);
 }
 
 gp_status geometry_build_shape(gp_ctx *ctx, const gp_shape *shape, double t, gp_body *body_out)
 {
+    Range nvtx_range("geometry_build_shape");
     if (!ctx || !shape || shape->kind < GP_CIRCLE || shape->kind > GP_FLOWER) return GP_INVALID;
     if (shape->orbit_r != 0.0 && !(shape->orbit_period > 0.0)) return GP_INVALID;
     const double two_pi = 6.283185307179586;
@@ -768,6 +778,7 @@ gp_status gp_cycle(gp_ctx *ctx, double *x, const double *b)
 
 gp_status mg_solve(gp_ctx *ctx, double *x, const double *b, double tol, gp_report *rep)
 {
+    Range nvtx_range("mg_solve");
     if (!ctx || !x || !b || !(tol >= 0.0)) return GP_INVALID;
     gp_status s = ensure_coarse(ctx);
     if (s != GP_OK) return s;
@@ -807,6 +818,7 @@ gp_status mg_solve(gp_ctx *ctx, double *x, const double *b, double tol, gp_repor
         for (k = 1; multi ? cycles < c->prm.max_cycles : k <= c->prm.max_cycles; k++) {
             int which = (kry ? 2 : 0) + (mixed ? 1 : 0);
             if (multi) c->inner_now = std::min(c->inner_now, c->prm.max_cycles - cycles);
+            Range iter_range("mg_solve iteration");
             if (!run_graph(c, which, x, b)) solve_iteration(c, which, x, b);
             const int done = kry ? 2 : multi ? c->inner_now : 1;
             cycles += done;
@@ -876,6 +888,7 @@ gp_status cn_step(gp_ctx *ctx, double *x, double *N1, double *N2, int step, cons
                   double dt, double Re, const gp_body *body, const gp_walls *walls, double tol, double eps, int kmax,
                   gp_cn_report *rep)
 {
+    Range nvtx_range("cn_step");
     if (!ctx || !x || !N1 || !N2 || step < 0 || !(dt > 0.0) || !(Re > 0.0) || !(tol >= 0.0) || kmax < 1)
         return GP_INVALID;
     Ctx *c = &ctx->c;
@@ -1023,6 +1036,7 @@ gp_status gp_cycle_t(gp_ctx *ctx, double *lam, const double *c)
 
 gp_status mg_solve_t(gp_ctx *ctx, double *lam, const double *c, double tol, gp_report *rep)
 {
+    Range nvtx_range("mg_solve_t");
     if (!lam || !c || !(tol >= 0.0)) return GP_INVALID;
     gp_status st = adjoint_ready(ctx, 0, false);
     if (st != GP_OK) return st;
@@ -1036,6 +1050,7 @@ gp_status cn_step_adjoint(gp_ctx *ctx, int step, const double *x_m, const double
                           const double *xbar_next, double *xbar_m, double *nbar0, double *nbar1, double *nbar2,
                           double *fbar, double *abar)
 {
+    Range nvtx_range("cn_step_adjoint");
     if (!ctx || !x_m || !xbar_next || !xbar_m || !nbar0 || !nbar1 || !nbar2 || !fbar || !abar || step < 0 ||
         !(dt > 0.0) || !(Re > 0.0) || !(tol >= 0.0))
         return GP_INVALID;
