@@ -383,6 +383,18 @@ constexpr int TT_RLO = 10;           // rows loaded above (and below) the owned 
 constexpr int TT_CLO = 16;           // columns loaded left of the owned ones (TMA x offsets: multiples of 16 bytes)
 constexpr unsigned long long TT_WAIT_NS = 2000000000ull;  // bound on the wait for the tile copies
 template <typename T> __host__ __device__ constexpr int tt_lh() { return TileGeom<T>::TH + 2 * TT_RLO; }
+// every TMA x coordinate (c0 - TT_CLO with c0 a multiple of TW) and the window
+// width must be whole 16-byte units of the one-byte box-code map, which makes
+// them whole units of the value frames too
+static_assert(TT_CLO % 16 == 0, "the box-code map's x coordinate must be a multiple of 16 bytes");
+static_assert(TileGeom<float>::TW % 16 == 0 && TileGeom<double>::TW % 16 == 0, "tile widths: multiples of 16");
+static_assert(TileGeom<float>::LW % 16 == 0 && TileGeom<double>::LW % 16 == 0, "window widths: multiples of 16");
+// the colour windows stay inside the loaded window: colour 0 reaches 9 cells
+// below / 8 above the owned ones and a box reads one row (column) below and two
+// above (right of) its cell
+static_assert(TT_RLO >= 10 && TT_CLO >= 10, "halo too small for the five-colour window");
+static_assert(TileGeom<float>::LW - TT_CLO - TileGeom<float>::TW >= 10 &&
+              TileGeom<double>::LW - TT_CLO - TileGeom<double>::TW >= 10, "right halo too small");
 
 template <typename T> __host__ __device__ constexpr size_t tt_smem()
 {
