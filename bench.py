@@ -100,16 +100,16 @@ class ClockSampler:
 
 def kernel_source_sha1():
     """sha1 of the source of the roofline kernel (the box constants, the box
-    solve and the tiled sweep in ops.cu): DRAM traffic measured by ncu stays
-    valid while this text is unchanged."""
+    solve and the streaming sweep in ops.cu): DRAM traffic measured by ncu
+    stays valid while this text is unchanged."""
     src = open(os.path.join(ROOT, "paper_1911_00994_gb300", "csrc", "ops.cu")).read()
     parts = []
     a = src.index("template <typename T> struct BoxK")
     parts.append(src[a:src.index("template <typename T> struct LevelArgs", a)])
-    a = src.index("__device__ __forceinline__ void box_solve(")
-    parts.append(src[a:src.index("    p[0] += dp;\n}\n", a)])
-    a = src.index("template <typename T> struct TileGeom;")
-    b = src.index("k_box_tma(", a)
+    a = src.index("template <typename T, bool ALL = false, typename View>")
+    parts.append(src[a:src.index("// the same on frames of row pitch", a)])
+    a = src.index("template <typename T> struct WaveGeom;")
+    b = src.index("k_box_wave(", a)
     parts.append(src[a:src.index("\n}\n", b)])
     return hashlib.sha1("".join(parts).encode()).hexdigest()
 
@@ -701,13 +701,15 @@ def run_ours(args):
         return None
 
     hbm, src = peaks()
-    # algorithmic bytes of one launch of the FP32 tiled full-box sweep (all
-    # five colours): per cell of the N x N grid, read x and b (3 words each)
-    # and the box-code byte, write x (3 words)
+    # algorithmic bytes of one launch of the FP32 streaming full-box sweep
+    # (all five colours): per cell of the N x N grid, read x and b (3 words
+    # each) and the box-code byte, write x (3 words)
     bytes_per_launch = N * N * (9 * 4 + 1.0)
     avg_ms = box_ms / max(1, nbox)
     achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
-    tr = ncu_traffic("k_box_tma<float>", N)
+    # levels from 4096^2 stream down strips of rows, smaller ones use tiles
+    roof_kernel = "k_box_wave<float>" if N >= 4096 else "k_box_tma<float>"
+    tr = ncu_traffic(roof_kernel, N) if N >= 4096 else None
     line = {
         "metric": METRIC, "value": value, "unit": "V-cycles/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -733,7 +735,8 @@ def run_ours(args):
         "largest_solve_flower7_8192": big,
         "cavity_cn_steps": cav,
         "accuracy_sol_exa": acc,
-        "roofline": {"kernel": "k_box_tma<float> (finest-level full-box sweep, five colours in one pass)", "bound": "hbm",
+        "roofline": {"kernel": roof_kernel + " (finest-level full-box sweep, five colours in one pass)",
+                     "bound": "hbm",
                      "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "peak_source": src, "avg_launch_ms": avg_ms, "launches": nbox,
                      "timing": "CUDA events on the solver stream around every launch, second pass of the timed steps",

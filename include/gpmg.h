@@ -91,6 +91,9 @@ typedef struct gp_params {
                            many as the last corrections' reduction rate predicts are still needed
                            to reach tol, so the cycle count stays that of one cycle per
                            correction while the FP64 residuals are fewer */
+    int wave_min;       /* tiled levels with at least this many cells per side stream their full
+                           boxes down strips of rows (same iterate as the tiles); 0: 4096;
+                           negative: never */
 } gp_params;
 
 #define GP_MAX_INNER 8

@@ -26,6 +26,9 @@ enum RowKind : uint8_t { K_BCU = 0, K_EXTRAP = 1, K_COPY = 2, K_WALL = 3, K_BOXG
 constexpr int MAX_LEVELS = 16;
 constexpr int MAX_MARCH = 64;
 constexpr int NSCAL = 32;
+// scalar slot of an FP32 iterate holding its pending pressure shift (the
+// internal and ghost pressures are the stored ones plus this value)
+constexpr int PSHIFT_SLOT = 1;
 constexpr int MAX_CUTCOL = 64;  // colours of the cut boxes
 constexpr int ADJ_KMAX = 8;  // Picard iterations cn_step_adjoint can differentiate
 // box codes (one byte per cell): a full box (internal cell, no ghost face)

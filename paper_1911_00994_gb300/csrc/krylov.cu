@@ -20,6 +20,7 @@ void fix_inactive_t(Ctx *c, double *lam, const double *cc);
 template <typename T> void cycle_rec(Ctx *c, int lev, T *x, const T *b);
 template <typename T> void zero_vec(Ctx *c, T *x, long long n);
 void to_float(Ctx *c, const double *a, float *b, long long n);
+void float_to_double(Ctx *c, const float *e, double *y, long long n);
 
 enum { KS_RHO = 0, KS_ALPHA = 1, KS_OMEGA = 2, KS_BETA = 3 };
 
@@ -166,8 +167,7 @@ static void precondition(Ctx *c, const double *v, double *y)
         to_float(c, v, l0.bf, n);
         zero_vec<float>(c, l0.xf, n);
         cycle_rec<float>(c, 0, l0.xf, l0.bf);
-        k_to_double<<<vblocks(n), 256, 0, c->stream>>>(l0.xf, y, n);
-        c->launches++;
+        float_to_double(c, l0.xf, y, n);
     } else {
         zero_vec<double>(c, y, n);
         cycle_rec<double>(c, 0, y, v);

@@ -20,6 +20,7 @@ namespace gpmg {
 constexpr int SMALL_N = 64;  // levels whose whole relaxation runs in one block
 constexpr size_t SMALL_STAGE_BYTES = 200 * 1024;  // x and b of such a level staged in shared memory up to this size
 constexpr int TILE_MIN_N = 128;  // default smallest FP32 level swept by TMA tiles (gp_params.tile_min overrides)
+constexpr int WAVE_MIN_N = 4096;  // default smallest tiled level swept down strips of rows (gp_params.wave_min)
 constexpr int GHOST_BLOCK_ROWS = 1024;  // at most this many ghost-class rows: the lambda sweeps in one block
 constexpr int CUT_SPLIT = 64;  // cut boxes per colour above which the cut sweep leaves a single block
 constexpr int CUT_COLOUR_LAUNCHES = 6;  // at most this many colours: one launch per colour, else one cluster
@@ -234,7 +235,7 @@ __global__ void k_ghost_residual(GhostList gh, int nrows, const T *x, const T *b
 // mean row (h^2 * sum of internal p) and the norm; one block
 template <typename T, typename R>
 __global__ void k_residual_final(const double *part, int nb, const T *b, R *r, long long imean, double h2,
-                                 unsigned long long *maxbits, double *out)
+                                 unsigned long long *maxbits, double *out, const T *x, const int *nint)
 {
     __shared__ double ss[256], sm[256];
     double s = 0.0, m = 0.0;
@@ -253,7 +254,9 @@ __global__ void k_residual_final(const double *part, int nb, const T *b, R *r, l
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        double rm = (double)b[imean] - h2 * ss[0];
+        // an FP32 iterate carries its pressure shift unapplied (PSHIFT_SLOT)
+        const double sig = sizeof(T) == 4 ? (double)x[imean + PSHIFT_SLOT] * (double)*nint : 0.0;
+        double rm = (double)b[imean] - h2 * (ss[0] + sig);
         r[imean] = (R)rm;
         double g = __longlong_as_double((long long)*maxbits);
         double nrm = nanmax(nanmax(sm[0], g), fabs(rm));
@@ -264,27 +267,45 @@ __global__ void k_residual_final(const double *part, int nb, const T *b, R *r, l
 
 // ------------------------------------------------------------ box smoother
 
-// full boxes (no ghost border): Schur complement of the pressure unknown,
-// colour (i + 3 j) mod 5; borders that are not internal stay frozen
+// One frame's slots around a box, addressed by (rows up, columns right) of
+// the box's cell: a frame of uniform row pitch (global memory or a tile), or
+// four separately addressed rows -1 .. 2 (a ring of rows in shared memory).
+template <typename T> struct PitchRows {
+    T *c;
+    int pitch;
+    __device__ __forceinline__ T &at(int dr, int dc) const { return c[dr * pitch + dc]; }
+};
+template <typename T> struct RingRows {
+    T *r[4];
+    __device__ __forceinline__ T &at(int dr, int dc) const { return r[dr + 1][dc]; }
+};
+
 // Box relaxation of one cell without ghost borders (Sect. 4.1.1): Schur
-// complement of the pressure unknown.  u, v, p point at the cell's slot in
-// arrays of row pitch `pitch` (global frames or a shared-memory tile); bu, bv,
-// bW, bE, bS, bN, bC: the right-hand side of the box's five rows.  W, E, S,
-// Nn: the faces that are internal (the others stay frozen); ALL: all four are.
-template <typename T, bool ALL = false>
-__device__ __forceinline__ void box_solve(T *u, T *v, T *p, const int pitch, const T bW, const T bE, const T bS,
-                                          const T bN, const T bC, const T xi, bool W, bool E, bool S, bool Nn,
-                                          const BoxK<T> &K)
+// complement of the pressure unknown.  U, V, Pv: the u, v and p frames around
+// the cell; bW, bE, bS, bN, bC: the right-hand side of the box's five rows.
+// W, E, S, Nn: the faces that are internal (the others stay frozen); ALL: all
+// four are.
+template <typename T, bool ALL = false, typename View>
+__device__ __forceinline__ void box_solve_v(const View &U, const View &V, const View &Pv, const T bW, const T bE,
+                                            const T bS, const T bN, const T bC, const T xi, bool W, bool E, bool S,
+                                            bool Nn, const BoxK<T> &K)
 {
-    const int Pp = pitch;
     const T a = K.a, d = K.d, q = K.q;
     if (ALL) W = E = S = Nn = true;
     T rW = 0, rE = 0, rS = 0, rN = 0;
-    if (W) rW = bW - (d * u[0] - a * (u[1] + u[-1] + u[Pp] + u[-Pp]) + q * (p[0] - p[-1]));
-    if (E) rE = bE - (d * u[1] - a * (u[2] + u[0] + u[1 + Pp] + u[1 - Pp]) + q * (p[1] - p[0]));
-    if (S) rS = bS - (d * v[0] - a * (v[1] + v[-1] + v[Pp] + v[-Pp]) + q * (p[0] - p[-Pp]));
-    if (Nn) rN = bN - (d * v[Pp] - a * (v[Pp + 1] + v[Pp - 1] + v[2 * Pp] + v[0]) + q * (p[Pp] - p[0]));
-    T rC = bC - (q * (u[1] - u[0] + v[Pp] - v[0]) - xi);
+    if (W)
+        rW = bW - (d * U.at(0, 0) - a * (U.at(0, 1) + U.at(0, -1) + U.at(1, 0) + U.at(-1, 0)) +
+                   q * (Pv.at(0, 0) - Pv.at(0, -1)));
+    if (E)
+        rE = bE - (d * U.at(0, 1) - a * (U.at(0, 2) + U.at(0, 0) + U.at(1, 1) + U.at(-1, 1)) +
+                   q * (Pv.at(0, 1) - Pv.at(0, 0)));
+    if (S)
+        rS = bS - (d * V.at(0, 0) - a * (V.at(0, 1) + V.at(0, -1) + V.at(1, 0) + V.at(-1, 0)) +
+                   q * (Pv.at(0, 0) - Pv.at(-1, 0)));
+    if (Nn)
+        rN = bN - (d * V.at(1, 0) - a * (V.at(1, 1) + V.at(1, -1) + V.at(2, 0) + V.at(0, 0)) +
+                   q * (Pv.at(1, 0) - Pv.at(0, 0)));
+    T rC = bC - (q * (U.at(0, 1) - U.at(0, 0) + V.at(1, 0) - V.at(0, 0)) - xi);
     // eliminating the velocities leaves c1 dp = rC - c0 for the pressure;
     // each direction contributes to c0, and c1 depends only on which faces
     // take part
@@ -322,16 +343,26 @@ __device__ __forceinline__ void box_solve(T *u, T *v, T *p, const int pitch, con
     // velocity corrections with dp known
     T fW = rW - q * dp, fE = rE + q * dp, fS = rS - q * dp, fN = rN + q * dp;
     if (W && E) {
-        u[0] += (d * fW + a * fE) * K.idet;
-        u[1] += (a * fW + d * fE) * K.idet;
-    } else if (W) u[0] += fW * K.id;
-    else if (E) u[1] += fE * K.id;
+        U.at(0, 0) += (d * fW + a * fE) * K.idet;
+        U.at(0, 1) += (a * fW + d * fE) * K.idet;
+    } else if (W) U.at(0, 0) += fW * K.id;
+    else if (E) U.at(0, 1) += fE * K.id;
     if (S && Nn) {
-        v[0] += (d * fS + a * fN) * K.idet;
-        v[Pp] += (a * fS + d * fN) * K.idet;
-    } else if (S) v[0] += fS * K.id;
-    else if (Nn) v[Pp] += fN * K.id;
-    p[0] += dp;
+        V.at(0, 0) += (d * fS + a * fN) * K.idet;
+        V.at(1, 0) += (a * fS + d * fN) * K.idet;
+    } else if (S) V.at(0, 0) += fS * K.id;
+    else if (Nn) V.at(1, 0) += fN * K.id;
+    Pv.at(0, 0) += dp;
+}
+
+// the same on frames of row pitch `pitch`, u, v, p at the cell's slot
+template <typename T, bool ALL = false>
+__device__ __forceinline__ void box_solve(T *u, T *v, T *p, const int pitch, const T bW, const T bE, const T bS,
+                                          const T bN, const T bC, const T xi, bool W, bool E, bool S, bool Nn,
+                                          const BoxK<T> &K)
+{
+    box_solve_v<T, ALL>(PitchRows<T>{u, pitch}, PitchRows<T>{v, pitch}, PitchRows<T>{p, pitch}, bW, bE, bS, bN, bC,
+                        xi, W, E, S, Nn, K);
 }
 
 // the same with the right-hand side read at bu, bv, bp (bN at bv[bpitch])
@@ -538,6 +569,233 @@ __global__ void __launch_bounds__(TileGeom<T>::THREADS) k_box_tma(const __grid_c
         V *dst = (V *)(y + f * A.F + (long long)(r0 + rr) * A.P + c0) + vv;
         *dst = *src;
     }
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x < NSCAL) y[3 * A.F + threadIdx.x] = x[3 * A.F + threadIdx.x];
+}
+
+// All five colours of the full boxes in one pass, streaming down strips of
+// rows.  Block (sx, sy) owns TW slot columns [c0, c0 + TW) of the frame rows
+// [r0, r0 + SH) (all three frames).  Its colour-c window is the same as the
+// tile sweep's: cells within 2 (4 - c) + 1 columns (rows) before and 2 (4 - c)
+// after the owned ones.  Instead of one window per tile, the block walks up
+// its rows in steps of R cell rows: at step s colour c relaxes the cell rows
+// [A0 + s R - 2 c, A0 + s R - 2 c + R) of its window (A0 = r0 - 10), one row
+// per warp, a lane per box of the row.  A box reads and writes only slots of
+// boxes at most two rows away, so with colour c trailing colour c - 1 by two
+// rows every box sees exactly the updates of the colour-by-colour sweep:
+// lower colours within two rows are done (in an earlier step, or earlier in
+// this step), higher colours within two rows are not yet.  The windows only
+// widen the owned slots horizontally, so a strip of rows recomputes 9 of
+// every TW + 9 boxes (the 32-row tiles recompute 48%).
+//
+// The frames stream through a ring of RB = 4 R rows in shared memory: chunk k
+// (frame rows [A0 + k R, A0 + k R + R)) is brought by TMA into ring rows
+// [k R mod RB, ...).  Step s reads chunks s - 1 .. s + 1; chunk s + 2 is
+// copied during step s into the slot of chunk s - 2, which the block wrote
+// out (owned rows, 16 bytes a lane) at the end of step s - 1, when its rows
+// had become final.  The right-hand side is read from global memory, pulled
+// into L2 two steps ahead by a bulk tensor prefetch.  As in the tile sweep
+// the result goes to the level's other vector y, a complete copy of the
+// swept x.
+template <typename T> struct WaveGeom;
+template <> struct WaveGeom<float> {
+    static constexpr int TW = 128, LW = 160;
+};
+template <> struct WaveGeom<double> {
+    static constexpr int TW = 64, LW = 96;
+};
+constexpr int WV_R = 8;               // cell rows per step and frame rows per chunk; one warp each
+constexpr int WV_RB = 4 * WV_R;       // ring rows
+constexpr int WV_THREADS = 32 * WV_R;
+constexpr int WV_A = 10;              // colour 0's window starts 10 rows below the owned ones
+// colour 4 trails colour 0 by 8 rows and a box reads one row below its cell:
+// step s reads frame rows [A0 + s R - 8, A0 + s R + R + 3), inside chunks s - 1 .. s + 1
+static_assert(WV_R >= 8 && WV_R + 3 <= 2 * WV_R, "a step must read only chunks s - 1 .. s + 1");
+// R rows up move the colour pattern (i + 3 j) mod 5 by one column: -3 R = 1 (mod 5)
+static_assert((3 * WV_R) % 5 == 4, "the per-step phase advance assumes -3 R = 1 (mod 5)");
+// every box of a colour row fits the 32 lanes of its warp
+static_assert((WaveGeom<float>::TW + 16 + 1 + 4) / 5 <= 32 && (WaveGeom<double>::TW + 16 + 1 + 4) / 5 <= 32,
+              "a colour row holds more boxes than a warp has lanes");
+// TMA: x coordinates c0 - TT_CLO and widths in whole 16-byte units of the box-code map
+static_assert(WaveGeom<float>::TW % 16 == 0 && WaveGeom<double>::TW % 16 == 0, "strip widths: multiples of 16");
+static_assert(WaveGeom<float>::LW % 16 == 0 && WaveGeom<double>::LW % 16 == 0, "window widths: multiples of 16");
+static_assert(WaveGeom<float>::LW - TT_CLO - WaveGeom<float>::TW >= 10 &&
+              WaveGeom<double>::LW - TT_CLO - WaveGeom<double>::TW >= 10, "right halo too small");
+// the write-out: one 16-byte vector per lane covers a strip row of a frame
+static_assert(WaveGeom<float>::TW * sizeof(float) <= 32 * 16 && WaveGeom<double>::TW * sizeof(double) <= 32 * 16,
+              "a strip row must be at most 32 vectors of 16 bytes");
+
+template <typename T> __host__ __device__ constexpr size_t wv_smem()
+{
+    return (size_t)WV_RB * WaveGeom<T>::LW * (3 * sizeof(T) + 1) + 4 * sizeof(uint64_t);
+}
+
+// the four ring rows -1 .. 2 around a box, as element offsets into a frame
+template <typename T> struct RingRows4 {
+    T *c;
+    int o0, o1, o2, o3;
+    __device__ __forceinline__ T &at(int dr, int dc) const
+    {
+        return c[(dr < 0 ? o0 : dr == 0 ? o1 : dr == 1 ? o2 : o3) + dc];
+    }
+};
+
+// wait for the phase of the given parity of the barrier, at most `ns` nanoseconds
+__device__ __forceinline__ bool mbar_wait_parity_bounded(uint64_t *bar, unsigned parity, unsigned long long ns)
+{
+    unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > ns) return false;
+    return true;
+}
+
+__device__ __forceinline__ void tma_prefetch_3d(const CUtensorMap *map, int x, int y, int z)
+{
+    asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];"
+                 :
+                 : "l"(map), "r"(x), "r"(y), "r"(z)
+                 : "memory");
+}
+
+// the right-hand side of the box rows of cell (i, j): bW, bE, bS, bN, bC
+// (32-bit slot offsets: 3 F + P stays below 2^31 on the levels swept here)
+template <typename T> __device__ __forceinline__ void wave_rhs(const T *b, int F, int P, int i, int j, T *q)
+{
+    const int gs = (j + 1) * P + (i + 1);
+    q[0] = b[gs];
+    q[1] = b[gs + 1];
+    q[2] = b[F + gs];
+    q[3] = b[F + gs + P];
+    q[4] = b[2 * F + gs];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(WV_THREADS) k_box_wave(const __grid_constant__ CUtensorMap mx,
+                                                         const __grid_constant__ CUtensorMap mc,
+                                                         const __grid_constant__ CUtensorMap mb, LevelArgs<T> A,
+                                                         const T *x, const T *b, T *y, int SH, unsigned *err)
+{
+    constexpr int TW = WaveGeom<T>::TW, LW = WaveGeom<T>::LW, R = WV_R, RB = WV_RB, FR = RB * LW;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    T *su = (T *)smem_raw;
+    T *sv = su + FR;
+    T *sp = sv + FR;
+    uint8_t *sc = (uint8_t *)(sp + FR);
+    uint64_t *bar = (uint64_t *)(sc + FR);
+    const int N = A.N;
+    const int c0 = blockIdx.x * TW, r0 = blockIdx.y * SH;
+    const int col0 = c0 - TT_CLO, A0 = r0 - WV_A;
+    const int rend = min(r0 + SH, N + 2);
+    // colour 4's window ends at min(r0 - 1 + SH, N) and its rows at step s
+    // start at A0 + s R - 8; every colour's window ends at the same step
+    const int S = (min(r0 - 1 + SH, N) - A0 + 8 + R - 1) / R;
+    const int NCH = S + 1;  // chunks 0 .. S
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < 4; q++)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar + q)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    auto load_chunk = [&](int k) {
+        const int q = k & 3;
+        const unsigned bytes = (unsigned)(R * LW * (3 * sizeof(T) + 1));
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar + q)), "r"(bytes)
+                     : "memory");
+        for (int f = 0; f < 3; f++) tma_load_3d(su + f * FR + q * R * LW, &mx, col0, A0 + k * R, f, bar + q);
+        tma_load_2d(sc + q * R * LW, &mc, col0, A0 + k * R, bar + q);
+        tma_prefetch_3d(&mb, max(col0, 0), max(A0 + k * R, 0), 0);  // a hint: kept inside the tensor
+    };
+    if (threadIdx.x == 0) {
+        load_chunk(0);
+        load_chunk(1);
+    }
+    const T xi = x[3 * A.F];
+    const int F = (int)A.F, P = A.P;
+    // Lane `lane` of warp `warp` relaxes, at step s, the box of colour c in
+    // cell row j = A0 + s R - 2 c + warp and column i = iu_c + ph_c + 5 lane,
+    // the first cell of the colour pattern (i + 3 j) mod 5 = c at or after
+    // iu_c plus every fifth; R = 8 rows move the pattern by one column, so
+    // ph_c advances by one (mod 5) per step.  bq[c]: the right-hand side of
+    // that box, loaded one step ahead of its use.
+    int ph[5];
+    T bq[5][5];
+#pragma unroll
+    for (int c = 0; c < 5; c++) {
+        const int lo = 2 * (4 - c) + 1, hi = lo - 1, iu = c0 - 1 - lo, j = A0 - 2 * c + warp;
+        ph[c] = (int)((unsigned)(c + (5 << 28) - 3 * j - iu) % 5u);
+        const int i = iu + ph[c] + 5 * lane;
+#pragma unroll
+        for (int k = 0; k < 5; k++) bq[c][k] = (T)0;
+        if (j >= max(r0 - 1 - lo, 0) && j < min(r0 - 1 + SH + hi, N) && i >= max(iu, 0) && i < min(c0 - 1 + TW + hi, N))
+            wave_rhs(b, F, P, i, j, bq[c]);
+    }
+    using V = typename Vec16<T>::type;
+    constexpr int VW = 16 / sizeof(T);
+    // owned rows of chunk k, one warp per row and one 16-byte vector per lane
+    auto write_chunk = [&](int k) {
+        const int X = A0 + k * R + warp, col = c0 + lane * VW;
+        if (X >= r0 && X < rend && lane * VW < TW && col < A.P) {
+            const int o = ((k * R + warp) & (RB - 1)) * LW + TT_CLO + lane * VW;
+            const long long g = (long long)X * A.P + col;
+#pragma unroll
+            for (int f = 0; f < 3; f++) *(V *)(y + f * A.F + g) = *(const V *)(su + f * FR + o);
+        }
+    };
+    for (int s = 0; s < S; s++) {
+        bool ok = true;
+        if (s == 0) ok = mbar_wait_parity_bounded(bar, 0, TT_WAIT_NS);
+        ok = mbar_wait_parity_bounded(bar + ((s + 1) & 3), ((s + 1) >> 2) & 1, TT_WAIT_NS) && ok;
+        if (!__syncthreads_and(ok)) {
+            // copies still in flight get a second bounded wait before the
+            // block leaves; the NaN in the scalar block makes the solve fail
+            if (s == 0) mbar_wait_parity_bounded(bar, 0, TT_WAIT_NS / 2);
+            mbar_wait_parity_bounded(bar + ((s + 1) & 3), ((s + 1) >> 2) & 1, TT_WAIT_NS / 2);
+            if (threadIdx.x == 0) {
+                atomicOr(err + 2, 1u);
+                y[3 * A.F] = (T)NAN;
+            }
+            return;
+        }
+        // chunk s + 2 into the slot of chunk s - 2 (written out before the
+        // barrier above); the generic-proxy reads are ordered before the copy
+        if (threadIdx.x == 0 && s + 2 < NCH) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            load_chunk(s + 2);
+        }
+#pragma unroll
+        for (int c = 0; c < 5; c++) {
+            const int lo = 2 * (4 - c) + 1, hi = lo - 1, iu = c0 - 1 - lo;
+            const int jlo = max(r0 - 1 - lo, 0), jhi = min(r0 - 1 + SH + hi, N);
+            const int ilo = max(iu, 0), ihi = min(c0 - 1 + TW + hi, N);
+            const int t = s * R + warp - 2 * c, j = A0 + t;  // frame rows j .. j + 3 = J - 1 .. J + 2
+            const int i = iu + ph[c] + 5 * lane;
+            if (j >= jlo && j < jhi && i >= ilo && i < ihi) {
+                const int lc = i + 1 - col0;
+                const int o0 = ((t) & (RB - 1)) * LW + lc, o1 = ((t + 1) & (RB - 1)) * LW + lc;
+                const int o2 = ((t + 2) & (RB - 1)) * LW + lc, o3 = ((t + 3) & (RB - 1)) * LW + lc;
+                const unsigned code = sc[o1];
+                if (code & BOX_FULL) {
+                    const RingRows4<T> U{su, o0, o1, o2, o3}, Vv{sv, o0, o1, o2, o3}, Pv{sp, o0, o1, o2, o3};
+                    const T *q = bq[c];
+                    if (code == BOX_ALL)
+                        box_solve_v<T, true>(U, Vv, Pv, q[0], q[1], q[2], q[3], q[4], xi, true, true, true, true, A.K);
+                    else
+                        box_solve_v<T>(U, Vv, Pv, q[0], q[1], q[2], q[3], q[4], xi, code & BOX_W, code & BOX_E,
+                                       code & BOX_S, code & BOX_N, A.K);
+                }
+            }
+            // this colour's box of the next step: R rows up, the pattern one column on
+            ph[c] = ph[c] == 4 ? 0 : ph[c] + 1;
+            const int jn = j + R, in = iu + ph[c] + 5 * lane;
+            if (jn >= jlo && jn < jhi && in >= ilo && in < ihi) wave_rhs(b, F, P, in, jn, bq[c]);
+            __syncthreads();
+        }
+        // chunk s - 1 is final: its rows are written by boxes of rows at most
+        // two below, the last of them colour 4 of this step
+        if (s >= 1) write_chunk(s - 1);
+    }
+    write_chunk(S - 1);
+    write_chunk(S);
     if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x < NSCAL) y[3 * A.F + threadIdx.x] = x[3 * A.F + threadIdx.x];
 }
 
@@ -885,7 +1143,7 @@ __global__ void k_scalar_partial(LevelArgs<T> A, const T *x, const T *b, double 
 // xi <- mean(div u - b_c); shift <- (b_mean - h^2 sum p) / (h^2 n_int)
 template <typename T>
 __global__ void k_scalar_final(const double *part, int nb, T *x, const T *b, long long imean, double h2, const int *nint,
-                               double *shift)
+                               double *shift, int defer)
 {
     __shared__ double ss[256], sm[256];
     double s = 0.0, m = 0.0;
@@ -906,7 +1164,11 @@ __global__ void k_scalar_final(const double *part, int nb, T *x, const T *b, lon
     if (threadIdx.x == 0) {
         double n = (double)*nint;
         x[imean] = (T)(ss[0] / n);
-        shift[0] = ((double)b[imean] - h2 * sm[0]) / (h2 * n);
+        const double sh = ((double)b[imean] - h2 * sm[0]) / (h2 * n);
+        shift[0] = sh;
+        // deferred: the shift that makes the stored pressures satisfy the
+        // mean row, kept beside xi instead of being added to every p
+        if (defer) x[imean + PSHIFT_SLOT] = (T)sh;
     }
 }
 
@@ -1162,8 +1424,12 @@ __global__ void __launch_bounds__(256) k_prolong4(int Nf, int Pf, long long Ff, 
     if (row == 0 && c0 < NSCAL)
         for (int q = 0; q < 4; q++) y[3 * Ff + c0 + q] = c0 + q == 0 ? x[3 * Ff] + eH[3 * Fc] : x[3 * Ff + c0 + q];
     const uint8_t *tc[3] = {tUc, tVc, tPc};
+    // an FP32 coarse iterate carries its pressure shift unapplied: every
+    // pressure correction (weights summing to one) gets it once
+    const T sigH = sizeof(T) == 4 ? eH[3 * Fc + PSHIFT_SLOT] : (T)0;
 #pragma unroll
     for (int g = 0; g < 3; g++) {
+        const T sg = g == G_P ? sigH : (T)0;
         uint8_t pc[4];
         T xv[4], out[4];
         ldt4(pcode + g * Ff + s0, pc);
@@ -1187,7 +1453,7 @@ __global__ void __launch_bounds__(256) k_prolong4(int Nf, int Pf, long long Ff, 
                 for (int a = 0; a < nj; a++)
                     for (int bb = 0; bb < ni; bb++)
                         sacc += (wj[a] * wi[bb]) * e[(long long)(KJ[a] + 1) * Pc + (KI[bb] + 1)];
-                out[q] = xv[q] + sacc;
+                out[q] = xv[q] + (sacc + sg);
                 continue;
             }
             for (int a = 0; a < nj; a++)
@@ -1197,7 +1463,7 @@ __global__ void __launch_bounds__(256) k_prolong4(int Nf, int Pf, long long Ff, 
                     sacc += w * e[(long long)(KJ[a] + 1) * Pc + (KI[bb] + 1)];
                     ws += w;
                 }
-            if (ws > (T)0) out[q] = xv[q] + (ws == (T)1 ? sacc : sacc / ws);
+            if (ws > (T)0) out[q] = xv[q] + ((ws == (T)1 ? sacc : sacc / ws) + sg);
         }
         st4(y + g * Ff + s0, out);
     }
@@ -1233,10 +1499,20 @@ __global__ void k_to_float(const double *a, float *b, long long n)
     if (k < n) b[k] = (float)a[k];
 }
 
-__global__ void k_add_float(double *x, const float *e, long long n)
+// y (+)= e for an FP32 iterate e of the finest level, its pending pressure
+// shift applied to the internal and ghost pressures (and not copied itself)
+__global__ void k_float_to_double(long long F, const uint8_t *tP, const float *e, double *y, long long n, int add)
 {
     long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (k < n) x[k] += (double)e[k];
+    if (k >= n) return;
+    double v = (double)e[k];
+    if (k >= 2 * F && k < 3 * F) {
+        const uint8_t t = tP[k - 2 * F];
+        if (t == T_INTERNAL || t == T_GHOST) v = (double)(e[k] + e[3 * F + PSHIFT_SLOT]);
+    } else if (k == 3 * F + PSHIFT_SLOT) {
+        v = 0.0;
+    }
+    y[k] = add ? y[k] + v : v;
 }
 
 // ---------------------------------------------- one-block kernels, small levels
@@ -1451,13 +1727,13 @@ static EncodeTiledFn encode_fn()
 // tensor map over `nf` frames of a level (x: column, y: frame row, z:
 // frame when nf = 3), box = the tile window of k_box_tma
 static bool encode_frames(CUtensorMap *m, const void *base, CUtensorMapDataType dt, int esize, const Level &l,
-                          long long frame_stride_bytes, int nf, int LW, int LH)
+                          long long frame_stride_bytes, int nf, int LW, int LH, int box_nf = 0)
 {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
     cuuint64_t dims[3] = {(cuuint64_t)l.P, (cuuint64_t)(l.N + 2), (cuuint64_t)nf};
     cuuint64_t strides[2] = {(cuuint64_t)l.P * esize, (cuuint64_t)frame_stride_bytes};
-    cuuint32_t box[3] = {(cuuint32_t)LW, (cuuint32_t)LH, (cuuint32_t)nf};
+    cuuint32_t box[3] = {(cuuint32_t)LW, (cuuint32_t)LH, (cuuint32_t)(box_nf > 0 ? box_nf : nf)};
     cuuint32_t es[3] = {1, 1, 1};
     return fn(m, dt, nf > 1 ? 3 : 2, const_cast<void *>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
@@ -1473,6 +1749,15 @@ template <typename T> static bool tiled(Ctx *c, int lev)
     // extra passes over memory they save
     int tmin = c->prm.tile_min != 0 ? c->prm.tile_min : sizeof(T) == 4 ? TILE_MIN_N : -1;
     return tmin >= 0 && l.N >= tmin && tile_scratch<T>(c, lev) && encode_fn();
+}
+
+// does this tiled level stream its full boxes down strips of rows (k_box_wave)
+template <typename T> static bool wave(Ctx *c, int lev)
+{
+    int wmin = c->prm.wave_min != 0 ? c->prm.wave_min : WAVE_MIN_N;
+    const Level &l = c->lv[lev];
+    // the sweep addresses the right-hand side with 32-bit slot offsets
+    return wmin >= 0 && l.N >= wmin && 3 * l.F + l.P < (1ll << 31) && tiled<T>(c, lev);
 }
 
 void prepare_cuts(Ctx *c)
@@ -1797,6 +2082,8 @@ void tiles_init()
     if (done) return;
     cudaFuncSetAttribute(k_box_tma<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tt_smem<double>());
     cudaFuncSetAttribute(k_box_tma<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tt_smem<float>());
+    cudaFuncSetAttribute(k_box_wave<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wv_smem<double>());
+    cudaFuncSetAttribute(k_box_wave<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wv_smem<float>());
     cudaFuncSetAttribute(k_smooth_small<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMALL_STAGE_BYTES);
     cudaFuncSetAttribute(k_smooth_small<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMALL_STAGE_BYTES);
     done = true;
@@ -1843,7 +2130,7 @@ template <typename T, typename R> void residual_into(Ctx *c, int lev, const T *x
     if (l.h_nrows > 0)
         k_ghost_residual<T, R><<<(l.h_nrows + 255) / 256, 256, 0, st>>>(l.gh, l.h_nrows, x, b, r, c->maxbits);
     double h = c->prm.L / (double)l.N;
-    k_residual_final<T, R><<<1, 256, 0, st>>>(c->part, nb, b, r, 3 * l.F, h * h, c->maxbits, c->red);
+    k_residual_final<T, R><<<1, 256, 0, st>>>(c->part, nb, b, r, 3 * l.F, h * h, c->maxbits, c->red, x, l.nint);
     c->launches += 2 + (l.h_nrows > 0);
 }
 
@@ -1862,7 +2149,43 @@ template <typename T> static void box_pass(Ctx *c, int lev, const T *in, T *out,
     cudaStream_t st = c->stream;
     LevelArgs<T> A = level_args<T>(c, lev);
     bool done = false;
-    if (out != in) {
+    if (out != in && wave<T>(c, lev)) {
+        constexpr int TW = WaveGeom<T>::TW, LW = WaveGeom<T>::LW;
+        const CUtensorMapDataType dt = sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+        const long long fs = l.F * (long long)sizeof(T);
+        CUtensorMap mx, mc, mb;
+        if (encode_frames(&mx, in, dt, (int)sizeof(T), l, fs, 3, LW, WV_R, 1) &&
+            encode_frames(&mc, l.bcode, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, l, l.F, 1, LW, WV_R) &&
+            encode_frames(&mb, b, dt, (int)sizeof(T), l, fs, 3, LW, WV_R, 3)) {
+            // strips of TW columns, each cut into segments of SH rows so that
+            // the grid is about one wave of resident blocks
+            static int resident = 0;
+            if (resident <= 0) {
+                int dev = 0, sms = 0, per_sm = 0;
+                cudaGetDevice(&dev);
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+                if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_box_wave<T>, WV_THREADS, wv_smem<T>()) !=
+                        cudaSuccess ||
+                    per_sm < 1) {
+                    cudaGetLastError();
+                    per_sm = 1;
+                }
+                resident = sms * per_sm;
+            }
+            const int gx = (l.P + TW - 1) / TW, rows = l.N + 2;
+            int nseg = resident / gx;
+            nseg = nseg < 1 ? 1 : nseg > (rows + WV_R - 1) / WV_R ? (rows + WV_R - 1) / WV_R : nseg;
+            int SH = (rows + nseg - 1) / nseg;
+            SH = (SH + WV_R - 1) / WV_R * WV_R;
+            nseg = (rows + SH - 1) / SH;
+            tmr_begin(c, KT_BOX_FULL, lev);
+            k_box_wave<T><<<dim3(gx, nseg), WV_THREADS, wv_smem<T>(), st>>>(mx, mc, mb, A, in, b, out, SH, c->err);
+            tmr_end(c, KT_BOX_FULL, lev);
+            c->launches++;
+            done = true;
+        }
+    }
+    if (out != in && !done) {
         constexpr int TW = TileGeom<T>::TW, LW = TileGeom<T>::LW, TH = TileGeom<T>::TH;
         const CUtensorMapDataType dt = sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
         CUtensorMap mx, mc;
@@ -1944,9 +2267,15 @@ template <typename T> void scalar_update(Ctx *c, int lev, T *x, const T *b)
     k_scalar_partial<T><<<nb, 256, 0, st>>>(A, x, b, c->part);
     tmr_end(c, KT_SCALAR, lev);
     double h = c->prm.L / (double)l.N;
-    k_scalar_final<T><<<1, 256, 0, st>>>(c->part, nb, x, b, 3 * l.F, h * h, l.nint, c->red + 1);
-    k_pshift<T><<<dim3((l.P / 4 + 255) / 256, l.N + 2), 256, 0, st>>>(A, x, c->red + 1);
-    c->launches += 3;
+    // FP32 iterates (the inner cycles of the mixed mode) keep the pressure
+    // shift pending: every row but the mean row is blind to a constant added
+    // to the internal and ghost pressures, so the shift is applied only where
+    // the iterate leaves its level (the mean-row residual, the prolongation,
+    // the FP64 update); FP64 iterates get it at once
+    const bool defer = sizeof(T) == 4;
+    k_scalar_final<T><<<1, 256, 0, st>>>(c->part, nb, x, b, 3 * l.F, h * h, l.nint, c->red + 1, defer);
+    if (!defer) k_pshift<T><<<dim3((l.P / 4 + 255) / 256, l.N + 2), 256, 0, st>>>(A, x, c->red + 1);
+    c->launches += defer ? 2 : 3;
 }
 
 template <typename T> void ghost_sweep(Ctx *c, int lev, T *x, const T *b)
@@ -2085,7 +2414,15 @@ void to_float(Ctx *c, const double *a, float *b, long long n)
 
 void add_float(Ctx *c, double *x, const float *e, long long n)
 {
-    k_add_float<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(x, e, n);
+    const Level &l = c->lv[0];
+    k_float_to_double<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(l.F, l.tP, e, x, n, 1);
+    c->launches++;
+}
+
+void float_to_double(Ctx *c, const float *e, double *y, long long n)
+{
+    const Level &l = c->lv[0];
+    k_float_to_double<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(l.F, l.tP, e, y, n, 0);
     c->launches++;
 }
 

@@ -27,7 +27,8 @@ class gp_params(ctypes.Structure):
                 ("gamma", ctypes.c_int), ("lam", ctypes.c_int), ("dtau", ctypes.c_double), ("snap", ctypes.c_double),
                 ("precision", ctypes.c_int), ("max_cycles", ctypes.c_int), ("cn_buffers", ctypes.c_int),
                 ("graphs", ctypes.c_int), ("band", ctypes.c_int), ("krylov", ctypes.c_int),
-                ("tile_min", ctypes.c_int), ("adjoint", ctypes.c_int), ("inner", ctypes.c_int)]
+                ("tile_min", ctypes.c_int), ("adjoint", ctypes.c_int), ("inner", ctypes.c_int),
+                ("wave_min", ctypes.c_int)]
 
 
 class gp_report(ctypes.Structure):
@@ -188,7 +189,7 @@ class Solver:
 
     def __init__(self, N, x0, y0, L, levels=None, alpha=None, nu1=2, nu2=1, gamma=1, lam=5, dtau=0.9,
                  snap=0.3, precision=GP_FP64, max_cycles=100, device="cuda", stream=None, cn_buffers=True,
-                 graphs=True, band=0, krylov=False, tile_min=0, adjoint=False, inner=0):
+                 graphs=True, band=0, krylov=False, tile_min=0, adjoint=False, inner=0, wave_min=0):
         import torch
         self.torch = torch
         self.L = lib()
@@ -209,6 +210,7 @@ class Solver:
         p.tile_min = int(tile_min)
         p.adjoint = 1 if adjoint else 0
         p.inner = int(inner)
+        p.wave_min = int(wave_min)
         self.prm = p
         nb = ctypes.c_size_t(0)
         st = self.L.gp_workspace_size(ctypes.byref(p), ctypes.byref(nb))

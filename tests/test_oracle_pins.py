@@ -19,6 +19,10 @@ not by the oracle itself.
   cycles (from zero, then from the first's result), prolongation and
   post-smoothing composed from the pinned pieces; it converges to the dense
   solution.
+* Eq. (LS) fixes the pressure only through the mean row: adding a constant to
+  every internal and ghost pressure leaves every other row's residual
+  unchanged (the momentum rows see pressure differences, the pressure ghost
+  rows have weights summing to zero, no other row reads p), on every level.
 """
 import numpy as np
 import pytest
@@ -366,3 +370,24 @@ def test_openmp_build_gives_the_same_iterate():
     _, x4 = o4.cycle(x, b)
     assert np.array_equal(x1, x4)
     assert np.array_equal(o1.residual(x1, b)[0], o4.residual(x4, b)[0])
+
+
+@pytest.mark.parametrize("case,N", [("flower5", 128), ("circle_off", 128), ("ellipse", 256), ("flower7", 128),
+                                    ("nobody", 64)])
+def test_pressure_constant_only_changes_the_mean_row(case, N):
+    shape, x0, L = CASES[case]
+    o, phi, st = make_oracle(case, N, alpha=2.0 * (L / N) ** 2)
+    assert st == 0, o.error()
+    for lev in range(o.levels):
+        Nl = N >> lev
+        t = o.types(lev)
+        n = t.size
+        pbeg = n - 1 - Nl * Nl
+        ind = np.zeros(n)
+        pt = t[pbeg:n - 1]
+        ind[pbeg:n - 1] = ((pt == 1) | (pt == 2)).astype(float)
+        r, _ = o.residual(ind, np.zeros(n), lev=lev)
+        assert np.abs(r[:-1]).max() <= 1e-9, lev
+        # the mean row h^2 sum p over the internal cells sees it
+        h = L / Nl
+        assert abs(-r[-1] - h * h * np.count_nonzero(pt == 1)) <= 1e-9 * (1 + h * h * Nl * Nl), lev
