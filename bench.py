@@ -128,6 +128,9 @@ def ncu_traffic(kernel, N):
     return None
 
 
+WAVE_MIN = 0  # gp_params.wave_min of every case (0: the library's default)
+
+
 def build_case(N, precision, device, stream, levels=None, krylov=False, inner=0, gamma=1, alpha=None):
     import torch
     from paper_1911_00994_gb300 import gpmg
@@ -135,7 +138,7 @@ def build_case(N, precision, device, stream, levels=None, krylov=False, inner=0,
     h = 1.0 / N
     alpha = h / (2.0 * 1000.0) if alpha is None else alpha
     s = gpmg.Solver(N, 0.0, 0.0, 1.0, levels=levels, alpha=alpha, precision=precision, device=device,
-                    max_cycles=200, stream=stream, krylov=krylov, inner=inner, gamma=gamma)
+                    max_cycles=200, stream=stream, krylov=krylov, inner=inner, gamma=gamma, wave_min=WAVE_MIN)
     phi = torch.from_numpy(W.phi_half_lattice(W.flower(0.2, 0.05, 5, 0.5, 0.5), N, 0.0, 0.0, 1.0)).to(device)
     st = s.geometry(phi, 0)
     if st:
@@ -707,9 +710,10 @@ def run_ours(args):
     bytes_per_launch = N * N * (9 * 4 + 1.0)
     avg_ms = box_ms / max(1, nbox)
     achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
-    # levels from 4096^2 stream down strips of rows, smaller ones use tiles
-    roof_kernel = "k_box_wave<float>" if N >= 4096 else "k_box_tma<float>"
-    tr = ncu_traffic(roof_kernel, N) if N >= 4096 else None
+    # levels from 4096^2 (or --wave-min) stream down strips of rows, smaller ones use tiles
+    wmin = WAVE_MIN if WAVE_MIN != 0 else 4096
+    roof_kernel = "k_box_wave<float>" if 0 <= wmin <= N else "k_box_tma<float>"
+    tr = ncu_traffic(roof_kernel, N)
     line = {
         "metric": METRIC, "value": value, "unit": "V-cycles/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -849,7 +853,11 @@ def main():
     ap.add_argument("--no-wcycle", action="store_true")
     ap.add_argument("--no-cavity", action="store_true")
     ap.add_argument("--accuracy", action="store_true", help="add the Sect. 5.1 accuracy study (about 3.5 min)")
+    ap.add_argument("--wave-min", type=int, default=0,
+                    help="smallest level swept down strips of rows (gp_params.wave_min; 0: library default)")
     args = ap.parse_args()
+    global WAVE_MIN
+    WAVE_MIN = args.wave_min
     if args.impl == "reference":
         args.steps = 2 if args.steps is None else args.steps
         args.warmup = 1 if args.warmup is None else args.warmup
