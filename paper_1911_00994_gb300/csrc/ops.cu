@@ -560,11 +560,14 @@ __global__ void __launch_bounds__(TileGeom<T>::THREADS) k_box_tma(const __grid_c
     // multiples of 32 elements, so every row segment is whole vectors)
     using V = typename Vec16<T>::type;
     constexpr int VW = 16 / sizeof(T);
+    // (compile-time strides: TH rows of TW / VW vectors per frame, the edge
+    // tiles' missing rows and columns skipped)
     const int rows = min(TH, A.N + 2 - r0), vpr = min(TW, A.P - c0) / VW;
-    const int per_frame = rows * vpr;
-    for (int k = threadIdx.x; k < 3 * per_frame; k += blockDim.x) {
-        const int f = k / per_frame, rem = k - f * per_frame;
-        const int rr = rem / vpr, vv = rem - rr * vpr;
+    constexpr int VPR = TW / VW, PER_FRAME = TH * VPR;
+    for (int k = threadIdx.x; k < 3 * PER_FRAME; k += blockDim.x) {
+        const int f = k / PER_FRAME, rem = k - f * PER_FRAME;
+        const int rr = rem / VPR, vv = rem - rr * VPR;
+        if (rr >= rows || vv >= vpr) continue;
         const V *src = (const V *)(su + f * FR + (rr + TT_RLO) * LW + TT_CLO) + vv;
         V *dst = (V *)(y + f * A.F + (long long)(r0 + rr) * A.P + c0) + vv;
         *dst = *src;
@@ -1475,10 +1478,15 @@ template <typename T> __global__ void k_copy_t(const T *a, T *b, long long n)
     if (k < n) b[k] = a[k];
 }
 
+// x[0, n) = 0: 16-byte stores where x is 16-byte aligned, then the tail
 template <typename T> __global__ void k_zero(T *x, long long n)
 {
-    long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (k < n) x[k] = 0;
+    using V = typename Vec16<T>::type;
+    constexpr int VW = 16 / sizeof(T);
+    const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long nv = ((uintptr_t)x % 16 == 0) ? n / VW : 0;
+    if (k < nv) ((V *)x)[k] = V{};
+    for (long long q = nv * VW + k; q < n; q += (long long)gridDim.x * blockDim.x) x[q] = 0;
 }
 
 // x = 0 on inactive nodes of a level
@@ -1513,6 +1521,36 @@ __global__ void k_float_to_double(long long F, const uint8_t *tP, const float *e
         v = 0.0;
     }
     y[k] = add ? y[k] + v : v;
+}
+
+// the same on four consecutive slots per thread (n a multiple of 4; F is a
+// multiple of 32, so a quad lies in one frame or in the scalar block)
+__global__ void k_float_to_double4(long long F, const uint8_t *tP, const float *e, double *y, long long n, int add)
+{
+    const long long q = 4 * (blockIdx.x * (long long)blockDim.x + threadIdx.x);
+    if (q >= n) return;
+    float ev[4];
+    double v[4];
+    ld4(e + q, ev);
+#pragma unroll
+    for (int k = 0; k < 4; k++) v[k] = (double)ev[k];
+    if (q >= 2 * F && q < 3 * F) {
+        uint8_t t[4];
+        ldt4(tP + (q - 2 * F), t);
+        const float sig = e[3 * F + PSHIFT_SLOT];
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            if (t[k] == T_INTERNAL || t[k] == T_GHOST) v[k] = (double)(ev[k] + sig);
+    } else if (q <= 3 * F + PSHIFT_SLOT && 3 * F + PSHIFT_SLOT < q + 4) {
+        v[3 * F + PSHIFT_SLOT - q] = 0.0;
+    }
+    if (add) {
+        double yv[4];
+        ld4(y + q, yv);
+#pragma unroll
+        for (int k = 0; k < 4; k++) v[k] += yv[k];
+    }
+    st4(y + q, v);
 }
 
 // ---------------------------------------------- one-block kernels, small levels
@@ -2396,7 +2434,8 @@ template <typename T> void prolong_level(Ctx *c, int lev, const T *eH, T *x) { p
 
 template <typename T> void zero_vec(Ctx *c, T *x, long long n)
 {
-    k_zero<T><<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(x, n);
+    const long long nv = (n + 16 / (long long)sizeof(T) - 1) / (16 / (long long)sizeof(T));
+    k_zero<T><<<(unsigned)((nv + 255) / 256), 256, 0, c->stream>>>(x, n);
     c->launches++;
 }
 
@@ -2412,19 +2451,19 @@ void to_float(Ctx *c, const double *a, float *b, long long n)
     c->launches++;
 }
 
-void add_float(Ctx *c, double *x, const float *e, long long n)
+static void f2d(Ctx *c, const float *e, double *y, long long n, int add)
 {
     const Level &l = c->lv[0];
-    k_float_to_double<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(l.F, l.tP, e, x, n, 1);
+    if (n % 4 == 0 && (uintptr_t)e % 16 == 0 && (uintptr_t)y % 16 == 0)
+        k_float_to_double4<<<(unsigned)((n / 4 + 255) / 256), 256, 0, c->stream>>>(l.F, l.tP, e, y, n, add);
+    else
+        k_float_to_double<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(l.F, l.tP, e, y, n, add);
     c->launches++;
 }
 
-void float_to_double(Ctx *c, const float *e, double *y, long long n)
-{
-    const Level &l = c->lv[0];
-    k_float_to_double<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(l.F, l.tP, e, y, n, 0);
-    c->launches++;
-}
+void add_float(Ctx *c, double *x, const float *e, long long n) { f2d(c, e, x, n, 1); }
+
+void float_to_double(Ctx *c, const float *e, double *y, long long n) { f2d(c, e, y, n, 0); }
 
 #define INST(T)                                                                 \
     template void residual<T>(Ctx *, int, const T *, const T *, T *);           \
