@@ -362,6 +362,63 @@ def accuracy_study(Ns=(60, 120), T=0.5):
     return out
 
 
+def mac3d_box(dev, stream, N=256, steps=3):
+    """The 3-D MAC extension on the box [0, 1]^3 (walls only): FP64 V(2,1)
+    cycles to ||r||_inf <= 1e-10 from zero, the right-hand side seeded
+    normals on the interior momentum and continuity rows; the 7-colour box
+    relaxation of the finest level timed per launch."""
+    import numpy as np
+    import torch
+    from paper_1911_00994_gb300 import mac3d
+    levels = 1
+    while (N >> levels) >= 4 and 4 * ((N >> levels) + 2) ** 3 + 1 > 1024:
+        levels += 1
+    levels += 1
+    h = 1.0 / N
+    alpha = h / (2.0 * 1000.0)  # Re = 1000, dt = h
+    s = mac3d.Solver3D(N, levels, alpha, device=dev, stream=stream)
+    S = N + 2
+    F = S ** 3
+    t = s.types(0)
+    rng = np.random.default_rng(0)
+    b = np.zeros(mac3d.plain_len(N))
+    act = t == 1
+    b[:4 * F][act] = rng.standard_normal(int(act.sum()))
+    bg = s.to_device(b)
+    x = s.new_vec()
+    st, cyc, res, hist = s.solve(x, bg, 1e-10, 200)
+    if st:
+        return {"N": N, "status": "failed: " + s.error()}
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    cycles = 0
+    for _ in range(steps):
+        x.zero_()
+        st, cyc, res, hist = s.solve(x, bg, 1e-10, 200)
+        cycles += cyc
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / steps
+    s.timer_start(0)
+    x.zero_()
+    s.solve(x, bg, 1e-10, 200)
+    nbox, box_ms = s.timer_stop()
+    hbm, src = peaks()
+    sweep_ms = 7.0 * box_ms / max(1, nbox)
+    # algorithmic bytes of one seven-colour sweep: per cell read x and b (4
+    # words each) and the four type bytes, write x (4 words), FP64
+    sweep_bytes = N ** 3 * (12 * 8 + 4.0)
+    rho = float((hist[-1] / hist[max(0, len(hist) - 5)]) ** (1.0 / min(4, len(hist) - 1))) if len(hist) > 1 else None
+    return {"N": N, "unknowns": int((t != 0).sum()) + 1, "levels": levels, "Re": 1000.0, "dt": "h",
+            "precision": "fp64", "cycle": "V(2,1)", "time_to_tol_ms": ms, "cycles_per_step": cycles / steps,
+            "cycles_per_s": cycles / steps / (ms / 1e3), "rho_last4": rho,
+            "box_sweep": {"kernel": "k3_box (seven colour launches)", "ms_per_sweep": sweep_ms,
+                          "achieved_gbs": sweep_bytes / (sweep_ms / 1e3) / 1e9,
+                          "frac_of_hbm": sweep_bytes / (sweep_ms / 1e3) / 1e9 / hbm,
+                          "algorithmic_bytes_per_sweep": sweep_bytes}}
+
+
 def largest_solve(dev, stream, N=8192, steps=2):
     """The largest single solve: the seven-petal flower
     r = 0.5 + 0.1 sin(7 theta) on [-1, 1]^2 at 8192^2 (201 M unknowns),
@@ -694,6 +751,7 @@ def run_ours(args):
     adj = adjoint_rollout(dev, stream) if not args.no_adjoint else None
     mov = moving_ellipse(dev, stream, steps=args.moving_steps, warm=args.moving_warm) if not args.no_moving else None
     big = largest_solve(dev, stream) if not args.no_large else None
+    m3d = mac3d_box(dev, stream) if not args.no_3d else None
     cav = cavity_cn_steps(dev, stream, N=N) if not args.no_cavity else None
     acc = accuracy_study() if args.accuracy else None
 
@@ -737,6 +795,7 @@ def run_ours(args):
         "adjoint_rollout_orbiting_circle_512": adj,
         "moving_ellipse_1024": mov,
         "largest_solve_flower7_8192": big,
+        "mac3d_box_256": m3d,
         "cavity_cn_steps": cav,
         "accuracy_sol_exa": acc,
         "roofline": {"kernel": roof_kernel + " (finest-level full-box sweep, five colours in one pass)",
@@ -850,6 +909,7 @@ def main():
     ap.add_argument("--moving-steps", type=int, default=20, help="timed steps of the moving ellipse (the config: 200)")
     ap.add_argument("--moving-warm", type=int, default=4, help="untimed steps before them (the config: 0, from rest)")
     ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--no-3d", action="store_true", help="skip the 3-D box-domain solve (256^3)")
     ap.add_argument("--no-wcycle", action="store_true")
     ap.add_argument("--no-cavity", action="store_true")
     ap.add_argument("--accuracy", action="store_true", help="add the Sect. 5.1 accuracy study (about 3.5 min)")

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 OUT = os.path.join(HERE, "libgpmg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["geometry.cu", "ops.cu", "coarse.cu", "solver.cu", "noalloc.cu", "cn.cu", "krylov.cu", "adjoint.cu",
-           "probe.cu", "levelset.cu"]
+           "probe.cu", "levelset.cu", "mac3d.cu"]
 EXTRA = {"geometry.cu": ["-fmad=false"]}
 
 

@@ -75,3 +75,33 @@ def test_invalid_sizes_are_rejected_on_the_host():
     q = gpmg.gp_params.from_buffer_copy(p)
     q.N, q.levels = 60, 3
     assert L.gp_workspace_size(ctypes.byref(q), ctypes.byref(nb)) == 0
+
+
+def declared_3d():
+    src = open(os.path.join(ROOT, "include", "gpmg3d.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^[A-Za-z_][\w \*]*?\b([a-z_][a-z0-9_]*)\s*\(", src, flags=re.M)
+    return sorted(set(n for n in names if n not in ("if", "while")))
+
+
+def test_3d_library_exports_and_binding_cover_gpmg3d_h():
+    from paper_1911_00994_gb300 import mac3d
+    lib = ctypes.CDLL(build.build())
+    names = declared_3d()
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(lib, n), n
+    assert {n for n, _, _ in mac3d.SIGNATURES} == set(names)
+
+
+def test_3d_sizes_are_checked_on_the_host():
+    # gp3_workspace_size makes no CUDA call: a size for valid hierarchies,
+    # GP_INVALID for N not divisible down the levels, a coarsest grid below
+    # 2 or a coarsest dense matrix above 1024 unknowns
+    from paper_1911_00994_gb300 import mac3d
+    L = mac3d.lib()
+    nb = ctypes.c_size_t(0)
+    assert L.gp3_workspace_size(64, 5, ctypes.byref(nb)) == 0 and nb.value > 0
+    assert L.gp3_vec_len(64) == 4 * 66 ** 3 + 32
+    for N, lev in ((64, 7), (48, 6), (64, 3), (0, 1), (64, 0)):
+        assert L.gp3_workspace_size(N, lev, ctypes.byref(nb)) == 1, (N, lev)
