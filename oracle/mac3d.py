@@ -1,6 +1,6 @@
 """Oracle of the 3-D MAC extension on the box domain: plain, slow, FP64 numpy.
 
-Test infrastructure only (imported by tests/ and bench.py's CPU baseline).
+Test infrastructure only (imported by tests/).
 The paper states that the method extends directly to three dimensions
 (Sect. 3, "Discretization in space"): the staggered grid gains a w velocity,
 the box of a cell holds its pressure and six faces (a 7 x 7 system, Sect.

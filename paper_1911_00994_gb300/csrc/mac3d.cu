@@ -29,6 +29,7 @@ struct Lev {
     int N, S;
     long long F, VL;
     double a, q, d, h3;  // alpha / h^2, 1 / h, 1 + 6 a, h^3
+    double ida, id, idet;  // 1 / (d + a), 1 / d, 1 / (d^2 - a^2): the box solves divide only once
     unsigned char *t;    // 4 F node types
     double *x, *b, *r;   // level vectors (x, b of the coarse levels; r of every level)
 };
@@ -197,8 +198,9 @@ __global__ void k3_residual_final(Lev L, const double *part, int nb, const doubl
 // everything else is frozen.  Eliminating the faces leaves one equation for
 // the pressure correction: per direction, both faces couple through -a and
 // give q (r_hi - r_lo + 2 q dp) / (d + a) to the continuity row, a single
-// face -q (r_lo - q dp) / d or q (r_hi + q dp) / d.  One thread per cell of
-// the colour, cells numbered along i within each (j, k) row.
+// face -q (r_lo - q dp) / d or q (r_hi + q dp) / d (with the level's
+// reciprocals: one division per box).  One thread per cell of the colour,
+// cells numbered along i within each (j, k) row.
 __global__ void __launch_bounds__(256) k3_box(Lev L, double *x, const double *b, int colour)
 {
     const int N = L.N;
@@ -231,14 +233,14 @@ __global__ void __launch_bounds__(256) k3_box(Lev L, double *x, const double *b,
     for (int dir = 0; dir < 3; dir++) {
         const bool lo = on[2 * dir], hi = on[2 * dir + 1];
         if (lo && hi) {
-            c0 += q * (r[2 * dir + 1] - r[2 * dir]) / (d + a);
-            c1 += 2.0 * q * q / (d + a);
+            c0 += q * (r[2 * dir + 1] - r[2 * dir]) * L.ida;
+            c1 += 2.0 * q * q * L.ida;
         } else if (lo) {
-            c0 -= q * r[2 * dir] / d;
-            c1 += q * q / d;
+            c0 -= q * r[2 * dir] * L.id;
+            c1 += q * q * L.id;
         } else if (hi) {
-            c0 += q * r[2 * dir + 1] / d;
-            c1 += q * q / d;
+            c0 += q * r[2 * dir + 1] * L.id;
+            c1 += q * q * L.id;
         }
     }
     if (c1 == 0.0) return;
@@ -248,13 +250,12 @@ __global__ void __launch_bounds__(256) k3_box(Lev L, double *x, const double *b,
         const bool lo = on[2 * dir], hi = on[2 * dir + 1];
         const double fl = r[2 * dir] - q * dp, fh = r[2 * dir + 1] + q * dp;
         if (lo && hi) {
-            const double det = d * d - a * a;
-            x[fe[2 * dir]] += (d * fl + a * fh) / det;
-            x[fe[2 * dir + 1]] += (a * fl + d * fh) / det;
+            x[fe[2 * dir]] += (d * fl + a * fh) * L.idet;
+            x[fe[2 * dir + 1]] += (a * fl + d * fh) * L.idet;
         } else if (lo) {
-            x[fe[2 * dir]] += fl / d;
+            x[fe[2 * dir]] += fl * L.id;
         } else if (hi) {
-            x[fe[2 * dir + 1]] += fh / d;
+            x[fe[2 * dir + 1]] += fh * L.id;
         }
     }
     x[3 * F + s] += dp;
@@ -633,6 +634,9 @@ static size_t carve(Ctx *c, char *base, int N, int levels)
             L.q = 1.0 / h;
             L.d = 1.0 + 6.0 * L.a;
             L.h3 = h * h * h;
+            L.ida = 1.0 / (L.d + L.a);
+            L.id = 1.0 / L.d;
+            L.idet = 1.0 / (L.d * L.d - L.a * L.a);
             L.t = t;
             L.x = x;
             L.b = b;
