@@ -404,6 +404,29 @@ def mac3d_box(dev, stream, N=256, steps=3):
     x.zero_()
     s.solve(x, bg, 1e-10, 200)
     nbox, box_ms = s.timer_stop()
+    # the same system with FP32 cycles (up to four) inside FP64 residual correction
+    del s
+    torch.cuda.empty_cache()
+    sm = mac3d.Solver3D(N, levels, alpha, precision=1, inner=4, device=dev, stream=stream)
+    xm = sm.new_vec()
+    stm, cm, rm, hm = sm.solve(xm, bg, 1e-10, 200)
+    e0.record(stream)
+    mcyc = 0
+    for _ in range(steps):
+        xm.zero_()
+        stm, cm, rm, hm = sm.solve(xm, bg, 1e-10, 200)
+        mcyc += cm
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    mixed = {"time_to_tol_ms": e0.elapsed_time(e1) / steps, "cycles_per_step": mcyc / steps,
+             "corrections_per_step": len(hm) - 1, "status": "ok" if stm == 0 else "failed: " + sm.error()}
+    sm.timer_start(0)
+    xm.zero_()
+    sm.solve(xm, bg, 1e-10, 200)
+    nboxf, boxf_ms = sm.timer_stop()
+    mixed["box_sweep_fp32_ms"] = 7.0 * boxf_ms / max(1, nboxf)
+    mixed["box_sweep_fp32_gbs"] = N ** 3 * (12 * 4 + 4.0) / (mixed["box_sweep_fp32_ms"] / 1e3) / 1e9
+    del sm
     hbm, src = peaks()
     sweep_ms = 7.0 * box_ms / max(1, nbox)
     # algorithmic bytes of one seven-colour sweep: per cell read x and b (4
@@ -417,7 +440,7 @@ def mac3d_box(dev, stream, N=256, steps=3):
     p64, _ = gpmg.fma_peak(dev, stream)
     ach = 135.0 * N ** 3 / (sweep_ms / 1e3) / 1e12
     return {"N": N, "unknowns": int((t != 0).sum()) + 1, "levels": levels, "Re": 1000.0, "dt": "h",
-            "precision": "fp64", "cycle": "V(2,1)", "time_to_tol_ms": ms, "cycles_per_step": cycles / steps,
+            "precision": "fp64", "cycle": "V(2,1)", "mixed": mixed, "time_to_tol_ms": ms, "cycles_per_step": cycles / steps,
             "cycles_per_s": cycles / steps / (ms / 1e3), "rho_last4": rho,
             "box_sweep": {"kernel": "k3_box (seven colour launches)", "ms_per_sweep": sweep_ms,
                           "achieved_gbs": sweep_bytes / (sweep_ms / 1e3) / 1e9,

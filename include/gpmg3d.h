@@ -50,15 +50,20 @@ long long gp3_vec_len(int N);
 
 /* bytes of device workspace for N cells per side and `levels` levels
  * (N, N/2, ..., N/2^(levels-1); N divisible by 2^(levels-1), coarsest >= 2,
- * at most 1024 unknowns on the coarsest level).  GP_INVALID otherwise. */
-gp_status gp3_workspace_size(int N, int levels, size_t *bytes);
+ * at most 1024 unknowns on the coarsest level) and precision (0 FP64,
+ * 1 mixed: adds the FP32 vectors).  GP_INVALID otherwise. */
+gp_status gp3_workspace_size(int N, int levels, int precision, size_t *bytes);
 
 /* Create a context: alpha = dt / (2 Re); nu1, nu2 pre/post relaxations;
- * lambda ghost sweeps of step dtau per relaxation.  ws: caller-owned device
- * workspace of at least gp3_workspace_size bytes, 256-byte aligned.  Builds
- * the node types of every level and the coarsest-level inverse (synchronous). */
+ * lambda ghost sweeps of step dtau per relaxation; precision 0: gp3_solve
+ * runs FP64 cycles; 1: each iteration rounds the FP64 residual to FP32, runs
+ * `inner` (1..16) FP32 cycles from zero on it and adds the correction to x in
+ * FP64 (the cycle pieces gp3_smooth ... gp3_cycle are FP64 in both).  ws:
+ * caller-owned device workspace of at least gp3_workspace_size bytes,
+ * 256-byte aligned.  Builds the node types of every level and the
+ * coarsest-level inverse (synchronous). */
 gp_status gp3_create(gp3_ctx **out, int N, int levels, double alpha, int nu1, int nu2, int lambda, double dtau,
-                     void *ws, size_t ws_bytes, cudaStream_t stream);
+                     int precision, int inner, void *ws, size_t ws_bytes, cudaStream_t stream);
 gp_status gp3_destroy(gp3_ctx *ctx);
 const char *gp3_last_error(gp3_ctx *ctx);
 
@@ -81,12 +86,13 @@ gp_status gp3_prolong(gp3_ctx *ctx, int level, const double *eH, double *x);
 /* one V(nu1, nu2) cycle on the finest level, in place */
 gp_status gp3_cycle(gp3_ctx *ctx, double *x, const double *b);
 
-/* cycles from x until ||b - M x||_inf <= tol or max_cycles; *cycles and
- * *res (may be NULL) report them, hist_host (may be NULL) receives the
- * residual before each cycle and after the last (max_cycles + 1 entries).
- * GP_NOT_CONVERGED at the cap, GP_DIVERGED on NaN or growth by 1e6. */
-gp_status gp3_solve(gp3_ctx *ctx, double *x, const double *b, double tol, int max_cycles, int *cycles, double *res,
-                    double *hist_host);
+/* iterations from x until the FP64 ||b - M x||_inf <= tol or max_cycles
+ * cycles (FP32 cycles in the mixed mode); *cycles, *iterations and *res (each
+ * may be NULL) report them, hist_host (may be NULL) receives the FP64
+ * residual before each iteration and after the last (at most max_cycles + 1
+ * entries).  GP_NOT_CONVERGED at the cap, GP_DIVERGED on NaN or growth by 1e6. */
+gp_status gp3_solve(gp3_ctx *ctx, double *x, const double *b, double tol, int max_cycles, int *cycles,
+                    int *iterations, double *res, double *hist_host);
 
 /* kernel timer: CUDA events around every box-relaxation launch of `level`
  * until gp3_timer_stop, which returns the launches and their total ms */

@@ -31,7 +31,8 @@ struct Lev {
     double a, q, d, h3;  // alpha / h^2, 1 / h, 1 + 6 a, h^3
     double ida, id, idet;  // 1 / (d + a), 1 / d, 1 / (d^2 - a^2): the box solves divide only once
     unsigned char *t;    // 4 F node types
-    double *x, *b, *r;   // level vectors (x, b of the coarse levels; r of every level)
+    double *x, *b, *r;   // FP64 level vectors (x, b of the coarse levels; r of every level)
+    float *xf, *bf, *rf; // FP32 level vectors of the mixed mode's inner cycles (x, b, r of every level)
 };
 
 __host__ __device__ inline long long vlen(int N)
@@ -80,23 +81,23 @@ __global__ void k3_types(int N, long long F, unsigned char *t)
 // (M x) of the velocity or continuity row at slot s of grid g (not the mean
 // row); X(e) returns entry e of the vector (a level vector, or a unit
 // vector when the dense matrix is assembled)
-template <typename Acc>
-__device__ inline double apply_row(const Lev &L, const unsigned char *t, int g, long long s, const Acc &X)
+template <typename T, typename Acc>
+__device__ inline T apply_row(const Lev &L, const unsigned char *t, int g, long long s, const Acc &X)
 {
     const long long F = L.F, S = L.S, S2 = S * S;
+    const T q = (T)L.q, d = (T)L.d, a = (T)L.a;
     const long long off[3] = {1, S, S2};
     const unsigned char ty = t[g * F + s];
     const long long e = g * F + s;
     if (g == 3) {
         if (ty != T_INTERNAL) return X(e);
         // continuity: q (u_E - u_W + v_N - v_S + w_T - w_B) - xi
-        return L.q * ((X(s + 1) - X(s)) + (X(F + s + S) - X(F + s)) + (X(2 * F + s + S2) - X(2 * F + s))) -
-               X(4 * F);
+        return q * ((X(s + 1) - X(s)) + (X(F + s + S) - X(F + s)) + (X(2 * F + s + S2) - X(2 * F + s))) - X(4 * F);
     }
     if (ty == T_INTERNAL) {
-        const double lap = X(e + 1) + X(e - 1) + X(e + S) + X(e - S) + X(e + S2) + X(e - S2);
+        const T lap = X(e + 1) + X(e - 1) + X(e + S) + X(e - S) + X(e + S2) + X(e - S2);
         // p of the cell on the + side (same slot) minus the cell on the - side
-        return L.d * X(e) - L.a * lap + L.q * (X(3 * F + s) - X(3 * F + s - off[g]));
+        return d * X(e) - a * lap + q * (X(3 * F + s) - X(3 * F + s - off[g]));
     }
     if (ty == T_BOXGHOST) {
         // the transverse axis that leaves [0, N): step inwards from the ghost
@@ -108,14 +109,14 @@ __device__ inline double apply_row(const Lev &L, const unsigned char *t, int g, 
             if (c == -1) in = off[ax];
             else if (c == N) in = -off[ax];
         }
-        return 0.375 * X(e) + 0.75 * X(e + in) - 0.125 * X(e + 2 * in);
+        return (T)0.375 * X(e) + (T)0.75 * X(e + in) - (T)0.125 * X(e + 2 * in);
     }
     return X(e);  // wall (Dirichlet) and inactive rows
 }
 
-struct VecAcc {
-    const double *v;
-    __device__ double operator()(long long e) const { return v[e]; }
+template <typename T> struct VecAcc {
+    const T *v;
+    __device__ T operator()(long long e) const { return v[e]; }
 };
 struct UnitAcc {
     long long c;
@@ -146,24 +147,28 @@ __device__ inline void block_sum_max(double s, double m, double *part)
 
 // r = b - M x over the four frames; per block [0] sum of the interior p,
 // [1] max |r| (grid-stride)
-__global__ void __launch_bounds__(256) k3_residual(Lev L, const double *x, const double *b, double *r, double *part)
+// (T: the arithmetic; R: the output, FP32 when the FP64 residual becomes the
+// right-hand side of the inner FP32 cycles)
+template <typename T, typename R>
+__global__ void __launch_bounds__(256) k3_residual(Lev L, const T *x, const T *b, R *r, double *part)
 {
-    const VecAcc X{x};
+    const VecAcc<T> X{x};
     double sp = 0.0, m = 0.0;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < 4 * L.F;
          e += (long long)gridDim.x * blockDim.x) {
         const int g = (int)(e / L.F);
         const long long s = e - g * L.F;
-        const double v = b[e] - apply_row(L, L.t, g, s, X);
-        r[e] = v;
-        m = (v != v || m != m) ? (double)NAN : fmax(m, fabs(v));
-        if (g == 3 && L.t[e] == T_INTERNAL) sp += x[e];
+        const T v = b[e] - apply_row<T>(L, L.t, g, s, X);
+        r[e] = (R)v;
+        m = (v != v || m != m) ? (double)NAN : fmax(m, fabs((double)v));
+        if (g == 3 && L.t[e] == T_INTERNAL) sp += (double)x[e];
     }
     block_sum_max(sp, m, part);
 }
 
 // the mean row and the norm: r[4F] = b[4F] - h^3 sum p
-__global__ void k3_residual_final(Lev L, const double *part, int nb, const double *b, double *r, double *out)
+template <typename T, typename R>
+__global__ void k3_residual_final(Lev L, const double *part, int nb, const T *b, R *r, double *out)
 {
     __shared__ double ss[256], sm[256];
     double s = 0.0, m = 0.0;
@@ -184,8 +189,8 @@ __global__ void k3_residual_final(Lev L, const double *part, int nb, const doubl
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        const double rm = b[4 * L.F] - L.h3 * ss[0];
-        r[4 * L.F] = rm;
+        const double rm = (double)b[4 * L.F] - L.h3 * ss[0];
+        r[4 * L.F] = (R)rm;
         const double a = sm[0];
         out[0] = (a != a || rm != rm) ? (double)NAN : fmax(a, fabs(rm));
     }
@@ -201,7 +206,8 @@ __global__ void k3_residual_final(Lev L, const double *part, int nb, const doubl
 // face -q (r_lo - q dp) / d or q (r_hi + q dp) / d (with the level's
 // reciprocals: one division per box).  One thread per cell of the colour,
 // cells numbered along i within each (j, k) row.
-__global__ void __launch_bounds__(256) k3_box(Lev L, double *x, const double *b, int colour)
+template <typename T>
+__global__ void __launch_bounds__(256) k3_box(Lev L, T *x, const T *b, int colour)
 {
     const int N = L.N;
     const int per_row = (N + NCOL - 1) / NCOL;
@@ -216,65 +222,67 @@ __global__ void __launch_bounds__(256) k3_box(Lev L, double *x, const double *b,
     if (i >= N) return;
     const long long S = L.S, S2 = S * S, F = L.F;
     const long long s = ((long long)(k + 1) * S + (j + 1)) * S + (i + 1);
-    const VecAcc X{x};
+    const VecAcc<T> X{x};
     // faces: lo and hi of each direction
     const long long fe[6] = {s, s + 1, F + s, F + s + S, 2 * F + s, 2 * F + s + S2};
     bool on[6];
-    double r[6];
+    T r[6];
 #pragma unroll
     for (int f = 0; f < 6; f++) {
         on[f] = L.t[fe[f]] == T_INTERNAL;
-        r[f] = on[f] ? b[fe[f]] - apply_row(L, L.t, f / 2, fe[f] - (f / 2) * F, X) : 0.0;
+        r[f] = on[f] ? b[fe[f]] - apply_row<T>(L, L.t, f / 2, fe[f] - (f / 2) * F, X) : (T)0;
     }
-    const double rC = b[3 * F + s] - apply_row(L, L.t, 3, s, X);
-    const double a = L.a, d = L.d, q = L.q;
-    double c0 = 0.0, c1 = 0.0;
+    const T rC = b[3 * F + s] - apply_row<T>(L, L.t, 3, s, X);
+    const T a = (T)L.a, d = (T)L.d, q = (T)L.q, ida = (T)L.ida, rd = (T)L.id, idet = (T)L.idet;
+    T c0 = 0, c1 = 0;
 #pragma unroll
     for (int dir = 0; dir < 3; dir++) {
         const bool lo = on[2 * dir], hi = on[2 * dir + 1];
         if (lo && hi) {
-            c0 += q * (r[2 * dir + 1] - r[2 * dir]) * L.ida;
-            c1 += 2.0 * q * q * L.ida;
+            c0 += q * (r[2 * dir + 1] - r[2 * dir]) * ida;
+            c1 += (T)2 * q * q * ida;
         } else if (lo) {
-            c0 -= q * r[2 * dir] * L.id;
-            c1 += q * q * L.id;
+            c0 -= q * r[2 * dir] * rd;
+            c1 += q * q * rd;
         } else if (hi) {
-            c0 += q * r[2 * dir + 1] * L.id;
-            c1 += q * q * L.id;
+            c0 += q * r[2 * dir + 1] * rd;
+            c1 += q * q * rd;
         }
     }
-    if (c1 == 0.0) return;
-    const double dp = (rC - c0) / c1;
+    if (c1 == (T)0) return;
+    const T dp = (rC - c0) / c1;
 #pragma unroll
     for (int dir = 0; dir < 3; dir++) {
         const bool lo = on[2 * dir], hi = on[2 * dir + 1];
-        const double fl = r[2 * dir] - q * dp, fh = r[2 * dir + 1] + q * dp;
+        const T fl = r[2 * dir] - q * dp, fh = r[2 * dir + 1] + q * dp;
         if (lo && hi) {
-            x[fe[2 * dir]] += (d * fl + a * fh) * L.idet;
-            x[fe[2 * dir + 1]] += (a * fl + d * fh) * L.idet;
+            x[fe[2 * dir]] += (d * fl + a * fh) * idet;
+            x[fe[2 * dir + 1]] += (a * fl + d * fh) * idet;
         } else if (lo) {
-            x[fe[2 * dir]] += fl * L.id;
+            x[fe[2 * dir]] += fl * rd;
         } else if (hi) {
-            x[fe[2 * dir + 1]] += fh * L.id;
+            x[fe[2 * dir + 1]] += fh * rd;
         }
     }
     x[3 * F + s] += dp;
 }
 
 // (xi, mean) step: per block [0] sum of (div u - b_c), [1] sum of p over the cells
-__global__ void __launch_bounds__(256) k3_scalar_partial(Lev L, const double *x, const double *b, double *part)
+template <typename T>
+__global__ void __launch_bounds__(256) k3_scalar_partial(Lev L, const T *x, const T *b, double *part)
 {
     const long long F = L.F, S = L.S, S2 = S * S;
-    double sd = 0.0, sp = 0.0;
+    const T q = (T)L.q;
+    T sd = 0, sp = 0;
     for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < F; s += (long long)gridDim.x * blockDim.x) {
         if (L.t[3 * F + s] != T_INTERNAL) continue;
-        const double div = L.q * ((x[s + 1] - x[s]) + (x[F + s + S] - x[F + s]) + (x[2 * F + s + S2] - x[2 * F + s]));
+        const T div = q * ((x[s + 1] - x[s]) + (x[F + s + S] - x[F + s]) + (x[2 * F + s + S2] - x[2 * F + s]));
         sd += div - b[3 * F + s];
         sp += x[3 * F + s];
     }
     __shared__ double ss[256], sm[256];
-    ss[threadIdx.x] = sd;
-    sm[threadIdx.x] = sp;
+    ss[threadIdx.x] = (double)sd;
+    sm[threadIdx.x] = (double)sp;
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
         if (threadIdx.x < o) {
@@ -290,7 +298,8 @@ __global__ void __launch_bounds__(256) k3_scalar_partial(Lev L, const double *x,
 }
 
 // xi <- mean(div u - b_c); shift[0] <- (b_mean - h^3 sum p) / (h^3 n_cells)
-__global__ void k3_scalar_final(Lev L, const double *part, int nb, double *x, const double *b, double *shift)
+template <typename T>
+__global__ void k3_scalar_final(Lev L, const double *part, int nb, T *x, const T *b, double *shift)
 {
     __shared__ double ss[256], sm[256];
     double s = 0.0, m = 0.0;
@@ -310,30 +319,30 @@ __global__ void k3_scalar_final(Lev L, const double *part, int nb, double *x, co
     }
     if (threadIdx.x == 0) {
         const double n = (double)L.N * L.N * L.N;
-        x[4 * L.F] = ss[0] / n;
-        shift[0] = (b[4 * L.F] - L.h3 * sm[0]) / (L.h3 * n);
+        x[4 * L.F] = (T)(ss[0] / n);
+        shift[0] = ((double)b[4 * L.F] - L.h3 * sm[0]) / (L.h3 * n);
     }
 }
 
-__global__ void k3_pshift(Lev L, double *x, const double *shift)
+template <typename T> __global__ void k3_pshift(Lev L, T *x, const double *shift)
 {
     const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (s >= L.F || L.t[3 * L.F + s] != T_INTERNAL) return;
-    x[3 * L.F + s] += shift[0];
+    x[3 * L.F + s] += (T)shift[0];
 }
 
 // Eq. (ghostrelax), Jacobi over the wall and box-ghost rows: upd = dtau r
-__global__ void k3_ghost_update(Lev L, const double *x, const double *b, double dtau, double *upd)
+template <typename T> __global__ void k3_ghost_update(Lev L, const T *x, const T *b, T dtau, T *upd)
 {
     const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (e >= 3 * L.F) return;
     const unsigned char ty = L.t[e];
     if (ty != T_WALL && ty != T_BOXGHOST) return;
     const int g = (int)(e / L.F);
-    upd[e] = dtau * (b[e] - apply_row(L, L.t, g, e - g * L.F, VecAcc{x}));
+    upd[e] = dtau * (b[e] - apply_row<T>(L, L.t, g, e - g * L.F, VecAcc<T>{x}));
 }
 
-__global__ void k3_ghost_apply(Lev L, double *x, const double *upd)
+template <typename T> __global__ void k3_ghost_apply(Lev L, T *x, const T *upd)
 {
     const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (e >= 3 * L.F) return;
@@ -351,7 +360,8 @@ __device__ inline int rclass(unsigned char t) { return t == T_INTERNAL ? 1 : (t 
 // a cell-centred axis the fine cells 2T, 2T + 1 weigh 1/2 each.  The
 // weighted sum when every fine node lies in the frame and is of the coarse
 // node's class, else the plain mean of those that are, 0 if none.
-__global__ void __launch_bounds__(256) k3_restrict(Lev f, Lev c, const double *r, double *bH)
+template <typename T>
+__global__ void __launch_bounds__(256) k3_restrict(Lev f, Lev c, const T *r, T *bH)
 {
     const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (e >= 4 * c.F) {
@@ -362,12 +372,12 @@ __global__ void __launch_bounds__(256) k3_restrict(Lev f, Lev c, const double *r
     const long long s = e - g * c.F;
     const int cc = rclass(c.t[e]);
     if (cc == 0) {
-        bH[e] = 0.0;
+        bH[e] = (T)0;
         return;
     }
     const int C[3] = {coord(s, c.S, 0), coord(s, c.S, 1), coord(s, c.S, 2)};
     const long long Sf = f.S;
-    double sw = 0.0, su = 0.0;
+    T sw = 0, su = 0;
     int cnt = 0;
     bool all = true;
     const int n2 = (g == 0) ? 3 : 2, n1 = (g == 1) ? 3 : 2, n0 = (g == 2) ? 3 : 2;  // offsets along k, j, i
@@ -376,19 +386,19 @@ __global__ void __launch_bounds__(256) k3_restrict(Lev f, Lev c, const double *r
             for (int oi = 0; oi < n2; oi++) {
                 const int o[3] = {oi, oj, ok};
                 int fc[3];
-                double w = 1.0;
+                T w = 1;
                 bool in = true;
                 for (int ax = 0; ax < 3; ax++) {
                     const bool own = g < 3 && ax == g;
                     const int off = own ? o[ax] - 1 : o[ax];
                     fc[ax] = 2 * C[ax] + off;
-                    w *= own ? (off == 0 ? 0.5 : 0.25) : 0.5;
+                    w *= own ? (off == 0 ? (T)0.5 : (T)0.25) : (T)0.5;
                     in = in && fc[ax] >= -1 && fc[ax] <= f.N;
                 }
                 if (in) {
                     const long long fs = ((long long)(fc[2] + 1) * Sf + (fc[1] + 1)) * Sf + (fc[0] + 1);
                     if (rclass(f.t[g * f.F + fs]) == cc) {
-                        const double v = r[g * f.F + fs];
+                        const T v = r[g * f.F + fs];
                         sw += w * v;
                         su += v;
                         cnt++;
@@ -397,7 +407,7 @@ __global__ void __launch_bounds__(256) k3_restrict(Lev f, Lev c, const double *r
                 }
                 all = false;
             }
-    bH[e] = all ? sw : (cnt > 0 ? su / cnt : 0.0);
+    bH[e] = all ? sw : (cnt > 0 ? su / (T)cnt : (T)0);
 }
 
 // interpolation taps of fine index fi along one axis: a face axis (aligned,
@@ -428,7 +438,8 @@ __device__ inline int taps3(int fi, bool aligned, int lo, int hi, int *K, double
 
 // Prolongation (Sect. 4.3): x += P eH on every active fine node, trilinear
 // over the active coarse nodes with the weights renormalised; xi += xi_H
-__global__ void __launch_bounds__(256) k3_prolong(Lev f, Lev c, const double *eH, double *x)
+template <typename T>
+__global__ void __launch_bounds__(256) k3_prolong(Lev f, Lev c, const T *eH, T *x)
 {
     const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (e >= 4 * f.F) {
@@ -447,7 +458,7 @@ __global__ void __launch_bounds__(256) k3_prolong(Lev f, Lev c, const double *eH
         n[ax] = taps3(coord(s, f.S, ax), own, lo, hi, K[ax], W[ax]);
     }
     const long long Sc = c.S;
-    double acc = 0.0, ws = 0.0;
+    T acc = 0, ws = 0;
     for (int a2 = 0; a2 < n[2]; a2++)
         for (int a1 = 0; a1 < n[1]; a1++)
             for (int a0 = 0; a0 < n[0]; a0++) {
@@ -455,11 +466,11 @@ __global__ void __launch_bounds__(256) k3_prolong(Lev f, Lev c, const double *eH
                 if (ci < -1 || ci > c.N || cj < -1 || cj > c.N || ck < -1 || ck > c.N) continue;
                 const long long cs = g * c.F + ((long long)(ck + 1) * Sc + (cj + 1)) * Sc + (ci + 1);
                 if (c.t[cs] == T_INACTIVE) continue;
-                const double w = W[0][a0] * W[1][a1] * W[2][a2];
+                const T w = (T)(W[0][a0] * W[1][a1] * W[2][a2]);
                 acc += w * eH[cs];
                 ws += w;
             }
-    if (ws > 0.0) x[e] += (ws == 1.0 ? acc : acc / ws);
+    if (ws > (T)0) x[e] += (ws == (T)1 ? acc : acc / ws);
 }
 
 // ------------------------------------------------------------ coarsest level
@@ -476,7 +487,7 @@ __global__ void k3_assemble(Lev L, double *M, int n)
         v = (col >= 3 * L.F && col < 4 * L.F && L.t[col] == T_INTERNAL) ? L.h3 : 0.0;
     } else {
         const int g = (int)(row / L.F);
-        v = apply_row(L, L.t, g, row - g * L.F, UnitAcc{col});
+        v = apply_row<double>(L, L.t, g, row - g * L.F, UnitAcc{col});
     }
     M[id] = v;
 }
@@ -552,36 +563,39 @@ __global__ void k3_gj_init(const double *M, double *A, int n)
 }
 
 // x[0, n) = Minv b, one warp per row (the right half of the eliminated [M | I])
-__global__ void k3_gemv(const double *A, int n, const double *b, double *x)
+template <typename T> __global__ void k3_gemv(const double *A, int n, const T *b, T *x)
 {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (warp >= n) return;
     double s = 0.0;
-    for (int c = lane; c < n; c += 32) s += A[(long long)warp * 2 * n + n + c] * b[c];
+    for (int c = lane; c < n; c += 32) s += A[(long long)warp * 2 * n + n + c] * (double)b[c];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) x[warp] = s;
+    if (lane == 0) x[warp] = (T)s;
 }
 
-__global__ void k3_zero(double *x, long long n)
+template <typename T> __global__ void k3_zero(T *x, long long n)
 {
     const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (e < n) x[e] = 0.0;
+    if (e < n) x[e] = (T)0;
 }
 
-__global__ void k3_copy(const double *a, double *b, long long n)
+// x += e over the four frames and xi: the FP32 correction of the mixed mode
+__global__ void k3_add_float(double *x, const float *e, long long n)
 {
-    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (e < n) b[e] = a[e];
+    const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k < n) x[k] += (double)e[k];
 }
 
 // ------------------------------------------------------------ host side
 
 struct Ctx {
     int N, L, nu1, nu2, lambda;
+    int precision, inner;  // 0 FP64 cycles; 1 up to `inner` FP32 cycles per FP64 residual correction
     double alpha, dtau;
     cudaStream_t st;
     Lev lv[MAX_LEVELS];
     double *part, *red, *upd, *colk, *A, *M;
+    float *updf;
     int *flag;
     int nc;        // unknowns of the coarsest level
     int npart;
@@ -605,8 +619,9 @@ static bool valid(int N, int levels)
     return 4 * Sc * Sc * Sc + 1 <= COARSE_MAX;
 }
 
-// carve the workspace (every array 256-byte aligned); with base == nullptr only count
-static size_t carve(Ctx *c, char *base, int N, int levels)
+// carve the workspace (every array 256-byte aligned); with base == nullptr
+// only count.  mixed: the FP32 vectors of the inner cycles too
+static size_t carve(Ctx *c, char *base, int N, int levels, bool mixed)
 {
     size_t off = 0;
     auto take = [&](size_t bytes) -> char * {
@@ -623,6 +638,9 @@ static size_t carve(Ctx *c, char *base, int N, int levels)
         double *x = l > 0 ? (double *)take(sizeof(double) * VL) : nullptr;
         double *b = l > 0 ? (double *)take(sizeof(double) * VL) : nullptr;
         double *r = (double *)take(sizeof(double) * VL);
+        float *xf = mixed ? (float *)take(sizeof(float) * VL) : nullptr;
+        float *bf = mixed ? (float *)take(sizeof(float) * VL) : nullptr;
+        float *rf = mixed ? (float *)take(sizeof(float) * VL) : nullptr;
         if (c) {
             Lev &L = c->lv[l];
             L.N = Nl;
@@ -641,6 +659,9 @@ static size_t carve(Ctx *c, char *base, int N, int levels)
             L.x = x;
             L.b = b;
             L.r = r;
+            L.xf = xf;
+            L.bf = bf;
+            L.rf = rf;
         }
     }
     const long long S0 = N + 2, F0 = S0 * S0 * S0;
@@ -650,6 +671,7 @@ static size_t carve(Ctx *c, char *base, int N, int levels)
     double *part = (double *)take(sizeof(double) * npart);
     double *red = (double *)take(sizeof(double) * 8);
     double *upd = (double *)take(sizeof(double) * 3 * F0);
+    float *updf = mixed ? (float *)take(sizeof(float) * 3 * F0) : nullptr;
     double *colk = (double *)take(sizeof(double) * nc);
     double *A = (double *)take(sizeof(double) * (size_t)nc * 2 * nc);
     double *M = (double *)take(sizeof(double) * (size_t)nc * nc);
@@ -658,6 +680,7 @@ static size_t carve(Ctx *c, char *base, int N, int levels)
         c->part = part;
         c->red = red;
         c->upd = upd;
+        c->updf = updf;
         c->colk = colk;
         c->A = A;
         c->M = M;
@@ -688,15 +711,30 @@ static int red_grid(long long n)
     return (int)(b < 1024 ? (b < 1 ? 1 : b) : 1024);
 }
 
-static void residual(Ctx *c, int l, const double *x, const double *b, double *r)
+// the level vectors and the ghost-sweep scratch of precision T
+template <typename T> struct Vecs;
+template <> struct Vecs<double> {
+    static double *x(const Lev &L) { return L.x; }
+    static double *b(const Lev &L) { return L.b; }
+    static double *r(const Lev &L) { return L.r; }
+    static double *upd(const Ctx *c) { return c->upd; }
+};
+template <> struct Vecs<float> {
+    static float *x(const Lev &L) { return L.xf; }
+    static float *b(const Lev &L) { return L.bf; }
+    static float *r(const Lev &L) { return L.rf; }
+    static float *upd(const Ctx *c) { return c->updf; }
+};
+
+template <typename T, typename R> static void residual(Ctx *c, int l, const T *x, const T *b, R *r)
 {
     const Lev &L = c->lv[l];
     const int nb = red_grid(4 * L.F);
-    k3_residual<<<nb, 256, 0, c->st>>>(L, x, b, r, c->part);
-    k3_residual_final<<<1, 256, 0, c->st>>>(L, c->part, nb, b, r, c->red);
+    k3_residual<T, R><<<nb, 256, 0, c->st>>>(L, x, b, r, c->part);
+    k3_residual_final<T, R><<<1, 256, 0, c->st>>>(L, c->part, nb, b, r, c->red);
 }
 
-static void smooth(Ctx *c, int l, double *x, const double *b, int nu)
+template <typename T> static void smooth(Ctx *c, int l, T *x, const T *b, int nu)
 {
     const Lev &L = c->lv[l];
     const int per_row = (L.N + NCOL - 1) / NCOL;
@@ -705,7 +743,7 @@ static void smooth(Ctx *c, int l, double *x, const double *b, int nu)
         for (int col = 0; col < NCOL; col++) {
             const bool timed = c->tmr_level == l && !c->ev.empty();
             if (timed) cudaEventRecord(c->ev[2 * (c->tmr_n % 256)], c->st);
-            k3_box<<<nblk(nbox), 256, 0, c->st>>>(L, x, b, col);
+            k3_box<T><<<nblk(nbox), 256, 0, c->st>>>(L, x, b, col);
             if (timed) {
                 cudaEventRecord(c->ev[2 * (c->tmr_n % 256) + 1], c->st);
                 cudaEventSynchronize(c->ev[2 * (c->tmr_n % 256) + 1]);
@@ -716,36 +754,38 @@ static void smooth(Ctx *c, int l, double *x, const double *b, int nu)
             }
         }
         const int nb = red_grid(L.F);
-        k3_scalar_partial<<<nb, 256, 0, c->st>>>(L, x, b, c->part);
-        k3_scalar_final<<<1, 256, 0, c->st>>>(L, c->part, nb, x, b, c->red + 1);
-        k3_pshift<<<nblk(L.F), 256, 0, c->st>>>(L, x, c->red + 1);
+        k3_scalar_partial<T><<<nb, 256, 0, c->st>>>(L, x, b, c->part);
+        k3_scalar_final<T><<<1, 256, 0, c->st>>>(L, c->part, nb, x, b, c->red + 1);
+        k3_pshift<T><<<nblk(L.F), 256, 0, c->st>>>(L, x, c->red + 1);
+        T *upd = Vecs<T>::upd(c);
         for (int s = 0; s < c->lambda; s++) {
-            k3_ghost_update<<<nblk(3 * L.F), 256, 0, c->st>>>(L, x, b, c->dtau, c->upd);
-            k3_ghost_apply<<<nblk(3 * L.F), 256, 0, c->st>>>(L, x, c->upd);
+            k3_ghost_update<T><<<nblk(3 * L.F), 256, 0, c->st>>>(L, x, b, (T)c->dtau, upd);
+            k3_ghost_apply<T><<<nblk(3 * L.F), 256, 0, c->st>>>(L, x, upd);
         }
     }
 }
 
-static void coarse_solve(Ctx *c, const double *b, double *x)
+template <typename T> static void coarse_solve(Ctx *c, const T *b, T *x)
 {
     const int n = c->nc;
-    k3_gemv<<<(unsigned)((n * 32 + 255) / 256), 256, 0, c->st>>>(c->A, n, b, x);
+    k3_gemv<T><<<(unsigned)((n * 32 + 255) / 256), 256, 0, c->st>>>(c->A, n, b, x);
 }
 
-static void cycle(Ctx *c, int l, double *x, const double *b)
+template <typename T> static void cycle(Ctx *c, int l, T *x, const T *b)
 {
     if (l == c->L - 1) {
-        coarse_solve(c, b, x);
+        coarse_solve<T>(c, b, x);
         return;
     }
     const Lev &L = c->lv[l], &C = c->lv[l + 1];
-    smooth(c, l, x, b, c->nu1);
-    residual(c, l, x, b, L.r);
-    k3_restrict<<<nblk(4 * C.F + 1), 256, 0, c->st>>>(L, C, L.r, C.b);
-    k3_zero<<<nblk(C.VL), 256, 0, c->st>>>(C.x, C.VL);
-    cycle(c, l + 1, C.x, C.b);
-    k3_prolong<<<nblk(4 * L.F + 1), 256, 0, c->st>>>(L, C, C.x, x);
-    smooth(c, l, x, b, c->nu2);
+    T *r = Vecs<T>::r(L), *xc = Vecs<T>::x(C), *bc = Vecs<T>::b(C);
+    smooth<T>(c, l, x, b, c->nu1);
+    residual<T, T>(c, l, x, b, r);
+    k3_restrict<T><<<nblk(4 * C.F + 1), 256, 0, c->st>>>(L, C, r, bc);
+    k3_zero<T><<<nblk(C.VL), 256, 0, c->st>>>(xc, C.VL);
+    cycle<T>(c, l + 1, xc, bc);
+    k3_prolong<T><<<nblk(4 * L.F + 1), 256, 0, c->st>>>(L, C, xc, x);
+    smooth<T>(c, l, x, b, c->nu2);
 }
 
 static gp_status build_coarse(Ctx *c)
@@ -779,20 +819,20 @@ extern "C" {
 
 long long gp3_vec_len(int N) { return N >= 1 ? vlen(N) : 0; }
 
-gp_status gp3_workspace_size(int N, int levels, size_t *bytes)
+gp_status gp3_workspace_size(int N, int levels, int precision, size_t *bytes)
 {
-    if (!bytes || !valid(N, levels)) return GP_INVALID;
-    *bytes = carve(nullptr, nullptr, N, levels);
+    if (!bytes || !valid(N, levels) || precision < 0 || precision > 1) return GP_INVALID;
+    *bytes = carve(nullptr, nullptr, N, levels, precision == 1);
     return GP_OK;
 }
 
 gp_status gp3_create(gp3_ctx **out, int N, int levels, double alpha, int nu1, int nu2, int lambda, double dtau,
-                     void *ws, size_t ws_bytes, cudaStream_t stream)
+                     int precision, int inner, void *ws, size_t ws_bytes, cudaStream_t stream)
 {
     if (!out || !ws || !valid(N, levels) || !(alpha >= 0.0) || nu1 < 0 || nu2 < 0 || nu1 + nu2 < 1 || lambda < 0 ||
-        !(dtau > 0.0) || ((uintptr_t)ws % 256))
+        !(dtau > 0.0) || ((uintptr_t)ws % 256) || precision < 0 || precision > 1 || inner < 1 || inner > 16)
         return GP_INVALID;
-    if (ws_bytes < carve(nullptr, nullptr, N, levels)) return GP_INVALID;
+    if (ws_bytes < carve(nullptr, nullptr, N, levels, precision == 1)) return GP_INVALID;
     nvtxRangePushA("gp3_create");
     gp3_ctx *h = new gp3_ctx();
     Ctx *c = &h->c;
@@ -803,12 +843,14 @@ gp_status gp3_create(gp3_ctx **out, int N, int levels, double alpha, int nu1, in
     c->nu2 = nu2;
     c->lambda = lambda;
     c->dtau = dtau;
+    c->precision = precision;
+    c->inner = inner;
     c->st = stream;
     c->tmr_level = -1;
     c->tmr_n = 0;
     c->tmr_ms = 0.0;
     c->msg[0] = 0;
-    carve(c, (char *)ws, N, levels);
+    carve(c, (char *)ws, N, levels, precision == 1);
     for (int l = 0; l < levels; l++) {
         const Lev &L = c->lv[l];
         k3_types<<<nblk(4 * L.F), 256, 0, stream>>>(L.N, L.F, L.t);
@@ -845,7 +887,7 @@ gp_status gp3_residual(gp3_ctx *h, int level, const double *x, const double *b, 
 {
     if (!h || !x || !b || !r || level < 0 || level >= h->c.L) return GP_INVALID;
     Ctx *c = &h->c;
-    residual(c, level, x, b, r);
+    residual<double, double>(c, level, x, b, r);
     if (norm_host) {
         cudaMemcpyAsync(norm_host, c->red, sizeof(double), cudaMemcpyDeviceToHost, c->st);
         if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_check(c, "gp3_residual");
@@ -856,7 +898,7 @@ gp_status gp3_residual(gp3_ctx *h, int level, const double *x, const double *b, 
 gp_status gp3_smooth(gp3_ctx *h, int level, double *x, const double *b, int nu)
 {
     if (!h || !x || !b || level < 0 || level >= h->c.L || nu < 0) return GP_INVALID;
-    smooth(&h->c, level, x, b, nu);
+    smooth<double>(&h->c, level, x, b, nu);
     return cuda_check(&h->c, "gp3_smooth");
 }
 
@@ -864,7 +906,7 @@ gp_status gp3_restrict(gp3_ctx *h, int level, const double *r, double *bH)
 {
     if (!h || !r || !bH || level < 0 || level >= h->c.L - 1) return GP_INVALID;
     Ctx *c = &h->c;
-    k3_restrict<<<nblk(4 * c->lv[level + 1].F + 1), 256, 0, c->st>>>(c->lv[level], c->lv[level + 1], r, bH);
+    k3_restrict<double><<<nblk(4 * c->lv[level + 1].F + 1), 256, 0, c->st>>>(c->lv[level], c->lv[level + 1], r, bH);
     return cuda_check(c, "gp3_restrict");
 }
 
@@ -872,7 +914,7 @@ gp_status gp3_prolong(gp3_ctx *h, int level, const double *eH, double *x)
 {
     if (!h || !eH || !x || level < 0 || level >= h->c.L - 1) return GP_INVALID;
     Ctx *c = &h->c;
-    k3_prolong<<<nblk(4 * c->lv[level].F + 1), 256, 0, c->st>>>(c->lv[level], c->lv[level + 1], eH, x);
+    k3_prolong<double><<<nblk(4 * c->lv[level].F + 1), 256, 0, c->st>>>(c->lv[level], c->lv[level + 1], eH, x);
     return cuda_check(c, "gp3_prolong");
 }
 
@@ -880,23 +922,28 @@ gp_status gp3_cycle(gp3_ctx *h, double *x, const double *b)
 {
     if (!h || !x || !b) return GP_INVALID;
     nvtxRangePushA("gp3_cycle");
-    cycle(&h->c, 0, x, b);
+    cycle<double>(&h->c, 0, x, b);
     nvtxRangePop();
     return cuda_check(&h->c, "gp3_cycle");
 }
 
-gp_status gp3_solve(gp3_ctx *h, double *x, const double *b, double tol, int max_cycles, int *cycles, double *res,
-                    double *hist_host)
+gp_status gp3_solve(gp3_ctx *h, double *x, const double *b, double tol, int max_cycles, int *cycles,
+                    int *iterations, double *res, double *hist_host)
 {
     if (!h || !x || !b || !(tol > 0.0) || max_cycles < 0) return GP_INVALID;
     Ctx *c = &h->c;
     nvtxRangePushA("gp3_solve");
     const Lev &L = c->lv[0];
+    const bool mixed = c->precision == 1;
     double r0 = 0.0, rn = 0.0;
-    int k = 0;
+    int k = 0, ncyc = 0;
     gp_status st = GP_OK;
     for (;; k++) {
-        residual(c, 0, x, b, L.r);
+        // the FP64 residual (mixed: written rounded to FP32 as the inner cycles' right-hand side)
+        if (mixed)
+            residual<double, float>(c, 0, x, b, L.bf);
+        else
+            residual<double, double>(c, 0, x, b, L.r);
         cudaMemcpyAsync(&rn, c->red, sizeof(double), cudaMemcpyDeviceToHost, c->st);
         if (cudaStreamSynchronize(c->st) != cudaSuccess) {
             st = cuda_check(c, "gp3_solve");
@@ -909,13 +956,24 @@ gp_status gp3_solve(gp3_ctx *h, double *x, const double *b, double tol, int max_
             break;
         }
         if (rn <= tol) break;
-        if (k == max_cycles) {
+        if (ncyc >= max_cycles) {
             st = fail(c, GP_NOT_CONVERGED, "gp3_solve: not converged");
             break;
         }
-        cycle(c, 0, x, b);
+        if (mixed) {
+            // up to `inner` FP32 cycles from zero on the correction, added to x in FP64
+            const int n = c->inner < max_cycles - ncyc ? c->inner : max_cycles - ncyc;
+            k3_zero<float><<<nblk(L.VL), 256, 0, c->st>>>(L.xf, L.VL);
+            for (int q = 0; q < n; q++) cycle<float>(c, 0, L.xf, L.bf);
+            k3_add_float<<<nblk(4 * L.F + 1), 256, 0, c->st>>>(x, L.xf, 4 * L.F + 1);
+            ncyc += n;
+        } else {
+            cycle<double>(c, 0, x, b);
+            ncyc++;
+        }
     }
-    if (cycles) *cycles = k;
+    if (cycles) *cycles = ncyc;
+    if (iterations) *iterations = k;
     if (res) *res = rn;
     nvtxRangePop();
     return st;

@@ -19,10 +19,11 @@ _sig_done = False
 
 SIGNATURES = [
     ("gp3_vec_len", ctypes.c_longlong, [ctypes.c_int]),
-    ("gp3_workspace_size", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]),
+    ("gp3_workspace_size", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_size_t)]),
     ("gp3_create", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int, ctypes.c_double,
-                                  ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_void_p,
-                                  ctypes.c_size_t, ctypes.c_void_p]),
+                                  ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                  ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     ("gp3_destroy", ctypes.c_int, [ctypes.c_void_p]),
     ("gp3_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("gp3_types", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
@@ -33,8 +34,8 @@ SIGNATURES = [
     ("gp3_prolong", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     ("gp3_cycle", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("gp3_solve", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_int,
-                                 ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
-                                 ctypes.POINTER(ctypes.c_double)]),
+                                 ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     ("gp3_timer_start", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("gp3_timer_stop", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong),
                                       ctypes.POINTER(ctypes.c_double)]),
@@ -61,14 +62,15 @@ class Solver3D:
     """One 3-D context on the box domain: caller-owned workspace (a torch
     byte tensor on the device) and the device stream."""
 
-    def __init__(self, N, levels, alpha, nu1=2, nu2=1, lam=5, dtau=0.9, device="cuda", stream=None):
+    def __init__(self, N, levels, alpha, nu1=2, nu2=1, lam=5, dtau=0.9, precision=0, inner=4, device="cuda",
+                 stream=None):
         import torch
         self.torch = torch
         self.L = lib()
         self.N, self.levels = N, levels
         self.device = torch.device(device)
         nb = ctypes.c_size_t(0)
-        st = self.L.gp3_workspace_size(N, levels, ctypes.byref(nb))
+        st = self.L.gp3_workspace_size(N, levels, precision, ctypes.byref(nb))
         if st:
             raise GpmgError(st, "gp3_workspace_size")
         self.ws = torch.empty(nb.value + 256, dtype=torch.uint8, device=self.device)
@@ -76,8 +78,8 @@ class Solver3D:
         self._ws_ptr = ctypes.c_void_p((base + 255) // 256 * 256)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         ctx = ctypes.c_void_p()
-        st = self.L.gp3_create(ctypes.byref(ctx), N, levels, alpha, nu1, nu2, lam, dtau, self._ws_ptr, nb.value,
-                               ctypes.c_void_p(self.stream.cuda_stream))
+        st = self.L.gp3_create(ctypes.byref(ctx), N, levels, alpha, nu1, nu2, lam, dtau, precision, inner, self._ws_ptr,
+                               nb.value, ctypes.c_void_p(self.stream.cuda_stream))
         if st:
             raise GpmgError(st, "gp3_create")
         self.ctx = ctx
@@ -141,11 +143,13 @@ class Solver3D:
         self._check(self.L.gp3_cycle(self.ctx, _ptr(x), _ptr(b)), "gp3_cycle")
 
     def solve(self, x, b, tol, max_cycles=100):
-        """Returns (status, cycles, final residual, residual history)."""
-        cyc, res = ctypes.c_int(0), ctypes.c_double(0.0)
+        """Returns (status, cycles, final residual, FP64 residual history:
+        one entry before each iteration and one after the last)."""
+        cyc, it, res = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_double(0.0)
         h = (ctypes.c_double * (max_cycles + 1))()
-        st = self.L.gp3_solve(self.ctx, _ptr(x), _ptr(b), tol, max_cycles, ctypes.byref(cyc), ctypes.byref(res), h)
-        return st, cyc.value, res.value, np.array(h[:cyc.value + 1])
+        st = self.L.gp3_solve(self.ctx, _ptr(x), _ptr(b), tol, max_cycles, ctypes.byref(cyc), ctypes.byref(it),
+                              ctypes.byref(res), h)
+        return st, cyc.value, res.value, np.array(h[:it.value + 1])
 
     def timer_start(self, lev=0):
         self._check(self.L.gp3_timer_start(self.ctx, lev), "gp3_timer_start")

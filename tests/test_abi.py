@@ -101,7 +101,10 @@ def test_3d_sizes_are_checked_on_the_host():
     from paper_1911_00994_gb300 import mac3d
     L = mac3d.lib()
     nb = ctypes.c_size_t(0)
-    assert L.gp3_workspace_size(64, 5, ctypes.byref(nb)) == 0 and nb.value > 0
+    assert L.gp3_workspace_size(64, 5, 0, ctypes.byref(nb)) == 0 and nb.value > 0
+    n64 = nb.value
+    assert L.gp3_workspace_size(64, 5, 1, ctypes.byref(nb)) == 0 and nb.value > n64
+    assert L.gp3_workspace_size(64, 5, 2, ctypes.byref(nb)) == 1
     assert L.gp3_vec_len(64) == 4 * 66 ** 3 + 32
     for N, lev in ((64, 7), (48, 6), (64, 3), (0, 1), (64, 0)):
-        assert L.gp3_workspace_size(N, lev, ctypes.byref(nb)) == 1, (N, lev)
+        assert L.gp3_workspace_size(N, lev, 0, ctypes.byref(nb)) == 1, (N, lev)

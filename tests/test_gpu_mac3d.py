@@ -143,3 +143,30 @@ def test_polynomial_field_is_the_discrete_solution():
     st, cyc, res, hist = s.solve(xg, s.to_device(b), 1e-11, 80)
     assert st == 0, s.error()
     assert rel(s.to_flat(xg), xe) <= 1e-9
+
+
+@pytest.mark.parametrize("inner", [1, 4])
+def test_mixed_precision_solve_reaches_the_fp64_solution(inner):
+    # FP32 cycles inside FP64 residual correction (the spec precision
+    # scheme): the oracle's FP64 solution to the tolerance, with at most one
+    # correction's worth of cycles more than the FP64 cycles
+    from paper_1911_00994_gb300 import mac3d
+    N, levels = 16, 3
+    alpha = 2.0 / N ** 2
+    o = M.Mac3D(N, alpha, levels)
+    b = rand_vec(o, 0, 6)
+    xo, ho = o.solve(np.zeros_like(b), b, 1e-12, 60)
+    s64 = mac3d.Solver3D(N, levels, alpha)
+    x64 = s64.new_vec()
+    st, c64, r64, h64 = s64.solve(x64, s64.to_device(b), 1e-10, 80)
+    assert st == 0, s64.error()
+    s = mac3d.Solver3D(N, levels, alpha, precision=1, inner=inner)
+    xg = s.new_vec()
+    st, cyc, res, hist = s.solve(xg, s.to_device(b), 1e-10, 80)
+    assert st == 0, s.error()
+    assert res <= 1e-10 and hist[-1] <= 1e-10
+    assert rel(s.to_flat(xg), xo) <= 1e-8
+    assert cyc <= c64 + inner
+    # one FP64 residual per correction: fewer than cycles once corrections run several
+    if inner > 1:
+        assert len(hist) - 1 < cyc
