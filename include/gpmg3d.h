@@ -94,6 +94,24 @@ gp_status gp3_cycle(gp3_ctx *ctx, double *x, const double *b);
 gp_status gp3_solve(gp3_ctx *ctx, double *x, const double *b, double tol, int max_cycles, int *cycles,
                     int *iterations, double *res, double *hist_host);
 
+/* Ghost points of the sphere |x - c| < R (Sect. 3.3 in 3-D) on the grids of a
+ * level with N cells per side (the object is phi = R - |x - c| > 0).  Every
+ * velocity node of the box interior with phi >= 0 and a fluid neighbour
+ * (phi < 0) among its six is a ghost.  Algorithm 1 on the trilinear
+ * interpolant of phi on the grid's own nodes gives its boundary point B; its
+ * row of Eq. (BCu) interpolates at B from the 27 nodes G - (k, l, m) s h
+ * (k, l, m in {0, 1, 2}, s = the signs of the normal at G) with the weights
+ * L_k(theta_x) L_l(theta_y) L_m(theta_z), theta = s (x_G - x_B) / h.  The
+ * paper has no 3-D formulas; these are its 2-D rows with a third axis.
+ * Device outputs of capacity cap (order unspecified): node[n] and st[27 n]
+ * as indices into the level vector (frame g * (N + 2)^3 + slot), B[3 n],
+ * theta[3 n], w[27 n] (stencil node (k, l, m) at 9 m + 3 l + k).
+ * count_dev: two device ints of scratch; *count_host receives the number of
+ * ghosts.  Synchronises the stream.  GP_GEOMETRY when the ghosts exceed cap,
+ * a march does not leave the object or a stencil leaves the frame. */
+gp_status gp3_sphere_ghosts(int N, double cx, double cy, double cz, double R, int cap, int *count_dev, int *node,
+                            double *B, double *theta, int *st, double *w, int *count_host, cudaStream_t stream);
+
 /* kernel timer: CUDA events around every box-relaxation launch of `level`
  * until gp3_timer_stop, which returns the launches and their total ms */
 gp_status gp3_timer_start(gp3_ctx *ctx, int level);

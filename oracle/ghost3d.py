@@ -130,7 +130,8 @@ class Ghosts3D:
             Hp = H
             H = (H[0] - 0.5 * h * n[0], H[1] - 0.5 * h * n[1], H[2] - 0.5 * h * n[2])
             steps += 1
-        dist = math.sqrt((Hp[0] - H[0]) ** 2 + (Hp[1] - H[1]) ** 2 + (Hp[2] - H[2]) ** 2)
+        dx, dy, dz = Hp[0] - H[0], Hp[1] - H[1], Hp[2] - H[2]
+        dist = math.sqrt(dx * dx + dy * dy + dz * dz)
         nb = math.ceil(math.log2(dist / (0.01 * h)))
         K = H
         Mid = H

@@ -1,8 +1,8 @@
 """Build libgpmg.so in place with nvcc for sm_103a (GB300).
 
-Each translation unit compiles in parallel; geometry.cu is compiled with
--fmad=false (its floating-point decisions must use separately rounded
-operations).  The library links the CUDA runtime statically.
+Each translation unit compiles in parallel; geometry.cu and ghost3d.cu are
+compiled with -fmad=false (their floating-point decisions must use
+separately rounded operations).  The library links the CUDA runtime statically.
 """
 from __future__ import annotations
 
@@ -18,8 +18,8 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 OUT = os.path.join(HERE, "libgpmg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["geometry.cu", "ops.cu", "coarse.cu", "solver.cu", "noalloc.cu", "cn.cu", "krylov.cu", "adjoint.cu",
-           "probe.cu", "levelset.cu", "mac3d.cu"]
-EXTRA = {"geometry.cu": ["-fmad=false"]}
+           "probe.cu", "levelset.cu", "mac3d.cu", "ghost3d.cu"]
+EXTRA = {"geometry.cu": ["-fmad=false"], "ghost3d.cu": ["-fmad=false"]}
 
 
 def nvcc() -> str:

@@ -36,6 +36,10 @@ SIGNATURES = [
     ("gp3_solve", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_int,
                                  ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                  ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    ("gp3_sphere_ghosts", ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]),
     ("gp3_timer_start", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("gp3_timer_stop", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong),
                                       ctypes.POINTER(ctypes.c_double)]),
@@ -158,3 +162,29 @@ class Solver3D:
         n, ms = ctypes.c_longlong(0), ctypes.c_double(0.0)
         self._check(self.L.gp3_timer_stop(self.ctx, ctypes.byref(n), ctypes.byref(ms)), "gp3_timer_stop")
         return int(n.value), float(ms.value)
+
+
+def sphere_ghosts(N, c, R, cap=200000, device="cuda"):
+    """gp3_sphere_ghosts: the 3-D ghost rows of a sphere on a grid of N cells
+    per side, as numpy arrays sorted by node index (node, B, theta, st, w)."""
+    import torch
+    L = lib()
+    dev = torch.device(device)
+    cnt = torch.zeros(2, dtype=torch.int32, device=dev)
+    node = torch.zeros(max(cap, 1), dtype=torch.int32, device=dev)
+    B = torch.zeros(3 * max(cap, 1), dtype=torch.float64, device=dev)
+    th = torch.zeros(3 * max(cap, 1), dtype=torch.float64, device=dev)
+    st = torch.zeros(27 * max(cap, 1), dtype=torch.int32, device=dev)
+    w = torch.zeros(27 * max(cap, 1), dtype=torch.float64, device=dev)
+    n = ctypes.c_int(0)
+    stream = torch.cuda.current_stream(dev)
+    rc = L.gp3_sphere_ghosts(N, c[0], c[1], c[2], R, cap, _ptr(cnt), _ptr(node), _ptr(B), _ptr(th), _ptr(st),
+                             _ptr(w), ctypes.byref(n), ctypes.c_void_p(stream.cuda_stream))
+    if rc:
+        raise GpmgError(rc, "gp3_sphere_ghosts")
+    k = n.value
+    nd = node[:k].cpu().numpy()
+    o = np.argsort(nd)
+    return dict(node=nd[o], B=B[:3 * k].cpu().numpy().reshape(k, 3)[o],
+                theta=th[:3 * k].cpu().numpy().reshape(k, 3)[o], st=st[:27 * k].cpu().numpy().reshape(k, 27)[o],
+                w=w[:27 * k].cpu().numpy().reshape(k, 27)[o])
