@@ -579,26 +579,30 @@ __global__ void __launch_bounds__(TileGeom<T>::THREADS) k_box_tma(const __grid_c
 // rows.  Block (sx, sy) owns TW slot columns [c0, c0 + TW) of the frame rows
 // [r0, r0 + SH) (all three frames).  Its colour-c window is the same as the
 // tile sweep's: cells within 2 (4 - c) + 1 columns (rows) before and 2 (4 - c)
-// after the owned ones.  Instead of one window per tile, the block walks up
-// its rows in steps of R cell rows: at step s colour c relaxes the cell rows
-// [A0 + s R - 2 c, A0 + s R - 2 c + R) of its window (A0 = r0 - 10), one row
-// per warp, a lane per box of the row.  A box reads and writes only slots of
-// boxes at most two rows away, so with colour c trailing colour c - 1 by two
-// rows every box sees exactly the updates of the colour-by-colour sweep:
-// lower colours within two rows are done (in an earlier step, or earlier in
-// this step), higher colours within two rows are not yet.  The windows only
-// widen the owned slots horizontally, so a strip of rows recomputes 9 of
-// every TW + 9 boxes (the 32-row tiles recompute 48%).
+// after the owned ones.  The block walks up its rows in phases: in phase d
+// colour c relaxes the R cell rows [A0 + R d - (R + 2) c, ... + R) of its
+// window (A0 = r0 - 10), all five colours in the same phase, with one block
+// barrier between phases.  A box of cell row j reads frame rows j .. j + 3
+// and writes frame rows j + 1 and j + 2, so colours R + 2 rows apart touch
+// disjoint rows within a phase; across phases every box sees exactly the
+// updates of the colour-by-colour sweep: colour c - 1 has finished every row
+// up to two above it, colour c + 1 has not reached any row within two below.
+// The windows only widen the owned slots horizontally, so a strip recomputes
+// 9 of every TW + 9 boxes (the 32-row tiles recompute 48%).
 //
-// The frames stream through a ring of RB = 4 R rows in shared memory: chunk k
-// (frame rows [A0 + k R, A0 + k R + R)) is brought by TMA into ring rows
-// [k R mod RB, ...).  Step s reads chunks s - 1 .. s + 1; chunk s + 2 is
-// copied during step s into the slot of chunk s - 2, which the block wrote
-// out (owned rows, 16 bytes a lane) at the end of step s - 1, when its rows
-// had become final.  The right-hand side is read from global memory, pulled
-// into L2 two steps ahead by a bulk tensor prefetch.  As in the tile sweep
-// the result goes to the level's other vector y, a complete copy of the
-// swept x.
+// A phase holds twenty row tasks (five colours x R = 4 rows) for ten warps:
+// warp w takes tasks w and w + 10, task t being row t mod 4 of colour t / 4,
+// one lane per box of the row.
+//
+// The frames stream through a ring of ten chunks of R rows in shared memory:
+// chunk n (frame rows [C0 + n R, C0 + n R + R), C0 = A0 - 4 (R + 2)) lives
+// in ring rows [(n mod 10) R, ...).  Phase d reads chunks d .. d + 7; chunk
+// d + 8 is copied by TMA during phase d into the slot of chunk d - 2, whose
+// owned rows the block wrote out (16 bytes a lane) during phase d - 1, chunk
+// n being final once phase n is over.  The right-hand side is read from
+// global memory, pulled into L2 two chunks ahead by a bulk tensor prefetch.
+// As in the tile sweep the result goes to the level's other vector y, a
+// complete copy of the swept x.
 template <typename T> struct WaveGeom;
 template <> struct WaveGeom<float> {
     static constexpr int TW = 128, LW = 160;
@@ -606,15 +610,20 @@ template <> struct WaveGeom<float> {
 template <> struct WaveGeom<double> {
     static constexpr int TW = 64, LW = 96;
 };
-constexpr int WV_R = 8;               // cell rows per step and frame rows per chunk; one warp each
-constexpr int WV_RB = 4 * WV_R;       // ring rows
-constexpr int WV_THREADS = 32 * WV_R;
+constexpr int WV_R = 4;               // cell rows of a colour per phase, frame rows per chunk
+constexpr int WV_LAG = WV_R + 2;      // rows between consecutive colours within a phase
+constexpr int WV_NCHK = 10;           // ring chunks
+constexpr int WV_RB = WV_NCHK * WV_R; // ring rows
+constexpr int WV_NW = 10;             // warps: two of the 5 R row tasks each
+constexpr int WV_THREADS = 32 * WV_NW;
 constexpr int WV_A = 10;              // colour 0's window starts 10 rows below the owned ones
-// colour 4 trails colour 0 by 8 rows and a box reads one row below its cell:
-// step s reads frame rows [A0 + s R - 8, A0 + s R + R + 3), inside chunks s - 1 .. s + 1
-static_assert(WV_R >= 8 && WV_R + 3 <= 2 * WV_R, "a step must read only chunks s - 1 .. s + 1");
-// R rows up move the colour pattern (i + 3 j) mod 5 by one column: -3 R = 1 (mod 5)
-static_assert((3 * WV_R) % 5 == 4, "the per-step phase advance assumes -3 R = 1 (mod 5)");
+// phase d reads frame rows [C0 + R d, C0 + R d + 4 LAG + R + 3) = chunks d .. d + 7,
+// chunk d is final after it, and the ring holds chunks d - 1 (written out) .. d + 8 (in flight)
+static_assert(WV_R == 4 && WV_LAG == 6 && (4 * WV_LAG + WV_R + 3 - 1) / WV_R == 7 && WV_NCHK == 10,
+              "the chunk schedule is worked out for R = 4");
+static_assert(5 * WV_R == 2 * WV_NW, "two row tasks per warp");
+// R rows up move the colour pattern (i + 3 j) mod 5 by three columns: -3 R = 3 (mod 5)
+static_assert((3 * WV_R) % 5 == 2, "the per-phase pattern advance assumes -3 R = 3 (mod 5)");
 // every box of a colour row fits the 32 lanes of its warp
 static_assert((WaveGeom<float>::TW + 16 + 1 + 4) / 5 <= 32 && (WaveGeom<double>::TW + 16 + 1 + 4) / 5 <= 32,
               "a colour row holds more boxes than a warp has lanes");
@@ -626,10 +635,13 @@ static_assert(WaveGeom<float>::LW - TT_CLO - WaveGeom<float>::TW >= 10 &&
 // the write-out: one 16-byte vector per lane covers a strip row of a frame
 static_assert(WaveGeom<float>::TW * sizeof(float) <= 32 * 16 && WaveGeom<double>::TW * sizeof(double) <= 32 * 16,
               "a strip row must be at most 32 vectors of 16 bytes");
+// TMA destinations: every chunk slot and frame of the ring starts on 128 bytes
+static_assert((WV_R * WaveGeom<float>::LW) % 128 == 0 && (WV_R * WaveGeom<double>::LW) % 128 == 0,
+              "chunk slots must stay 128-byte aligned");
 
 template <typename T> __host__ __device__ constexpr size_t wv_smem()
 {
-    return (size_t)WV_RB * WaveGeom<T>::LW * (3 * sizeof(T) + 1) + 4 * sizeof(uint64_t);
+    return (size_t)WV_RB * WaveGeom<T>::LW * (3 * sizeof(T) + 1) + WV_NCHK * sizeof(uint64_t);
 }
 
 // the four ring rows -1 .. 2 around a box, as element offsets into a frame
@@ -672,10 +684,10 @@ template <typename T> __device__ __forceinline__ void wave_rhs(const T *b, int F
 }
 
 template <typename T>
-__global__ void __launch_bounds__(WV_THREADS) k_box_wave(const __grid_constant__ CUtensorMap mx,
-                                                         const __grid_constant__ CUtensorMap mc,
-                                                         const __grid_constant__ CUtensorMap mb, LevelArgs<T> A,
-                                                         const T *x, const T *b, T *y, int SH, unsigned *err)
+__global__ void __launch_bounds__(WV_THREADS, 2) k_box_wave(const __grid_constant__ CUtensorMap mx,
+                                                            const __grid_constant__ CUtensorMap mc,
+                                                            const __grid_constant__ CUtensorMap mb, LevelArgs<T> A,
+                                                            const T *x, const T *b, T *y, int SH, unsigned *err)
 {
     constexpr int TW = WaveGeom<T>::TW, LW = WaveGeom<T>::LW, R = WV_R, RB = WV_RB, FR = RB * LW;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -686,100 +698,123 @@ __global__ void __launch_bounds__(WV_THREADS) k_box_wave(const __grid_constant__
     uint64_t *bar = (uint64_t *)(sc + FR);
     const int N = A.N;
     const int c0 = blockIdx.x * TW, r0 = blockIdx.y * SH;
-    const int col0 = c0 - TT_CLO, A0 = r0 - WV_A;
+    const int col0 = c0 - TT_CLO, A0 = r0 - WV_A, C0 = A0 - 4 * WV_LAG;
     const int rend = min(r0 + SH, N + 2);
-    // colour 4's window ends at min(r0 - 1 + SH, N) and its rows at step s
-    // start at A0 + s R - 8; every colour's window ends at the same step
-    const int S = (min(r0 - 1 + SH, N) - A0 + 8 + R - 1) / R;
-    const int NCH = S + 1;  // chunks 0 .. S
+    // phases: until colour 4, the last, has passed the end of its window
+    // (every other colour's window ends earlier in phase terms)
+    int ND = 0;
+#pragma unroll
+    for (int c = 0; c < 5; c++) {
+        const int jhi = min(r0 - 1 + SH + 2 * (4 - c), N);
+        ND = max(ND, (jhi - (A0 - WV_LAG * c) + R - 1) / R);
+    }
+    const int LAST = ND + 6;  // the highest chunk the phases read
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        for (int q = 0; q < 4; q++)
+        for (int q = 0; q < WV_NCHK; q++)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar + q)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    auto load_chunk = [&](int k) {
-        const int q = k & 3;
+    const int rows_total = N + 2;
+    auto load_chunk = [&](int n) {
+        const int q = n % WV_NCHK, X = C0 + n * R;
         const unsigned bytes = (unsigned)(R * LW * (3 * sizeof(T) + 1));
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar + q)), "r"(bytes)
                      : "memory");
-        for (int f = 0; f < 3; f++) tma_load_3d(su + f * FR + q * R * LW, &mx, col0, A0 + k * R, f, bar + q);
-        tma_load_2d(sc + q * R * LW, &mc, col0, A0 + k * R, bar + q);
-        tma_prefetch_3d(&mb, max(col0, 0), max(A0 + k * R, 0), 0);  // a hint: kept inside the tensor
+        for (int f = 0; f < 3; f++) tma_load_3d(su + f * FR + q * R * LW, &mx, col0, X, f, bar + q);
+        tma_load_2d(sc + q * R * LW, &mc, col0, X, bar + q);
+        // a hint for the right-hand side two chunks on, kept inside the tensor
+        const int Xb = X + 2 * R;
+        if (Xb < rows_total) tma_prefetch_3d(&mb, max(col0, 0), max(Xb, 0), 0);
+    };
+    // chunk n sits in slot n mod 10, the (n / 10)-th copy into that slot
+    auto wait_chunk = [&](int n, unsigned long long ns) {
+        return mbar_wait_parity_bounded(bar + n % WV_NCHK, (unsigned)(n / WV_NCHK) & 1u, ns);
     };
     if (threadIdx.x == 0) {
-        load_chunk(0);
-        load_chunk(1);
+        for (int n = 0; n < 8; n++) load_chunk(n);
     }
     const T xi = x[3 * A.F];
     const int F = (int)A.F, P = A.P;
-    // Lane `lane` of warp `warp` relaxes, at step s, the box of colour c in
-    // cell row j = A0 + s R - 2 c + warp and column i = iu_c + ph_c + 5 lane,
-    // the first cell of the colour pattern (i + 3 j) mod 5 = c at or after
-    // iu_c plus every fifth; R = 8 rows move the pattern by one column, so
-    // ph_c advances by one (mod 5) per step.  bq[c]: the right-hand side of
-    // that box, loaded one step ahead of its use.
-    int ph[5];
-    T bq[5][5];
+    // task k of this warp: row rr of colour cc; at phase d its cell row is
+    // j = A0 + R d - LAG cc + rr, at ring row lm = (j - C0) mod RB, and lane
+    // `lane` relaxes column i = iu + ph + 5 lane, the first cell of the colour
+    // pattern (i + 3 j) mod 5 = cc at or after iu plus every fifth.  bq[k]:
+    // the right-hand side of that box, loaded one phase ahead of its use.
+    int cc[2], jt[2], lm[2], ph[2], iu[2], jlo[2], jhi[2], ilo[2], ihi[2];
+    T bq[2][5];
 #pragma unroll
-    for (int c = 0; c < 5; c++) {
-        const int lo = 2 * (4 - c) + 1, hi = lo - 1, iu = c0 - 1 - lo, j = A0 - 2 * c + warp;
-        ph[c] = (int)((unsigned)(c + (5 << 28) - 3 * j - iu) % 5u);
-        const int i = iu + ph[c] + 5 * lane;
+    for (int k = 0; k < 2; k++) {
+        const int t = warp + WV_NW * k, rr = t & 3;
+        cc[k] = t >> 2;
+        const int lo = 2 * (4 - cc[k]) + 1, hi = lo - 1;
+        iu[k] = c0 - 1 - lo;
+        jlo[k] = max(r0 - 1 - lo, 0);
+        jhi[k] = min(r0 - 1 + SH + hi, N);
+        ilo[k] = max(iu[k], 0);
+        ihi[k] = min(c0 - 1 + TW + hi, N);
+        jt[k] = A0 - WV_LAG * cc[k] + rr;
+        lm[k] = 4 * WV_LAG - WV_LAG * cc[k] + rr;  // j - C0 at phase 0, in [0, RB)
+        ph[k] = (int)((unsigned)(cc[k] + (5 << 28) - 3 * jt[k] - iu[k]) % 5u);
+        const int i = iu[k] + ph[k] + 5 * lane;
 #pragma unroll
-        for (int k = 0; k < 5; k++) bq[c][k] = (T)0;
-        if (j >= max(r0 - 1 - lo, 0) && j < min(r0 - 1 + SH + hi, N) && i >= max(iu, 0) && i < min(c0 - 1 + TW + hi, N))
-            wave_rhs(b, F, P, i, j, bq[c]);
+        for (int q = 0; q < 5; q++) bq[k][q] = (T)0;
+        if (jt[k] >= jlo[k] && jt[k] < jhi[k] && i >= ilo[k] && i < ihi[k]) wave_rhs(b, F, P, i, jt[k], bq[k]);
     }
     using V = typename Vec16<T>::type;
     constexpr int VW = 16 / sizeof(T);
-    // owned rows of chunk k, one warp per row and one 16-byte vector per lane
-    auto write_chunk = [&](int k) {
-        const int X = A0 + k * R + warp, col = c0 + lane * VW;
-        if (X >= r0 && X < rend && lane * VW < TW && col < A.P) {
-            const int o = ((k * R + warp) & (RB - 1)) * LW + TT_CLO + lane * VW;
-            const long long g = (long long)X * A.P + col;
-#pragma unroll
-            for (int f = 0; f < 3; f++) *(V *)(y + f * A.F + g) = *(const V *)(su + f * FR + o);
+    // owned rows of chunk n: twelve (frame, row) pairs over the ten warps,
+    // one 16-byte vector per lane
+    auto write_chunk = [&](int n) {
+        const int col = c0 + lane * VW;
+        if (lane * VW >= TW || col >= A.P) return;
+        for (int p = warp; p < 3 * R; p += WV_NW) {
+            const int f = p / R, rr = p - f * R, X = C0 + n * R + rr;
+            if (X >= r0 && X < rend) {
+                const int o = ((n % WV_NCHK) * R + rr) * LW + TT_CLO + lane * VW;
+                *(V *)(y + f * A.F + (long long)X * A.P + col) = *(const V *)(su + f * FR + o);
+            }
         }
     };
-    for (int s = 0; s < S; s++) {
+    for (int d = 0; d < ND; d++) {
+        // chunks d .. d + 7 are needed; d + 7 is the only one not yet confirmed
+        // (at d = 0: all eight of the prologue)
         bool ok = true;
-        if (s == 0) ok = mbar_wait_parity_bounded(bar, 0, TT_WAIT_NS);
-        ok = mbar_wait_parity_bounded(bar + ((s + 1) & 3), ((s + 1) >> 2) & 1, TT_WAIT_NS) && ok;
+        if (d == 0)
+            for (int n = 0; n < 7; n++) ok = wait_chunk(n, TT_WAIT_NS) && ok;
+        ok = wait_chunk(d + 7, TT_WAIT_NS) && ok;
         if (!__syncthreads_and(ok)) {
             // copies still in flight get a second bounded wait before the
             // block leaves; the NaN in the scalar block makes the solve fail
-            if (s == 0) mbar_wait_parity_bounded(bar, 0, TT_WAIT_NS / 2);
-            mbar_wait_parity_bounded(bar + ((s + 1) & 3), ((s + 1) >> 2) & 1, TT_WAIT_NS / 2);
+            if (d == 0)
+                for (int n = 0; n < 7; n++) wait_chunk(n, TT_WAIT_NS / 2);
+            wait_chunk(d + 7, TT_WAIT_NS / 2);
             if (threadIdx.x == 0) {
                 atomicOr(err + 2, 1u);
                 y[3 * A.F] = (T)NAN;
             }
             return;
         }
-        // chunk s + 2 into the slot of chunk s - 2 (written out before the
+        // chunk d + 8 into the slot of chunk d - 2 (written out before the
         // barrier above); the generic-proxy reads are ordered before the copy
-        if (threadIdx.x == 0 && s + 2 < NCH) {
+        if (threadIdx.x == 0 && d + 8 <= LAST) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            load_chunk(s + 2);
+            load_chunk(d + 8);
         }
 #pragma unroll
-        for (int c = 0; c < 5; c++) {
-            const int lo = 2 * (4 - c) + 1, hi = lo - 1, iu = c0 - 1 - lo;
-            const int jlo = max(r0 - 1 - lo, 0), jhi = min(r0 - 1 + SH + hi, N);
-            const int ilo = max(iu, 0), ihi = min(c0 - 1 + TW + hi, N);
-            const int t = s * R + warp - 2 * c, j = A0 + t;  // frame rows j .. j + 3 = J - 1 .. J + 2
-            const int i = iu + ph[c] + 5 * lane;
-            if (j >= jlo && j < jhi && i >= ilo && i < ihi) {
+        for (int k = 0; k < 2; k++) {
+            const int i = iu[k] + ph[k] + 5 * lane;
+            if (jt[k] >= jlo[k] && jt[k] < jhi[k] && i >= ilo[k] && i < ihi[k]) {
                 const int lc = i + 1 - col0;
-                const int o0 = ((t) & (RB - 1)) * LW + lc, o1 = ((t + 1) & (RB - 1)) * LW + lc;
-                const int o2 = ((t + 2) & (RB - 1)) * LW + lc, o3 = ((t + 3) & (RB - 1)) * LW + lc;
+                const int l1 = lm[k] + 1 < RB ? lm[k] + 1 : lm[k] + 1 - RB;
+                const int l2 = lm[k] + 2 < RB ? lm[k] + 2 : lm[k] + 2 - RB;
+                const int l3 = lm[k] + 3 < RB ? lm[k] + 3 : lm[k] + 3 - RB;
+                const int o0 = lm[k] * LW + lc, o1 = l1 * LW + lc, o2 = l2 * LW + lc, o3 = l3 * LW + lc;
                 const unsigned code = sc[o1];
                 if (code & BOX_FULL) {
                     const RingRows4<T> U{su, o0, o1, o2, o3}, Vv{sv, o0, o1, o2, o3}, Pv{sp, o0, o1, o2, o3};
-                    const T *q = bq[c];
+                    const T *q = bq[k];
                     if (code == BOX_ALL)
                         box_solve_v<T, true>(U, Vv, Pv, q[0], q[1], q[2], q[3], q[4], xi, true, true, true, true, A.K);
                     else
@@ -787,18 +822,19 @@ __global__ void __launch_bounds__(WV_THREADS) k_box_wave(const __grid_constant__
                                        code & BOX_S, code & BOX_N, A.K);
                 }
             }
-            // this colour's box of the next step: R rows up, the pattern one column on
-            ph[c] = ph[c] == 4 ? 0 : ph[c] + 1;
-            const int jn = j + R, in = iu + ph[c] + 5 * lane;
-            if (jn >= jlo && jn < jhi && in >= ilo && in < ihi) wave_rhs(b, F, P, in, jn, bq[c]);
-            __syncthreads();
+            // this task's box of the next phase: R rows up, the pattern three columns on
+            jt[k] += R;
+            lm[k] = lm[k] + R < RB ? lm[k] + R : lm[k] + R - RB;
+            ph[k] = ph[k] + 3 < 5 ? ph[k] + 3 : ph[k] - 2;
+            const int in = iu[k] + ph[k] + 5 * lane;
+            if (jt[k] >= jlo[k] && jt[k] < jhi[k] && in >= ilo[k] && in < ihi[k]) wave_rhs(b, F, P, in, jt[k], bq[k]);
         }
-        // chunk s - 1 is final: its rows are written by boxes of rows at most
-        // two below, the last of them colour 4 of this step
-        if (s >= 1) write_chunk(s - 1);
+        // chunk d - 1 became final with phase d - 1 and is not read any more
+        if (d >= 1) write_chunk(d - 1);
     }
-    write_chunk(S - 1);
-    write_chunk(S);
+    __syncthreads();
+    for (int n = ND - 1; n <= LAST; n++)
+        if (n >= 0) write_chunk(n);
     if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x < NSCAL) y[3 * A.F + threadIdx.x] = x[3 * A.F + threadIdx.x];
 }
 
