@@ -698,7 +698,7 @@ __global__ void __launch_bounds__(WV_THREADS, 2) k_box_wave(const __grid_constan
     uint64_t *bar = (uint64_t *)(sc + FR);
     const int N = A.N;
     const int c0 = blockIdx.x * TW, r0 = blockIdx.y * SH;
-    const int col0 = c0 - TT_CLO, A0 = r0 - WV_A, C0 = A0 - 4 * WV_LAG;
+    const int col0 = c0 - TT_CLO, A0 = r0 - WV_A;
     const int rend = min(r0 + SH, N + 2);
     // phases: until colour 4, the last, has passed the end of its window
     // (every other colour's window ends earlier in phase terms)
@@ -708,7 +708,8 @@ __global__ void __launch_bounds__(WV_THREADS, 2) k_box_wave(const __grid_constan
         const int jhi = min(r0 - 1 + SH + 2 * (4 - c), N);
         ND = max(ND, (jhi - (A0 - WV_LAG * c) + R - 1) / R);
     }
-    const int LAST = ND + 6;  // the highest chunk the phases read
+    // the highest chunk a box reads: colour 0's last row plus two
+    const int LAST = (min(r0 - 1 + SH + 8, N) + 2 - A0) / R;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int q = 0; q < WV_NCHK; q++)
@@ -718,14 +719,14 @@ __global__ void __launch_bounds__(WV_THREADS, 2) k_box_wave(const __grid_constan
     __syncthreads();
     const int rows_total = N + 2;
     auto load_chunk = [&](int n) {
-        const int q = n % WV_NCHK, X = C0 + n * R;
+        const int q = n % WV_NCHK, X = A0 + n * R;
         const unsigned bytes = (unsigned)(R * LW * (3 * sizeof(T) + 1));
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar + q)), "r"(bytes)
                      : "memory");
         for (int f = 0; f < 3; f++) tma_load_3d(su + f * FR + q * R * LW, &mx, col0, X, f, bar + q);
         tma_load_2d(sc + q * R * LW, &mc, col0, X, bar + q);
-        // a hint for the right-hand side two chunks on, kept inside the tensor
-        const int Xb = X + 2 * R;
+        // a hint for the right-hand side three chunks on, kept inside the tensor
+        const int Xb = X + 3 * R;
         if (Xb < rows_total) tma_prefetch_3d(&mb, max(col0, 0), max(Xb, 0), 0);
     };
     // chunk n sits in slot n mod 10, the (n / 10)-th copy into that slot
@@ -733,34 +734,41 @@ __global__ void __launch_bounds__(WV_THREADS, 2) k_box_wave(const __grid_constan
         return mbar_wait_parity_bounded(bar + n % WV_NCHK, (unsigned)(n / WV_NCHK) & 1u, ns);
     };
     if (threadIdx.x == 0) {
-        for (int n = 0; n < 8; n++) load_chunk(n);
+        load_chunk(0);
+        if (LAST >= 1) load_chunk(1);
     }
     const T xi = x[3 * A.F];
     const int F = (int)A.F, P = A.P;
     // task k of this warp: row rr of colour cc; at phase d its cell row is
-    // j = A0 + R d - LAG cc + rr, at ring row lm = (j - C0) mod RB, and lane
-    // `lane` relaxes column i = iu + ph + 5 lane, the first cell of the colour
-    // pattern (i + 3 j) mod 5 = cc at or after iu plus every fifth.  bq[k]:
-    // the right-hand side of that box, loaded one phase ahead of its use.
-    int cc[2], jt[2], lm[2], ph[2], iu[2], jlo[2], jhi[2], ilo[2], ihi[2];
-    T bq[2][5];
+    // j = A0 + R d - LAG cc + rr, at ring row lm = (j - A0) mod RB (rows
+    // below A0 are never read), and lane `lane` relaxes column
+    // i = iu + ph + 5 lane, the first cell of the colour pattern
+    // (i + 3 j) mod 5 = cc at or after iu plus every fifth.  bq[k]: the
+    // right-hand side of that box, bn[k] the next phase's; each is loaded two
+    // phases ahead of its use.
+    int jt[2], lm[2], ph[2], iu[2], jlo[2], jhi[2], ilo[2], ihi[2];
+    T bq[2][5], bn[2][5];
+    auto in_window = [&](int k, int j, int i) {
+        return j >= jlo[k] && j < jhi[k] && i >= ilo[k] && i < ihi[k];
+    };
 #pragma unroll
     for (int k = 0; k < 2; k++) {
-        const int t = warp + WV_NW * k, rr = t & 3;
-        cc[k] = t >> 2;
-        const int lo = 2 * (4 - cc[k]) + 1, hi = lo - 1;
+        const int t = warp + WV_NW * k, rr = t & 3, cc = t >> 2;
+        const int lo = 2 * (4 - cc) + 1, hi = lo - 1;
         iu[k] = c0 - 1 - lo;
         jlo[k] = max(r0 - 1 - lo, 0);
         jhi[k] = min(r0 - 1 + SH + hi, N);
         ilo[k] = max(iu[k], 0);
         ihi[k] = min(c0 - 1 + TW + hi, N);
-        jt[k] = A0 - WV_LAG * cc[k] + rr;
-        lm[k] = 4 * WV_LAG - WV_LAG * cc[k] + rr;  // j - C0 at phase 0, in [0, RB)
-        ph[k] = (int)((unsigned)(cc[k] + (5 << 28) - 3 * jt[k] - iu[k]) % 5u);
-        const int i = iu[k] + ph[k] + 5 * lane;
+        jt[k] = A0 - WV_LAG * cc + rr;
+        lm[k] = (2 * RB - WV_LAG * cc + rr) % RB;
+        ph[k] = (int)((unsigned)(cc + (5 << 28) - 3 * jt[k] - iu[k]) % 5u);
 #pragma unroll
-        for (int q = 0; q < 5; q++) bq[k][q] = (T)0;
-        if (jt[k] >= jlo[k] && jt[k] < jhi[k] && i >= ilo[k] && i < ihi[k]) wave_rhs(b, F, P, i, jt[k], bq[k]);
+        for (int q = 0; q < 5; q++) bq[k][q] = bn[k][q] = (T)0;
+        const int i = iu[k] + ph[k] + 5 * lane;
+        if (in_window(k, jt[k], i)) wave_rhs(b, F, P, i, jt[k], bq[k]);
+        const int p1 = ph[k] + 3 < 5 ? ph[k] + 3 : ph[k] - 2, i1 = iu[k] + p1 + 5 * lane;
+        if (in_window(k, jt[k] + R, i1)) wave_rhs(b, F, P, i1, jt[k] + R, bn[k]);
     }
     using V = typename Vec16<T>::type;
     constexpr int VW = 16 / sizeof(T);
@@ -770,7 +778,7 @@ __global__ void __launch_bounds__(WV_THREADS, 2) k_box_wave(const __grid_constan
         const int col = c0 + lane * VW;
         if (lane * VW >= TW || col >= A.P) return;
         for (int p = warp; p < 3 * R; p += WV_NW) {
-            const int f = p / R, rr = p - f * R, X = C0 + n * R + rr;
+            const int f = p / R, rr = p - f * R, X = A0 + n * R + rr;
             if (X >= r0 && X < rend) {
                 const int o = ((n % WV_NCHK) * R + rr) * LW + TT_CLO + lane * VW;
                 *(V *)(y + f * A.F + (long long)X * A.P + col) = *(const V *)(su + f * FR + o);
@@ -778,34 +786,32 @@ __global__ void __launch_bounds__(WV_THREADS, 2) k_box_wave(const __grid_constan
         }
     };
     for (int d = 0; d < ND; d++) {
-        // chunks d .. d + 7 are needed; d + 7 is the only one not yet confirmed
-        // (at d = 0: all eight of the prologue)
+        // phase d reads chunks d - 6 .. d + 1 (those in 0 .. LAST); d + 1 is
+        // the only one not yet confirmed (at d = 0: both of the prologue)
         bool ok = true;
-        if (d == 0)
-            for (int n = 0; n < 7; n++) ok = wait_chunk(n, TT_WAIT_NS) && ok;
-        ok = wait_chunk(d + 7, TT_WAIT_NS) && ok;
+        if (d == 0) ok = wait_chunk(0, TT_WAIT_NS);
+        if (d + 1 <= LAST) ok = wait_chunk(d + 1, TT_WAIT_NS) && ok;
         if (!__syncthreads_and(ok)) {
             // copies still in flight get a second bounded wait before the
             // block leaves; the NaN in the scalar block makes the solve fail
-            if (d == 0)
-                for (int n = 0; n < 7; n++) wait_chunk(n, TT_WAIT_NS / 2);
-            wait_chunk(d + 7, TT_WAIT_NS / 2);
+            if (d == 0) wait_chunk(0, TT_WAIT_NS / 2);
+            if (d + 1 <= LAST) wait_chunk(d + 1, TT_WAIT_NS / 2);
             if (threadIdx.x == 0) {
                 atomicOr(err + 2, 1u);
                 y[3 * A.F] = (T)NAN;
             }
             return;
         }
-        // chunk d + 8 into the slot of chunk d - 2 (written out before the
+        // chunk d + 2 into the slot of chunk d - 8 (written out before the
         // barrier above); the generic-proxy reads are ordered before the copy
-        if (threadIdx.x == 0 && d + 8 <= LAST) {
+        if (threadIdx.x == 0 && d + 2 <= LAST) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            load_chunk(d + 8);
+            load_chunk(d + 2);
         }
 #pragma unroll
         for (int k = 0; k < 2; k++) {
             const int i = iu[k] + ph[k] + 5 * lane;
-            if (jt[k] >= jlo[k] && jt[k] < jhi[k] && i >= ilo[k] && i < ihi[k]) {
+            if (in_window(k, jt[k], i)) {
                 const int lc = i + 1 - col0;
                 const int l1 = lm[k] + 1 < RB ? lm[k] + 1 : lm[k] + 1 - RB;
                 const int l2 = lm[k] + 2 < RB ? lm[k] + 2 : lm[k] + 2 - RB;
@@ -822,19 +828,22 @@ __global__ void __launch_bounds__(WV_THREADS, 2) k_box_wave(const __grid_constan
                                        code & BOX_S, code & BOX_N, A.K);
                 }
             }
-            // this task's box of the next phase: R rows up, the pattern three columns on
+            // this task's box of the next phase: R rows up, the pattern three
+            // columns on; its right-hand side is already loaded, the one of
+            // the phase after is fetched now
             jt[k] += R;
             lm[k] = lm[k] + R < RB ? lm[k] + R : lm[k] + R - RB;
             ph[k] = ph[k] + 3 < 5 ? ph[k] + 3 : ph[k] - 2;
-            const int in = iu[k] + ph[k] + 5 * lane;
-            if (jt[k] >= jlo[k] && jt[k] < jhi[k] && in >= ilo[k] && in < ihi[k]) wave_rhs(b, F, P, in, jt[k], bq[k]);
+#pragma unroll
+            for (int q = 0; q < 5; q++) bq[k][q] = bn[k][q];
+            const int p2 = ph[k] + 3 < 5 ? ph[k] + 3 : ph[k] - 2, i2 = iu[k] + p2 + 5 * lane;
+            if (in_window(k, jt[k] + R, i2)) wave_rhs(b, F, P, i2, jt[k] + R, bn[k]);
         }
-        // chunk d - 1 became final with phase d - 1 and is not read any more
-        if (d >= 1) write_chunk(d - 1);
+        // chunk d - 7 became final with phase d - 1 and is not read any more
+        if (d >= 7) write_chunk(d - 7);
     }
     __syncthreads();
-    for (int n = ND - 1; n <= LAST; n++)
-        if (n >= 0) write_chunk(n);
+    for (int n = max(ND - 7, 0); n <= LAST; n++) write_chunk(n);
     if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x < NSCAL) y[3 * A.F + threadIdx.x] = x[3 * A.F + threadIdx.x];
 }
 
