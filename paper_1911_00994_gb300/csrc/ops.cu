@@ -747,6 +747,7 @@ __global__ void __launch_bounds__(WV_THREADS, 2) k_box_wave(const __grid_constan
     // right-hand side of that box, bn[k] the next phase's; each is loaded two
     // phases ahead of its use.
     int jt[2], lm[2], ph[2], iu[2], jlo[2], jhi[2], ilo[2], ihi[2];
+    bool act[2], actn[2];  // the lane's box of this phase, of the next, lies in the window
     T bq[2][5], bn[2][5];
     auto in_window = [&](int k, int j, int i) {
         return j >= jlo[k] && j < jhi[k] && i >= ilo[k] && i < ihi[k];
@@ -766,9 +767,11 @@ __global__ void __launch_bounds__(WV_THREADS, 2) k_box_wave(const __grid_constan
 #pragma unroll
         for (int q = 0; q < 5; q++) bq[k][q] = bn[k][q] = (T)0;
         const int i = iu[k] + ph[k] + 5 * lane;
-        if (in_window(k, jt[k], i)) wave_rhs(b, F, P, i, jt[k], bq[k]);
+        act[k] = in_window(k, jt[k], i);
+        if (act[k]) wave_rhs(b, F, P, i, jt[k], bq[k]);
         const int p1 = ph[k] + 3 < 5 ? ph[k] + 3 : ph[k] - 2, i1 = iu[k] + p1 + 5 * lane;
-        if (in_window(k, jt[k] + R, i1)) wave_rhs(b, F, P, i1, jt[k] + R, bn[k]);
+        actn[k] = in_window(k, jt[k] + R, i1);
+        if (actn[k]) wave_rhs(b, F, P, i1, jt[k] + R, bn[k]);
     }
     using V = typename Vec16<T>::type;
     constexpr int VW = 16 / sizeof(T);
@@ -788,14 +791,20 @@ __global__ void __launch_bounds__(WV_THREADS, 2) k_box_wave(const __grid_constan
     for (int d = 0; d < ND; d++) {
         // phase d reads chunks d - 6 .. d + 1 (those in 0 .. LAST); d + 1 is
         // the only one not yet confirmed (at d = 0: both of the prologue)
+        // (warp 0 waits on the barriers, the block barrier passes the copies
+        // on to the other warps)
         bool ok = true;
-        if (d == 0) ok = wait_chunk(0, TT_WAIT_NS);
-        if (d + 1 <= LAST) ok = wait_chunk(d + 1, TT_WAIT_NS) && ok;
+        if (warp == 0) {
+            if (d == 0) ok = wait_chunk(0, TT_WAIT_NS);
+            if (d + 1 <= LAST) ok = wait_chunk(d + 1, TT_WAIT_NS) && ok;
+        }
         if (!__syncthreads_and(ok)) {
             // copies still in flight get a second bounded wait before the
             // block leaves; the NaN in the scalar block makes the solve fail
-            if (d == 0) wait_chunk(0, TT_WAIT_NS / 2);
-            if (d + 1 <= LAST) wait_chunk(d + 1, TT_WAIT_NS / 2);
+            if (warp == 0) {
+                if (d == 0) wait_chunk(0, TT_WAIT_NS / 2);
+                if (d + 1 <= LAST) wait_chunk(d + 1, TT_WAIT_NS / 2);
+            }
             if (threadIdx.x == 0) {
                 atomicOr(err + 2, 1u);
                 y[3 * A.F] = (T)NAN;
@@ -810,9 +819,8 @@ __global__ void __launch_bounds__(WV_THREADS, 2) k_box_wave(const __grid_constan
         }
 #pragma unroll
         for (int k = 0; k < 2; k++) {
-            const int i = iu[k] + ph[k] + 5 * lane;
-            if (in_window(k, jt[k], i)) {
-                const int lc = i + 1 - col0;
+            if (act[k]) {
+                const int lc = iu[k] + ph[k] + 5 * lane + 1 - col0;
                 const int l1 = lm[k] + 1 < RB ? lm[k] + 1 : lm[k] + 1 - RB;
                 const int l2 = lm[k] + 2 < RB ? lm[k] + 2 : lm[k] + 2 - RB;
                 const int l3 = lm[k] + 3 < RB ? lm[k] + 3 : lm[k] + 3 - RB;
@@ -836,8 +844,10 @@ __global__ void __launch_bounds__(WV_THREADS, 2) k_box_wave(const __grid_constan
             ph[k] = ph[k] + 3 < 5 ? ph[k] + 3 : ph[k] - 2;
 #pragma unroll
             for (int q = 0; q < 5; q++) bq[k][q] = bn[k][q];
+            act[k] = actn[k];
             const int p2 = ph[k] + 3 < 5 ? ph[k] + 3 : ph[k] - 2, i2 = iu[k] + p2 + 5 * lane;
-            if (in_window(k, jt[k] + R, i2)) wave_rhs(b, F, P, i2, jt[k] + R, bn[k]);
+            actn[k] = in_window(k, jt[k] + R, i2);
+            if (actn[k]) wave_rhs(b, F, P, i2, jt[k] + R, bn[k]);
         }
         // chunk d - 7 became final with phase d - 1 and is not read any more
         if (d >= 7) write_chunk(d - 7);
