@@ -94,6 +94,10 @@ typedef struct gp_params {
     int wave_min;       /* tiled levels with at least this many cells per side stream their full
                            boxes down strips of rows (same iterate as the tiles); 0: 4096;
                            negative: never */
+    int fuse_restrict;  /* positive: the cycle restricts each level's residual in the pass that
+                           computes it (the fine residual never goes to memory; the right-hand sides
+                           equal the separate passes' but for the rounding of the mean row's sum);
+                           0: a residual pass, then a restriction pass (faster on GB300) */
 } gp_params;
 
 #define GP_MAX_INNER 8

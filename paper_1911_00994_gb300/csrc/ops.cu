@@ -235,7 +235,8 @@ __global__ void k_ghost_residual(GhostList gh, int nrows, const T *x, const T *b
 // mean row (h^2 * sum of internal p) and the norm; one block
 template <typename T, typename R>
 __global__ void k_residual_final(const double *part, int nb, const T *b, R *r, long long imean, double h2,
-                                 unsigned long long *maxbits, double *out, const T *x, const int *nint)
+                                 unsigned long long *maxbits, double *out, const T *x, const int *nint,
+                                 R *also = nullptr)
 {
     __shared__ double ss[256], sm[256];
     double s = 0.0, m = 0.0;
@@ -258,6 +259,7 @@ __global__ void k_residual_final(const double *part, int nb, const T *b, R *r, l
         const double sig = sizeof(T) == 4 ? (double)x[imean + PSHIFT_SLOT] * (double)*nint : 0.0;
         double rm = (double)b[imean] - h2 * (ss[0] + sig);
         r[imean] = (R)rm;
+        if (also) *also = (R)rm;  // the mean row of a restricted right-hand side
         double g = __longlong_as_double((long long)*maxbits);
         double nrm = nanmax(nanmax(sm[0], g), fabs(rm));
         out[0] = nrm;
@@ -1430,6 +1432,176 @@ __global__ void k_restrict(int Nf, int Pf, long long Ff, const uint8_t *tUf, con
     }
 }
 
+// The residual of a level restricted in one pass (the cycle's residual and
+// Eq. restop / restop5 fused): block tiles of RR_TX x RR_TY coarse slots,
+// grid-stride.  For each tile the block first computes, into shared memory,
+// the fine residuals of the fine slots its restriction stencils reach: the
+// internal rows from x and b (the expressions of k_residual4, so the same
+// bits), the ghost-class rows read from r (k_ghost_residual wrote them just
+// before), 0 elsewhere.  Then each thread restricts one coarse slot exactly
+// as k_restrict does and zeroes the coarse iterate.  The fine residual never
+// goes to memory.  Per block: [0] the sum of p over the internal fine cells
+// of its tiles (each fine cell lies in the stencil of one coarse cell), for
+// the mean row that k_residual_final then writes into bH; [1] 0 (no norm).
+constexpr int RR_TX = 32, RR_TY = 8;
+// fine slots of a tile's stencils: columns [2 C0 - 4, 2 C0 + 64) (whole
+// 16-byte quads), rows [2 R0 - 2, 2 R0 + 15)
+constexpr int RR_FW = 2 * RR_TX + 4, RR_FH = 2 * RR_TY + 1, RR_QW = RR_FW / 4;
+static_assert(RR_TX * RR_TY == 256, "one coarse slot per thread");
+static_assert(RR_TX % 2 == 0 && RR_FW % 4 == 0, "quads of the region start on 16-byte slots");
+
+template <typename T> __host__ __device__ constexpr size_t rr_smem()
+{
+    return (size_t)3 * RR_FW * RR_FH * (sizeof(T) + 1);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_residual_restrict(LevelArgs<T> A, int Nc, int Pc, long long Fc,
+                                                           const uint8_t *tUc, const uint8_t *tVc,
+                                                           const uint8_t *tPc, const T *x, const T *b, const T *r,
+                                                           T *bH, T *xz, double *part)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *rs = (T *)smem_raw;                                      // [3][RR_FH][RR_FW]
+    uint8_t *ts = (uint8_t *)(rs + 3 * RR_FW * RR_FH);         // [3][RR_FH][RR_FW]
+    constexpr int FS = RR_FW * RR_FH;
+    const int Nf = A.N, P = A.P;
+    const long long Ff = A.F;
+    const T *u = x, *v = x + Ff, *p = x + 2 * Ff;
+    const T xi = x[3 * Ff];
+    const int ntx = (Pc + RR_TX - 1) / RR_TX, nty = (Nc + 2 + RR_TY - 1) / RR_TY;
+    double psum = 0.0;
+    for (int tile = blockIdx.x; tile < ntx * nty; tile += gridDim.x) {
+        const int C0 = (tile % ntx) * RR_TX, R0 = (tile / ntx) * RR_TY;
+        const int fc0 = 2 * C0 - 4, fr0 = 2 * R0 - 2;  // slot of the region's first column and row
+        for (int e4 = threadIdx.x; e4 < RR_QW * RR_FH; e4 += blockDim.x) {
+            const int fr = e4 / RR_QW, qc = e4 - fr * RR_QW;
+            const int row = fr0 + fr, c4 = fc0 + 4 * qc, e = fr * RR_FW + 4 * qc;
+            T ru[4] = {0, 0, 0, 0}, rv[4] = {0, 0, 0, 0}, rp[4] = {0, 0, 0, 0};
+            uint8_t tu[4] = {T_INACTIVE, T_INACTIVE, T_INACTIVE, T_INACTIVE}, tv[4], tp[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) tv[q] = tp[q] = T_INACTIVE;
+            // the pitch is a multiple of 32, so a quad is wholly in or out of the frame
+            if (row >= 0 && row < Nf + 2 && c4 >= 0 && c4 < P) {
+                const int s0 = row * P + c4;  // F < 2^31 (checked when the context is created)
+                ldt4(A.tU + s0, tu);
+                ldt4(A.tV + s0, tv);
+                ldt4(A.tP + s0, tp);
+                // as in k_residual4: every load issued before the types are
+                // tested, neighbour rows and columns clamped into the frame
+                // on its first and last rows, where no internal row is
+                const int up = row < Nf + 1 ? P : 0, dn = row > 0 ? P : 0, lf = s0 > 0 ? 1 : 0;
+                T uh[6], uU[4], uD[4], vh[6], vU[4], vD[4], ph[5], pD[4], bu[4], bv[4], bp[4];
+                ld4(u + s0, uh + 1);
+                uh[0] = u[s0 - lf];
+                uh[5] = u[s0 + 4];
+                ld4(u + s0 + up, uU);
+                ld4(u + s0 - dn, uD);
+                ld4(v + s0, vh + 1);
+                vh[0] = v[s0 - lf];
+                vh[5] = v[s0 + 4];
+                ld4(v + s0 + up, vU);
+                ld4(v + s0 - dn, vD);
+                ld4(p + s0, ph + 1);
+                ph[0] = p[s0 - lf];
+                ld4(p + s0 - dn, pD);
+                ld4(b + s0, bu);
+                ld4(b + Ff + s0, bv);
+                ld4(b + 2 * Ff + s0, bp);
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    // internal rows: the expressions of k_residual4; ghost-class
+                    // rows (few): k_ghost_residual's values in r
+                    if (tu[q] == T_INTERNAL) {
+                        T Au = A.d * uh[q + 1] - A.a * (uh[q + 2] + uh[q] + uU[q] + uD[q]) + A.q * (ph[q + 1] - ph[q]);
+                        ru[q] = bu[q] - Au;
+                    } else if (same_class(T_GHOST, tu[q])) {
+                        ru[q] = r[s0 + q];
+                    }
+                    if (tv[q] == T_INTERNAL) {
+                        T Av = A.d * vh[q + 1] - A.a * (vh[q + 2] + vh[q] + vU[q] + vD[q]) + A.q * (ph[q + 1] - pD[q]);
+                        rv[q] = bv[q] - Av;
+                    } else if (same_class(T_GHOST, tv[q])) {
+                        rv[q] = r[Ff + s0 + q];
+                    }
+                    if (tp[q] == T_INTERNAL) {
+                        T Ac = A.q * (uh[q + 2] - uh[q + 1] + vU[q] - vh[q + 1]) - xi;
+                        rp[q] = bp[q] - Ac;
+                        // the tile's own fine cells: columns [2 C0 - 1, 2 C0 + 63), rows from 2 R0 - 1
+                        const int fc = 4 * qc + q;
+                        if (fr >= 1 && fc >= 3 && fc < RR_FW - 1) psum += (double)ph[q + 1];
+                    } else if (same_class(T_GHOST, tp[q])) {
+                        rp[q] = r[2 * Ff + s0 + q];
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                rs[e + q] = ru[q];
+                rs[FS + e + q] = rv[q];
+                rs[2 * FS + e + q] = rp[q];
+                ts[e + q] = tu[q];
+                ts[FS + e + q] = tv[q];
+                ts[2 * FS + e + q] = tp[q];
+            }
+        }
+        __syncthreads();
+        const int col = C0 + (threadIdx.x % RR_TX), row = R0 + threadIdx.x / RR_TX;
+        if (col < Pc && row < Nc + 2) {
+            const int I = col - 1, J = row - 1;
+            const long long sc = (long long)row * Pc + col;
+            const uint8_t tcg[3] = {tUc[sc], tVc[sc], tPc[sc]};
+#pragma unroll
+            for (int g = 0; g < 3; g++) {
+                const uint8_t t = tcg[g];
+                T out = 0;
+                if (t != T_INACTIVE) {
+                    bool all = true;
+                    int cnt = 0;
+                    T sw = 0, su = 0;
+#pragma unroll
+                    for (int k = 0; k < 6; k++) {
+                        if (g == G_P && k >= 4) break;
+                        int di, dj;
+                        if (g == G_U) { di = k % 3 - 1; dj = k / 3; }
+                        else if (g == G_V) { di = k % 2; dj = k / 2 - 1; }
+                        else { di = k % 2; dj = k / 2; }
+                        const int fi = 2 * I + di, fj = 2 * J + dj;
+                        // the fine slot, clamped into the frame, lies in the tile's region
+                        const int ci = min(max(fi, -1), Nf), cj = min(max(fj, -1), Nf);
+                        const int e = (cj + 1 - fr0) * RR_FW + (ci + 1 - fc0);
+                        const T wt = g == G_U ? (T)(k % 3 == 1 ? 0.25 : 0.125)
+                                   : g == G_V ? (T)(k / 2 == 1 ? 0.25 : 0.125) : (T)0.25;
+                        if (in_grid(g, Nf, fi, fj) && same_class(t, ts[g * FS + e])) {
+                            const T rv = rs[g * FS + e];
+                            sw += wt * rv;
+                            su += rv;
+                            cnt++;
+                        } else all = false;
+                    }
+                    out = all ? sw : (cnt > 0 ? su / (T)cnt : (T)0);
+                }
+                bH[g * Fc + sc] = out;
+                if (xz) xz[g * Fc + sc] = (T)0;  // the coarse iterate starts from zero
+            }
+        }
+        __syncthreads();
+    }
+    if (xz && blockIdx.x == 0)
+        for (int q = threadIdx.x; q < NSCAL; q += blockDim.x) xz[3 * Fc + q] = (T)0;
+    __shared__ double ss[256];
+    ss[threadIdx.x] = psum;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) ss[threadIdx.x] += ss[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = ss[0];
+        part[2 * blockIdx.x + 1] = 0.0;
+    }
+}
+
 // Prolongation code of every fine node (one byte per slot and grid, once per
 // geometry): PRO_ON when the node is in its grid and active (it receives
 // x + P e), PRO_ALL when besides every coarse node of its interpolation
@@ -2475,6 +2647,40 @@ template <typename T> void restrict_level(Ctx *c, int lev, const T *r, T *bH, T 
     c->launches++;
 }
 
+// the residual of `lev` restricted into bH, the coarse iterate xz zeroed, in
+// one pass over the fine frames (k_residual_restrict); r receives only the
+// ghost-class rows, the mean row goes straight into bH
+template <typename T> void residual_restrict(Ctx *c, int lev, const T *x, const T *b, T *r, T *bH, T *xz)
+{
+    const Level &f = c->lv[lev], &C = c->lv[lev + 1];
+    cudaStream_t st = c->stream;
+    static int resident = 0;
+    if (resident <= 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_residual_restrict<T>, 256, rr_smem<T>()) !=
+                cudaSuccess ||
+            per_sm < 1) {
+            cudaGetLastError();
+            per_sm = 1;
+        }
+        resident = sms * per_sm;
+    }
+    const long long ntiles = (long long)((C.P + RR_TX - 1) / RR_TX) * ((C.N + 2 + RR_TY - 1) / RR_TY);
+    const int nb = (int)(ntiles < resident ? ntiles : resident);
+    if (f.h_nrows > 0)
+        k_ghost_residual<T, T><<<(f.h_nrows + 255) / 256, 256, 0, st>>>(f.gh, f.h_nrows, x, b, r, c->maxbits);
+    tmr_begin(c, KT_RESTRICT, lev);
+    k_residual_restrict<T><<<nb, 256, rr_smem<T>(), st>>>(level_args<T>(c, lev), C.N, C.P, C.F, C.tU, C.tV, C.tP, x,
+                                                          b, r, bH, xz, c->part);
+    tmr_end(c, KT_RESTRICT, lev);
+    const double h = c->prm.L / (double)f.N;
+    k_residual_final<T, T><<<1, 256, 0, st>>>(c->part, nb, b, r, 3 * f.F, h * h, c->maxbits, c->red, x, f.nint,
+                                              bH + 3 * C.F);
+    c->launches += 2 + (f.h_nrows > 0);
+}
+
 template <typename T> void prolong_to(Ctx *c, int lev, const T *eH, const T *x, T *y)
 {
     const Level &f = c->lv[lev], &C = c->lv[lev + 1];
@@ -2530,6 +2736,7 @@ void float_to_double(Ctx *c, const float *e, double *y, long long n) { f2d(c, e,
     template T *post_buffer<T>(Ctx *, int, T *, int);                           \
     template void prolong_to<T>(Ctx *, int, const T *, const T *, T *);         \
     template void restrict_level<T>(Ctx *, int, const T *, T *, T *);           \
+    template void residual_restrict<T>(Ctx *, int, const T *, const T *, T *, T *, T *); \
     template void prolong_level<T>(Ctx *, int, const T *, T *);                 \
     template void zero_vec<T>(Ctx *, T *, long long);                           \
     template void zero_inactive<T>(Ctx *, int, T *);

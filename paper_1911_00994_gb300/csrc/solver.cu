@@ -22,6 +22,7 @@ template <typename T> void scalar_update(Ctx *c, int lev, T *x, const T *b);
 template <typename T> void ghost_sweep(Ctx *c, int lev, T *x, const T *b);
 template <typename T> void smooth(Ctx *c, int lev, T *x, const T *b, int nu);
 template <typename T> void restrict_level(Ctx *c, int lev, const T *r, T *bH, T *xz);
+template <typename T> void residual_restrict(Ctx *c, int lev, const T *x, const T *b, T *r, T *bH, T *xz);
 template <typename T> void prolong_level(Ctx *c, int lev, const T *eH, T *x);
 template <typename T> void prolong_to(Ctx *c, int lev, const T *eH, const T *x, T *y);
 template <typename T> void smooth_from(Ctx *c, int lev, T *x, T *in, const T *b, int nu);
@@ -260,9 +261,13 @@ template <typename T> void cycle_rec(Ctx *c, int lev, T *x, const T *b)
     }
     smooth<T>(c, lev, x, b, c->prm.nu1);
     T *r = Vecs<T>::r(c, lev);
-    residual<T>(c, lev, x, b, r);
     T *xH = Vecs<T>::x(c, lev + 1), *bH = Vecs<T>::b(c, lev + 1);
-    restrict_level<T>(c, lev, r, bH, xH);  // also zeroes xH
+    if (c->prm.fuse_restrict > 0) {
+        residual_restrict<T>(c, lev, x, b, r, bH, xH);  // also zeroes xH
+    } else {
+        residual<T>(c, lev, x, b, r);
+        restrict_level<T>(c, lev, r, bH, xH);  // also zeroes xH
+    }
     for (int k = 0; k < c->prm.gamma; k++) cycle_rec<T>(c, lev + 1, xH, bH);
     T *y = post_buffer<T>(c, lev, x, c->prm.nu2);
     prolong_to<T>(c, lev, xH, x, y);

@@ -28,7 +28,7 @@ class gp_params(ctypes.Structure):
                 ("precision", ctypes.c_int), ("max_cycles", ctypes.c_int), ("cn_buffers", ctypes.c_int),
                 ("graphs", ctypes.c_int), ("band", ctypes.c_int), ("krylov", ctypes.c_int),
                 ("tile_min", ctypes.c_int), ("adjoint", ctypes.c_int), ("inner", ctypes.c_int),
-                ("wave_min", ctypes.c_int)]
+                ("wave_min", ctypes.c_int), ("fuse_restrict", ctypes.c_int)]
 
 
 class gp_report(ctypes.Structure):
@@ -189,7 +189,8 @@ class Solver:
 
     def __init__(self, N, x0, y0, L, levels=None, alpha=None, nu1=2, nu2=1, gamma=1, lam=5, dtau=0.9,
                  snap=0.3, precision=GP_FP64, max_cycles=100, device="cuda", stream=None, cn_buffers=True,
-                 graphs=True, band=0, krylov=False, tile_min=0, adjoint=False, inner=0, wave_min=0):
+                 graphs=True, band=0, krylov=False, tile_min=0, adjoint=False, inner=0, wave_min=0,
+                 fuse_restrict=0):
         import torch
         self.torch = torch
         self.L = lib()
@@ -211,6 +212,7 @@ class Solver:
         p.adjoint = 1 if adjoint else 0
         p.inner = int(inner)
         p.wave_min = int(wave_min)
+        p.fuse_restrict = int(fuse_restrict)
         self.prm = p
         nb = ctypes.c_size_t(0)
         st = self.L.gp_workspace_size(ctypes.byref(p), ctypes.byref(nb))
