@@ -49,9 +49,9 @@ typedef struct gp3_ctx gp3_ctx;
 long long gp3_vec_len(int N);
 
 /* bytes of device workspace for N cells per side and `levels` levels
- * (N, N/2, ..., N/2^(levels-1); N divisible by 2^(levels-1), coarsest >= 2,
- * at most 1024 unknowns on the coarsest level) and precision (0 FP64,
- * 1 mixed: adds the FP32 vectors).  GP_INVALID otherwise. */
+ * (N, N/2, ..., N/2^(levels-1); N <= 1024, divisible by 2^(levels-1),
+ * coarsest >= 2, at most 1024 unknowns on the coarsest level) and precision
+ * (0 FP64, 1 mixed: adds the FP32 vectors).  GP_INVALID otherwise. */
 gp_status gp3_workspace_size(int N, int levels, int precision, size_t *bytes);
 
 /* Create a context: alpha = dt / (2 Re); nu1, nu2 pre/post relaxations;

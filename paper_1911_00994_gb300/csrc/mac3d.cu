@@ -33,7 +33,13 @@ struct Lev {
     unsigned char *t;    // 4 F node types
     double *x, *b, *r;   // FP64 level vectors (x, b of the coarse levels; r of every level)
     float *xf, *bf, *rf; // FP32 level vectors of the mixed mode's inner cycles (x, b, r of every level)
+    long long *gl;       // the wall and box-ghost rows (vector entries), listed once at creation
+    int ng;              // how many
 };
+
+// wall and box-ghost rows of a level with N cells per side: per grid 2 N^2
+// on its own walls and 4 N (N - 1) half a cell outside the others
+__host__ __device__ inline long long ghost_cap(int N) { return 18LL * N * N; }
 
 __host__ __device__ inline long long vlen(int N)
 {
@@ -44,19 +50,26 @@ __host__ __device__ inline long long vlen(int N)
 // ------------------------------------------------------------ node types
 
 // coordinate of slot s along array axis ax (0: i, 1: j, 2: k), in [-1, N]
+// (32-bit: a frame has fewer than 2^31 slots for N <= 1024)
 __device__ inline int coord(long long s, int S, int ax)
 {
-    const long long S2 = (long long)S * S;
-    if (ax == 0) return (int)(s % S) - 1;
-    if (ax == 1) return (int)((s / S) % S) - 1;
-    return (int)(s / S2) - 1;
+    const unsigned u = (unsigned)s, US = (unsigned)S;
+    if (ax == 0) return (int)(u % US) - 1;
+    if (ax == 1) return (int)((u / US) % US) - 1;
+    return (int)(u / (US * US)) - 1;
+}
+
+// the frame (0 u, 1 v, 2 w, 3 p) of vector entry e < 4 F
+__device__ inline int frame_of(long long e, long long F)
+{
+    return e < F ? 0 : e < 2 * F ? 1 : e < 3 * F ? 2 : 3;
 }
 
 __global__ void k3_types(int N, long long F, unsigned char *t)
 {
     const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (e >= 4 * F) return;
-    const int g = (int)(e / F);
+    const int g = frame_of(e, F);
     const long long s = e - g * F;
     const int S = N + 2;
     int c[3] = {coord(s, S, 0), coord(s, S, 1), coord(s, S, 2)};
@@ -156,7 +169,7 @@ __global__ void __launch_bounds__(256) k3_residual(Lev L, const T *x, const T *b
     double sp = 0.0, m = 0.0;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < 4 * L.F;
          e += (long long)gridDim.x * blockDim.x) {
-        const int g = (int)(e / L.F);
+        const int g = frame_of(e, L.F);
         const long long s = e - g * L.F;
         const T v = b[e] - apply_row<T>(L, L.t, g, s, X);
         r[e] = (R)v;
@@ -210,13 +223,13 @@ template <typename T>
 __global__ void __launch_bounds__(256) k3_box(Lev L, T *x, const T *b, int colour)
 {
     const int N = L.N;
-    const int per_row = (N + NCOL - 1) / NCOL;
-    const long long n = (long long)per_row * N * N;
-    const long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const unsigned per_row = (N + NCOL - 1) / NCOL;
+    const unsigned n = per_row * N * N;  // below 2^31 for N <= 1024
+    const unsigned id = blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= n) return;
     const int m = (int)(id % per_row);
-    const long long jk = id / per_row;
-    const int j = (int)(jk % N), k = (int)(jk / N);
+    const unsigned jk = id / per_row;
+    const int j = (int)(jk % (unsigned)N), k = (int)(jk / (unsigned)N);
     // first i with (i + 2 j + 3 k) mod 7 = colour
     const int i = (int)((unsigned)(colour + 7 * 4 * (N + 1) - 2 * j - 3 * k) % 7u) + NCOL * m;
     if (i >= N) return;
@@ -331,23 +344,37 @@ template <typename T> __global__ void k3_pshift(Lev L, T *x, const double *shift
     x[3 * L.F + s] += (T)shift[0];
 }
 
-// Eq. (ghostrelax), Jacobi over the wall and box-ghost rows: upd = dtau r
-template <typename T> __global__ void k3_ghost_update(Lev L, const T *x, const T *b, T dtau, T *upd)
+// the wall and box-ghost rows of a level into L.gl (order unspecified; the
+// sweeps below are Jacobi, so it does not matter); one atomic per warp
+__global__ void k3_ghost_list(Lev L, int *count)
 {
     const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (e >= 3 * L.F) return;
-    const unsigned char ty = L.t[e];
-    if (ty != T_WALL && ty != T_BOXGHOST) return;
-    const int g = (int)(e / L.F);
-    upd[e] = dtau * (b[e] - apply_row<T>(L, L.t, g, e - g * L.F, VecAcc<T>{x}));
+    const bool is = e < 3 * L.F && (L.t[e] == T_WALL || L.t[e] == T_BOXGHOST);
+    const unsigned m = __ballot_sync(0xffffffffu, is);
+    if (m == 0u) return;
+    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(count, __popc(m));
+    base = __shfl_sync(m, base, leader);
+    const int k = base + __popc(m & ((1u << lane) - 1u));
+    if (is && k < ghost_cap(L.N)) L.gl[k] = e;
+}
+
+// Eq. (ghostrelax), Jacobi over the listed wall and box-ghost rows: upd = dtau r
+template <typename T> __global__ void k3_ghost_update(Lev L, const T *x, const T *b, T dtau, T *upd)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= L.ng) return;
+    const long long e = L.gl[k];
+    const int g = frame_of(e, L.F);
+    upd[k] = dtau * (b[e] - apply_row<T>(L, L.t, g, e - g * L.F, VecAcc<T>{x}));
 }
 
 template <typename T> __global__ void k3_ghost_apply(Lev L, T *x, const T *upd)
 {
-    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (e >= 3 * L.F) return;
-    const unsigned char ty = L.t[e];
-    if (ty == T_WALL || ty == T_BOXGHOST) x[e] += upd[e];
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= L.ng) return;
+    x[L.gl[k]] += upd[k];
 }
 
 // ------------------------------------------------------------ transfers
@@ -368,7 +395,7 @@ __global__ void __launch_bounds__(256) k3_restrict(Lev f, Lev c, const T *r, T *
         if (e == 4 * c.F) bH[4 * c.F] = r[4 * f.F];  // the mean row: injected
         return;
     }
-    const int g = (int)(e / c.F);
+    const int g = frame_of(e, c.F);
     const long long s = e - g * c.F;
     const int cc = rclass(c.t[e]);
     if (cc == 0) {
@@ -412,27 +439,28 @@ __global__ void __launch_bounds__(256) k3_restrict(Lev f, Lev c, const T *r, T *
 
 // interpolation taps of fine index fi along one axis: a face axis (aligned,
 // even: the coarse face, odd: the two around it) or a cell-centred axis
-// (the two coarse cells around, extrapolated past [lo, hi])
-__device__ inline int taps3(int fi, bool aligned, int lo, int hi, int *K, double *w)
+// (the two coarse cells around fi / 2 - 1/4, extrapolated past [lo, hi]).
+// The weights are multiples of 1/4 below 2 in magnitude, so they and their
+// products are exact in either precision.
+template <typename T> __device__ inline int taps3(int fi, bool aligned, int lo, int hi, int *K, T *w)
 {
     if (aligned) {
         if ((fi & 1) == 0) {
             K[0] = fi / 2;
-            w[0] = 1.0;
+            w[0] = (T)1;
             return 1;
         }
         K[0] = (fi - 1) / 2;
         K[1] = (fi + 1) / 2;
-        w[0] = w[1] = 0.5;
+        w[0] = w[1] = (T)0.5;
         return 2;
     }
-    const double cpos = fi / 2.0 - 0.25;
-    int k0 = (int)floor(cpos);
+    int k0 = (fi - 1) >> 1;  // floor(fi / 2 - 1/4)
     k0 = k0 < lo ? lo : (k0 > hi - 1 ? hi - 1 : k0);
     K[0] = k0;
     K[1] = k0 + 1;
-    w[1] = cpos - k0;
-    w[0] = 1.0 - w[1];
+    w[1] = (T)(2 * fi - 1 - 4 * k0) * (T)0.25;  // fi / 2 - 1/4 - k0
+    w[0] = (T)1 - w[1];
     return 2;
 }
 
@@ -447,26 +475,41 @@ __global__ void __launch_bounds__(256) k3_prolong(Lev f, Lev c, const T *eH, T *
         return;
     }
     if (f.t[e] == T_INACTIVE) return;
-    const int g = (int)(e / f.F);
+    const int g = frame_of(e, f.F);
     const long long s = e - g * f.F;
-    int K[3][2];
-    double W[3][2];
+    int K[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+    T W[3][2];
     int n[3];
+#pragma unroll
     for (int ax = 0; ax < 3; ax++) {
         const bool own = g < 3 && ax == g;
         const int lo = g == 3 ? 0 : (own ? 0 : -1), hi = g == 3 ? c.N - 1 : c.N;
-        n[ax] = taps3(coord(s, f.S, ax), own, lo, hi, K[ax], W[ax]);
+        n[ax] = taps3<T>(coord(s, f.S, ax), own, lo, hi, K[ax], W[ax]);
     }
-    const long long Sc = c.S;
+    // per axis and tap: the coarse slot offset, or -1 outside the frame
+    // (entries of the coarse vector stay below 2^31: 4 (N/2 + 2)^3 for N <= 1024)
+    const int Sc = c.S;
+    int off[3][2];
+#pragma unroll
+    for (int ax = 0; ax < 3; ax++) {
+        const int stride = ax == 0 ? 1 : ax == 1 ? Sc : Sc * Sc;
+#pragma unroll
+        for (int a = 0; a < 2; a++)
+            off[ax][a] = (a < n[ax] && K[ax][a] >= -1 && K[ax][a] <= c.N) ? (K[ax][a] + 1) * stride : -1;
+    }
+    const int gbase = g * (int)c.F;
     T acc = 0, ws = 0;
-    for (int a2 = 0; a2 < n[2]; a2++)
-        for (int a1 = 0; a1 < n[1]; a1++)
-            for (int a0 = 0; a0 < n[0]; a0++) {
-                const int ci = K[0][a0], cj = K[1][a1], ck = K[2][a2];
-                if (ci < -1 || ci > c.N || cj < -1 || cj > c.N || ck < -1 || ck > c.N) continue;
-                const long long cs = g * c.F + ((long long)(ck + 1) * Sc + (cj + 1)) * Sc + (ci + 1);
+#pragma unroll
+    for (int a2 = 0; a2 < 2; a2++)
+#pragma unroll
+        for (int a1 = 0; a1 < 2; a1++)
+#pragma unroll
+            for (int a0 = 0; a0 < 2; a0++) {
+                // a one-tap axis has off = -1 for its second tap; the sum runs in tap order
+                if (off[0][a0] < 0 || off[1][a1] < 0 || off[2][a2] < 0) continue;
+                const int cs = gbase + off[2][a2] + off[1][a1] + off[0][a0];
                 if (c.t[cs] == T_INACTIVE) continue;
-                const T w = (T)(W[0][a0] * W[1][a1] * W[2][a2]);
+                const T w = W[0][a0] * W[1][a1] * W[2][a2];
                 acc += w * eH[cs];
                 ws += w;
             }
@@ -611,7 +654,8 @@ static inline unsigned nblk(long long n) { return (unsigned)((n + 255) / 256); }
 
 static bool valid(int N, int levels)
 {
-    if (N < 2 || levels < 1 || levels > MAX_LEVELS || N > 2048) return false;
+    // N <= 1024 keeps every frame below 2^31 slots (32-bit slot arithmetic)
+    if (N < 2 || levels < 1 || levels > MAX_LEVELS || N > 1024) return false;
     if (N % (1 << (levels - 1))) return false;
     const int Nc = N >> (levels - 1);
     if (Nc < 2) return false;
@@ -641,6 +685,7 @@ static size_t carve(Ctx *c, char *base, int N, int levels, bool mixed)
         float *xf = mixed ? (float *)take(sizeof(float) * VL) : nullptr;
         float *bf = mixed ? (float *)take(sizeof(float) * VL) : nullptr;
         float *rf = mixed ? (float *)take(sizeof(float) * VL) : nullptr;
+        long long *gl = (long long *)take(sizeof(long long) * ghost_cap(Nl));
         if (c) {
             Lev &L = c->lv[l];
             L.N = Nl;
@@ -662,16 +707,17 @@ static size_t carve(Ctx *c, char *base, int N, int levels, bool mixed)
             L.xf = xf;
             L.bf = bf;
             L.rf = rf;
+            L.gl = gl;
+            L.ng = 0;
         }
     }
-    const long long S0 = N + 2, F0 = S0 * S0 * S0;
     const int Nc = N >> (levels - 1);
     const long long Sc = Nc + 2;
     const int nc = (int)(4 * Sc * Sc * Sc + 1);
     double *part = (double *)take(sizeof(double) * npart);
     double *red = (double *)take(sizeof(double) * 8);
-    double *upd = (double *)take(sizeof(double) * 3 * F0);
-    float *updf = mixed ? (float *)take(sizeof(float) * 3 * F0) : nullptr;
+    double *upd = (double *)take(sizeof(double) * ghost_cap(N));
+    float *updf = mixed ? (float *)take(sizeof(float) * ghost_cap(N)) : nullptr;
     double *colk = (double *)take(sizeof(double) * nc);
     double *A = (double *)take(sizeof(double) * (size_t)nc * 2 * nc);
     double *M = (double *)take(sizeof(double) * (size_t)nc * nc);
@@ -759,8 +805,8 @@ template <typename T> static void smooth(Ctx *c, int l, T *x, const T *b, int nu
         k3_pshift<T><<<nblk(L.F), 256, 0, c->st>>>(L, x, c->red + 1);
         T *upd = Vecs<T>::upd(c);
         for (int s = 0; s < c->lambda; s++) {
-            k3_ghost_update<T><<<nblk(3 * L.F), 256, 0, c->st>>>(L, x, b, (T)c->dtau, upd);
-            k3_ghost_apply<T><<<nblk(3 * L.F), 256, 0, c->st>>>(L, x, upd);
+            k3_ghost_update<T><<<nblk(L.ng), 256, 0, c->st>>>(L, x, b, (T)c->dtau, upd);
+            k3_ghost_apply<T><<<nblk(L.ng), 256, 0, c->st>>>(L, x, upd);
         }
     }
 }
@@ -852,8 +898,20 @@ gp_status gp3_create(gp3_ctx **out, int N, int levels, double alpha, int nu1, in
     c->msg[0] = 0;
     carve(c, (char *)ws, N, levels, precision == 1);
     for (int l = 0; l < levels; l++) {
-        const Lev &L = c->lv[l];
+        Lev &L = c->lv[l];
         k3_types<<<nblk(4 * L.F), 256, 0, stream>>>(L.N, L.F, L.t);
+        // the wall and box-ghost rows, counted in flag[1]
+        int ng = 0;
+        cudaMemsetAsync(c->flag + 1, 0, sizeof(int), stream);
+        k3_ghost_list<<<nblk(3 * L.F), 256, 0, stream>>>(L, c->flag + 1);
+        cudaMemcpyAsync(&ng, c->flag + 1, sizeof(int), cudaMemcpyDeviceToHost, stream);
+        if (cudaStreamSynchronize(stream) != cudaSuccess || ng > ghost_cap(L.N)) {
+            cudaGetLastError();
+            nvtxRangePop();
+            gp3_destroy(h);
+            return GP_CUDA;
+        }
+        L.ng = ng;
     }
     gp_status st = build_coarse(c);
     nvtxRangePop();

@@ -97,7 +97,8 @@ def test_3d_library_exports_and_binding_cover_gpmg3d_h():
 def test_3d_sizes_are_checked_on_the_host():
     # gp3_workspace_size makes no CUDA call: a size for valid hierarchies,
     # GP_INVALID for N not divisible down the levels, a coarsest grid below
-    # 2 or a coarsest dense matrix above 1024 unknowns
+    # 2, a coarsest dense matrix above 1024 unknowns or N above 1024 (frames
+    # of 2^31 slots or more)
     from paper_1911_00994_gb300 import mac3d
     L = mac3d.lib()
     nb = ctypes.c_size_t(0)
@@ -106,5 +107,6 @@ def test_3d_sizes_are_checked_on_the_host():
     assert L.gp3_workspace_size(64, 5, 1, ctypes.byref(nb)) == 0 and nb.value > n64
     assert L.gp3_workspace_size(64, 5, 2, ctypes.byref(nb)) == 1
     assert L.gp3_vec_len(64) == 4 * 66 ** 3 + 32
-    for N, lev in ((64, 7), (48, 6), (64, 3), (0, 1), (64, 0)):
+    assert L.gp3_workspace_size(1024, 9, 0, ctypes.byref(nb)) == 0
+    for N, lev in ((64, 7), (48, 6), (64, 3), (0, 1), (64, 0), (2048, 10)):
         assert L.gp3_workspace_size(N, lev, 0, ctypes.byref(nb)) == 1, (N, lev)
