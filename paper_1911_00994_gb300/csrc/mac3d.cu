@@ -99,7 +99,8 @@ __device__ inline T apply_row(const Lev &L, const unsigned char *t, int g, long 
 {
     const long long F = L.F, S = L.S, S2 = S * S;
     const T q = (T)L.q, d = (T)L.d, a = (T)L.a;
-    const long long off[3] = {1, S, S2};
+    // the slot stride along axis ax (selected, not indexed: no local array)
+    auto off = [&](int ax) -> long long { return ax == 0 ? 1 : ax == 1 ? S : S2; };
     const unsigned char ty = t[g * F + s];
     const long long e = g * F + s;
     if (g == 3) {
@@ -110,17 +111,18 @@ __device__ inline T apply_row(const Lev &L, const unsigned char *t, int g, long 
     if (ty == T_INTERNAL) {
         const T lap = X(e + 1) + X(e - 1) + X(e + S) + X(e - S) + X(e + S2) + X(e - S2);
         // p of the cell on the + side (same slot) minus the cell on the - side
-        return d * X(e) - a * lap + q * (X(3 * F + s) - X(3 * F + s - off[g]));
+        return d * X(e) - a * lap + q * (X(3 * F + s) - X(3 * F + s - off(g)));
     }
     if (ty == T_BOXGHOST) {
         // the transverse axis that leaves [0, N): step inwards from the ghost
         const int N = L.N;
         long long in = 0;
+#pragma unroll
         for (int ax = 0; ax < 3; ax++) {
             if (ax == g) continue;
             const int c = coord(s, L.S, ax);
-            if (c == -1) in = off[ax];
-            else if (c == N) in = -off[ax];
+            if (c == -1) in = off(ax);
+            else if (c == N) in = -off(ax);
         }
         return (T)0.375 * X(e) + (T)0.75 * X(e + in) - (T)0.125 * X(e + 2 * in);
     }
@@ -134,6 +136,19 @@ template <typename T> struct VecAcc {
 struct UnitAcc {
     long long c;
     __device__ double operator()(long long e) const { return e == c ? 1.0 : 0.0; }
+};
+
+// |v| as the bits of v with the sign cleared, and back
+template <typename T> struct AbsBits3;
+template <> struct AbsBits3<float> {
+    typedef unsigned int U;
+    __device__ static U of(float v) { return __float_as_uint(v) & 0x7fffffffu; }
+    __device__ static double value(U u) { return (double)__uint_as_float(u); }
+};
+template <> struct AbsBits3<double> {
+    typedef unsigned long long U;
+    __device__ static U of(double v) { return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull; }
+    __device__ static double value(U u) { return __longlong_as_double((long long)u); }
 };
 
 // a sum and a NaN-keeping maximum over a block of 256 threads; thread 0
@@ -166,17 +181,21 @@ template <typename T, typename R>
 __global__ void __launch_bounds__(256) k3_residual(Lev L, const T *x, const T *b, R *r, double *part)
 {
     const VecAcc<T> X{x};
-    double sp = 0.0, m = 0.0;
+    // per thread: the sum of p in T and max |r| as the integer maximum of
+    // sign-cleared bits (the numeric order for non-negative floats, NaN
+    // above infinity), so an FP32 residual does no FP64 work per entry
+    T sp = 0;
+    typename AbsBits3<T>::U mb = 0;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < 4 * L.F;
          e += (long long)gridDim.x * blockDim.x) {
         const int g = frame_of(e, L.F);
         const long long s = e - g * L.F;
         const T v = b[e] - apply_row<T>(L, L.t, g, s, X);
         r[e] = (R)v;
-        m = (v != v || m != m) ? (double)NAN : fmax(m, fabs((double)v));
-        if (g == 3 && L.t[e] == T_INTERNAL) sp += (double)x[e];
+        mb = max(mb, AbsBits3<T>::of(v));
+        if (g == 3 && L.t[e] == T_INTERNAL) sp += x[e];
     }
-    block_sum_max(sp, m, part);
+    block_sum_max((double)sp, AbsBits3<T>::value(mb), part);
 }
 
 // the mean row and the norm: r[4F] = b[4F] - h^3 sum p
