@@ -770,10 +770,23 @@ static gp_status cuda_check(Ctx *c, const char *where)
     return GP_CUDA;
 }
 
-static int red_grid(long long n)
+// blocks of 256 threads for a grid-stride reduction kernel over n entries:
+// one wave of resident blocks (a partial second wave would leave SMs idle),
+// at most the 1024 partial results the workspace holds
+template <typename K> static int red_grid(K kernel, long long n, int &cache)
 {
+    if (cache <= 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, 0) != cudaSuccess || per_sm < 1) {
+            cudaGetLastError();
+            per_sm = 1;
+        }
+        cache = sms * per_sm < 1024 ? sms * per_sm : 1024;
+    }
     const long long b = (n + 255) / 256;
-    return (int)(b < 1024 ? (b < 1 ? 1 : b) : 1024);
+    return (int)(b < cache ? (b < 1 ? 1 : b) : cache);
 }
 
 // the level vectors and the ghost-sweep scratch of precision T
@@ -794,7 +807,8 @@ template <> struct Vecs<float> {
 template <typename T, typename R> static void residual(Ctx *c, int l, const T *x, const T *b, R *r)
 {
     const Lev &L = c->lv[l];
-    const int nb = red_grid(4 * L.F);
+    static int resident = 0;
+    const int nb = red_grid(k3_residual<T, R>, 4 * L.F, resident);
     k3_residual<T, R><<<nb, 256, 0, c->st>>>(L, x, b, r, c->part);
     k3_residual_final<T, R><<<1, 256, 0, c->st>>>(L, c->part, nb, b, r, c->red);
 }
@@ -818,7 +832,8 @@ template <typename T> static void smooth(Ctx *c, int l, T *x, const T *b, int nu
                 c->tmr_n++;
             }
         }
-        const int nb = red_grid(L.F);
+        static int resident = 0;
+        const int nb = red_grid(k3_scalar_partial<T>, L.F, resident);
         k3_scalar_partial<T><<<nb, 256, 0, c->st>>>(L, x, b, c->part);
         k3_scalar_final<T><<<1, 256, 0, c->st>>>(L, c->part, nb, x, b, c->red + 1);
         k3_pshift<T><<<nblk(L.F), 256, 0, c->st>>>(L, x, c->red + 1);
