@@ -379,21 +379,20 @@ __global__ void k3_ghost_list(Lev L, int *count)
     if (is && k < ghost_cap(L.N)) L.gl[k] = e;
 }
 
-// Eq. (ghostrelax), Jacobi over the listed wall and box-ghost rows: upd = dtau r
-template <typename T> __global__ void k3_ghost_update(Lev L, const T *x, const T *b, T dtau, T *upd)
+// Eq. (ghostrelax): lambda Jacobi sweeps x += dtau r over the listed wall and
+// box-ghost rows.  On the box domain no listed row reads another: a wall row
+// reads only itself, a box-ghost row itself and the two interior nodes
+// inwards of it, which the sweeps leave alone.  So lambda sweeps over the
+// whole list are lambda updates of each row in turn, one thread per row and
+// one launch, with the same operations as sweep-by-sweep passes.
+template <typename T> __global__ void k3_ghost_sweeps(Lev L, T *x, const T *b, T dtau, int lambda)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= L.ng) return;
     const long long e = L.gl[k];
     const int g = frame_of(e, L.F);
-    upd[k] = dtau * (b[e] - apply_row<T>(L, L.t, g, e - g * L.F, VecAcc<T>{x}));
-}
-
-template <typename T> __global__ void k3_ghost_apply(Lev L, T *x, const T *upd)
-{
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= L.ng) return;
-    x[L.gl[k]] += upd[k];
+    const T be = b[e];
+    for (int it = 0; it < lambda; it++) x[e] += dtau * (be - apply_row<T>(L, L.t, g, e - g * L.F, VecAcc<T>{x}));
 }
 
 // ------------------------------------------------------------ transfers
@@ -656,8 +655,7 @@ struct Ctx {
     double alpha, dtau;
     cudaStream_t st;
     Lev lv[MAX_LEVELS];
-    double *part, *red, *upd, *colk, *A, *M;
-    float *updf;
+    double *part, *red, *colk, *A, *M;
     int *flag;
     int nc;        // unknowns of the coarsest level
     int npart;
@@ -735,8 +733,6 @@ static size_t carve(Ctx *c, char *base, int N, int levels, bool mixed)
     const int nc = (int)(4 * Sc * Sc * Sc + 1);
     double *part = (double *)take(sizeof(double) * npart);
     double *red = (double *)take(sizeof(double) * 8);
-    double *upd = (double *)take(sizeof(double) * ghost_cap(N));
-    float *updf = mixed ? (float *)take(sizeof(float) * ghost_cap(N)) : nullptr;
     double *colk = (double *)take(sizeof(double) * nc);
     double *A = (double *)take(sizeof(double) * (size_t)nc * 2 * nc);
     double *M = (double *)take(sizeof(double) * (size_t)nc * nc);
@@ -744,8 +740,6 @@ static size_t carve(Ctx *c, char *base, int N, int levels, bool mixed)
     if (c) {
         c->part = part;
         c->red = red;
-        c->upd = upd;
-        c->updf = updf;
         c->colk = colk;
         c->A = A;
         c->M = M;
@@ -795,13 +789,11 @@ template <> struct Vecs<double> {
     static double *x(const Lev &L) { return L.x; }
     static double *b(const Lev &L) { return L.b; }
     static double *r(const Lev &L) { return L.r; }
-    static double *upd(const Ctx *c) { return c->upd; }
 };
 template <> struct Vecs<float> {
     static float *x(const Lev &L) { return L.xf; }
     static float *b(const Lev &L) { return L.bf; }
     static float *r(const Lev &L) { return L.rf; }
-    static float *upd(const Ctx *c) { return c->updf; }
 };
 
 template <typename T, typename R> static void residual(Ctx *c, int l, const T *x, const T *b, R *r)
@@ -837,11 +829,7 @@ template <typename T> static void smooth(Ctx *c, int l, T *x, const T *b, int nu
         k3_scalar_partial<T><<<nb, 256, 0, c->st>>>(L, x, b, c->part);
         k3_scalar_final<T><<<1, 256, 0, c->st>>>(L, c->part, nb, x, b, c->red + 1);
         k3_pshift<T><<<nblk(L.F), 256, 0, c->st>>>(L, x, c->red + 1);
-        T *upd = Vecs<T>::upd(c);
-        for (int s = 0; s < c->lambda; s++) {
-            k3_ghost_update<T><<<nblk(L.ng), 256, 0, c->st>>>(L, x, b, (T)c->dtau, upd);
-            k3_ghost_apply<T><<<nblk(L.ng), 256, 0, c->st>>>(L, x, upd);
-        }
+        if (c->lambda > 0) k3_ghost_sweeps<T><<<nblk(L.ng), 256, 0, c->st>>>(L, x, b, (T)c->dtau, c->lambda);
     }
 }
 
