@@ -11,6 +11,8 @@
 * Transfers: the restriction reproduces linear fields at interior coarse
   nodes; the prolongation reproduces linear coarse corrections in the interior.
 * Multigrid reaches the dense solve of the assembled matrix.
+* Among the wall and box-ghost rows the assembled matrix is diagonal, and a
+  box-ghost row's other columns are interior nodes.
 """
 import itertools
 
@@ -197,3 +199,27 @@ def test_multigrid_reaches_the_dense_solution_and_converges_fast():
     # the box domain keeps the textbook rate of a box smoother (three relaxations)
     rho = (hist[-1] / hist[-5]) ** 0.25
     assert rho < 0.25, rho
+
+
+@pytest.mark.parametrize("N", [4, 8])
+def test_wall_and_box_ghost_rows_read_no_other_of_their_kind(N):
+    # on the box domain a wall row (x = b) reads only its own node and a
+    # box-ghost row (3/8, 3/4, -1/8 along the axis that leaves the box) its
+    # own node and two interior nodes, so among these rows the matrix is
+    # diagonal: lambda Jacobi sweeps over them equal lambda updates of each
+    # row in turn, which the GPU's one-launch ghost sweeps rely on
+    o = M.Mac3D(N, 2.0 / N ** 2, 1)
+    A = o.assemble(0)
+    t = o.types[0]
+    rows = np.flatnonzero(np.concatenate([np.isin(t[:3].reshape(-1), (M.WALL, M.BOXGHOST)),
+                                          np.zeros(t[3].size + 1, bool)]))
+    assert rows.size == 3 * (6 * N * N - 4 * N)
+    sub = A[np.ix_(rows, rows)]
+    assert np.count_nonzero(sub - np.diag(np.diag(sub))) == 0
+    assert np.all(np.diag(sub) != 0.0)
+    # and the other nodes a box-ghost row reads are interior
+    box = np.flatnonzero(np.concatenate([t[:3].reshape(-1) == M.BOXGHOST, np.zeros(t[3].size + 1, bool)]))
+    internal = np.concatenate([t.reshape(-1) == M.INTERNAL, [False]])
+    for e in box:
+        cols = np.flatnonzero(A[e])
+        assert np.all(internal[cols[cols != e]])
